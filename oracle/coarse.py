@@ -1,0 +1,154 @@
+"""Coarse space of the two-level Schwarz method (Sec. 2.2, Methods,
+Algorithm 3 set-up and correction, Eq. 7-8), FP64.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Set-up, in the order of Algorithm 3:
+1. pseudo-plane-wave trial Robin data: for k directions theta_m = 2 pi m / k
+   walk the window perimeter counter-clockwise from its (x-, y-) corner and
+   accumulate the phase phi += kd * (d . ds), kd = k0 dx sqrt(eps) averaged
+   over the two cells of the step; the trial datum is exp(-j phi) on every
+   interface slot (Methods: "compute the wave vector inside the medium ...
+   accumulate the phase around the boundary");
+2. Gram-Schmidt (modified, l2 over the slots) per window -> Q_w;
+3. homogeneous local solves with Robin data q_{w,m}: Phi_{w,m} = M.solve;
+4. traces of the restricted basis fields on the neighbours' boundaries
+   (extract_neighboring_bc) -> the columns of B Q;
+5. assemble the normal matrix of Eq. 8.
+The Rayleigh-Ritz step (eig of (x, y)) keeps all k Ritz vectors in this
+build, which leaves span(Q) and hence the correction unchanged; it is
+omitted (reading).
+
+Coarse equation (reading of Eq. 7): after adding sum_m z_{w,m} Phi_{w,m} to
+window w the boundary mismatch becomes e_bc + (BQ - Q) z, so the coarse
+problem is  min || (BQ - Q) z + e_bc ||  solved through its normal
+equations (Eq. 8):  C^H C z = -C^H e_bc,  C = BQ - Q.
+
+Trials that Gram-Schmidt finds exactly dependent are dropped (zero basis
+vector, zero field); their coefficients are pinned to zero by a unit
+diagonal in the normal matrix.
+
+Parity: pinned in tests/test_oracle_coarse.py (normal-equation solve equals
+numpy.linalg.lstsq; the correction removes a mismatch that lies in the
+range of C; Gram-Schmidt orthonormality; exact plane-wave phase on a
+homogeneous window).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .partition import Windows, WIN, CORE, SIDES, traces, kd_map
+
+
+def perimeter_walk(win: Windows, w: int):
+    """Counter-clockwise list of (side, t, gx, gy) around window w."""
+    x0, y0 = int(win.x0[w]), int(win.y0[w])
+    walk = []
+    for t in range(WIN):
+        walk.append((2, t, x0 + t, y0))
+    for t in range(WIN):
+        walk.append((1, t, x0 + WIN - 1, y0 + t))
+    for t in range(WIN - 1, -1, -1):
+        walk.append((3, t, x0 + t, y0 + WIN - 1))
+    for t in range(WIN - 1, -1, -1):
+        walk.append((0, t, x0, y0 + t))
+    return walk
+
+
+def plane_wave_trials(win: Windows, eps, dx, wavelength, k: int) -> np.ndarray:
+    """[n_win][k][4][80] trial Robin data (zero on grid-edge sides)."""
+    kd = kd_map(eps, dx, wavelength)
+    out = np.zeros((win.n, k, SIDES, WIN), dtype=np.complex128)
+    for w in range(win.n):
+        walk = perimeter_walk(win, w)
+        for m in range(k):
+            th = 2.0 * np.pi * m / k
+            d = np.array([np.cos(th), np.sin(th)])
+            phi = 0.0
+            prev = None
+            for (s, t, gx, gy) in walk:
+                if prev is not None:
+                    px, py = prev
+                    step = np.array([gx - px, gy - py], dtype=np.float64)
+                    kav = 0.5 * (kd[py, px] + kd[gy, gx])
+                    phi += kav * float(d @ step)
+                prev = (gx, gy)
+                if win.interface[w, s]:
+                    out[w, m, s, t] = np.exp(-1j * phi)
+    return out
+
+
+def gram_schmidt(X: np.ndarray, drop_tol: float = 1e-10) -> np.ndarray:
+    """Modified Gram-Schmidt of the k rows of each window's [k][320] block."""
+    nw, k = X.shape[:2]
+    Q = X.reshape(nw, k, -1).astype(np.complex128).copy()
+    for w in range(nw):
+        for m in range(k):
+            v = Q[w, m]
+            n0 = np.linalg.norm(v)
+            for i in range(m):
+                v = v - np.vdot(Q[w, i], v) * Q[w, i]
+            nv = np.linalg.norm(v)
+            Q[w, m] = 0.0 if (n0 == 0 or nv <= drop_tol * n0) else v / nv
+    return Q.reshape(X.shape)
+
+
+class CoarseSpace:
+    """Q, Phi, C = BQ - Q and the factored normal matrix C^H C."""
+
+    def __init__(self, win: Windows, eps, dx, wavelength, k: int, local_solve):
+        """local_solve(g [n_win][4][80]) -> fields [n_win][80][80]: the
+        homogeneous (zero-source) local Robin solver of every window."""
+        self.win, self.k = win, k
+        self.eps, self.dx, self.wavelength = eps, dx, wavelength
+        X = plane_wave_trials(win, eps, dx, wavelength, k)
+        self.Q = gram_schmidt(X)                       # [n][k][4][80]
+        self.Phi = np.zeros((win.n, k, WIN, WIN), dtype=np.complex128)
+        for m in range(k):
+            self.Phi[:, m] = local_solve(self.Q[:, m])
+        self.C = self.assemble_C()
+        self.N = self.C.conj().T @ self.C
+        # Trial vectors removed by Gram-Schmidt (exactly dependent trials,
+        # e.g. symmetric direction sets on a corner window's two sides) give
+        # zero columns; their unknowns are pinned to z = 0 by a unit diagonal.
+        self.dropped = ~np.any(self.Q.reshape(win.n * k, -1), axis=1)
+        self.N[self.dropped, self.dropped] = 1.0
+        self.L = np.linalg.cholesky(self.N)
+
+    def restricted_field(self, w: int, f_loc: np.ndarray) -> np.ndarray:
+        """R~_w^T f: window field placed on w's core only."""
+        win = self.win
+        u = np.zeros((win.ny, win.nx), dtype=np.complex128)
+        cx, cy = win.core_offset(w)
+        a, b = w % win.nwx, w // win.nwx
+        u[CORE * b:CORE * b + CORE, CORE * a:CORE * a + CORE] = f_loc[cy:cy + CORE, cx:cx + CORE]
+        return u
+
+    def assemble_C(self) -> np.ndarray:
+        win, k = self.win, self.k
+        nrow = win.n * SIDES * WIN
+        C = np.zeros((nrow, win.n * k), dtype=np.complex128)
+        for w in range(win.n):
+            for m in range(k):
+                u = self.restricted_field(w, self.Phi[w, m])
+                col = traces(win, u, self.eps, self.dx, self.wavelength).ravel()
+                q = np.zeros((win.n, SIDES, WIN), dtype=np.complex128)
+                q[w] = self.Q[w, m]
+                C[:, w * k + m] = col - q.ravel()
+        return C
+
+    def solve(self, e_bc: np.ndarray) -> np.ndarray:
+        """z = (C^H C)^{-1} (-C^H e_bc) via the Cholesky factor (Eq. 8)."""
+        rhs = -self.C.conj().T @ e_bc.ravel()
+        rhs[self.dropped] = 0.0
+        y = np.linalg.solve(self.L, rhs)
+        return np.linalg.solve(self.L.conj().T, y)
+
+    def correction(self, z: np.ndarray) -> np.ndarray:
+        """sum_w R~_w^T sum_m z_{w,m} Phi_{w,m} as a global field."""
+        win, k = self.win, self.k
+        loc = np.einsum("wm,wmyx->wyx", z.reshape(win.n, k), self.Phi)
+        u = np.zeros((win.ny, win.nx), dtype=np.complex128)
+        for w in range(win.n):
+            u += self.restricted_field(w, loc[w])
+        return u

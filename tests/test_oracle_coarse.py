@@ -1,0 +1,105 @@
+"""Pins of the coarse-space oracle (Eq. 7-8, Algorithm 3) and trend pins of
+the two-level preconditioner (Table 1: two-level needs fewer iterations)."""
+import numpy as np
+import pytest
+
+from oracle import coarse, fdfd, krylov, partition as P, schwarz
+from paper_2509_03622_gb300 import workloads as wl
+
+LAM = 1.55e-6
+
+
+def test_plane_wave_phase_homogeneous_window():
+    """Homogeneous eps: the accumulated phase is exactly kd d.(r - r_corner)."""
+    n = 192
+    eps = np.full((n, n), 2.1, np.float32)
+    dx = LAM / 25
+    win = P.Windows(n, n)
+    X = coarse.plane_wave_trials(win, eps, dx, LAM, 8)
+    kd = 2 * np.pi / 25 * np.sqrt(np.float64(np.float32(2.1)))
+    w = 4  # interior window (1, 1) of the 3 x 3 layout
+    x0, y0 = win.x0[w], win.y0[w]
+    for m in range(8):
+        th = 2 * np.pi * m / 8
+        for (s, t, gx, gy) in coarse.perimeter_walk(win, w):
+            ph = kd * (np.cos(th) * (gx - x0) + np.sin(th) * (gy - y0))
+            assert abs(X[w, m, s, t] - np.exp(-1j * ph)) < 1e-9
+
+
+def test_gram_schmidt_orthonormal():
+    g = wl.rng(0)
+    X = g.standard_normal((3, 10, 4, 80)) + 1j * g.standard_normal((3, 10, 4, 80))
+    X[1, :, 0] = 0  # a window with one grid-edge side
+    Q = coarse.gram_schmidt(X).reshape(3, 10, -1)
+    for w in range(3):
+        G = Q[w].conj() @ Q[w].T
+        assert np.allclose(G, np.eye(10), atol=1e-12)
+    assert not np.any(Q.reshape(3, 10, 4, 80)[1, :, 0])
+
+
+@pytest.fixture(scope="module")
+def small_exact():
+    n, dx = 192, LAM / 25
+    eps = wl.rectangles_eps(n, n, npml=20, n_rect=10, seed=31)
+    S = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact")
+    return S
+
+
+def test_normal_equations_equal_lstsq(small_exact):
+    cs = small_exact.coarse
+    e = wl.rng(1).standard_normal(cs.C.shape[0]) + 0j
+    z = cs.solve(e)
+    z_ls, *_ = np.linalg.lstsq(cs.C, -e, rcond=None)
+    assert np.linalg.norm(z - z_ls) / np.linalg.norm(z_ls) < 1e-8
+
+
+def test_correction_acts_through_traces(small_exact):
+    """Trace(sum R~^T z Phi) - Q z equals C z for any z (C's columns are the
+    traces of the restricted basis fields minus the window's own data), and
+    a mismatch in the range of C is removed exactly."""
+    S = small_exact
+    cs = S.coarse
+    z0 = wl.rng(2).standard_normal(cs.C.shape[1]) + 1j * wl.rng(3).standard_normal(cs.C.shape[1])
+    z0[cs.dropped] = 0.0  # dropped trials carry no unknown
+    corr = cs.correction(z0)
+    tr = P.traces(S.win, corr, S.eps, S.dx, S.wavelength)
+    Qz = np.einsum("wm,wmst->wst", z0.reshape(S.win.n, cs.k), cs.Q)
+    assert np.allclose((tr - Qz).ravel(), cs.C @ z0, atol=1e-12 * np.max(np.abs(tr)))
+    e_bc = -(cs.C @ z0)
+    assert np.allclose(cs.solve(e_bc), z0, rtol=1e-7, atol=1e-9)
+
+
+@pytest.mark.slow
+def test_two_level_stationary_trend_table1():
+    """Trend of Table 1 for the literal Algorithm 3 loop with exact local
+    solves: on a homogeneous 256^2 grid at 24 cells per wavelength (4 x 4
+    windows) the two-level loop (k = 36) needs several times fewer
+    iterations than the one-level loop."""
+    n, dx = 256, LAM / 24
+    eps = np.ones((n, n), np.float32)
+    b = fdfd.source_rhs(wl.point_source(n, n), dx, LAM)
+    S1 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=0, local="exact")
+    S2 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=36, local="exact")
+    _, it1, r1 = schwarz.stationary_solve(S1, b, tol=1e-6, max_iters=80)
+    _, it2, r2 = schwarz.stationary_solve(S2, b, tol=1e-6, max_iters=80)
+    assert r1 <= 1e-6 and r2 <= 1e-6
+    assert 3 * it2 <= it1
+
+
+@pytest.mark.slow
+def test_exact_oras_beats_jacobi_in_fgmres():
+    """One-level ORAS with exact local Robin solves as the FGMRES
+    preconditioner converges where Jacobi-GMRES(30) stagnates."""
+    n, dx = 256, LAM / 25
+    eps = np.ones((n, n), np.float32)
+    A = fdfd.assemble_operator(eps, dx, LAM, 20)
+    b = fdfd.source_rhs(wl.point_source(n, n), dx, LAM)
+    S1 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=0, local="exact")
+    mv = lambda v: A @ v
+    x, i1 = krylov.fgmres(mv, b, precond=S1, restart=30, tol=1e-6, max_iters=100)
+    d = A.diagonal()
+    _, ij = krylov.fgmres(mv, b, precond=lambda v: v / d, restart=30, tol=1e-6, max_iters=100)
+    assert i1["converged"] and i1["iters"] < 40
+    assert not ij["converged"]
+    xs = fdfd.DirectSolver(A).solve(b)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-4
