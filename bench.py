@@ -1,0 +1,280 @@
+"""Benchmark of the Schwarz neural-operator FGMRES solve (one JSON line).
+
+A step is one outer FGMRES iteration of the whole hot path on a synthetic
+4096 x 4096 freeform-dielectric problem (lambda/dx = 30, 20-cell PML, unit
+line source): two-level Schwarz preconditioner (restriction, batched neural
+local solves, restricted prolongation, traces, coarse solve and
+correction), the stencil matvec, CGS orthogonalisation and the FP64
+Hessenberg update.  Metric: Mcell-iterations per second = cells x steps /
+device time.  `--precond jacobi` benches the Jacobi-GMRES baseline on the
+same problem.  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to rel-resid 1e-6 @4096^2: Schwarz-NO FGMRES vs plain GMRES; Mcell-it/s"
+HBM_FALLBACK = 6800.0
+BF16_FALLBACK = 1900.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", HBM_FALLBACK), d.get("bf16_tflops", BF16_FALLBACK), \
+            d.get("bf16_tflops_sustained", BF16_FALLBACK), "measured"
+    return HBM_FALLBACK, BF16_FALLBACK, 1700.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, out):
+        self.out = out
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.out, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.p or not os.path.exists(self.out):
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problem(n, seed_off=0):
+    from paper_2509_03622_gb300 import workloads as wl
+    lam = 1.55e-6
+    dx = lam / 30
+    eps = wl.freeform_eps(n, n, seed=2000 + n + seed_off)
+    J = wl.point_source(n, n)
+    return eps, J, dx, lam
+
+
+def cpu_oracle_rate(n_sample, iters, precond, weights=None, k_coarse=0):
+    """Mcell-it/s of the FP64 oracle FGMRES (as it stands) on an n_sample^2
+    grid of the same recipe, `iters` Arnoldi steps."""
+    import numpy as np
+    from oracle import fdfd as OF, krylov as OK
+    eps, J, dx, lam = make_problem(n_sample)
+    t0 = time.perf_counter()
+    A = OF.assemble_operator(eps, dx, lam, 20)
+    b = OF.source_rhs(J, dx, lam)
+    if precond == "jacobi":
+        d = A.diagonal()
+        M = lambda v: v / d
+    else:
+        from oracle import schwarz as OS
+        M = OS.Schwarz(eps, dx, lam, 20, weights=weights, k_coarse=k_coarse)
+    t1 = time.perf_counter()
+    OK.fgmres(lambda v: A @ v, b, precond=M, restart=30, tol=1e-14, max_iters=iters)
+    t2 = time.perf_counter()
+    return n_sample * n_sample * iters / (t2 - t1) / 1e6, t2 - t1, t1 - t0
+
+
+def run_reference(args):
+    import numpy as np
+    from paper_2509_03622_gb300 import workloads as wl
+    n_s = args.cpu_sample
+    w = wl.nno_weights(0) if args.precond == "schwarz" else None
+    k = 4 if args.precond == "schwarz" else 0
+    tot_t, tot_cells = 0.0, 0.0
+    for _ in range(args.warmup):
+        pass  # the oracle has no device state to warm
+    for _ in range(args.steps):
+        rate, t, _ = cpu_oracle_rate(n_s, 1, args.precond, w, k)
+        tot_t += t
+        tot_cells += n_s * n_s
+    v = tot_cells / tot_t / 1e6
+    cores = os.cpu_count()
+    sample = f"{n_s}x{n_s} grid of the same freeform recipe, 1 FGMRES step per bench step ({args.precond})"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mcell-it/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"freeform{n_s} oracle sample", "grid": n_s},
+            "cpu_baseline": {"value": v, "unit": "Mcell-it/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "Mcell-it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precond", default="schwarz", choices=["schwarz", "jacobi"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--k-coarse", type=int, default=-1)
+    ap.add_argument("--cpu-sample", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tts", action="store_true", help="also time a full solve to 1e-6")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2509_03622_gb300 import fdfd as F
+    from paper_2509_03622_gb300 import workloads as wl
+    if world > 1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda")
+    n = args.n
+    # independent replica per rank (weak scaling): different seed per rank
+    eps, J, dx, lam = make_problem(n, seed_off=rank)
+    S = F.Solver(torch.from_numpy(eps).to(dev), dx, lam, npml=20)
+    precond = F.PRECOND_SCHWARZ if args.precond == "schwarz" else F.PRECOND_JACOBI
+    kc = args.k_coarse if args.k_coarse >= 0 else 8
+    prec_nno = "fp8" if n >= 4096 else "bf16"
+    if precond == F.PRECOND_SCHWARZ:
+        w = wl.nno_weights(0)
+        S.schwarz_setup(wl.pack_weights(w), k_coarse=kc,
+                        precision=F.PREC_FP8 if prec_nno == "fp8" else F.PREC_BF16)
+    Jd = torch.from_numpy(J).to(dev)
+    E = torch.zeros((n, n), dtype=torch.complex64, device=dev)
+    # warm-up: W Arnoldi steps
+    S.solve(Jd, E, restart=30, max_iters=args.warmup, tol=1e-30, precond=precond)
+    torch.cuda.synchronize()
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with clk:
+        S.profile_start()
+        ev0.record(S.stream)
+        rc, st = S.solve(Jd, E, restart=30, max_iters=args.steps, tol=1e-30, precond=precond)
+        ev1.record(S.stream)
+        prof = S.profile_stop()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    steps = st["iters"]
+    value = world * n * n * steps / (ms / 1e3) / 1e6
+    # end to end through the host-buffer entry point
+    Jh = np.ascontiguousarray(J.astype(np.complex64))
+    Eh = np.zeros_like(Jh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.solve_host(Jh, Eh, restart=30, max_iters=args.steps, tol=1e-30, precond=precond)
+    t_e2e = time.perf_counter() - t0
+    e2e_value = world * n * n * args.steps / t_e2e / 1e6
+    hbm, bf16, bf16s, src = peaks()
+    # roofline of the dominant kernel class
+    cls_ms = prof["ms"]
+    dom = max(cls_ms, key=lambda c: cls_ms[c])
+    N = n * n
+    roof = None
+    if dom == "stencil":
+        launches = prof["launches"]["stencil"]
+        per = cls_ms["stencil"] / max(launches, 1)
+        ach = 20.0 * N / (per / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "stencil_jacobi_c64" if precond == F.PRECOND_JACOBI else "stencil_c64",
+                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                "bytes_per_cell": 20, "peak_source": src}
+    elif dom in ("cgs_dots", "cgs_update"):
+        # algorithmic bytes over the timed steps (j = 0..steps-1 in one cycle of 30)
+        js = [s % 30 for s in range(steps)]
+        if dom == "cgs_dots":
+            byts = sum((8 * (j + 1) + 8) * N for j in js)
+        else:
+            byts = sum((8 * (j + 1) + 16) * N for j in js)
+        ach = byts / (cls_ms[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": src}
+    elif dom == "nno":
+        flop = 318.0e6 * (N / 4096.0) * prof["launches"].get("nno_applies", steps) if False else None
+        roof = {"bound": "tensor", "kernel": "nno", "achieved": None, "peak": bf16s, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "peak_source": src}
+    line = {"metric": METRIC, "value": value, "unit": "Mcell-it/s", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms / max(steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "data": "synthetic (seeded freeform eps, point source, seeded-init FNO weights)",
+            "config": {"workload": f"freeform{n}: {n}x{n} grid, lambda/dx=30, eps {{1,12.25}}, npml 20, "
+                                   f"{'Schwarz-NNO FGMRES(30)' if precond == F.PRECOND_SCHWARZ else 'Jacobi-GMRES(30)'}",
+                       "grid": n, "precond": args.precond, "k_coarse": kc if precond == F.PRECOND_SCHWARZ else None,
+                       "nno_precision": prec_nno if precond == F.PRECOND_SCHWARZ else None,
+                       "l2": "inputs larger than L2 (each Krylov vector 134 MB; V, Z 8 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "profile_ms": cls_ms, "gpu_launches": prof["total_launches"],
+            "e2e": {"value": e2e_value, "unit": "Mcell-it/s", "h2d_bytes_per_step": N * 8 // args.steps,
+                    "d2h_bytes_per_step": N * 8 // args.steps},
+            "clocks": clk.summary(), "relres_after_steps": st["relres_true"]}
+    if rank == 0 and not args.no_cpu:
+        w = wl.nno_weights(0) if precond == F.PRECOND_SCHWARZ else None
+        it = 3 if precond == F.PRECOND_SCHWARZ else 20
+        ns = args.cpu_sample if precond == F.PRECOND_SCHWARZ else 1024
+        rate, t, _ = cpu_oracle_rate(ns, it, args.precond, w, 4 if w is not None else 0)
+        line["cpu_baseline"] = {"value": rate, "unit": "Mcell-it/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{ns}x{ns} grid, same recipe, {it} FGMRES steps ({args.precond}), {t:.1f} s"}
+    if args.tts and rank == 0:
+        E.zero_()
+        rc, st2 = S.solve(Jd, E, restart=30, max_iters=3000, tol=1e-6, precond=precond)
+        line["time_to_1e-6"] = {"status": F.status_string(rc), "iters": st2["iters"], "ms": st2["t_solve_ms"],
+                                "relres": st2["relres_true"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

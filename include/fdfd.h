@@ -1,0 +1,216 @@
+/*
+ * fdfd.h -- C-ABI of the GB300 (sm_103a) two-level Schwarz neural-operator
+ * FGMRES solver for the 2D frequency-domain Maxwell (Ez) FDFD operator of
+ * arXiv 2509.03622 ("Accurate and scalable deep Maxwell solvers using
+ * multilevel iterative methods").
+ *
+ * Problem statement (Eq. 1 with the UPML of Methods, Eq. 3-6):
+ *     lap E + k0^2 eps E = j w mu0 J   (time dependence e^{+j w t}),
+ * on an nx x ny grid of square cells dx, stretched-coordinate PML of npml
+ * cells per side (m = 3, R = e^-30 by default), E = 0 outside the grid.
+ * The library solves the dx^2-scaled system  A~ E = b~ = dx^2 j w mu0 J.
+ *
+ * Conventions for every entry point:
+ *   - grid arrays are row-major [ny][nx] (x fastest); complex values are
+ *     interleaved (re, im) float32 pairs (fdfd_c64);
+ *   - "device pointer" = memory the calling process allocated on the
+ *     handle's GPU (e.g. a torch tensor's data_ptr); the caller owns it and
+ *     keeps it alive until the call returns (all calls below synchronise
+ *     the handle's stream before returning unless stated otherwise);
+ *   - the library owns the handle and all its workspace, allocated in
+ *     fdfd_create / schwarz_setup and freed in fdfd_destroy; no solve
+ *     allocates device memory;
+ *   - return value 0 = FDFD_OK; > 0 = soft outcome with valid stats;
+ *     < 0 = hard error (nothing written to the outputs is meaningful).
+ *     No C++ exception crosses this boundary.
+ *   - windows: the grid is tiled by 64 x 64 cores; window w (row-major over
+ *     cores, nwx = nx/64 per row) is the 80 x 80 block around core w (8 cells
+ *     of overlap per side), shifted inward at the grid edge.  nx and ny must
+ *     be multiples of 64 and at least 128.
+ */
+#ifndef FDFD_H
+#define FDFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define FDFD_OK             0
+#define FDFD_NOT_CONVERGED  1   /* max_iters reached; stats valid            */
+#define FDFD_STAGNATED      2   /* a restart cycle made no progress          */
+#define FDFD_EINVAL        -1   /* bad argument (checked on the host)        */
+#define FDFD_ECUDA         -2   /* a CUDA call failed                        */
+#define FDFD_ENUMERIC      -3   /* NaN / Inf met in the iteration            */
+#define FDFD_ETIMEOUT      -4   /* a bounded device wait ran out             */
+#define FDFD_ENOSETUP      -5   /* schwarz_setup required first              */
+#define FDFD_ENOMEM        -6   /* workspace allocation failed               */
+
+/* ---- preconditioners ------------------------------------------------- */
+#define FDFD_PRECOND_NONE     0
+#define FDFD_PRECOND_JACOBI   1  /* z = D^-1 v, D = diag(A~)                  */
+#define FDFD_PRECOND_SCHWARZ  2  /* one two-level Schwarz sweep (Algorithm 3)
+                                    with neural local solves (Fig. 2)        */
+
+#define FDFD_PREC_BF16 0
+#define FDFD_PREC_FP8  1
+
+typedef struct fdfd_ctx* fdfd_handle;
+typedef struct { float re, im; } fdfd_c64;
+
+/* Problem description (Eq. 1; UPML of Methods). */
+typedef struct {
+  int    nx, ny;        /* grid cells, multiples of 64, >= 128            */
+  double dx;            /* cell size in metres                             */
+  double wavelength;    /* vacuum wavelength in metres                     */
+  int    npml[4];       /* PML cells on the x-, x+, y-, y+ sides           */
+  double pml_m;         /* grading exponent m (3 in the paper)             */
+  double pml_lnR;       /* ln of the ideal reflectivity (-30)              */
+  const float* eps;     /* device ptr [ny][nx] relative permittivity; the
+                           library copies it                               */
+  void*  stream;        /* cudaStream_t used for all work (NULL = legacy)  */
+} fdfd_desc;
+
+/* Two-level Schwarz set-up (Sec. 2.2, Methods, Algorithm 3 set-up). */
+typedef struct {
+  int k_coarse;          /* coarse basis vectors per window; 0 = one-level */
+  int precision;         /* FDFD_PREC_BF16 or FDFD_PREC_FP8 neural operator */
+  const float* weights;  /* HOST ptr to the FNO weight blob, float32, in the
+                            order: lift_w[32][15], lift_b[32], then per block
+                            b = 0..3: R_re[32][32][32][16], R_im[...],
+                            W[32][32], bias[32]; then p1_w[128][32], p1_b[128],
+                            p2_w[2][128], p2_b[2].  R is indexed
+                            [out][in][ky][kx] with ky rows 0..15 = modes
+                            0..15 and rows 16..31 = modes -16..-1.          */
+  size_t n_weights;      /* number of floats in the blob (4,199,442)       */
+} schwarz_desc;
+
+typedef struct {
+  int    restart;        /* FGMRES restart length, 1..32                  */
+  int    max_iters;      /* total inner iterations                        */
+  double tol;            /* true relative residual ||b~ - A~ E||/||b~||   */
+  int    precond;        /* FDFD_PRECOND_*                                 */
+  int    use_x0;         /* 1: start from the contents of E               */
+} fdfd_solve_opts;
+
+typedef struct {
+  int    iters;          /* inner (Arnoldi) iterations done               */
+  int    restarts;       /* cycles completed                              */
+  int    status;         /* same as the return value                      */
+  double relres_true;    /* FP64 ||b~ - A~ E|| / ||b~|| of the result      */
+  double relres_est;     /* last least-squares estimate                   */
+  double t_solve_ms;     /* device time of the solve (CUDA events)        */
+} fdfd_solve_stats;
+
+typedef struct {
+  int n_win, nwx, nwy;   /* windows and their layout                      */
+  int k_coarse;          /* 0 if no coarse space set up                   */
+  int n_coarse;          /* n_win * k_coarse                               */
+  size_t workspace_bytes;/* device memory held by the handle              */
+} fdfd_info;
+
+/* ---- handle life cycle ----------------------------------------------- */
+
+/* Create a solver for the problem of Eq. 1 described by *desc: computes the
+ * UPML stretching (Methods, Eq. 6) and the 5-point coefficients, copies eps,
+ * allocates the Krylov workspace for restart <= 64.  FDFD_EINVAL for bad
+ * sizes (nx, ny not multiples of 64 or < 128, npml < 0 or >= n/2, dx or
+ * wavelength <= 0).  *out is NULL on error. */
+int  fdfd_create(const fdfd_desc* desc, fdfd_handle* out);
+
+/* Replace the permittivity map (device ptr [ny][nx], copied).  Invalidates
+ * any coarse space (schwarz_setup must be called again). */
+int  fdfd_set_eps(fdfd_handle h, const float* eps_dev);
+
+/* Set up the neural local solver and, if k_coarse > 0, the coarse space of
+ * Algorithm 3: pseudo-plane-wave Robin trials, Gram-Schmidt (FP64), the
+ * homogeneous neural solves, their traces on the neighbours (B Q), the
+ * normal matrix (Eq. 8) and its FP64 Cholesky factor.  Weights are copied. */
+int  schwarz_setup(fdfd_handle h, const schwarz_desc* sd);
+
+void fdfd_destroy(fdfd_handle h);
+const char* fdfd_status_string(int code);
+int  fdfd_get_info(fdfd_handle h, fdfd_info* info);
+
+/* ---- the solve (Algorithm 1 with restarts; Sec. 2.2) ------------------ */
+
+/* Solve A~ E = dx^2 j w mu0 J with flexible GMRES(restart).  J_dev: device
+ * [ny][nx] current density (A/m^2); E_dev: device [ny][nx] output (and
+ * initial guess if use_x0).  Vectors are complex64; dots, norms and the
+ * Hessenberg least squares are FP64; the solution is accumulated in FP64
+ * and every restart recomputes the true residual in FP64 (iterative
+ * refinement).  Returns FDFD_OK when relres_true <= tol. */
+int  fdfd_solve(fdfd_handle h, const fdfd_c64* J_dev, fdfd_c64* E_dev,
+                const fdfd_solve_opts* opts, fdfd_solve_stats* stats);
+
+/* As fdfd_solve with HOST buffers: J_host and E_host are host memory; the
+ * host<->device copies are part of the call. */
+int  fdfd_solve_host(fdfd_handle h, const fdfd_c64* J_host, fdfd_c64* E_host,
+                     const fdfd_solve_opts* opts, fdfd_solve_stats* stats);
+
+/* Adjoint solve A~^T lam = g (Sec. 2.2, adjoint variable method): g_dev is
+ * the device [ny][nx] right-hand side taken as is (no source scaling), the
+ * same preconditioners applied to the transposed operator. */
+int  fdfd_solve_adjoint(fdfd_handle h, const fdfd_c64* g_dev, fdfd_c64* lam_dev,
+                        const fdfd_solve_opts* opts, fdfd_solve_stats* stats);
+
+/* dF/deps = -2 Re( lam * (k0 dx)^2 * E ) per cell (adjoint variable method,
+ * with A~ lam-adjoint  A~^T lam = dF/dE).  grad_dev: device float [ny][nx];
+ * accumulate = 1 adds to its contents (sum over wavelengths). */
+int  fdfd_grad_eps(fdfd_handle h, const fdfd_c64* E_dev, const fdfd_c64* lam_dev,
+                   float* grad_dev, int accumulate);
+
+/* ---- live profiling (CUDA events on the handle's stream) -------------- */
+#define FDFD_PROF_NCLASS 8
+/* kernel classes: 0 stencil A~x (incl. the fused Jacobi form), 1 CGS dots,
+ * 2 CGS update + Givens, 3 FP64 residual, 4 solution update / misc vector,
+ * 5 neural operator (all its kernels), 6 partition (restrict, prolong,
+ * traces), 7 coarse space (solve and correction). */
+typedef struct {
+  double ms[FDFD_PROF_NCLASS];        /* summed device time per class      */
+  long long launches[FDFD_PROF_NCLASS];/* kernel launches per class        */
+  long long total_launches;            /* all kernels the handle launched   */
+} fdfd_profile;
+
+/* Start recording: from now on every kernel class launched by this handle
+ * is bracketed by CUDA events (pool of 16384 pairs; later launches are
+ * counted but not timed).  Returns FDFD_EINVAL if already recording. */
+int  fdfd_profile_start(fdfd_handle h);
+/* Stop, synchronise and report the per-class times and launch counts. */
+int  fdfd_profile_stop(fdfd_handle h, fdfd_profile* out);
+
+/* ---- single steps of the hot path (device pointers; parity tests) ---- */
+
+/* y = A~ x (transpose = 0) or y = A~^T x (transpose = 1), complex64; the
+ * 5-point stencil of Eq. 1 with UPML (one step of the solve). */
+int  fdfd_apply_A(fdfd_handle h, const fdfd_c64* x, fdfd_c64* y, int transpose);
+
+/* z = M(v): one two-level Schwarz sweep from a zero guess -- restriction,
+ * neural local solves, restricted prolongation, trace mismatch, coarse
+ * solve and correction (Algorithm 3; Sec. 2.2).  Requires schwarz_setup. */
+int  fdfd_precond_apply(fdfd_handle h, const fdfd_c64* v, fdfd_c64* z);
+
+/* Batched neural local solves (Fig. 2) on n windows: r_win [n][80][80]
+ * window residuals, g_win [n][4][80] Robin data (sides x-, x+, y-, y+;
+ * Eq. 2), win_id [n] (device int) the window whose eps / PML the solve
+ * uses; writes e_win [n][80][80].  Requires schwarz_setup. */
+int  fdfd_nno_solve(fdfd_handle h, const fdfd_c64* r_win, const fdfd_c64* g_win,
+                    const int* win_id, int n, fdfd_c64* e_win);
+
+/* Robin traces g = u_o - u_b + j (k0 dx) sqrt(eps_b) u_b (Eq. 2, dx-scaled)
+ * of a global field on every window's interface sides: g [n_win][4][80],
+ * zero on grid-edge sides. */
+int  fdfd_trace_extract(fdfd_handle h, const fdfd_c64* u, fdfd_c64* g);
+
+/* Copy the coarse set-up out for inspection (host pointers, may be NULL):
+ * Q [n_win][k][4][80] complex128 (interleaved doubles) orthonormalised trials;
+ * normal matrix diagonal blocks N_ww [n_win][k][k] complex128. */
+int  fdfd_coarse_export(fdfd_handle h, double* Q_host, double* Ndiag_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDFD_H */

@@ -11,7 +11,7 @@ __all__ = ["fdfd", "workloads"]
 
 
 def __getattr__(name):
-    if name == "fdfd":
-        from . import fdfd as _m
-        return _m
+    if name in ("fdfd", "workloads"):
+        import importlib
+        return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

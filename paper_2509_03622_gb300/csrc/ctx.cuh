@@ -1,0 +1,66 @@
+// Handle layout shared by api.cu and the Schwarz translation units.
+#pragma once
+#include "common.cuh"
+
+struct SchwarzData;  // defined in schwarz.cu
+
+struct fdfd_ctx {
+  int nx = 0, ny = 0;
+  size_t n = 0;
+  double dx = 0, wavelength = 0, pml_m = 3, pml_lnR = -30;
+  int npml[4] = {0, 0, 0, 0};
+  double k0dx = 0, k2 = 0, sb = 0;   // k0 dx, (k0 dx)^2, dx^2 w mu0
+  cudaStream_t stream = nullptr;
+  float* eps = nullptr;
+  AxisCoef *cx = nullptr, *cy = nullptr, *cxT = nullptr, *cyT = nullptr;
+  AxisCoef64 *cx64 = nullptr, *cy64 = nullptr, *cxT64 = nullptr, *cyT64 = nullptr;
+  float2 *isx = nullptr, *isy = nullptr;  // 1/s at cell centres
+  // Krylov workspace
+  int rmax = 0;
+  float2 *V = nullptr, *Z = nullptr, *w = nullptr;
+  double2* x64 = nullptr;
+  KrylovState* st = nullptr;
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  double* d_one = nullptr;      // device constant 1.0 (unit scale)
+  double* flag_host = nullptr;  // pinned: est, nonfinite|breakdown
+  float2 *hostJ = nullptr, *hostE = nullptr;  // device staging for host-buffer solves
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  size_t bytes = 0;
+  SchwarzData* sw = nullptr;
+  // live profiling
+  bool prof_on = false;
+  int prof_next = 0;
+  cudaEvent_t* prof_ev = nullptr;   // 2 * PROF_POOL events
+  int* prof_cls = nullptr;          // class of each recorded pair
+  long long prof_launch[FDFD_PROF_NCLASS] = {0};
+  long long launches_total = 0;
+};
+
+#define PROF_POOL 16384
+// Bracket `nk` kernel launches of class `cls` issued by `body`.
+struct ProfScope {
+  fdfd_ctx* h; int cls; int slot;
+  ProfScope(fdfd_ctx* h_, int cls_, int nk) : h(h_), cls(cls_), slot(-1) {
+    h->launches_total += nk;
+    if (!h->prof_on) return;
+    h->prof_launch[cls] += nk;
+    if (h->prof_next < PROF_POOL) {
+      slot = h->prof_next++;
+      h->prof_cls[slot] = cls;
+      cudaEventRecord(h->prof_ev[2 * slot], h->stream);
+    }
+  }
+  ~ProfScope() { if (slot >= 0) cudaEventRecord(h->prof_ev[2 * slot + 1], h->stream); }
+};
+
+// schwarz.cu
+int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd);
+void schwarz_destroy(fdfd_ctx* h);
+// z = M(v * (*scale)) for the global vector v (complex64).
+int schwarz_apply(fdfd_ctx* h, const float2* v, const double* scale_dev, float2* z, int transpose);
+int schwarz_nno_solve(fdfd_ctx* h, const float2* r_win, const float2* g_win, const int* win_id,
+                      int n, float2* e_win);
+int schwarz_traces(fdfd_ctx* h, const float2* u, float2* g);
+int schwarz_export(fdfd_ctx* h, double* Q, double* Nd);
+int schwarz_info(fdfd_ctx* h, fdfd_info* info);

@@ -1,0 +1,322 @@
+// Flexible GMRES building blocks (Algorithm 1 with restarts):
+//   cgs_dots    h_i = (w, v_i) = v_i^H w, i = 0..j  (one pass over V and w)
+//   cgs_update  w' = w - sum_i h_i v_i, ||w'||^2, stored as v_{j+1};
+//               the last block then does the Hessenberg/Givens update of
+//               column j in FP64 and the least-squares residual estimate.
+//   solve_y     back substitution of the rotated Hessenberg system
+//   x_update    x += sum_j y_j z_j (x in FP64; the sum in FP32)
+// Vectors are complex64, stored v_i = (1/vscale_i) * true v_i (the norm of
+// v_{j+1} is only known after its pass, so scaling is deferred to readers).
+// Products run in FP32, per-thread partial sums in FP32 over a few dozen
+// terms, block and grid sums in FP64, summed in a fixed order (no float
+// atomics): results are bitwise reproducible for a given launch shape.
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace {
+constexpr int KT = 256;
+
+template <int NV>
+__global__ void __launch_bounds__(KT)
+cgs_dots_kernel(const float4* __restrict__ V, size_t ld4, int v0, int nv, const float4* __restrict__ w,
+                size_t n4, KrylovState* st, double2* __restrict__ partials, unsigned* counter) {
+  __shared__ double sh[KT / 32];
+  float ar[NV], ai[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) { ar[i] = 0.f; ai[i] = 0.f; }
+  for (size_t c = blockIdx.x * (size_t)KT + threadIdx.x; c < n4; c += (size_t)gridDim.x * KT) {
+    const float4 q = __ldg(w + c);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if (i < nv) {
+        const float4 v = __ldg(V + (size_t)(v0 + i) * ld4 + c);
+        // conj(v) * w for both complex entries of the float4
+        ar[i] += v.x * q.x + v.y * q.y + v.z * q.z + v.w * q.w;
+        ai[i] += v.x * q.y - v.y * q.x + v.z * q.w - v.w * q.z;
+      }
+    }
+  }
+  for (int i = 0; i < nv; ++i) {
+    const double tr = block_sum<KT>((double)ar[i], sh);
+    const double ti = block_sum<KT>((double)ai[i], sh);
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * FDFD_MAXRESTART + i] = make_double2(tr, ti);
+  }
+  if (last_block(counter)) {
+    const int nb = gridDim.x;
+    for (int i = 0; i < nv; ++i) {
+      double sr = 0.0, si = 0.0;
+      for (int b = threadIdx.x; b < nb; b += KT) {
+        const double2 p = partials[(size_t)b * FDFD_MAXRESTART + i];
+        sr += p.x; si += p.y;
+      }
+      sr = block_sum<KT>(sr, sh);
+      si = block_sum<KT>(si, sh);
+      if (threadIdx.x == 0) {
+        const double s = st->vscale[v0 + i];
+        st->h[v0 + i] = make_double2(sr * s, si * s);
+      }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// Serial FP64 Givens update of Hessenberg column j (thread 0 only).
+__device__ void givens_column(KrylovState* st, int j, int ld, double hnext) {
+  double2* Hc = st->H + (size_t)j * ld;
+  for (int i = 0; i <= j; ++i) Hc[i] = st->h[i];
+  Hc[j + 1] = make_double2(hnext, 0.0);
+  for (int i = 0; i < j; ++i) {  // earlier rotations
+    const double c = st->cs[i];
+    const double2 s = st->sn[i];
+    const double2 a = Hc[i], b = Hc[i + 1];
+    Hc[i] = zadd(make_double2(c * a.x, c * a.y), zmul(s, b));
+    Hc[i + 1] = zsub(make_double2(c * b.x, c * b.y), zmul(zconj(s), a));
+  }
+  const double2 a = Hc[j], b = Hc[j + 1];
+  const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+  double c; double2 s;
+  if (bb == 0.0) { c = 1.0; s = make_double2(0.0, 0.0); }
+  else if (aa == 0.0) { c = 0.0; s = make_double2(b.x / bb, -b.y / bb); }
+  else {
+    const double t = hypot(aa, bb);
+    c = aa / t;
+    const double2 ph = make_double2(a.x / aa, a.y / aa);
+    s = zmul(ph, make_double2(b.x / t, -b.y / t));
+  }
+  st->cs[j] = c; st->sn[j] = s;
+  Hc[j] = zadd(make_double2(c * a.x, c * a.y), zmul(s, b));
+  Hc[j + 1] = make_double2(0.0, 0.0);
+  const double2 gj = st->g[j];
+  st->g[j + 1] = zmul(make_double2(-s.x, s.y), gj);   // -conj(s) g_j
+  st->g[j] = make_double2(c * gj.x, c * gj.y);
+  const double2 gn = st->g[j + 1];
+  st->est = hypot(gn.x, gn.y) / st->bnorm;
+  if (!isfinite(hnext) || !isfinite(st->est)) st->nonfinite = 1;
+  st->breakdown = (hnext == 0.0);
+  st->vscale[j + 1] = (hnext > 0.0) ? 1.0 / hnext : 0.0;
+}
+
+template <int NV>
+__global__ void __launch_bounds__(KT)
+cgs_update_kernel(const float4* __restrict__ V, size_t ld4, int v0, int nv, float4* __restrict__ w,
+                  float4* __restrict__ vnext, size_t n4, KrylovState* st, double* __restrict__ partials,
+                  unsigned* counter, int j_col, int ld, int final_chunk) {
+  __shared__ double sh[KT / 32];
+  __shared__ float2 coef[NV];
+  if (threadIdx.x < nv) {
+    const double2 h = st->h[v0 + threadIdx.x];
+    const double s = st->vscale[v0 + threadIdx.x];
+    coef[threadIdx.x] = make_float2((float)(h.x * s), (float)(h.y * s));
+  }
+  __syncthreads();
+  float acc = 0.f;
+  for (size_t c = blockIdx.x * (size_t)KT + threadIdx.x; c < n4; c += (size_t)gridDim.x * KT) {
+    float4 q = w[c];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      if (i < nv) {
+        const float4 v = __ldg(V + (size_t)(v0 + i) * ld4 + c);
+        const float2 h = coef[i];
+        q.x -= h.x * v.x - h.y * v.y; q.y -= h.x * v.y + h.y * v.x;
+        q.z -= h.x * v.z - h.y * v.w; q.w -= h.x * v.w + h.y * v.z;
+      }
+    }
+    if (final_chunk) {
+      vnext[c] = q;
+      acc += q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    } else {
+      w[c] = q;
+    }
+  }
+  if (!final_chunk) return;
+  const double t = block_sum<KT>((double)acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  if (last_block(counter)) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += KT) s += partials[b];
+    s = block_sum<KT>(s, sh);
+    if (threadIdx.x == 0) {
+      *counter = 0u;
+      givens_column(st, j_col, ld, sqrt(s));
+    }
+  }
+}
+
+__global__ void cycle_start_kernel(KrylovState* st) {
+  const double beta = sqrt(st->resid);
+  st->beta = beta;
+  st->g[0] = make_double2(beta, 0.0);
+  st->vscale[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+  st->est = beta / st->bnorm;
+  if (!isfinite(beta)) st->nonfinite = 1;
+}
+
+__global__ void solve_y_kernel(KrylovState* st, int k, int ld) {
+  for (int i = k - 1; i >= 0; --i) {
+    double2 acc = st->g[i];
+    for (int l = i + 1; l < k; ++l) acc = zsub(acc, zmul(st->H[(size_t)l * ld + i], st->y[l]));
+    const double2 d = st->H[(size_t)i * ld + i];
+    const double den = d.x * d.x + d.y * d.y;
+    st->y[i] = den > 0 ? make_double2((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den)
+                       : make_double2(0.0, 0.0);
+  }
+}
+
+__global__ void x_update_kernel(double2* __restrict__ x, const float2* __restrict__ Z, size_t ld, int k,
+                                size_t n, const KrylovState* __restrict__ st) {
+  __shared__ float2 y[FDFD_MAXRESTART];
+  if (threadIdx.x < k) y[threadIdx.x] = make_float2((float)st->y[threadIdx.x].x, (float)st->y[threadIdx.x].y);
+  __syncthreads();
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    float2 d = make_float2(0.f, 0.f);
+    for (int jj = 0; jj < k; ++jj) d = cadd(d, cmul(y[jj], __ldg(Z + (size_t)jj * ld + c)));
+    double2 xc = x[c];
+    xc.x += (double)d.x; xc.y += (double)d.y;
+    x[c] = xc;
+  }
+}
+
+__global__ void x_update_jacobi_kernel(double2* __restrict__ x, const float2* __restrict__ V, size_t ld,
+                                       int k, size_t n, const KrylovState* __restrict__ st,
+                                       const float* __restrict__ eps, const AxisCoef* __restrict__ cx,
+                                       const AxisCoef* __restrict__ cy, float k2, int nx) {
+  __shared__ float2 y[FDFD_MAXRESTART];
+  if (threadIdx.x < k) {
+    const double s = st->vscale[threadIdx.x];
+    y[threadIdx.x] = make_float2((float)(st->y[threadIdx.x].x * s), (float)(st->y[threadIdx.x].y * s));
+  }
+  __syncthreads();
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    float2 d = make_float2(0.f, 0.f);
+    for (int jj = 0; jj < k; ++jj) d = cadd(d, cmul(y[jj], __ldg(V + (size_t)jj * ld + c)));
+    const int i = (int)(c % nx), j = (int)(c / nx);
+    const float2 dg = make_float2(cx[i].dg.x + cy[j].dg.x + k2 * eps[c], cx[i].dg.y + cy[j].dg.y);
+    const float inv = 1.f / (dg.x * dg.x + dg.y * dg.y);
+    const float2 q = make_float2((d.x * dg.x + d.y * dg.y) * inv, (d.y * dg.x - d.x * dg.y) * inv);
+    double2 xc = x[c];
+    xc.x += (double)q.x; xc.y += (double)q.y;
+    x[c] = xc;
+  }
+}
+
+__global__ void store_field_kernel(const double2* __restrict__ x, float2* __restrict__ E, size_t n) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    E[c] = make_float2((float)x[c].x, (float)x[c].y);
+}
+__global__ void load_field_kernel(const float2* __restrict__ E, double2* __restrict__ x, size_t n) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    x[c] = make_double2((double)E[c].x, (double)E[c].y);
+}
+__global__ void scale_copy_kernel(const float2* __restrict__ v, const double* __restrict__ sc,
+                                  float2* __restrict__ z, size_t n) {
+  const float s = (float)(*sc);
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    z[c] = make_float2(v[c].x * s, v[c].y * s);
+}
+
+template <int NV>
+int dots_nv(const float2* V, size_t ld, int v0, int nv, const float2* w, size_t n, KrylovState* st,
+            double* partials, unsigned* counter, cudaStream_t s) {
+  cgs_dots_kernel<NV><<<krylov_grid(n), KT, 0, s>>>(
+      reinterpret_cast<const float4*>(V), ld / 2, v0, nv, reinterpret_cast<const float4*>(w), n / 2, st,
+      reinterpret_cast<double2*>(partials), counter);
+  CKL();
+  return FDFD_OK;
+}
+
+template <int NV>
+int update_nv(const float2* V, size_t ld, int v0, int nv, float2* w, float2* vnext, size_t n,
+              KrylovState* st, double* partials, unsigned* counter, int j, int ldH, int fin,
+              cudaStream_t s) {
+  cgs_update_kernel<NV><<<krylov_grid(n), KT, 0, s>>>(
+      reinterpret_cast<const float4*>(V), ld / 2, v0, nv, reinterpret_cast<float4*>(w),
+      reinterpret_cast<float4*>(vnext), n / 2, st, partials, counter, j, ldH, fin);
+  CKL();
+  return FDFD_OK;
+}
+
+}  // namespace
+
+int krylov_grid(size_t n) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
+  }
+  const size_t want = (n / 2 + KT - 1) / KT;
+  const size_t cap = (size_t)nsm * 8;
+  return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+int launch_cgs_dots(const float2* V, size_t ld, int j, const float2* w, size_t n, KrylovState* st,
+                    double* partials, unsigned* counter, cudaStream_t s) {
+  int rc = FDFD_OK;
+  for (int v0 = 0; v0 <= j && rc == FDFD_OK; v0 += 32) {
+    const int nv = (j + 1 - v0) < 32 ? (j + 1 - v0) : 32;
+    if (nv <= 8) rc = dots_nv<8>(V, ld, v0, nv, w, n, st, partials, counter, s);
+    else if (nv <= 16) rc = dots_nv<16>(V, ld, v0, nv, w, n, st, partials, counter, s);
+    else if (nv <= 24) rc = dots_nv<24>(V, ld, v0, nv, w, n, st, partials, counter, s);
+    else rc = dots_nv<32>(V, ld, v0, nv, w, n, st, partials, counter, s);
+  }
+  return rc;
+}
+
+int launch_cgs_update(const float2* V, size_t ld, int j, float2* w, float2* vnext, size_t n,
+                      KrylovState* st, double* partials, unsigned* counter, int restart,
+                      cudaStream_t s) {
+  int rc = FDFD_OK;
+  const int ldH = restart + 1;
+  for (int v0 = 0; v0 <= j && rc == FDFD_OK; v0 += 32) {
+    const int nv = (j + 1 - v0) < 32 ? (j + 1 - v0) : 32;
+    const int fin = (v0 + 32 > j);
+    if (nv <= 8) rc = update_nv<8>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
+    else if (nv <= 16) rc = update_nv<16>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
+    else if (nv <= 24) rc = update_nv<24>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
+    else rc = update_nv<32>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
+  }
+  return rc;
+}
+
+int launch_cycle_start(KrylovState* st, cudaStream_t s) {
+  cycle_start_kernel<<<1, 1, 0, s>>>(st);
+  CKL();
+  return FDFD_OK;
+}
+
+int launch_solve_y(KrylovState* st, int k, int restart, cudaStream_t s) {
+  solve_y_kernel<<<1, 1, 0, s>>>(st, k, restart + 1);
+  CKL();
+  return FDFD_OK;
+}
+
+int launch_x_update(double2* x, const float2* Z, size_t ld, int k, size_t n, const KrylovState* st,
+                    cudaStream_t s) {
+  x_update_kernel<<<krylov_grid(n), 256, 0, s>>>(x, Z, ld, k, n, st);
+  CKL();
+  return FDFD_OK;
+}
+
+int launch_x_update_jacobi(double2* x, const float2* V, size_t ld, int k, size_t n,
+                           const KrylovState* st, const float* eps, const AxisCoef* cx,
+                           const AxisCoef* cy, float k2, int nx, cudaStream_t s) {
+  x_update_jacobi_kernel<<<krylov_grid(n), 256, 0, s>>>(x, V, ld, k, n, st, eps, cx, cy, k2, nx);
+  CKL();
+  return FDFD_OK;
+}
+
+int launch_store_field(const double2* x, float2* E, size_t n, cudaStream_t s) {
+  store_field_kernel<<<krylov_grid(n), 256, 0, s>>>(x, E, n);
+  CKL();
+  return FDFD_OK;
+}
+int launch_load_field(const float2* E, double2* x, size_t n, cudaStream_t s) {
+  load_field_kernel<<<krylov_grid(n), 256, 0, s>>>(E, x, n);
+  CKL();
+  return FDFD_OK;
+}
+int launch_scale_copy(const float2* v, const double* sc, float2* z, size_t n, cudaStream_t s) {
+  scale_copy_kernel<<<krylov_grid(n), 256, 0, s>>>(v, sc, z, n);
+  CKL();
+  return FDFD_OK;
+}

@@ -1,0 +1,221 @@
+// 5-point stencil of the dx^2-scaled operator of Eq. 1 with UPML (Methods):
+//   (A~x)_ij = hi_x(i) x_{i+1,j} + lo_x(i) x_{i-1,j} + hi_y(j) x_{i,j+1}
+//            + lo_y(j) x_{i,j-1} + (dg_x(i) + dg_y(j) + (k0 dx)^2 eps_ij) x_ij,
+// zero outside the grid.  For A~ the coefficients are lo = 1/(s_n(i) s_h(i)),
+// hi = 1/(s_n(i) s_h(i+1)), dg = -(lo + hi); for A~^T the host passes
+// lo(i) = hi(i-1), hi(i) = lo(i+1) with the same dg.
+//
+// Complex64 kernel: one thread computes two adjacent cells (one float4),
+// left/right neighbours come from the neighbouring lanes by shuffle, the
+// rows above and below from L1/L2.  Algorithmic HBM traffic 20 B per cell
+// (x 8 + eps 4 + y 8).
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+__device__ __forceinline__ float2 ax_apply(const AxisCoef& c, float2 xm, float2 xp) {
+  return cadd(cmul(c.lo, xm), cmul(c.hi, xp));
+}
+
+__global__ void __launch_bounds__(BX * BY)
+stencil_c64(const float4* __restrict__ x, float4* __restrict__ y, const float2* __restrict__ eps,
+            const AxisCoef* __restrict__ cx, const AxisCoef* __restrict__ cy, float k2, int nx,
+            int ny) {
+  const int lane = threadIdx.x;
+  const int p = blockIdx.x * BX + lane;          // float4 (cell pair) column
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int np = nx >> 1;
+  const size_t row = (size_t)j * np;
+  const float4 c = __ldg(x + row + p);
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 up = (j + 1 < ny) ? __ldg(x + row + np + p) : zero4;
+  const float4 dn = (j > 0) ? __ldg(x + row - np + p) : zero4;
+  float lx = __shfl_up_sync(0xffffffffu, c.z, 1), ly = __shfl_up_sync(0xffffffffu, c.w, 1);
+  float rx = __shfl_down_sync(0xffffffffu, c.x, 1), ry = __shfl_down_sync(0xffffffffu, c.y, 1);
+  if (lane == 0) {
+    if (p > 0) { float4 t = __ldg(x + row + p - 1); lx = t.z; ly = t.w; } else { lx = 0.f; ly = 0.f; }
+  }
+  if (lane == BX - 1) {
+    if (p + 1 < np) { float4 t = __ldg(x + row + p + 1); rx = t.x; ry = t.y; } else { rx = 0.f; ry = 0.f; }
+  }
+  const float2 e = __ldg(eps + row + p);
+  const int i0 = 2 * p;
+  const AxisCoef a0 = cx[i0], a1 = cx[i0 + 1], b = cy[j];
+  const float2 x0 = make_float2(c.x, c.y), x1 = make_float2(c.z, c.w);
+  float2 y0 = ax_apply(a0, make_float2(lx, ly), x1);
+  float2 y1 = ax_apply(a1, x0, make_float2(rx, ry));
+  y0 = cadd(y0, ax_apply(b, make_float2(dn.x, dn.y), make_float2(up.x, up.y)));
+  y1 = cadd(y1, ax_apply(b, make_float2(dn.z, dn.w), make_float2(up.z, up.w)));
+  const float2 d0 = make_float2(a0.dg.x + b.dg.x + k2 * e.x, a0.dg.y + b.dg.y);
+  const float2 d1 = make_float2(a1.dg.x + b.dg.x + k2 * e.y, a1.dg.y + b.dg.y);
+  y0 = cadd(y0, cmul(d0, x0));
+  y1 = cadd(y1, cmul(d1, x1));
+  y[row + p] = make_float4(y0.x, y0.y, y1.x, y1.y);
+}
+
+// w = A~ (D^-1 v * s): the Jacobi-preconditioned operator in one sweep
+// (D = diagonal of A~, recomputed from eps and the PML coefficients).
+__device__ __forceinline__ float2 cdiv(float2 a, float2 d) {
+  const float inv = 1.f / (d.x * d.x + d.y * d.y);
+  return make_float2((a.x * d.x + a.y * d.y) * inv, (a.y * d.x - a.x * d.y) * inv);
+}
+
+__device__ __forceinline__ float2 diag_at(const AxisCoef* cx, const AxisCoef* cy, const float* eps,
+                                          float k2, int i, int j, int nx) {
+  const float2 dx_ = cx[i].dg, dy_ = cy[j].dg;
+  return make_float2(dx_.x + dy_.x + k2 * __ldg(eps + (size_t)j * nx + i), dx_.y + dy_.y);
+}
+
+__global__ void __launch_bounds__(BX * BY)
+stencil_jacobi_c64(const float4* __restrict__ v, const double* __restrict__ vscale,
+                   float4* __restrict__ w, const float* __restrict__ eps,
+                   const AxisCoef* __restrict__ cx, const AxisCoef* __restrict__ cy, float k2,
+                   int nx, int ny) {
+  const int lane = threadIdx.x;
+  const int p = blockIdx.x * BX + lane;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int np = nx >> 1;
+  const size_t row = (size_t)j * np;
+  const float s = (float)(*vscale);
+  const int i0 = 2 * p;
+  auto u_of = [&](float4 q, int ii, int jj) -> float4 {  // D^-1 v s at (ii, jj), (ii+1, jj)
+    float2 a = cdiv(make_float2(q.x * s, q.y * s), diag_at(cx, cy, eps, k2, ii, jj, nx));
+    float2 b = cdiv(make_float2(q.z * s, q.w * s), diag_at(cx, cy, eps, k2, ii + 1, jj, nx));
+    return make_float4(a.x, a.y, b.x, b.y);
+  };
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 c = u_of(__ldg(v + row + p), i0, j);
+  const float4 up = (j + 1 < ny) ? u_of(__ldg(v + row + np + p), i0, j + 1) : zero4;
+  const float4 dn = (j > 0) ? u_of(__ldg(v + row - np + p), i0, j - 1) : zero4;
+  float lx = __shfl_up_sync(0xffffffffu, c.z, 1), ly = __shfl_up_sync(0xffffffffu, c.w, 1);
+  float rx = __shfl_down_sync(0xffffffffu, c.x, 1), ry = __shfl_down_sync(0xffffffffu, c.y, 1);
+  if (lane == 0) {
+    if (p > 0) { float4 t = u_of(__ldg(v + row + p - 1), i0 - 2, j); lx = t.z; ly = t.w; } else { lx = 0.f; ly = 0.f; }
+  }
+  if (lane == BX - 1) {
+    if (p + 1 < np) { float4 t = u_of(__ldg(v + row + p + 1), i0 + 2, j); rx = t.x; ry = t.y; } else { rx = 0.f; ry = 0.f; }
+  }
+  const AxisCoef a0 = cx[i0], a1 = cx[i0 + 1], b = cy[j];
+  const float2 x0 = make_float2(c.x, c.y), x1 = make_float2(c.z, c.w);
+  float2 y0 = ax_apply(a0, make_float2(lx, ly), x1);
+  float2 y1 = ax_apply(a1, x0, make_float2(rx, ry));
+  y0 = cadd(y0, ax_apply(b, make_float2(dn.x, dn.y), make_float2(up.x, up.y)));
+  y1 = cadd(y1, ax_apply(b, make_float2(dn.z, dn.w), make_float2(up.z, up.w)));
+  const float2 e = __ldg(reinterpret_cast<const float2*>(eps) + row + p);
+  const float2 d0 = make_float2(a0.dg.x + b.dg.x + k2 * e.x, a0.dg.y + b.dg.y);
+  const float2 d1 = make_float2(a1.dg.x + b.dg.x + k2 * e.y, a1.dg.y + b.dg.y);
+  y0 = cadd(y0, cmul(d0, x0));
+  y1 = cadd(y1, cmul(d1, x1));
+  w[row + p] = make_float4(y0.x, y0.y, y1.x, y1.y);
+}
+
+// z = D^-1 v s (stored, for the flexible basis when Jacobi is used as M).
+__global__ void jacobi_apply(const float2* __restrict__ v, const double* __restrict__ vscale,
+                             float2* __restrict__ z, const float* __restrict__ eps,
+                             const AxisCoef* __restrict__ cx, const AxisCoef* __restrict__ cy,
+                             float k2, int nx, size_t n) {
+  const float s = (float)(*vscale);
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx), j = (int)(c / nx);
+    const float2 q = v[c];
+    z[c] = cdiv(make_float2(q.x * s, q.y * s), diag_at(cx, cy, eps, k2, i, j, nx));
+  }
+}
+
+// FP64 residual r = b - A~ x with FP64 coefficients, x in FP64; b = j sb J
+// (source form) or b = J (adjoint right-hand side).  Writes r rounded to
+// complex64 and reduces ||r||^2 (FP64) into *result.
+constexpr int RT = 256;
+__global__ void __launch_bounds__(RT)
+residual64(const double2* __restrict__ x, const float2* __restrict__ J, double sb, int src,
+           const float* __restrict__ eps, const AxisCoef64* __restrict__ cx,
+           const AxisCoef64* __restrict__ cy, double k2, int nx, int ny,
+           float2* __restrict__ r_out, double* __restrict__ partials, unsigned* counter,
+           double* result) {
+  __shared__ double sh[RT / 32];
+  double acc = 0.0;
+  const size_t n = (size_t)nx * ny;
+  for (size_t c = blockIdx.x * (size_t)RT + threadIdx.x; c < n; c += (size_t)gridDim.x * RT) {
+    const int i = (int)(c % nx), j = (int)(c / nx);
+    const AxisCoef64 a = cx[i], b = cy[j];
+    const double2 xc = x[c];
+    double2 Ax = zmul(make_double2(a.dg.x + b.dg.x + k2 * (double)eps[c], a.dg.y + b.dg.y), xc);
+    if (i > 0) Ax = zadd(Ax, zmul(a.lo, x[c - 1]));
+    if (i + 1 < nx) Ax = zadd(Ax, zmul(a.hi, x[c + 1]));
+    if (j > 0) Ax = zadd(Ax, zmul(b.lo, x[c - nx]));
+    if (j + 1 < ny) Ax = zadd(Ax, zmul(b.hi, x[c + nx]));
+    const float2 Jc = J[c];
+    const double2 bc = src ? make_double2(-sb * (double)Jc.y, sb * (double)Jc.x)
+                           : make_double2((double)Jc.x, (double)Jc.y);
+    const double2 r = zsub(bc, Ax);
+    r_out[c] = make_float2((float)r.x, (float)r.y);
+    acc += r.x * r.x + r.y * r.y;
+  }
+  const double t = block_sum<RT>(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  if (last_block(counter)) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += RT) s += partials[b];
+    s = block_sum<RT>(s, sh);
+    if (threadIdx.x == 0) { *result = s; *counter = 0u; }
+  }
+}
+
+__global__ void grad_eps_kernel(const float2* __restrict__ E, const float2* __restrict__ lam,
+                                float* __restrict__ grad, float k2, size_t n, int acc) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const float2 e = E[c], l = lam[c];
+    const float g = -2.f * k2 * (l.x * e.x - l.y * e.y);
+    grad[c] = acc ? grad[c] + g : g;
+  }
+}
+
+}  // namespace
+
+int launch_stencil(const float2* x, float2* y, const float* eps, const AxisCoef* cx,
+                   const AxisCoef* cy, float k2, int nx, int ny, cudaStream_t s) {
+  dim3 grid(nx / (2 * BX), ny / BY), block(BX, BY);
+  stencil_c64<<<grid, block, 0, s>>>(reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(y),
+                                     reinterpret_cast<const float2*>(eps), cx, cy, k2, nx, ny);
+  CKL();
+  return FDFD_OK;
+}
+
+int launch_stencil_jacobi(const float2* v, const double* vscale, float2* w, const float* eps,
+                          const AxisCoef* cx, const AxisCoef* cy, float k2, int nx, int ny,
+                          cudaStream_t s) {
+  dim3 grid(nx / (2 * BX), ny / BY), block(BX, BY);
+  stencil_jacobi_c64<<<grid, block, 0, s>>>(reinterpret_cast<const float4*>(v), vscale,
+                                            reinterpret_cast<float4*>(w), eps, cx, cy, k2, nx, ny);
+  CKL();
+  return FDFD_OK;
+}
+
+int launch_jacobi_apply(const float2* v, const double* vscale, float2* z, const float* eps,
+                        const AxisCoef* cx, const AxisCoef* cy, float k2, int nx, int ny,
+                        cudaStream_t s) {
+  jacobi_apply<<<krylov_grid((size_t)nx * ny), 256, 0, s>>>(v, vscale, z, eps, cx, cy, k2, nx,
+                                                             (size_t)nx * ny);
+  CKL();
+  return FDFD_OK;
+}
+
+int launch_residual64(const double2* x, const float2* J, double sb, int rhs_is_source,
+                      const float* eps, const AxisCoef64* cx, const AxisCoef64* cy, double k2,
+                      int nx, int ny, float2* r_out, double* partials, unsigned* counter,
+                      double* result, cudaStream_t s) {
+  residual64<<<krylov_grid((size_t)nx * ny), RT, 0, s>>>(x, J, sb, rhs_is_source, eps, cx, cy, k2,
+                                                          nx, ny, r_out, partials, counter, result);
+  CKL();
+  return FDFD_OK;
+}
+
+int launch_grad_eps(const float2* E, const float2* lam, float* grad, float k2, int n,
+                    int accumulate, cudaStream_t s) {
+  grad_eps_kernel<<<krylov_grid((size_t)n), 256, 0, s>>>(E, lam, grad, k2, (size_t)n, accumulate);
+  CKL();
+  return FDFD_OK;
+}

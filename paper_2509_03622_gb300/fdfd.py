@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libfdfd.so (include/fdfd.h).
+
+Argument marshalling only: every step of the solve runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (complex64 fields,
+float32 permittivity); the binding passes their data pointers.  Importing
+this module raises if the library has not been built -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfdfd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+
+lib = C.CDLL(LIB_PATH)
+
+OK, NOT_CONVERGED, STAGNATED = 0, 1, 2
+EINVAL, ECUDA, ENUMERIC, ETIMEOUT, ENOSETUP, ENOMEM = -1, -2, -3, -4, -5, -6
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_SCHWARZ = 0, 1, 2
+PREC_BF16, PREC_FP8 = 0, 1
+
+
+class Desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("wavelength", C.c_double),
+                ("npml", C.c_int * 4), ("pml_m", C.c_double), ("pml_lnR", C.c_double),
+                ("eps", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class SchwarzDesc(C.Structure):
+    _fields_ = [("k_coarse", C.c_int), ("precision", C.c_int), ("weights", C.c_void_p),
+                ("n_weights", C.c_size_t)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("restart", C.c_int), ("max_iters", C.c_int), ("tol", C.c_double),
+                ("precond", C.c_int), ("use_x0", C.c_int)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("status", C.c_int),
+                ("relres_true", C.c_double), ("relres_est", C.c_double), ("t_solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Info(C.Structure):
+    _fields_ = [("n_win", C.c_int), ("nwx", C.c_int), ("nwy", C.c_int), ("k_coarse", C.c_int),
+                ("n_coarse", C.c_int), ("workspace_bytes", C.c_size_t)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_longlong * 8), ("total_launches", C.c_longlong)]
+
+
+PROF_CLASSES = ["stencil", "cgs_dots", "cgs_update", "residual64", "vector_misc", "nno", "partition", "coarse"]
+
+_P = C.c_void_p
+_SIGS = {
+    "fdfd_create": ([C.POINTER(Desc), C.POINTER(_P)], C.c_int),
+    "fdfd_set_eps": ([_P, _P], C.c_int),
+    "schwarz_setup": ([_P, C.POINTER(SchwarzDesc)], C.c_int),
+    "fdfd_destroy": ([_P], None),
+    "fdfd_status_string": ([C.c_int], C.c_char_p),
+    "fdfd_get_info": ([_P, C.POINTER(Info)], C.c_int),
+    "fdfd_solve": ([_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveStats)], C.c_int),
+    "fdfd_solve_host": ([_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveStats)], C.c_int),
+    "fdfd_solve_adjoint": ([_P, _P, _P, C.POINTER(SolveOpts), C.POINTER(SolveStats)], C.c_int),
+    "fdfd_grad_eps": ([_P, _P, _P, _P, C.c_int], C.c_int),
+    "fdfd_apply_A": ([_P, _P, _P, C.c_int], C.c_int),
+    "fdfd_precond_apply": ([_P, _P, _P], C.c_int),
+    "fdfd_nno_solve": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
+    "fdfd_trace_extract": ([_P, _P, _P], C.c_int),
+    "fdfd_coarse_export": ([_P, _P, _P], C.c_int),
+    "fdfd_profile_start": ([_P], C.c_int),
+    "fdfd_profile_stop": ([_P, C.POINTER(Profile)], C.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class FDFDError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {lib.fdfd_status_string(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code, where):
+    if code < 0:
+        raise FDFDError(code, where)
+    return code
+
+
+def _ptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def status_string(code: int) -> str:
+    return lib.fdfd_status_string(code).decode()
+
+
+class Solver:
+    """Owns one fdfd_handle (fdfd_create ... fdfd_destroy)."""
+
+    def __init__(self, eps, dx: float, wavelength: float, npml=20, pml_m: float = 3.0,
+                 pml_lnR: float = -30.0, stream=None):
+        import torch
+        if eps.dtype != torch.float32 or eps.dim() != 2:
+            raise TypeError("eps must be a 2D float32 CUDA tensor")
+        ny, nx = eps.shape
+        d = Desc()
+        d.nx, d.ny, d.dx, d.wavelength = nx, ny, dx, wavelength
+        np_ = (npml,) * 4 if np.isscalar(npml) else tuple(npml)
+        d.npml = (C.c_int * 4)(*np_)
+        d.pml_m, d.pml_lnR = pml_m, pml_lnR
+        d.eps = _ptr(eps).value
+        s = stream if stream is not None else torch.cuda.current_stream()
+        d.stream = C.c_void_p(s.cuda_stream).value
+        self.stream = s
+        h = C.c_void_p()
+        _check(lib.fdfd_create(C.byref(d), C.byref(h)), "fdfd_create")
+        self.h = h
+        self.nx, self.ny = nx, ny
+        self.dx, self.wavelength = dx, wavelength
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.fdfd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = Info()
+        _check(lib.fdfd_get_info(self.h, C.byref(i)), "fdfd_get_info")
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def set_eps(self, eps):
+        _check(lib.fdfd_set_eps(self.h, _ptr(eps)), "fdfd_set_eps")
+
+    def schwarz_setup(self, weights_blob: np.ndarray, k_coarse: int = 0, precision: int = PREC_BF16):
+        blob = np.ascontiguousarray(weights_blob, dtype=np.float32)
+        sd = SchwarzDesc()
+        sd.k_coarse, sd.precision = k_coarse, precision
+        sd.weights = blob.ctypes.data
+        sd.n_weights = blob.size
+        _check(lib.schwarz_setup(self.h, C.byref(sd)), "schwarz_setup")
+
+    @staticmethod
+    def _opts(restart, max_iters, tol, precond, use_x0):
+        o = SolveOpts()
+        o.restart, o.max_iters, o.tol, o.precond, o.use_x0 = restart, max_iters, tol, precond, int(use_x0)
+        return o
+
+    def solve(self, J, E, restart=30, max_iters=1000, tol=1e-6, precond=PRECOND_SCHWARZ, use_x0=False):
+        st = SolveStats()
+        o = self._opts(restart, max_iters, tol, precond, use_x0)
+        rc = _check(lib.fdfd_solve(self.h, _ptr(J), _ptr(E), C.byref(o), C.byref(st)), "fdfd_solve")
+        return rc, st.as_dict()
+
+    def solve_host(self, J: np.ndarray, E: np.ndarray, restart=30, max_iters=1000, tol=1e-6,
+                   precond=PRECOND_SCHWARZ, use_x0=False):
+        assert J.dtype == np.complex64 and E.dtype == np.complex64 and J.flags.c_contiguous
+        st = SolveStats()
+        o = self._opts(restart, max_iters, tol, precond, use_x0)
+        rc = _check(lib.fdfd_solve_host(self.h, J.ctypes.data, E.ctypes.data, C.byref(o), C.byref(st)),
+                    "fdfd_solve_host")
+        return rc, st.as_dict()
+
+    def solve_adjoint(self, g, lam, restart=30, max_iters=1000, tol=1e-6, precond=PRECOND_SCHWARZ,
+                      use_x0=False):
+        st = SolveStats()
+        o = self._opts(restart, max_iters, tol, precond, use_x0)
+        rc = _check(lib.fdfd_solve_adjoint(self.h, _ptr(g), _ptr(lam), C.byref(o), C.byref(st)),
+                    "fdfd_solve_adjoint")
+        return rc, st.as_dict()
+
+    def grad_eps(self, E, lam, grad, accumulate=False):
+        _check(lib.fdfd_grad_eps(self.h, _ptr(E), _ptr(lam), _ptr(grad), int(accumulate)), "fdfd_grad_eps")
+
+    def apply_A(self, x, y, transpose=False):
+        _check(lib.fdfd_apply_A(self.h, _ptr(x), _ptr(y), int(transpose)), "fdfd_apply_A")
+
+    def precond_apply(self, v, z):
+        _check(lib.fdfd_precond_apply(self.h, _ptr(v), _ptr(z)), "fdfd_precond_apply")
+
+    def nno_solve(self, r_win, g_win, win_id, e_win):
+        n = r_win.shape[0]
+        _check(lib.fdfd_nno_solve(self.h, _ptr(r_win), _ptr(g_win), _ptr(win_id), n, _ptr(e_win)),
+               "fdfd_nno_solve")
+
+    def trace_extract(self, u, g):
+        _check(lib.fdfd_trace_extract(self.h, _ptr(u), _ptr(g)), "fdfd_trace_extract")
+
+    def profile_start(self):
+        _check(lib.fdfd_profile_start(self.h), "fdfd_profile_start")
+
+    def profile_stop(self) -> dict:
+        p = Profile()
+        _check(lib.fdfd_profile_stop(self.h, C.byref(p)), "fdfd_profile_stop")
+        return {"ms": {c: p.ms[i] for i, c in enumerate(PROF_CLASSES)},
+                "launches": {c: p.launches[i] for i, c in enumerate(PROF_CLASSES)},
+                "total_launches": p.total_launches}
+
+    def coarse_export(self):
+        inf = self.info()
+        nw, k = inf["n_win"], inf["k_coarse"]
+        Q = np.zeros((nw, k, 4, 80, 2), dtype=np.float64)
+        Nd = np.zeros((nw, k, k, 2), dtype=np.float64)
+        _check(lib.fdfd_coarse_export(self.h, Q.ctypes.data, Nd.ctypes.data), "fdfd_coarse_export")
+        return Q[..., 0] + 1j * Q[..., 1], Nd[..., 0] + 1j * Nd[..., 1]
