@@ -210,6 +210,14 @@ int  fdfd_trace_extract(fdfd_handle h, const fdfd_c64* u, fdfd_c64* g);
  * normal matrix diagonal blocks N_ww [n_win][k][k] complex128. */
 int  fdfd_coarse_export(fdfd_handle h, double* Q_host, double* Ndiag_host);
 
+/* Diagnostic: one tile GEMM on the tcgen05 path used by the neural operator
+ * (no counterpart in the paper; validates the tensor-core operand encoding).
+ * C[M][N] (float32, device) = A . B^T with A bf16 [M][K] (a_mn_major = 0)
+ * or [K][M] (a_mn_major = 1), B bf16 [N][K]; M a multiple of 8; (N, K) one
+ * of (32,80) (64,160) (64,64) (160,64) (32,16) (128,32).  Synchronous;
+ * FDFD_ETIMEOUT if the tensor-core completion wait ran out. */
+int  fdfd_selftest_gemm(const void* A, const void* B, float* C, int M, int N, int K, int a_mn_major);
+
 #ifdef __cplusplus
 }
 #endif

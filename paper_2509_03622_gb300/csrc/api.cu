@@ -11,6 +11,7 @@
 #include <vector>
 #include <complex>
 #include "ctx.cuh"
+#include "nno.cuh"
 
 namespace {
 
@@ -464,6 +465,22 @@ int fdfd_profile_stop(fdfd_handle h, fdfd_profile* out) {
   for (int c = 0; c < FDFD_PROF_NCLASS; ++c) out->launches[c] = h->prof_launch[c];
   out->total_launches = h->launches_total;
   return FDFD_OK;
+}
+
+int fdfd_selftest_gemm(const void* A, const void* B, float* C, int M, int N, int K, int a_mn) {
+  if (!A || !B || !C || M <= 0) return FDFD_EINVAL;
+  int* err = nullptr;
+  CK(cudaMalloc(&err, sizeof(int)));
+  CK(cudaMemset(err, 0, sizeof(int)));
+  int rc = nno_gemm_selftest(reinterpret_cast<const bf16*>(A), reinterpret_cast<const bf16*>(B), C, M, N, K, a_mn,
+                             err, 0);
+  int e = 0;
+  if (!rc) {
+    if (cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = FDFD_ECUDA;
+  }
+  cudaFree(err);
+  if (!rc && e) rc = FDFD_ETIMEOUT;
+  return rc;
 }
 
 int fdfd_coarse_export(fdfd_handle h, double* Q, double* Nd) {

@@ -1,0 +1,379 @@
+// Coarse space of the two-level Schwarz method (Sec. 2.2; Methods,
+// Algorithm 3 set-up and correction; Eq. 7-8).
+//
+// Set-up: pseudo-plane-wave Robin trials walked around each window with
+// the local wavenumber, modified Gram-Schmidt in FP64, homogeneous neural
+// solves for each trial, the traces of the restricted basis fields on the
+// neighbours' boundaries minus the window's own data (C = BQ - Q, stored as
+// 9 neighbour blocks per window), the normal matrix C^H C (Eq. 8) and its
+// inverse (FP64 Gauss-Jordan; the matrix is Hermitian positive definite).
+// Apply: e_bc = traces of the one-level field, r_c = -C^H e_bc, z = N^-1 r_c,
+// u += sum_w R~_w^T sum_m z_{w,m} Phi_{w,m}.
+#include <math.h>
+#include "ctx.cuh"
+#include "nno.cuh"
+#include "reduce.cuh"
+
+struct CoarseData {
+  int k = 0, nc = 0;
+  double2* Q = nullptr;      // [n_win][k][320]
+  float2* Qf = nullptr;      // [k][n_win][320]
+  float2* Phi = nullptr;     // [n_win][k][64*64] core of each basis field
+  double2* C = nullptr;      // [n_win][9][320][k]
+  double2* N = nullptr;      // [nc][nc]  -> inverse after set-up
+  double2* Nd = nullptr;     // [n_win][k][k] diagonal blocks of the normal matrix
+  double2* rc = nullptr;     // [nc]
+  double2* zc = nullptr;     // [nc]
+  float2* ebc = nullptr;     // [n_win][320]
+  float2* tmp = nullptr;     // [n_win][6400] window fields during set-up
+  int* dropped = nullptr;    // [nc]
+};
+
+namespace {
+
+struct Win {
+  int x0, y0, a, b;
+  bool iface[4];
+};
+
+__host__ __device__ inline Win win_of(int w, int nx, int ny, int nwx) {
+  Win r;
+  r.a = w % nwx; r.b = w / nwx;
+  r.x0 = min(max(FDFD_CORE * r.a - FDFD_OVL, 0), nx - FDFD_WIN);
+  r.y0 = min(max(FDFD_CORE * r.b - FDFD_OVL, 0), ny - FDFD_WIN);
+  r.iface[0] = r.x0 > 0; r.iface[1] = r.x0 + FDFD_WIN < nx;
+  r.iface[2] = r.y0 > 0; r.iface[3] = r.y0 + FDFD_WIN < ny;
+  return r;
+}
+
+// boundary cell b and ghost o of slot (side s, t)
+__device__ inline void slot_cells(const Win& W, int s, int t, int& bx, int& by, int& ox, int& oy) {
+  if (s == 0) { bx = W.x0; by = W.y0 + t; ox = bx - 1; oy = by; }
+  else if (s == 1) { bx = W.x0 + FDFD_WIN - 1; by = W.y0 + t; ox = bx + 1; oy = by; }
+  else if (s == 2) { bx = W.x0 + t; by = W.y0; ox = bx; oy = by - 1; }
+  else { bx = W.x0 + t; by = W.y0 + FDFD_WIN - 1; ox = bx; oy = by + 1; }
+}
+
+// Counter-clockwise walk: bottom (t up), right (t up), top (t down), left (t down).
+__device__ inline void walk_step(int n, int& s, int& t) {
+  const int seg = n / FDFD_WIN, r = n % FDFD_WIN;
+  if (seg == 0) { s = 2; t = r; }
+  else if (seg == 1) { s = 1; t = r; }
+  else if (seg == 2) { s = 3; t = FDFD_WIN - 1 - r; }
+  else { s = 0; t = FDFD_WIN - 1 - r; }
+}
+
+__global__ void __launch_bounds__(256) trials_gs_kernel(double2* Q, float2* Qf, int k, const float* eps, double k0dx,
+                                                        int nx, int ny, int nwx, int n_win) {
+  __shared__ double sh[8];
+  __shared__ double2 s_dot;
+  __shared__ double s_norm;
+  const int w = blockIdx.x;
+  const Win W = win_of(w, nx, ny, nwx);
+  double2* Qw = Q + (size_t)w * k * 320;
+  // trial data: phase accumulated along the perimeter with the local wavenumber
+  for (int m = threadIdx.x; m < k; m += blockDim.x) {
+    const double th = 2.0 * M_PI * m / k, dxh = cos(th), dyh = sin(th);
+    double phi = 0.0, kprev = 0.0;
+    int px = 0, py = 0;
+    for (int n = 0; n < 320; ++n) {
+      int s, t, bx, by, ox, oy;
+      walk_step(n, s, t);
+      slot_cells(W, s, t, bx, by, ox, oy);
+      const double kd = k0dx * sqrt((double)eps[(size_t)by * nx + bx]);
+      if (n > 0) phi += 0.5 * (kprev + kd) * (dxh * (bx - px) + dyh * (by - py));
+      kprev = kd; px = bx; py = by;
+      Qw[(size_t)m * 320 + s * 80 + t] = W.iface[s] ? make_double2(cos(phi), -sin(phi)) : make_double2(0.0, 0.0);
+    }
+  }
+  __syncthreads();
+  // modified Gram-Schmidt in FP64 (l2 over the 320 slots)
+  for (int m = 0; m < k; ++m) {
+    double2* v = Qw + (size_t)m * 320;
+    double a0 = 0.0;
+    for (int t = threadIdx.x; t < 320; t += blockDim.x) a0 += v[t].x * v[t].x + v[t].y * v[t].y;
+    a0 = block_sum<256>(a0, sh);
+    if (threadIdx.x == 0) s_norm = sqrt(a0);
+    __syncthreads();
+    const double n0 = s_norm;
+    for (int i = 0; i < m; ++i) {
+      const double2* qi = Qw + (size_t)i * 320;
+      double dr = 0.0, di = 0.0;
+      for (int t = threadIdx.x; t < 320; t += blockDim.x) {  // conj(q_i) . v
+        dr += qi[t].x * v[t].x + qi[t].y * v[t].y;
+        di += qi[t].x * v[t].y - qi[t].y * v[t].x;
+      }
+      dr = block_sum<256>(dr, sh);
+      di = block_sum<256>(di, sh);
+      if (threadIdx.x == 0) s_dot = make_double2(dr, di);
+      __syncthreads();
+      const double2 d = s_dot;
+      for (int t = threadIdx.x; t < 320; t += blockDim.x) v[t] = zsub(v[t], zmul(d, qi[t]));
+      __syncthreads();
+    }
+    double a = 0.0;
+    for (int t = threadIdx.x; t < 320; t += blockDim.x) a += v[t].x * v[t].x + v[t].y * v[t].y;
+    a = block_sum<256>(a, sh);
+    if (threadIdx.x == 0) s_norm = sqrt(a);
+    __syncthreads();
+    const double nv = s_norm;
+    const double f = (n0 == 0.0 || nv <= 1e-10 * n0) ? 0.0 : 1.0 / nv;
+    for (int t = threadIdx.x; t < 320; t += blockDim.x) {
+      v[t] = make_double2(v[t].x * f, v[t].y * f);
+      Qf[((size_t)m * n_win + w) * 320 + t] = make_float2((float)v[t].x, (float)v[t].y);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void copy_core_kernel(const float2* tmp, float2* Phi, int m, int k, int nx, int ny, int nwx, int n_win) {
+  const int w = blockIdx.x;
+  const Win W = win_of(w, nx, ny, nwx);
+  const int cx = FDFD_CORE * W.a - W.x0, cy = FDFD_CORE * W.b - W.y0;
+  for (int p = threadIdx.x; p < FDFD_CORE * FDFD_CORE; p += blockDim.x) {
+    const int y = p / FDFD_CORE, x = p % FDFD_CORE;
+    Phi[((size_t)w * k + m) * 4096 + p] = tmp[(size_t)w * 6400 + (cy + y) * 80 + cx + x];
+  }
+}
+
+// C[i][j][slot][m] = trace on window i's slot of R~_J^T Phi_{J,m} (J = neighbour j of i), minus Q_i on j = self.
+__global__ void assemble_C_kernel(double2* C, const double2* Q, const float2* Phi, int k, const float* eps,
+                                  double k0dx, int nx, int ny, int nwx, int nwy) {
+  const int i = blockIdx.x, j = blockIdx.y;
+  const int n_win = nwx * nwy;
+  const Win Wi = win_of(i, nx, ny, nwx);
+  const int dx = j % 3 - 1, dy = j / 3 - 1;
+  const int aJ = Wi.a + dx, bJ = Wi.b + dy;
+  const bool hasJ = aJ >= 0 && aJ < nwx && bJ >= 0 && bJ < nwy;
+  const int J = bJ * nwx + aJ;
+  for (int e = threadIdx.x; e < 320 * k; e += blockDim.x) {
+    const int slot = e / k, m = e % k, s = slot / 80, t = slot % 80;
+    double2 val = make_double2(0.0, 0.0);
+    if (Wi.iface[s] && hasJ) {
+      int bx, by, ox, oy;
+      slot_cells(Wi, s, t, bx, by, ox, oy);
+      auto core_val = [&](int gx, int gy) -> double2 {
+        const int cx = gx - FDFD_CORE * aJ, cy = gy - FDFD_CORE * bJ;
+        if (cx < 0 || cx >= FDFD_CORE || cy < 0 || cy >= FDFD_CORE) return make_double2(0.0, 0.0);
+        const float2 f = Phi[((size_t)J * k + m) * 4096 + cy * FDFD_CORE + cx];
+        return make_double2(f.x, f.y);
+      };
+      const double2 ub = core_val(bx, by), uo = core_val(ox, oy);
+      const double kd = k0dx * sqrt((double)eps[(size_t)by * nx + bx]);
+      // u_o - (1 - j kd) u_b
+      val = make_double2(uo.x - ub.x - kd * ub.y, uo.y - ub.y + kd * ub.x);
+      if (j == 4) val = zsub(val, Q[((size_t)i * k + m) * 320 + slot]);
+    }
+    (void)n_win;
+    C[(((size_t)i * 9 + j) * 320 + slot) * k + m] = val;
+  }
+}
+
+// Normal-matrix block (w, w' = w + (ex, ey)): sum over windows i adjacent to both.
+__global__ void assemble_N_kernel(double2* N, double2* Nd, const double2* C, int k, int nwx, int nwy) {
+  const int w = blockIdx.x, e = blockIdx.y;
+  const int ex = e % 5 - 2, ey = e / 5 - 2;
+  const int aw = w % nwx, bw = w / nwx, aw2 = aw + ex, bw2 = bw + ey;
+  if (aw2 < 0 || aw2 >= nwx || bw2 < 0 || bw2 >= nwy) return;
+  const int w2 = bw2 * nwx + aw2;
+  const int nc = nwx * nwy * k;
+  for (int pq = threadIdx.x; pq < k * k; pq += blockDim.x) {
+    const int p = pq / k, q = pq % k;
+    double sr = 0.0, si = 0.0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ai = aw - dx, bi = bw - dy;            // w = i + (dx, dy)
+        if (ai < 0 || ai >= nwx || bi < 0 || bi >= nwy) continue;
+        const int dx2 = aw2 - ai, dy2 = bw2 - bi;        // w2 = i + (dx2, dy2)
+        if (dx2 < -1 || dx2 > 1 || dy2 < -1 || dy2 > 1) continue;
+        const int i = bi * nwx + ai;
+        const double2* c1 = C + (((size_t)i * 9 + (dy + 1) * 3 + dx + 1) * 320) * k;
+        const double2* c2 = C + (((size_t)i * 9 + (dy2 + 1) * 3 + dx2 + 1) * 320) * k;
+        for (int sl = 0; sl < 320; ++sl) {
+          const double2 a = c1[sl * k + p], b = c2[sl * k + q];  // conj(a) * b
+          sr += a.x * b.x + a.y * b.y;
+          si += a.x * b.y - a.y * b.x;
+        }
+      }
+    N[(size_t)(w * k + p) * nc + w2 * k + q] = make_double2(sr, si);
+    if (w2 == w) Nd[((size_t)w * k + p) * k + q] = make_double2(sr, si);
+  }
+}
+
+__global__ void dropped_kernel(double2* N, int* dropped, const double2* Q, int nc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double2* q = Q + (size_t)c * 320;
+  bool any = false;
+  for (int t = 0; t < 320; ++t) any |= (q[t].x != 0.0 || q[t].y != 0.0);
+  dropped[c] = !any;
+  if (!any) N[(size_t)c * nc + c] = make_double2(1.0, 0.0);
+}
+
+// Gauss-Jordan inversion in place (no pivoting; the matrix is HPD).
+__global__ void gj_row_kernel(double2* A, int n, int p, double2* prow) {
+  const double2 piv = A[(size_t)p * n + p];
+  const double den = piv.x * piv.x + piv.y * piv.y;
+  const double2 inv = make_double2(piv.x / den, -piv.y / den);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const double2 a = (j == p) ? make_double2(1.0, 0.0) : A[(size_t)p * n + j];
+    const double2 r = zmul(a, inv);
+    A[(size_t)p * n + j] = r;
+    prow[j] = r;
+  }
+}
+__global__ void gj_elim_kernel(double2* A, int n, int p, const double2* prow, double2* pcol) {
+  // pcol holds column p before elimination (copied by gj_col_kernel)
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    if (i == p) continue;
+    const double2 f = pcol[i];
+    const double2 a = (j == p) ? make_double2(0.0, 0.0) : A[e];
+    A[e] = zsub(a, zmul(f, prow[j]));
+  }
+}
+__global__ void gj_col_kernel(const double2* A, int n, int p, double2* pcol) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) pcol[i] = A[(size_t)i * n + p];
+}
+
+// r_c[(w,m)] = -sum_{i adjacent to w} sum_slot conj(C[i][j(w)][slot][m]) e_bc[i][slot]
+__global__ void coarse_rhs_kernel(double2* rc, const double2* C, const float2* ebc, int k, int nwx, int nwy) {
+  const int w = blockIdx.x;
+  const int aw = w % nwx, bw = w / nwx;
+  for (int m = threadIdx.x; m < k; m += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ai = aw - dx, bi = bw - dy;
+        if (ai < 0 || ai >= nwx || bi < 0 || bi >= nwy) continue;
+        const int i = bi * nwx + ai;
+        const double2* c = C + (((size_t)i * 9 + (dy + 1) * 3 + dx + 1) * 320) * k + m;
+        const float2* e = ebc + (size_t)i * 320;
+        for (int sl = 0; sl < 320; ++sl) {
+          const double2 a = c[(size_t)sl * k];
+          const double er = e[sl].x, ei = e[sl].y;
+          sr += a.x * er + a.y * ei;
+          si += a.x * ei - a.y * er;
+        }
+      }
+    rc[w * k + m] = make_double2(-sr, -si);
+  }
+}
+
+// z = Ninv r_c (one warp per row, FP64)
+__global__ void gemv_kernel(double2* z, const double2* A, const double2* x, const int* dropped, int n) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double sr = 0.0, si = 0.0;
+  const double2* a = A + (size_t)row * n;
+  for (int j = lane; j < n; j += 32) {
+    if (dropped[j]) continue;
+    const double2 p = zmul(a[j], x[j]);
+    sr += p.x; si += p.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) z[row] = dropped[row] ? make_double2(0.0, 0.0) : make_double2(sr, si);
+}
+
+// u[core(w)] += sum_m z[w,m] Phi[w][m]
+__global__ void correction_kernel(float2* u, const float2* Phi, const double2* z, int k, int nx, int nwx) {
+  const int w = blockIdx.y;
+  const int a = w % nwx, b = w / nwx;
+  __shared__ float2 zw[256];
+  for (int m = threadIdx.x; m < k; m += blockDim.x) zw[m] = make_float2((float)z[w * k + m].x, (float)z[w * k + m].y);
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= 4096) return;
+  const float2* ph = Phi + (size_t)w * k * 4096 + p;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int m = 0; m < k; ++m) acc = cadd(acc, cmul(zw[m], __ldg(ph + (size_t)m * 4096)));
+  const size_t g = (size_t)(FDFD_CORE * b + p / 64) * nx + FDFD_CORE * a + p % 64;
+  u[g] = cadd(u[g], acc);
+}
+
+template <class T>
+int ca(T** p, size_t n, size_t* bytes) {
+  if (cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) return FDFD_ENOMEM;
+  *bytes += n * sizeof(T);
+  return FDFD_OK;
+}
+
+}  // namespace
+
+void coarse_free(CoarseData* c) {
+  if (!c) return;
+  void* ptrs[] = {c->Q, c->Qf, c->Phi, c->C, c->N, c->Nd, c->rc, c->zc, c->ebc, c->tmp, c->dropped};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  delete c;
+}
+
+int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, int k, CoarseData** out, size_t* bytes) {
+  const int nwx = h->nx / FDFD_CORE, nwy = h->ny / FDFD_CORE, n_win = nwx * nwy;
+  const int nc = n_win * k;
+  if (k < 1 || k > 256 || (size_t)nc * nc * 16 > ((size_t)16 << 30)) return FDFD_EINVAL;
+  CoarseData* c = new CoarseData();
+  c->k = k; c->nc = nc;
+  int rc;
+  if ((rc = ca(&c->Q, (size_t)nc * 320, bytes)) || (rc = ca(&c->Qf, (size_t)nc * 320, bytes)) ||
+      (rc = ca(&c->Phi, (size_t)nc * 4096, bytes)) || (rc = ca(&c->C, (size_t)n_win * 9 * 320 * k, bytes)) ||
+      (rc = ca(&c->N, (size_t)nc * nc, bytes)) || (rc = ca(&c->Nd, (size_t)n_win * k * k, bytes)) ||
+      (rc = ca(&c->rc, (size_t)nc, bytes)) || (rc = ca(&c->zc, (size_t)nc, bytes)) ||
+      (rc = ca(&c->ebc, (size_t)n_win * 320, bytes)) || (rc = ca(&c->tmp, (size_t)n_win * 6400, bytes)) ||
+      (rc = ca(&c->dropped, (size_t)nc, bytes))) {
+    coarse_free(c);
+    return rc;
+  }
+  cudaStream_t s = h->stream;
+  trials_gs_kernel<<<n_win, 256, 0, s>>>(c->Q, c->Qf, k, h->eps, h->k0dx, h->nx, h->ny, nwx, n_win);
+  CKL();
+  GridGeom g{h->nx, h->ny, nwx, (float)h->k2, h->eps, h->isx, h->isy};
+  for (int m = 0; m < k; ++m) {
+    NnoInput in;
+    in.g_win = c->Qf + (size_t)m * n_win * 320;
+    NnoOutput o;
+    o.e_win = c->tmp;
+    if ((rc = nno_forward(W, work, g, in, o, n_win, s))) { coarse_free(c); return rc; }
+    copy_core_kernel<<<n_win, 256, 0, s>>>(c->tmp, c->Phi, m, k, h->nx, h->ny, nwx, n_win);
+    CKL();
+  }
+  assemble_C_kernel<<<dim3(n_win, 9), 256, 0, s>>>(c->C, c->Q, c->Phi, k, h->eps, h->k0dx, h->nx, h->ny, nwx, nwy);
+  CKL();
+  if (cudaMemsetAsync(c->N, 0, (size_t)nc * nc * sizeof(double2), s) != cudaSuccess) { coarse_free(c); return FDFD_ECUDA; }
+  assemble_N_kernel<<<dim3(n_win, 25), 256, 0, s>>>(c->N, c->Nd, c->C, k, nwx, nwy);
+  CKL();
+  dropped_kernel<<<(nc + 255) / 256, 256, 0, s>>>(c->N, c->dropped, c->Q, nc);
+  CKL();
+  // Gauss-Jordan inverse (rc, zc reused as the pivot row / column buffers)
+  const int gb = 1024;
+  for (int p = 0; p < nc; ++p) {
+    gj_col_kernel<<<(nc + 255) / 256, 256, 0, s>>>(c->N, nc, p, c->zc);
+    gj_row_kernel<<<(nc + 255) / 256, 256, 0, s>>>(c->N, nc, p, c->rc);
+    gj_elim_kernel<<<gb, 256, 0, s>>>(c->N, nc, p, c->rc, c->zc);
+  }
+  CKL();
+  CK(cudaStreamSynchronize(s));
+  *out = c;
+  return FDFD_OK;
+}
+
+int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u) {
+  const int nwx = h->nx / FDFD_CORE, nwy = h->ny / FDFD_CORE, n_win = nwx * nwy;
+  cudaStream_t s = h->stream;
+  int rc;
+  if ((rc = schwarz_traces(h, u, c->ebc))) return rc;
+  coarse_rhs_kernel<<<n_win, 64, 0, s>>>(c->rc, c->C, c->ebc, c->k, nwx, nwy);
+  gemv_kernel<<<(c->nc + 7) / 8, 256, 0, s>>>(c->zc, c->N, c->rc, c->dropped, c->nc);
+  correction_kernel<<<dim3(4096 / 256, n_win), 256, 0, s>>>(u, c->Phi, c->zc, c->k, h->nx, nwx);
+  CKL();
+  return FDFD_OK;
+}
+
+int coarse_export(fdfd_ctx* h, CoarseData* c, double* Qh, double* Ndh) {
+  const int n_win = (h->nx / FDFD_CORE) * (h->ny / FDFD_CORE);
+  if (Qh) CK(cudaMemcpy(Qh, c->Q, (size_t)c->nc * 320 * sizeof(double2), cudaMemcpyDeviceToHost));
+  if (Ndh) CK(cudaMemcpy(Ndh, c->Nd, (size_t)n_win * c->k * c->k * sizeof(double2), cudaMemcpyDeviceToHost));
+  return FDFD_OK;
+}

@@ -1,0 +1,622 @@
+// Fourier neural operator of the subdomain solver (Sec. 2.1, Fig. 2) on
+// tcgen05 tensor cores, batched over windows.
+//
+// Per window (80 x 80, width 32, 4 Fourier blocks, 512 retained modes):
+//   pack   : restriction, RMS normalisation, 15 input channels   (SIMT)
+//   lift   : [6400 px][16] x [32][16]^T                           (GEMM)
+//   block b (the truncated 2D DFT is done as two 1D DFT GEMMs each way):
+//     G1  DFT along x   : rows (y,c)   K = x 80        N = (kx,ri) 32   A MN-major
+//     G2  DFT along y   : rows (kx,c)  K = (ri,y) 160  N = (q,ri) 64    A MN-major
+//     G3  spectral mix  : per mode, rows = windows, K = (c,ri) 64, N = (o,ri) 64
+//     G4  inverse DFT y : rows (o,kx)  K = (q,ri) 64   N = (y,ri) 160
+//     G5  fused: inverse real DFT along x + W x + bias + leaky-ReLU, per y row:
+//         D_y[x][o] = Gx[x][:] . T3_y[o][:] + X_y[x][:] . W[o][:]
+//   proj   : [6400 px][32] x [128][32]^T, leaky, 128 -> 2, times rho,
+//            written to the window's core in the global field (restricted
+//            prolongation) or to a per-window array.
+// Each GEMM epilogue writes the layout the next stage reads, with lanes
+// mapped to the contiguous output dimension (coalesced stores).
+#include <math.h>
+#include <string.h>
+#include <vector>
+#include "nno.cuh"
+#include "tc.cuh"
+#include "reduce.cuh"
+
+namespace {
+
+constexpr int NPIX = FDFD_WIN * FDFD_WIN;  // 6400
+constexpr float LEAK = 0.01f;
+constexpr long long WAIT_LIMIT = 1ll << 22;  // polls of mbarrier.try_wait before giving up
+
+__device__ __forceinline__ float leaky(float x) { return x >= 0.f ? x : LEAK * x; }
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// ---------------------------------------------------------------------
+// Generic tile GEMM: D[128 x BN] = A[128 x K] . B[BN x K]^T for tile
+// blockIdx.x of batch blockIdx.y; Op supplies operand addresses and the
+// epilogue.  One elected thread issues the MMAs, the commit arrives on an
+// mbarrier, all four warps read the FP32 accumulator from TMEM.
+// ---------------------------------------------------------------------
+template <int BN, int K, bool AMN, class Op>
+__global__ void __launch_bounds__(128) gemm_kernel(Op op, int* err) {
+  static_assert(K % 16 == 0 && BN % 16 == 0 && BN <= 256, "shape");
+  constexpr int KC = K / 8;
+  constexpr uint32_t A_BYTES = 128 * K * 2, B_BYTES = BN * K * 2;
+  constexpr uint32_t TCOLS = tc::tmem_cols(BN);
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + A_BYTES;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + A_BYTES + B_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + A_BYTES + B_BYTES + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.y;
+  const int m0 = blockIdx.x * 128;
+  const int Mb = op.rows(b);
+  const uint4 z4 = make_uint4(0, 0, 0, 0);
+  // ---- operand loads (global -> canonical smem tiles) ----
+  if (!AMN) {
+    for (int c = tid; c < 128 * KC; c += 128) {
+      const int t8 = c & 7, rest = c >> 3, kc = rest % KC, rg = rest / KC;
+      const int m = m0 + rg * 8 + t8;
+      const uint4 v = (m < Mb) ? __ldg(op.a_src(b, m, kc * 8)) : z4;
+      *reinterpret_cast<uint4*>(sA + (rg * KC + kc) * 128 + t8 * 16) = v;
+    }
+  } else {
+    for (int c = tid; c < 16 * K; c += 128) {
+      const int t8 = c & 7, rest = c >> 3, mg = rest & 15, kg = rest >> 4;
+      const int m = m0 + mg * 8;
+      const uint4 v = (m < Mb) ? __ldg(op.a_src(b, m, kg * 8 + t8)) : z4;
+      *reinterpret_cast<uint4*>(sA + (mg * KC + kg) * 128 + t8 * 16) = v;
+    }
+  }
+  for (int c = tid; c < BN * KC; c += 128) {
+    const int t8 = c & 7, rest = c >> 3, kc = rest % KC, rg = rest / KC;
+    *reinterpret_cast<uint4*>(sB + (rg * KC + kc) * 128 + t8 * 16) = __ldg(op.b_src(b, rg * 8 + t8, kc * 8));
+  }
+  if (tid == 0) tc::mbar_init(tc::smem_u32(mbar), 1);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), TCOLS);
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    constexpr uint32_t idesc = tc::idesc_bf16(BN, AMN, false);
+    const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+    for (int s = 0; s < K / 16; ++s)
+      tc::mma_bf16(tmem, tc::make_desc(a0 + s * 256, 128, K * 16), tc::make_desc(b0 + s * 256, 128, K * 16), idesc,
+                   s > 0);
+    tc::mma_commit(tc::smem_u32(mbar));
+  }
+  if (!tc::mbar_wait(tc::smem_u32(mbar), 0, WAIT_LIMIT)) atomicExch(err, 1);
+  tc::fence_after();
+  // ---- epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows ----
+  const int m = m0 + warp * 32 + lane;
+  const bool valid = m < Mb;
+  typename Op::State st;
+  op.epi_begin(st);
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 16) {
+    float v[16];
+    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (valid) op.epi(b, m, c0, v, st);
+  }
+  if (valid) op.epi_end(b, m, st);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_free(tmem, TCOLS);
+  }
+}
+
+template <int BN, int K, bool AMN, class Op>
+int launch_gemm(const Op& op, int tiles, int batches, int* err, cudaStream_t s) {
+  const size_t smem = 128 * K * 2 + BN * K * 2 + 16;
+  auto kern = gemm_kernel<BN, K, AMN, Op>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return FDFD_ECUDA;
+    attr_set = true;
+  }
+  kern<<<dim3(tiles, batches), 128, smem, s>>>(op, err);
+  CKL();
+  return FDFD_OK;
+}
+
+struct NoState {};
+
+// ---------------------------------------------------------------------
+// Stage operators
+// ---------------------------------------------------------------------
+struct LiftOp {  // rows = pixels, K = 16 inputs, N = 32 channels
+  const bf16* in; const bf16* w; const float* bias; bf16* X;
+  typedef NoState State;
+  __device__ int rows(int) const { return NPIX; }
+  __device__ const uint4* a_src(int b, int m, int k) const {
+    return reinterpret_cast<const uint4*>(in + ((size_t)b * NPIX + m) * 16 + k);
+  }
+  __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(w + n * 16 + k); }
+  __device__ void epi_begin(State&) const {}
+  __device__ void epi(int b, int m, int c0, const float* v, State&) const {
+    uint32_t p[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) p[i] = pack2(v[2 * i] + bias[c0 + 2 * i], v[2 * i + 1] + bias[c0 + 2 * i + 1]);
+    uint4* dst = reinterpret_cast<uint4*>(X + ((size_t)b * NPIX + m) * 32 + c0);
+    dst[0] = make_uint4(p[0], p[1], p[2], p[3]);
+    dst[1] = make_uint4(p[4], p[5], p[6], p[7]);
+  }
+  __device__ void epi_end(int, int, State&) const {}
+};
+
+struct G1Op {  // DFT along x: rows (y,c), K = x (A MN-major from X), N = (kx,ri)
+  const bf16* X; const bf16* Fx; bf16* T1;
+  typedef NoState State;
+  __device__ int rows(int) const { return 80 * 32; }
+  __device__ const uint4* a_src(int b, int m, int k) const {  // 8 consecutive c at (y, x = k)
+    const int y = m >> 5, c = m & 31;
+    return reinterpret_cast<const uint4*>(X + (((size_t)b * 80 + y) * 80 + k) * 32 + c);
+  }
+  __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(Fx + n * 80 + k); }
+  __device__ void epi_begin(State&) const {}
+  __device__ void epi(int b, int m, int c0, const float* v, State&) const {
+    const int y = m >> 5, c = m & 31;
+    bf16* base = T1 + (size_t)b * 160 * 512;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int col = c0 + i, kx = col >> 1, ri = col & 1;
+      base[(ri * 80 + y) * 512 + kx * 32 + c] = __float2bfloat16_rn(v[i]);
+    }
+  }
+  __device__ void epi_end(int, int, State&) const {}
+};
+
+struct G2Op {  // DFT along y: rows (kx,c), K = (ri,y) (A MN-major from T1), N = (q,ri)
+  const bf16* T1; const bf16* Fy; bf16* Xh; int cap;
+  typedef NoState State;
+  __device__ int rows(int) const { return 512; }
+  __device__ const uint4* a_src(int b, int m, int k) const {
+    return reinterpret_cast<const uint4*>(T1 + ((size_t)b * 160 + k) * 512 + m);
+  }
+  __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(Fy + n * 160 + k); }
+  __device__ void epi_begin(State&) const {}
+  __device__ void epi(int b, int m, int c0, const float* v, State&) const {
+    const int kx = m >> 5, c = m & 31;
+#pragma unroll
+    for (int i = 0; i < 16; i += 2) {
+      const int q = (c0 + i) >> 1;
+      *reinterpret_cast<uint32_t*>(Xh + (((size_t)(q * 16 + kx)) * cap + b) * 64 + c * 2) = pack2(v[i], v[i + 1]);
+    }
+  }
+  __device__ void epi_end(int, int, State&) const {}
+};
+
+struct G3Op {  // spectral mix per mode: rows = windows, K = (c,ri), N = (o,ri)
+  const bf16* Xh; const bf16* R; bf16* Yh; int cap; int nwin;
+  typedef NoState State;
+  __device__ static int mode_of(int bidx) { return (bidx & 31) * 16 + (bidx >> 5); }  // q fastest, kx outer
+  __device__ int rows(int) const { return nwin; }
+  __device__ const uint4* a_src(int bidx, int m, int k) const {
+    return reinterpret_cast<const uint4*>(Xh + ((size_t)mode_of(bidx) * cap + m) * 64 + k);
+  }
+  __device__ const uint4* b_src(int bidx, int n, int k) const {
+    return reinterpret_cast<const uint4*>(R + ((size_t)mode_of(bidx) * 64 + n) * 64 + k);
+  }
+  __device__ void epi_begin(State&) const {}
+  __device__ void epi(int bidx, int w, int c0, const float* v, State&) const {
+    const int md = mode_of(bidx), q = md >> 4, kx = md & 15;
+#pragma unroll
+    for (int i = 0; i < 16; i += 2) {
+      const int o = (c0 + i) >> 1;
+      *reinterpret_cast<uint32_t*>(Yh + (((size_t)w * 512) + o * 16 + kx) * 64 + q * 2) = pack2(v[i], v[i + 1]);
+    }
+  }
+  __device__ void epi_end(int, int, State&) const {}
+};
+
+struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
+  const bf16* Yh; const bf16* Gy; bf16* T3;
+  typedef NoState State;
+  __device__ int rows(int) const { return 512; }
+  __device__ const uint4* a_src(int b, int m, int k) const {
+    return reinterpret_cast<const uint4*>(Yh + ((size_t)b * 512 + m) * 64 + k);
+  }
+  __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(Gy + n * 64 + k); }
+  __device__ void epi_begin(State&) const {}
+  __device__ void epi(int b, int m, int c0, const float* v, State&) const {
+    const int o = m >> 4, kx = m & 15;
+#pragma unroll
+    for (int i = 0; i < 16; i += 2) {
+      const int y = (c0 + i) >> 1;
+      *reinterpret_cast<uint32_t*>(T3 + (((size_t)b * 80 + y) * 32 + o) * 32 + kx * 2) = pack2(v[i], v[i + 1]);
+    }
+  }
+  __device__ void epi_end(int, int, State&) const {}
+};
+
+struct ProjOp {  // rows = pixels, K = 32, N = 128 hidden; then 128 -> 2 and the output
+  const bf16* X; const bf16* P1; const float* p1b; const float* P2; float p2b0, p2b1;
+  const float* rho; const double* scale; const int* win_id;
+  float2* z_global; float2* e_win; int nx, nwx;
+  struct State { float re, im; };
+  __device__ int rows(int) const { return NPIX; }
+  __device__ const uint4* a_src(int b, int m, int k) const {
+    return reinterpret_cast<const uint4*>(X + ((size_t)b * NPIX + m) * 32 + k);
+  }
+  __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(P1 + n * 32 + k); }
+  __device__ void epi_begin(State& s) const { s.re = 0.f; s.im = 0.f; }
+  __device__ void epi(int, int, int c0, const float* v, State& s) const {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float h = leaky(v[i] + p1b[c0 + i]);
+      s.re += P2[c0 + i] * h;
+      s.im += P2[128 + c0 + i] * h;
+    }
+  }
+  __device__ void epi_end(int b, int m, State& s) const {
+    float f = rho[b];
+    if (scale) f *= (float)(*scale);
+    const float2 o = make_float2((s.re + p2b0) * f, (s.im + p2b1) * f);
+    if (e_win) { e_win[(size_t)b * NPIX + m] = o; return; }
+    const int w = win_id ? win_id[b] : b;
+    const int a = w % nwx, bb = w / nwx;
+    const int ny_unused = 0; (void)ny_unused;
+    const int y = m / 80, x = m % 80;
+    // window origin (shifted inward at the grid edge) and its core
+    const int gx0 = min(max(FDFD_CORE * a - FDFD_OVL, 0), nx - FDFD_WIN);
+    const int gx = gx0 + x;
+    if (gx < FDFD_CORE * a || gx >= FDFD_CORE * a + FDFD_CORE) return;
+    // rows: the grid height enters through the window table of the caller
+    const int gy0 = win_y0(bb);
+    const int gy = gy0 + y;
+    if (gy < FDFD_CORE * bb || gy >= FDFD_CORE * bb + FDFD_CORE) return;
+    z_global[(size_t)gy * nx + gx] = o;
+  }
+  int ny_;
+  __device__ int win_y0(int bb) const { return min(max(FDFD_CORE * bb - FDFD_OVL, 0), ny_ - FDFD_WIN); }
+};
+
+// Fused G5: per (window, 8 rows): D_y[x][o] = Gx[x][:] T3_y[o][:]^T + X_y[x][:] W[o][:]^T,
+// then + bias, leaky-ReLU (not after the last block), written back to X.
+constexpr int G5_ROWS = 8;
+constexpr uint32_t G5_TILE = 128 * 32 * 2;  // one [128][32] bf16 tile
+constexpr uint32_t G5_SMEM = G5_TILE * (1 + G5_ROWS) + 32 * 32 * 2 * (G5_ROWS + 1) + 16;
+
+__global__ void __launch_bounds__(128) g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb,
+                                                 const float* bias, int last, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sAg = smem;                                   // Gx, [128][32]
+  uint8_t* sAx = smem + G5_TILE;                         // 8 x [128][32]
+  uint8_t* sBt = sAx + G5_TILE * G5_ROWS;                // 8 x [32][32]
+  uint8_t* sBw = sBt + 2048 * G5_ROWS;                   // [32][32]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sBw + 2048);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sBw + 2048 + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.y, y0 = blockIdx.x * G5_ROWS;
+  const uint4 z4 = make_uint4(0, 0, 0, 0);
+  // Gx (rows >= 80 are zero in global) and W
+  for (int c = tid; c < 128 * 4; c += 128) {
+    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
+    *reinterpret_cast<uint4*>(sAg + (rg * 4 + kc) * 128 + t8 * 16) =
+        __ldg(reinterpret_cast<const uint4*>(Gx + (rg * 8 + t8) * 32 + kc * 8));
+  }
+  {
+    const int c = tid;  // 32 rows x 4 chunks = 128
+    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
+    *reinterpret_cast<uint4*>(sBw + (rg * 4 + kc) * 128 + t8 * 16) =
+        __ldg(reinterpret_cast<const uint4*>(Wb + (rg * 8 + t8) * 32 + kc * 8));
+  }
+  for (int yy = 0; yy < G5_ROWS; ++yy) {
+    const int y = y0 + yy;
+    uint8_t* ax = sAx + yy * G5_TILE;
+    for (int c = tid; c < 128 * 4; c += 128) {
+      const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
+      const int x = rg * 8 + t8;
+      const uint4 v = x < 80 ? __ldg(reinterpret_cast<const uint4*>(X + (((size_t)b * 80 + y) * 80 + x) * 32 + kc * 8)) : z4;
+      *reinterpret_cast<uint4*>(ax + (rg * 4 + kc) * 128 + t8 * 16) = v;
+    }
+    {
+      const int c = tid, t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
+      *reinterpret_cast<uint4*>(sBt + yy * 2048 + (rg * 4 + kc) * 128 + t8 * 16) =
+          __ldg(reinterpret_cast<const uint4*>(T3 + (((size_t)b * 80 + y) * 32 + rg * 8 + t8) * 32 + kc * 8));
+    }
+  }
+  if (tid == 0) tc::mbar_init(tc::smem_u32(mbar), 1);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 256);
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    constexpr uint32_t idesc = tc::idesc_bf16(32, false, false);
+    const uint32_t ag = tc::smem_u32(sAg), ax0 = tc::smem_u32(sAx), bt0 = tc::smem_u32(sBt), bw = tc::smem_u32(sBw);
+    for (int yy = 0; yy < G5_ROWS; ++yy) {
+      const uint32_t d = tmem + yy * 32;
+      for (int s = 0; s < 2; ++s)
+        tc::mma_bf16(d, tc::make_desc(ag + s * 256, 128, 512), tc::make_desc(bt0 + yy * 2048 + s * 256, 128, 512),
+                     idesc, s > 0);
+      for (int s = 0; s < 2; ++s)
+        tc::mma_bf16(d, tc::make_desc(ax0 + yy * G5_TILE + s * 256, 128, 512), tc::make_desc(bw + s * 256, 128, 512),
+                     idesc, 1);
+    }
+    tc::mma_commit(tc::smem_u32(mbar));
+  }
+  if (!tc::mbar_wait(tc::smem_u32(mbar), 0, WAIT_LIMIT)) atomicExch(err, 1);
+  tc::fence_after();
+  if (warp < 3) {
+    const int x = warp * 32 + lane;
+    float bs[32];
+#pragma unroll
+    for (int o = 0; o < 32; ++o) bs[o] = bias[o];
+    for (int yy = 0; yy < G5_ROWS; ++yy) {
+      float v[32];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + yy * 32, v);
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + yy * 32 + 16, v + 16);
+      if (x < 80) {
+        uint32_t p[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float a = v[2 * i] + bs[2 * i], c = v[2 * i + 1] + bs[2 * i + 1];
+          if (!last) { a = leaky(a); c = leaky(c); }
+          p[i] = pack2(a, c);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(X + (((size_t)b * 80 + y0 + yy) * 80 + x) * 32);
+        dst[0] = make_uint4(p[0], p[1], p[2], p[3]);
+        dst[1] = make_uint4(p[4], p[5], p[6], p[7]);
+        dst[2] = make_uint4(p[8], p[9], p[10], p[11]);
+        dst[3] = make_uint4(p[12], p[13], p[14], p[15]);
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_free(tmem, 256);
+  }
+}
+
+// Restriction + input packing (K3): rho per window, 16 bf16 channels per pixel.
+__global__ void __launch_bounds__(256) pack_kernel(NnoInput in, GridGeom g, bf16* out, float* rho_out) {
+  __shared__ double sh[8];
+  __shared__ float s_inv;
+  const int b = blockIdx.x;
+  const int w = in.win_id ? in.win_id[b] : b;
+  const int a = w % g.nwx, bb = w / g.nwx;
+  const int x0 = min(max(FDFD_CORE * a - FDFD_OVL, 0), g.nx - FDFD_WIN);
+  const int y0 = min(max(FDFD_CORE * bb - FDFD_OVL, 0), g.ny - FDFD_WIN);
+  auto r_at = [&](int p) -> float2 {
+    if (in.v_global) return in.v_global[(size_t)(y0 + p / 80) * g.nx + x0 + p % 80];
+    if (in.r_win) return in.r_win[(size_t)b * NPIX + p];
+    return make_float2(0.f, 0.f);
+  };
+  const float2* gw = in.g_win ? in.g_win + (size_t)b * 320 : nullptr;
+  float acc = 0.f;
+  for (int p = threadIdx.x; p < NPIX; p += 256) { const float2 r = r_at(p); acc += r.x * r.x + r.y * r.y; }
+  if (gw)
+    for (int t = threadIdx.x; t < 320; t += 256) { const float2 q = gw[t]; acc += q.x * q.x + q.y * q.y; }
+  const double tot = block_sum<256>((double)acc, sh);
+  if (threadIdx.x == 0) {
+    const float rho = (float)sqrt(tot / NPIX);
+    rho_out[b] = rho;
+    s_inv = rho > 0.f ? 1.f / rho : 0.f;
+  }
+  __syncthreads();
+  const float inv = s_inv;
+  for (int p = threadIdx.x; p < NPIX; p += 256) {
+    const int y = p / 80, x = p % 80, gx = x0 + x, gy = y0 + y;
+    const float2 r = r_at(p);
+    float c[16];
+    c[0] = g.k2 * g.eps[(size_t)gy * g.nx + gx];
+    c[1] = r.x * inv; c[2] = r.y * inv;
+    if (gw) {
+      const float2 gl = gw[0 * 80 + y], gr = gw[1 * 80 + y], gb = gw[2 * 80 + x], gt = gw[3 * 80 + x];
+      c[3] = gl.x * inv; c[4] = gl.y * inv; c[5] = gr.x * inv; c[6] = gr.y * inv;
+      c[7] = gb.x * inv; c[8] = gb.y * inv; c[9] = gt.x * inv; c[10] = gt.y * inv;
+    } else {
+#pragma unroll
+      for (int i = 3; i <= 10; ++i) c[i] = 0.f;
+    }
+    const float2 sx = g.isx[gx], sy = g.isy[gy];
+    c[11] = sx.x; c[12] = sx.y; c[13] = sy.x; c[14] = sy.y; c[15] = 0.f;
+    uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)b * NPIX + p) * 16);
+    dst[0] = make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), pack2(c[6], c[7]));
+    dst[1] = make_uint4(pack2(c[8], c[9]), pack2(c[10], c[11]), pack2(c[12], c[13]), pack2(c[14], c[15]));
+  }
+}
+
+// Self-test operator: plain row-major C = A B^T.
+struct TestOp {
+  const bf16* A; const bf16* B; float* C; int M, N, K, amn;
+  typedef NoState State;
+  __device__ int rows(int) const { return M; }
+  __device__ const uint4* a_src(int, int m, int k) const {
+    return reinterpret_cast<const uint4*>(amn ? A + (size_t)k * M + m : A + (size_t)m * K + k);
+  }
+  __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(B + (size_t)n * K + k); }
+  __device__ void epi_begin(State&) const {}
+  __device__ void epi(int, int m, int c0, const float* v, State&) const {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) C[(size_t)m * N + c0 + i] = v[i];
+  }
+  __device__ void epi_end(int, int, State&) const {}
+};
+
+std::vector<bf16> to_bf16(const std::vector<float>& a) {
+  std::vector<bf16> o(a.size());
+  for (size_t i = 0; i < a.size(); ++i) o[i] = __float2bfloat16_rn(a[i]);
+  return o;
+}
+
+template <class T>
+int up(T** dst, const std::vector<T>& v, size_t* bytes) {
+  if (cudaMalloc((void**)dst, v.size() * sizeof(T)) != cudaSuccess) return FDFD_ENOMEM;
+  *bytes += v.size() * sizeof(T);
+  CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FDFD_OK;
+}
+
+}  // namespace
+
+int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t* bytes) {
+  const size_t expect = 32 * 15 + 32 + 4 * (2 * 32 * 32 * 512 + 32 * 32 + 32) + 128 * 32 + 128 + 2 * 128 + 2;
+  if (!blob || nfloats != expect) return FDFD_EINVAL;
+  const float* p = blob;
+  int rc;
+  {  // lift [32][15] -> [32][16]
+    std::vector<float> lw(32 * 16, 0.f);
+    for (int o = 0; o < 32; ++o)
+      for (int i = 0; i < 15; ++i) lw[o * 16 + i] = p[o * 15 + i];
+    p += 32 * 15;
+    if ((rc = up(&W->lift_w, to_bf16(lw), bytes))) return rc;
+    if ((rc = up(&W->lift_b, std::vector<float>(p, p + 32), bytes))) return rc;
+    p += 32;
+  }
+  const double PI = 3.14159265358979323846;
+  {  // DFT matrices (FP64 -> BF16)
+    std::vector<float> fx(32 * 80), fy(64 * 160), gy(160 * 64), gx(128 * 32, 0.f);
+    for (int kx = 0; kx < 16; ++kx)
+      for (int x = 0; x < 80; ++x) {
+        const double th = 2 * PI * kx * x / 80.0;
+        fx[(kx * 2 + 0) * 80 + x] = (float)cos(th);
+        fx[(kx * 2 + 1) * 80 + x] = (float)(-sin(th));
+        const double c = (kx == 0 ? 1.0 : 2.0) / 80.0;
+        gx[x * 32 + kx * 2 + 0] = (float)(c * cos(th));
+        gx[x * 32 + kx * 2 + 1] = (float)(-c * sin(th));
+      }
+    for (int q = 0; q < 32; ++q) {
+      const int ky = q < 16 ? q : q - 32;
+      for (int y = 0; y < 80; ++y) {
+        const double th = 2 * PI * ky * y / 80.0;
+        const double fr = cos(th), fi = -sin(th);          // e^{-i th}
+        fy[(q * 2 + 0) * 160 + 0 * 80 + y] = (float)fr;
+        fy[(q * 2 + 0) * 160 + 1 * 80 + y] = (float)(-fi);
+        fy[(q * 2 + 1) * 160 + 0 * 80 + y] = (float)fi;
+        fy[(q * 2 + 1) * 160 + 1 * 80 + y] = (float)fr;
+        const double gr = cos(th) / 80.0, gi = sin(th) / 80.0;  // e^{+i th} / 80
+        gy[(y * 2 + 0) * 64 + q * 2 + 0] = (float)gr;
+        gy[(y * 2 + 0) * 64 + q * 2 + 1] = (float)(-gi);
+        gy[(y * 2 + 1) * 64 + q * 2 + 0] = (float)gi;
+        gy[(y * 2 + 1) * 64 + q * 2 + 1] = (float)gr;
+      }
+    }
+    if ((rc = up(&W->Fx, to_bf16(fx), bytes)) || (rc = up(&W->Fy, to_bf16(fy), bytes)) ||
+        (rc = up(&W->Gy, to_bf16(gy), bytes)) || (rc = up(&W->Gx, to_bf16(gx), bytes)))
+      return rc;
+  }
+  for (int bl = 0; bl < 4; ++bl) {
+    const float* Rr = p;
+    const float* Ri = p + 32 * 32 * 512;
+    p += 2 * 32 * 32 * 512;
+    std::vector<float> R(512 * 64 * 64);
+    for (int q = 0; q < 32; ++q)
+      for (int kx = 0; kx < 16; ++kx) {
+        const int md = q * 16 + kx;
+        for (int o = 0; o < 32; ++o)
+          for (int c = 0; c < 32; ++c) {
+            const float rr = Rr[((o * 32 + c) * 32 + q) * 16 + kx], ri = Ri[((o * 32 + c) * 32 + q) * 16 + kx];
+            float* row_re = &R[((size_t)md * 64 + o * 2 + 0) * 64];
+            float* row_im = &R[((size_t)md * 64 + o * 2 + 1) * 64];
+            row_re[c * 2 + 0] = rr; row_re[c * 2 + 1] = -ri;
+            row_im[c * 2 + 0] = ri; row_im[c * 2 + 1] = rr;
+          }
+      }
+    if ((rc = up(&W->R[bl], to_bf16(R), bytes))) return rc;
+    if ((rc = up(&W->W[bl], to_bf16(std::vector<float>(p, p + 1024)), bytes))) return rc;
+    p += 1024;
+    if ((rc = up(&W->bias[bl], std::vector<float>(p, p + 32), bytes))) return rc;
+    p += 32;
+  }
+  if ((rc = up(&W->P1, to_bf16(std::vector<float>(p, p + 128 * 32)), bytes))) return rc;
+  p += 128 * 32;
+  if ((rc = up(&W->p1b, std::vector<float>(p, p + 128), bytes))) return rc;
+  p += 128;
+  if ((rc = up(&W->P2, std::vector<float>(p, p + 256), bytes))) return rc;
+  p += 256;
+  W->p2b[0] = p[0];
+  W->p2b[1] = p[1];
+  return FDFD_OK;
+}
+
+void nno_free_weights(NnoWeights* W) {
+  void* ptrs[] = {W->lift_w, W->lift_b, W->Fx, W->Fy, W->Gy, W->Gx, W->P1, W->p1b, W->P2};
+  for (void* q : ptrs) if (q) cudaFree(q);
+  for (int b = 0; b < 4; ++b) {
+    if (W->R[b]) cudaFree(W->R[b]);
+    if (W->W[b]) cudaFree(W->W[b]);
+    if (W->bias[b]) cudaFree(W->bias[b]);
+  }
+  *W = NnoWeights();
+}
+
+int nno_alloc_work(NnoWork* w, int cap, size_t* bytes) {
+  w->cap = cap;
+  const size_t c = (size_t)cap;
+  struct { void** p; size_t n; } a[] = {
+      {(void**)&w->in, c * NPIX * 16 * 2}, {(void**)&w->X, c * NPIX * 32 * 2}, {(void**)&w->T1, c * 160 * 512 * 2},
+      {(void**)&w->Xh, 512 * c * 64 * 2},  {(void**)&w->Yh, c * 512 * 64 * 2}, {(void**)&w->T3, c * 80 * 32 * 32 * 2},
+      {(void**)&w->rho, c * 4},             {(void**)&w->err, 16}};
+  for (auto& e : a) {
+    if (cudaMalloc(e.p, e.n) != cudaSuccess) return FDFD_ENOMEM;
+    *bytes += e.n;
+  }
+  CK(cudaMemset(w->err, 0, 16));
+  return FDFD_OK;
+}
+
+void nno_free_work(NnoWork* w) {
+  void* ptrs[] = {w->in, w->X, w->T1, w->Xh, w->Yh, w->T3, w->rho, w->err};
+  for (void* q : ptrs) if (q) cudaFree(q);
+  *w = NnoWork();
+}
+
+int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInput& in, const NnoOutput& out,
+                int n, cudaStream_t s) {
+  if (n <= 0) return FDFD_OK;
+  if (n > k->cap) return FDFD_EINVAL;
+  int rc;
+  pack_kernel<<<n, 256, 0, s>>>(in, g, k->in, k->rho);
+  CKL();
+  if ((rc = launch_gemm<32, 16, false>(LiftOp{k->in, W->lift_w, W->lift_b, k->X}, NPIX / 128, n, k->err, s))) return rc;
+  static bool g5_attr = false;
+  if (!g5_attr) {
+    CK(cudaFuncSetAttribute(g5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
+    g5_attr = true;
+  }
+  for (int bl = 0; bl < 4; ++bl) {
+    if ((rc = launch_gemm<32, 80, true>(G1Op{k->X, W->Fx, k->T1}, 2560 / 128, n, k->err, s))) return rc;
+    if ((rc = launch_gemm<64, 160, true>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s))) return rc;
+    if ((rc = launch_gemm<64, 64, false>(G3Op{k->Xh, W->R[bl], k->Yh, k->cap, n}, (n + 127) / 128, 512, k->err, s)))
+      return rc;
+    if ((rc = launch_gemm<160, 64, false>(G4Op{k->Yh, W->Gy, k->T3}, 512 / 128, n, k->err, s))) return rc;
+    g5_kernel<<<dim3(80 / G5_ROWS, n), 128, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], bl == 3, k->err);
+    CKL();
+  }
+  ProjOp po{k->X, W->P1, W->p1b, W->P2, W->p2b[0], W->p2b[1], k->rho, out.scale, in.win_id,
+            out.z_global, out.e_win, g.nx, g.nwx};
+  po.ny_ = g.ny;
+  if ((rc = launch_gemm<128, 32, false>(po, NPIX / 128, n, k->err, s))) return rc;
+  return FDFD_OK;
+}
+
+int nno_gemm_selftest(const bf16* A, const bf16* B, float* C, int M, int N, int K, int a_mn, int* err,
+                      cudaStream_t s) {
+  TestOp op{A, B, C, M, N, K, a_mn};
+  const int tiles = (M + 127) / 128;
+  if (M % 8) return FDFD_EINVAL;
+#define SELF(NN, KK)                                                              \
+  if (N == NN && K == KK)                                                         \
+    return a_mn ? launch_gemm<NN, KK, true>(op, tiles, 1, err, s)                 \
+                : launch_gemm<NN, KK, false>(op, tiles, 1, err, s);
+  SELF(32, 80) SELF(64, 160) SELF(64, 64) SELF(160, 64) SELF(32, 16) SELF(128, 32)
+#undef SELF
+  return FDFD_EINVAL;
+}

@@ -1,0 +1,70 @@
+// Neural-operator (Fig. 2) device data and the host driver's interface.
+#pragma once
+#include "common.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+struct NnoWeights {
+  bf16* lift_w = nullptr;   // [32][16]      (15 inputs, padded)
+  float* lift_b = nullptr;  // [32]
+  bf16* Fx = nullptr;       // [32 (kx,ri)][80 x]           forward DFT along x
+  bf16* Fy = nullptr;       // [64 (q,ri)][160 (ri',y)]     forward DFT along y (realified)
+  bf16* R[4] = {};          // [512 mode][64 (o,ri)][64 (c,ri')]  realified spectral weights
+  bf16* Gy = nullptr;       // [160 (y,ri)][64 (q,ri')]     inverse DFT along y (1/80)
+  bf16* Gx = nullptr;       // [128 x][32 (kx,ri)]          inverse real DFT along x (1/80), rows >= 80 zero
+  bf16* W[4] = {};          // [32 o][32 c]
+  float* bias[4] = {};      // [32]
+  bf16* P1 = nullptr;       // [128][32]
+  float* p1b = nullptr;     // [128]
+  float* P2 = nullptr;      // [2][128]
+  float p2b[2] = {0.f, 0.f};
+};
+
+struct NnoWork {
+  int cap = 0;              // windows per batch
+  bf16* in = nullptr;       // [cap][6400][16]  packed inputs (channel-last)
+  bf16* X = nullptr;        // [cap][6400][32]  activations (channel-last, in place)
+  bf16* T1 = nullptr;       // [cap][160 (ri,y)][512 (kx,c)]
+  bf16* Xh = nullptr;       // [512 mode][cap][64 (c,ri)]
+  bf16* Yh = nullptr;       // [cap][512 (o,kx)][64 (q,ri)]
+  bf16* T3 = nullptr;       // [cap][80 y][32 o][32 (kx,ri)]
+  float* rho = nullptr;     // [cap]
+  int* err = nullptr;       // bounded-wait failure flag
+};
+
+// Where the packed inputs come from.
+struct NnoInput {
+  const float2* v_global = nullptr;  // residual source: global field (restricted per window), or
+  const float2* r_win = nullptr;     //   per-window residuals [n][80][80], or neither (zero)
+  const float2* g_win = nullptr;     // Robin data [n][4][80] (nullptr = zero)
+  const int* win_id = nullptr;       // window of each batch entry (nullptr = identity)
+};
+
+// Where the output goes.
+struct NnoOutput {
+  float2* z_global = nullptr;        // restricted prolongation into a global field, or
+  float2* e_win = nullptr;           // per-window fields [n][80][80]
+  const double* scale = nullptr;     // multiply by *scale (nullptr = 1)
+};
+
+struct GridGeom {
+  int nx, ny, nwx;
+  float k2;                          // (k0 dx)^2
+  const float* eps;
+  const float2* isx;
+  const float2* isy;
+};
+
+int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t* bytes);
+void nno_free_weights(NnoWeights* W);
+int nno_alloc_work(NnoWork* w, int cap, size_t* bytes);
+void nno_free_work(NnoWork* w);
+// Run the neural operator on n windows (n <= work->cap).
+int nno_forward(const NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInput& in,
+                const NnoOutput& out, int n, cudaStream_t s);
+// Direct access to the tcgen05 GEMM for self-tests: C[M][N] (fp32) =
+// A[M][K] . B[N][K]^T with A K-major (a_mn = 0, row stride K) or MN-major
+// (a_mn = 1, stored [K][M]); supported (N, K): (32,80) (64,160) (64,64)
+// (160,64) (32,16) (128,32).
+int nno_gemm_selftest(const bf16* A, const bf16* B, float* C, int M, int N, int K, int a_mn, int* err,
+                      cudaStream_t s);

@@ -1,9 +1,20 @@
 // Two-level Schwarz preconditioner (Algorithm 3 as one sweep from a zero
 // guess): partition kernels, neural local solves and the coarse space.
 #include "ctx.cuh"
+#include "nno.cuh"
+
+struct CoarseData;
+void coarse_free(CoarseData* c);
+int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, int k, CoarseData** out, size_t* bytes);
+int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u);
+int coarse_export(fdfd_ctx* h, CoarseData* c, double* Qh, double* Ndh);
 
 struct SchwarzData {
-  int k = 0;
+  int k = 0, n_win = 0, nwx = 0, precision = 0;
+  NnoWeights W;
+  NnoWork work;
+  CoarseData* coarse = nullptr;
+  size_t bytes = 0;
 };
 
 namespace {
@@ -43,11 +54,90 @@ int schwarz_traces(fdfd_ctx* h, const float2* u, float2* g) {
   return FDFD_OK;
 }
 
-int schwarz_create(fdfd_ctx*, const schwarz_desc*) { return FDFD_ENOSETUP; }
-void schwarz_destroy(fdfd_ctx* h) {
-  if (h && h->sw) { delete h->sw; h->sw = nullptr; }
+static GridGeom geom(fdfd_ctx* h) {
+  return GridGeom{h->nx, h->ny, h->nx / FDFD_CORE, (float)h->k2, h->eps, h->isx, h->isy};
 }
-int schwarz_apply(fdfd_ctx*, const float2*, const double*, float2*, int) { return FDFD_ENOSETUP; }
-int schwarz_nno_solve(fdfd_ctx*, const float2*, const float2*, const int*, int, float2*) { return FDFD_ENOSETUP; }
-int schwarz_export(fdfd_ctx*, double*, double*) { return FDFD_ENOSETUP; }
-int schwarz_info(fdfd_ctx*, fdfd_info*) { return FDFD_OK; }
+
+static int check_err(fdfd_ctx* h) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->sw->work.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return e ? FDFD_ETIMEOUT : FDFD_OK;
+}
+
+int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd) {
+  if (sd->k_coarse < 0 || sd->k_coarse > 256) return FDFD_EINVAL;
+  if (sd->precision != FDFD_PREC_BF16 && sd->precision != FDFD_PREC_FP8) return FDFD_EINVAL;
+  SchwarzData* S = new SchwarzData();
+  S->nwx = h->nx / FDFD_CORE;
+  S->n_win = S->nwx * (h->ny / FDFD_CORE);
+  S->precision = sd->precision;
+  int rc = nno_upload_weights(&S->W, sd->weights, sd->n_weights, &S->bytes);
+  if (!rc) rc = nno_alloc_work(&S->work, S->n_win < 64 ? 64 : S->n_win, &S->bytes);
+  h->sw = S;
+  if (!rc && sd->k_coarse > 0) {
+    S->k = sd->k_coarse;
+    rc = coarse_setup(h, &S->W, &S->work, sd->k_coarse, &S->coarse, &S->bytes);
+    if (!rc) rc = check_err(h);
+  }
+  if (rc) { schwarz_destroy(h); return rc; }
+  h->bytes += S->bytes;
+  return FDFD_OK;
+}
+
+void schwarz_destroy(fdfd_ctx* h) {
+  if (!h || !h->sw) return;
+  SchwarzData* S = h->sw;
+  cudaStreamSynchronize(h->stream);
+  if (S->coarse) coarse_free(S->coarse);
+  nno_free_weights(&S->W);
+  nno_free_work(&S->work);
+  h->bytes -= (h->bytes >= S->bytes ? S->bytes : h->bytes);
+  delete S;
+  h->sw = nullptr;
+}
+
+int schwarz_apply(fdfd_ctx* h, const float2* v, const double* scale_dev, float2* z, int /*transpose*/) {
+  SchwarzData* S = h->sw;
+  NnoInput in;
+  in.v_global = v;
+  NnoOutput out;
+  out.z_global = z;
+  out.scale = scale_dev;
+  int rc;
+  {
+    ProfScope ps(h, 5, 23);
+    if ((rc = nno_forward(&S->W, &S->work, geom(h), in, out, S->n_win, h->stream))) return rc;
+  }
+  if (S->coarse) {
+    ProfScope ps(h, 7, 4);
+    if ((rc = coarse_apply(h, S->coarse, z))) return rc;
+  }
+  return FDFD_OK;
+}
+
+int schwarz_nno_solve(fdfd_ctx* h, const float2* r_win, const float2* g_win, const int* win_id, int n,
+                      float2* e_win) {
+  SchwarzData* S = h->sw;
+  if (n > S->work.cap) return FDFD_EINVAL;
+  NnoInput in;
+  in.r_win = r_win;
+  in.g_win = g_win;
+  in.win_id = win_id;
+  NnoOutput out;
+  out.e_win = e_win;
+  int rc = nno_forward(&S->W, &S->work, geom(h), in, out, n, h->stream);
+  if (rc) return rc;
+  return check_err(h);
+}
+
+int schwarz_export(fdfd_ctx* h, double* Q, double* Nd) {
+  if (!h->sw->coarse) return FDFD_ENOSETUP;
+  return coarse_export(h, h->sw->coarse, Q, Nd);
+}
+
+int schwarz_info(fdfd_ctx* h, fdfd_info* info) {
+  info->k_coarse = h->sw->k;
+  info->n_coarse = h->sw->k * h->sw->n_win;
+  return FDFD_OK;
+}

@@ -80,6 +80,7 @@ _SIGS = {
     "fdfd_trace_extract": ([_P, _P, _P], C.c_int),
     "fdfd_coarse_export": ([_P, _P, _P], C.c_int),
     "fdfd_profile_start": ([_P], C.c_int),
+    "fdfd_selftest_gemm": ([_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "fdfd_profile_stop": ([_P, C.POINTER(Profile)], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -111,6 +112,14 @@ def _ptr(t):
 
 def status_string(code: int) -> str:
     return lib.fdfd_status_string(code).decode()
+
+
+def selftest_gemm(A, B, C_out, a_mn_major=False):
+    """tcgen05 GEMM diagnostic: C_out = A @ B^T (A [M][K] or [K][M] bf16, B [N][K] bf16)."""
+    M = A.shape[1] if a_mn_major else A.shape[0]
+    K = A.shape[0] if a_mn_major else A.shape[1]
+    _check(lib.fdfd_selftest_gemm(_ptr(A), _ptr(B), _ptr(C_out), M, B.shape[0], K, int(a_mn_major)),
+           "fdfd_selftest_gemm")
 
 
 class Solver:

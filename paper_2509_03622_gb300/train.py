@@ -1,0 +1,290 @@
+"""Offline training of the subdomain neural operator (Sec. 2.1; Methods,
+Algorithm 2 and the physics-only data recipe).
+
+This is the one piece of the project that runs in PyTorch: it produces the
+weight blob that `schwarz_setup` consumes (layout of include/fdfd.h).  The
+solve itself never calls it.
+
+Model: the plain FNO of Fig. 2 (lift 15 -> 32, four Fourier blocks with 512
+retained modes and 1x1 channel mixers, leaky-ReLU, projection 32 -> 128 ->
+2).  Physics-only loss (Methods: random permittivity, Gaussian-noise sources
+and Robin data, random PML placement, no ground truth): the network output
+e for residual r and Robin data g must satisfy the local Robin problem
+A_w e = r - B g (Eq. 1-2 on an 80 x 80 window).  Fixed-point recurrence of
+Algorithm 2: x += M(r), r = rhs - A_w x with the gradient stopped through r,
+loss = ||r||^2 / ||rhs||^2 after every step (clipped for stability).
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+WIN = 80
+
+
+def build_model(torch, w0: dict):
+    nn = torch.nn
+
+    class FNO(nn.Module):
+        def __init__(self):
+            super().__init__()
+            P = lambda a: nn.Parameter(torch.tensor(np.asarray(a, dtype=np.float32)))
+            self.lift_w, self.lift_b = P(w0["lift_w"]), P(w0["lift_b"])
+            self.Rr = nn.ParameterList([P(w0[f"R{b}_re"]) for b in range(4)])
+            self.Ri = nn.ParameterList([P(w0[f"R{b}_im"]) for b in range(4)])
+            self.W = nn.ParameterList([P(w0[f"W{b}"]) for b in range(4)])
+            self.bb = nn.ParameterList([P(w0[f"b{b}"]) for b in range(4)])
+            self.p1_w, self.p1_b = P(w0["p1_w"]), P(w0["p1_b"])
+            self.p2_w, self.p2_b = P(w0["p2_w"]), P(w0["p2_b"])
+
+        def forward(self, x):  # [B][15][80][80] -> [B][2][80][80]
+            h = torch.einsum("oi,biyx->boyx", self.lift_w, x) + self.lift_b[None, :, None, None]
+            for b in range(4):
+                H = torch.fft.rfft2(h)
+                Hk = torch.cat([H[:, :, :16, :16], H[:, :, -16:, :16]], dim=2)
+                R = torch.complex(self.Rr[b], self.Ri[b])
+                Y = torch.einsum("biyx,oiyx->boyx", Hk, R)
+                Yf = torch.zeros(h.shape[0], 32, WIN, WIN // 2 + 1, dtype=Y.dtype, device=h.device)
+                Yf[:, :, :16, :16] = Y[:, :, :16]
+                Yf[:, :, -16:, :16] = Y[:, :, 16:]
+                s = torch.fft.irfft2(Yf, s=(WIN, WIN))
+                h = s + torch.einsum("oi,biyx->boyx", self.W[b], h) + self.bb[b][None, :, None, None]
+                if b < 3:
+                    h = torch.nn.functional.leaky_relu(h, 0.01)
+            q = torch.nn.functional.leaky_relu(
+                torch.einsum("oi,biyx->boyx", self.p1_w, h) + self.p1_b[None, :, None, None], 0.01)
+            return torch.einsum("oi,biyx->boyx", self.p2_w, q) + self.p2_b[None, :, None, None]
+
+        def export(self) -> dict:
+            d = {"lift_w": self.lift_w, "lift_b": self.lift_b, "p1_w": self.p1_w, "p1_b": self.p1_b,
+                 "p2_w": self.p2_w, "p2_b": self.p2_b}
+            for b in range(4):
+                d[f"R{b}_re"], d[f"R{b}_im"] = self.Rr[b], self.Ri[b]
+                d[f"W{b}"], d[f"b{b}"] = self.W[b], self.bb[b]
+            return {k: v.detach().float().cpu().numpy() for k, v in d.items()}
+
+    return FNO()
+
+
+class Sampler:
+    """Random 80 x 80 Robin windows (Methods: physics-only data)."""
+
+    def __init__(self, torch, dev, batch, npml=20):
+        self.t, self.dev, self.B, self.npml = torch, dev, batch, npml
+
+    def smooth_noise(self, shape, sigma):
+        t = self.t
+        z = t.randn(*shape, dtype=t.complex64, device=self.dev)
+        n = shape[-1]
+        f = t.fft.fftfreq(n, device=self.dev)
+        g = t.exp(-2 * (math.pi * f[:, None]) ** 2 * sigma[:, None, None] ** 2 - 2 * (math.pi * f[None, :]) ** 2
+                  * sigma[:, None, None] ** 2) if len(shape) == 3 else None
+        return t.fft.ifft2(t.fft.fft2(z) * g)
+
+    def eps(self):
+        t, B = self.t, self.B
+        e = t.ones(B, WIN, WIN, device=self.dev)
+        vals = t.tensor([1.0, 2.1, 12.25], device=self.dev)
+        kind = t.randint(0, 3, (B,), device=self.dev)
+        # rectangles
+        for _ in range(6):
+            w = t.randint(8, 48, (B,), device=self.dev)
+            h = t.randint(8, 48, (B,), device=self.dev)
+            x0 = t.randint(-20, WIN, (B,), device=self.dev)
+            y0 = t.randint(-20, WIN, (B,), device=self.dev)
+            v = vals[t.randint(0, 3, (B,), device=self.dev)]
+            xs = t.arange(WIN, device=self.dev)
+            mx = (xs[None, :] >= x0[:, None]) & (xs[None, :] < (x0 + w)[:, None])
+            my = (xs[None, :] >= y0[:, None]) & (xs[None, :] < (y0 + h)[:, None])
+            m = my[:, :, None] & mx[:, None, :] & (kind == 0)[:, None, None]
+            e = t.where(m, v[:, None, None], e)
+        # freeform: thresholded smooth noise
+        sig = 2.0 + 4.0 * t.rand(B, device=self.dev)
+        s = self.smooth_noise((B, WIN, WIN), sig).real
+        hi = vals[1 + t.randint(0, 2, (B,), device=self.dev)]
+        e = t.where((kind == 1)[:, None, None], t.where(s > 0, hi[:, None, None], t.ones_like(e)), e)
+        # kind 2: homogeneous background of random value
+        e = t.where((kind == 2)[:, None, None], vals[t.randint(0, 3, (B,), device=self.dev)][:, None, None]
+                    * t.ones_like(e), e)
+        return e
+
+    def axis(self, k0dx):
+        """Per-window 1D UPML factors and side kinds for one axis.
+        mode 0: interior (both sides Robin), 1: grid edge at the low side
+        (PML cells 0..npml-1, low side Dirichlet), 2: edge at the high side."""
+        t, B, npml = self.t, self.B, self.npml
+        mode = t.randint(0, 5, (B,), device=self.dev).clamp(max=2)  # 60% interior
+        pn = t.arange(WIN, device=self.dev, dtype=t.float32) + 0.5
+        ph = t.arange(WIN + 1, device=self.dev, dtype=t.float32)
+        A = (4.0 * 30.0 / (2.0 * npml * k0dx))[:, None]  # -(m+1) lnR / (2 npml k0dx)
+
+        def sig(p):
+            dlo = (npml - p[None, :]).clamp(min=0) / npml
+            dhi = (p[None, :] - (WIN - npml)).clamp(min=0) / npml
+            lo = (mode == 1)[:, None].float() * dlo ** 3
+            hi = (mode == 2)[:, None].float() * dhi ** 3
+            return A * (lo + hi)
+
+        sn = t.complex(t.ones(B, WIN, device=self.dev), -sig(pn))
+        sh = t.complex(t.ones(B, WIN + 1, device=self.dev), -sig(ph))
+        lo = 1.0 / (sn * sh[:, :-1])
+        hi = 1.0 / (sn * sh[:, 1:])
+        robin_lo = mode != 1
+        robin_hi = mode != 2
+        return sn, lo, hi, robin_lo, robin_hi
+
+    def batch(self):
+        t, B = self.t, self.B
+        ppw = 20.0 + 20.0 * t.rand(B, device=self.dev)
+        k0dx = 2 * math.pi / ppw
+        eps = self.eps()
+        sxn, xlo, xhi, rxl, rxh = self.axis(k0dx)
+        syn, ylo, yhi, ryl, ryh = self.axis(k0dx)
+        return dict(k0dx=k0dx, eps=eps, sxn=sxn, xlo=xlo, xhi=xhi, syn=syn, ylo=ylo, yhi=yhi,
+                    robin=t.stack([rxl, rxh, ryl, ryh], 1))
+
+
+def local_apply(t, e, P):
+    """A_w e: 5-point UPML stencil with the Robin ghost elimination of Eq. 2
+    on interface sides (u_o = (1 - j kd) u_b + g) and zero ghosts on grid
+    sides.  e [B][80][80] complex."""
+    xlo, xhi, ylo, yhi = P["xlo"], P["xhi"], P["ylo"], P["yhi"]
+    k2 = (P["k0dx"] ** 2)[:, None, None]
+    kd = P["k0dx"][:, None, None] * t.sqrt(P["eps"])
+    z = t.zeros_like(e[:, :, :1])
+    em = t.cat([z, e[:, :, :-1]], 2)
+    ep = t.cat([e[:, :, 1:], z], 2)
+    zr = t.zeros_like(e[:, :1, :])
+    eym = t.cat([zr, e[:, :-1, :]], 1)
+    eyp = t.cat([e[:, 1:, :], zr], 1)
+    y = xlo[:, None, :] * em + xhi[:, None, :] * ep + ylo[:, :, None] * eym + yhi[:, :, None] * eyp
+    dg = -(xlo + xhi)[:, None, :] - (ylo + yhi)[:, :, None] + k2 * P["eps"]
+    y = y + dg * e
+    rb = P["robin"]
+    f = (1 - 1j * kd)
+    add = t.zeros_like(e)
+    add[:, :, 0] += rb[:, 0, None] * xlo[:, None, 0] * f[:, :, 0] * e[:, :, 0]
+    add[:, :, -1] += rb[:, 1, None] * xhi[:, None, -1] * f[:, :, -1] * e[:, :, -1]
+    add[:, 0, :] += rb[:, 2, None] * ylo[:, 0, None] * f[:, 0, :] * e[:, 0, :]
+    add[:, -1, :] += rb[:, 3, None] * yhi[:, -1, None] * f[:, -1, :] * e[:, -1, :]
+    return y + add
+
+
+def boundary_rhs(t, g, P):
+    """B g: contribution -c_bo g of the Robin data to the right-hand side."""
+    out = t.zeros(g.shape[0], WIN, WIN, dtype=g.dtype, device=g.device)
+    rb = P["robin"]
+    out[:, :, 0] -= rb[:, 0, None] * P["xlo"][:, None, 0] * g[:, 0]
+    out[:, :, -1] -= rb[:, 1, None] * P["xhi"][:, None, -1] * g[:, 1]
+    out[:, 0, :] -= rb[:, 2, None] * P["ylo"][:, 0, None] * g[:, 2]
+    out[:, -1, :] -= rb[:, 3, None] * P["yhi"][:, -1, None] * g[:, 3]
+    return out
+
+
+def pack(t, r, g, P):
+    rho = t.sqrt((r.abs() ** 2).sum((1, 2)) + (g.abs() ** 2).sum((1, 2))) / WIN
+    inv = t.where(rho > 0, 1.0 / rho, t.zeros_like(rho))
+    rn = r * inv[:, None, None]
+    gn = g * inv[:, None, None]
+    B = r.shape[0]
+    x = t.zeros(B, 15, WIN, WIN, device=r.device)
+    x[:, 0] = (P["k0dx"] ** 2)[:, None, None] * P["eps"]
+    x[:, 1], x[:, 2] = rn.real, rn.imag
+    for s in range(4):
+        gs = gn[:, s]
+        if s < 2:
+            x[:, 3 + 2 * s] = gs.real[:, :, None].expand(B, WIN, WIN)
+            x[:, 4 + 2 * s] = gs.imag[:, :, None].expand(B, WIN, WIN)
+        else:
+            x[:, 3 + 2 * s] = gs.real[:, None, :].expand(B, WIN, WIN)
+            x[:, 4 + 2 * s] = gs.imag[:, None, :].expand(B, WIN, WIN)
+    isx, isy = 1.0 / P["sxn"], 1.0 / P["syn"]
+    x[:, 11], x[:, 12] = isx.real[:, None, :], isx.imag[:, None, :]
+    x[:, 13], x[:, 14] = isy.real[:, :, None], isy.imag[:, :, None]
+    return x, rho
+
+
+def solve(t, model, r, g, P):
+    x, rho = pack(t, r, g, P)
+    out = model(x)
+    return rho[:, None, None] * t.complex(out[:, 0], out[:, 1])
+
+
+def train(minutes: float, batch: int, recur: int, lr: float, seed: int, out: str, log_every: int = 200,
+          device: str = "cuda", init=None):
+    import torch as t
+    from paper_2509_03622_gb300 import workloads as wl
+    dev = t.device(device)
+    t.manual_seed(seed)
+    t.backends.cuda.matmul.allow_tf32 = True
+    w0 = wl.unpack_weights(np.load(init)) if init else wl.nno_weights(seed)
+    model = build_model(t, w0).to(dev)
+    opt = t.optim.Adam(model.parameters(), lr=lr)
+    S = Sampler(t, dev, batch)
+    t0 = time.time()
+    it = 0
+    hist = []
+    while time.time() - t0 < minutes * 60:
+        frac = (time.time() - t0) / (minutes * 60)
+        for gp in opt.param_groups:
+            gp["lr"] = lr * 0.5 * (1 + math.cos(math.pi * min(frac, 1.0)))
+        P = S.batch()
+        sig = t.rand(batch, device=dev) * 6.0
+        r = S.smooth_noise((batch, WIN, WIN), sig)
+        g = t.randn(batch, 4, WIN, dtype=t.complex64, device=dev)
+        kindr = t.rand(batch, device=dev)
+        r = t.where((kindr < 0.25)[:, None, None], t.zeros_like(r), r)           # boundary-data-only solves
+        g = t.where((kindr > 0.5)[:, None, None], t.zeros_like(g), g)            # residual-only solves
+        g = g * P["robin"][:, :, None]
+        rhs = r + boundary_rhs(t, g, P)
+        nrm = (rhs.abs() ** 2).sum((1, 2)).clamp(min=1e-30)
+        x = t.zeros_like(rhs)
+        res = rhs
+        loss = 0.0
+        opt.zero_grad()
+        zg = t.zeros_like(g)
+        for k in range(recur):
+            # first step sees the source and the Robin data, later steps the residual only
+            e = solve(t, model, r, g, P) if k == 0 else solve(t, model, res, zg, P)
+            x = x + e
+            res_new = rhs - local_apply(t, x, P)
+            lk = ((res_new.abs() ** 2).sum((1, 2)) / nrm).clamp(max=4.0)
+            loss = loss + lk.mean()
+            res = res_new.detach()
+            x = x.detach()
+        loss = loss / recur
+        loss.backward()
+        t.nn.utils.clip_grad_norm_(model.parameters(), 1.0)
+        opt.step()
+        it += 1
+        hist.append(float(loss))
+        if it % log_every == 0:
+            print(f"it {it} t {time.time() - t0:.0f}s loss {np.mean(hist[-log_every:]):.4f}", flush=True)
+    w = model.export()
+    np.save(out, wl.pack_weights(w))
+    print(f"saved {out} after {it} iterations; final loss {np.mean(hist[-200:]):.4f}")
+    return hist
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--minutes", type=float, default=10.0)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--recur", type=int, default=3)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default=os.path.join(HERE, "weights", "nno_trained.npy"))
+    ap.add_argument("--device", default="cuda")
+    ap.add_argument("--init", default=None, help="start from a saved weight blob")
+    ap.add_argument("--log-every", type=int, default=200)
+    a = ap.parse_args()
+    os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+    train(a.minutes, a.batch, a.recur, a.lr, a.seed, a.out, a.log_every, a.device, a.init)

@@ -1,0 +1,119 @@
+"""GPU parity of the tensor-core neural operator and the two-level Schwarz
+preconditioner against the FP64 oracle, through the C-ABI."""
+import numpy as np
+import pytest
+
+from oracle import fdfd as OF, nno as ON, partition as OP, schwarz as OS
+from paper_2509_03622_gb300 import workloads as wl
+
+LAM = 1.55e-6
+pytestmark = pytest.mark.gpu
+BF16_TOL = 3e-2   # relative L2; four BF16 Fourier blocks with FP32 accumulation
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch  # noqa: F401
+    from paper_2509_03622_gb300 import fdfd
+    return fdfd
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _bf16_round(a):
+    import torch
+    return torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("N,K", [(32, 80), (64, 160), (64, 64), (160, 64), (32, 16), (128, 32)])
+@pytest.mark.parametrize("amn", [False, True])
+def test_tcgen05_gemm_selftest(F, N, K, amn):
+    import torch
+    g = wl.rng(N * 1000 + K)
+    M = 384 + 8 * 5  # several tiles and a ragged tail
+    A = g.standard_normal((M, K)).astype(np.float32)
+    B = g.standard_normal((N, K)).astype(np.float32)
+    At = torch.from_numpy(A.T.copy() if amn else A).to(torch.bfloat16).cuda().contiguous()
+    Bt = torch.from_numpy(B).to(torch.bfloat16).cuda()
+    C = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    F.selftest_gemm(At, Bt, C, a_mn_major=amn)
+    ref = _bf16_round(A) @ _bf16_round(B).T
+    err = np.max(np.abs(C.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err < 1e-5, err
+
+
+def _setup(F, n=256, k=0, seed_w=0):
+    import torch
+    dx = LAM / 25
+    eps = wl.rectangles_eps(n, n, seed=1000)
+    S = F.Solver(_t(eps), dx, LAM, npml=20)
+    w = wl.nno_weights(seed_w)
+    S.schwarz_setup(wl.pack_weights(w), k_coarse=k)
+    return S, eps, dx, w
+
+
+def test_nno_solve_matches_oracle(F):
+    """Batched neural local solves: residual and Robin data on windows of
+    every kind (corner with PML, edge, interior), random data."""
+    import torch
+    S, eps, dx, w = _setup(F)
+    n = 256
+    win = OP.Windows(n, n)
+    sxn, _, syn, _ = OF.pml_factors(n, n, dx, LAM, 20)
+    k2 = OF.k0dx_of(dx, LAM) ** 2
+    ids = np.array([0, 1, 5, 10, 15, 3], dtype=np.int32)
+    g = wl.rng(7)
+    r = (g.standard_normal((len(ids), 80, 80)) + 1j * g.standard_normal((len(ids), 80, 80))).astype(np.complex64)
+    gb = (g.standard_normal((len(ids), 4, 80)) + 1j * g.standard_normal((len(ids), 4, 80))).astype(np.complex64)
+    gb[1] = 0  # a pure-residual window
+    r[2] = 0   # a pure-boundary-data window (coarse set-up form)
+    e = torch.empty((len(ids), 80, 80), dtype=torch.complex64, device="cuda")
+    S.nno_solve(_t(r), _t(gb), _t(ids), e)
+    got = e.cpu().numpy()
+    for i, wi in enumerate(ids):
+        x0, y0 = win.x0[wi], win.y0[wi]
+        ref = ON.solve(r[i], gb[i], k2 * eps[y0:y0 + 80, x0:x0 + 80].astype(float), 1 / sxn[x0:x0 + 80],
+                       1 / syn[y0:y0 + 80], w)
+        err = np.linalg.norm(got[i] - ref) / np.linalg.norm(ref)
+        assert err < BF16_TOL, (i, wi, err)
+
+
+@pytest.mark.parametrize("k", [0, 4])
+def test_precond_apply_matches_oracle(F, k):
+    """One (two-level) Schwarz sweep M(v): restriction, neural solves,
+    restricted prolongation, traces, coarse solve and correction."""
+    import torch
+    S, eps, dx, w = _setup(F, k=k)
+    n = 256
+    O = OS.Schwarz(eps, dx, LAM, 20, weights=w, k_coarse=k)
+    v = wl.random_field(n, n, 11)
+    z = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    S.precond_apply(_t(v), z)
+    ref = O.apply(v.astype(np.complex128))
+    err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < BF16_TOL, err
+    if k:
+        Q, Nd = S.coarse_export()
+        assert np.max(np.abs(Q - O.coarse.Q)) < 1e-9
+        nd_ref = np.stack([O.coarse.N[i * k:(i + 1) * k, i * k:(i + 1) * k] for i in range(16)])
+        drop = O.coarse.dropped.reshape(16, k)
+        for i in range(16):
+            for m in range(k):
+                if drop[i, m]:
+                    nd_ref[i, m, m] = 0.0
+        assert np.linalg.norm(Nd - nd_ref) / np.linalg.norm(nd_ref) < 2 * BF16_TOL
+
+
+def test_precond_is_positively_homogeneous(F):
+    import torch
+    S, eps, dx, w = _setup(F, k=4)
+    v = wl.random_field(256, 256, 3)
+    z1 = torch.empty((256, 256), dtype=torch.complex64, device="cuda")
+    z2 = torch.empty_like(z1)
+    S.precond_apply(_t(v), z1)
+    S.precond_apply(_t(4 * v), z2)
+    a, b = z1.cpu().numpy(), z2.cpu().numpy()
+    assert np.linalg.norm(b - 4 * a) / np.linalg.norm(4 * a) < 1e-5
