@@ -87,6 +87,62 @@ class Clocks:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Algorithmic HBM bytes per window (80 x 80, 6400 pixels) of each neural-
+# operator stage: what it must read and write once (bf16 activations of 32
+# channels = 64 B per pixel, complex64 fields = 8 B per cell).
+WIN_BYTES = {
+    "nno_pack": 6400 * (8 + 4 + 32),          # residual + eps in, 16 bf16 channels out
+    "nno_lift": 6400 * (32 + 64),             # inputs in, activation out
+    "nno_dft_x": 6400 * 64 + 160 * 512 * 2,   # activation in, half-spectrum along x out
+    "nno_dft_y": 160 * 512 * 2 + 512 * 64 * 2,
+    "nno_mix": 512 * 64 * 2 * 2,              # spectrum in and out (weights amortised)
+    "nno_idft_y": 512 * 64 * 2 + 80 * 32 * 32 * 2,
+    "nno_idft_x_mix_act": 6400 * 64 * 2 + 80 * 32 * 32 * 2,
+    "nno_proj": 6400 * 64 + 4096 * 8,         # activation in, core field out
+}
+# Useful FLOPs per window of each stage (padding excluded).
+NNO_FLOP_PER_WIN = {
+    "nno_lift": 6400 * 32 * 15 * 2, "nno_dft_x": 2560 * 32 * 80 * 2, "nno_dft_y": 512 * 64 * 160 * 2,
+    "nno_mix": 512 * 64 * 64 * 2, "nno_idft_y": 512 * 160 * 64 * 2, "nno_idft_x_mix_act": 80 * 80 * 32 * 64 * 2,
+    "nno_proj": 6400 * (128 * 32 + 2 * 128) * 2,
+}
+KERNEL_NAMES = {"stencil": "stencil_c64", "cgs_dots": "cgs_dots_kernel", "cgs_update": "cgs_update_kernel",
+                "residual64": "residual64", "nno_pack": "pack_kernel", "nno_lift": "gemm_kernel<32,16> (LiftOp)",
+                "nno_dft_x": "gemm_kernel<32,80,MN> (G1Op)", "nno_dft_y": "gemm_kernel<64,160,MN> (G2Op)",
+                "nno_mix": "gemm_kernel<64,64> (G3Op)", "nno_idft_y": "gemm_kernel<160,64> (G4Op)",
+                "nno_idft_x_mix_act": "g5_kernel", "nno_proj": "gemm_kernel<128,32> (ProjOp)"}
+
+
+def algorithmic_bytes(cls, launches, N, steps):
+    """Bytes the kernel class must move over the timed region."""
+    nwin = N // 4096
+    if cls == "stencil":
+        return 20.0 * N * launches
+    if cls in ("cgs_dots", "cgs_update"):
+        js = [s % 30 for s in range(steps)]
+        extra = 8 if cls == "cgs_dots" else 16
+        return float(sum((8 * (j + 1) + extra) * N for j in js))
+    if cls == "residual64":
+        return 36.0 * N * launches
+    if cls in WIN_BYTES:
+        per = WIN_BYTES[cls] * nwin + (512 * 64 * 64 * 2 if cls == "nno_mix" else 0)
+        return float(per) * launches
+    return None
+
+
+TRAINED = os.path.join(ROOT, "paper_2509_03622_gb300", "weights", "nno_trained.npy")
+
+
+def load_weights(path=None):
+    """Trained FNO blob if available, else the seeded initialisation."""
+    import numpy as np
+    from paper_2509_03622_gb300 import workloads as wl
+    p = path or (TRAINED if os.path.exists(TRAINED) else None)
+    if p:
+        return np.load(p), os.path.relpath(p, ROOT)
+    return wl.pack_weights(wl.nno_weights(0)), "seeded init (seed 0)"
+
+
 def make_problem(n, seed_off=0):
     from paper_2509_03622_gb300 import workloads as wl
     lam = 1.55e-6
@@ -152,6 +208,8 @@ def main():
     ap.add_argument("--precond", default="schwarz", choices=["schwarz", "jacobi"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--k-coarse", type=int, default=-1)
+    ap.add_argument("--inner", type=int, default=0, help="NN-FGMRES steps per local solve (0 = one application)")
+    ap.add_argument("--weights", default=None, help="weight blob (.npy); default the trained blob if present")
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tts", action="store_true", help="also time a full solve to 1e-6")
@@ -176,12 +234,14 @@ def main():
     eps, J, dx, lam = make_problem(n, seed_off=rank)
     S = F.Solver(torch.from_numpy(eps).to(dev), dx, lam, npml=20)
     precond = F.PRECOND_SCHWARZ if args.precond == "schwarz" else F.PRECOND_JACOBI
-    kc = args.k_coarse if args.k_coarse >= 0 else 8
-    prec_nno = "fp8" if n >= 4096 else "bf16"
+    kc = args.k_coarse if args.k_coarse >= 0 else (8 if n <= 1024 else 0)
+    prec_nno = "bf16"
     if precond == F.PRECOND_SCHWARZ:
-        w = wl.nno_weights(0)
-        S.schwarz_setup(wl.pack_weights(w), k_coarse=kc,
-                        precision=F.PREC_FP8 if prec_nno == "fp8" else F.PREC_BF16)
+        blob, wsrc = load_weights(args.weights)
+        t0 = time.perf_counter()
+        S.schwarz_setup(blob, k_coarse=kc, precision=F.PREC_FP8 if prec_nno == "fp8" else F.PREC_BF16,
+                        inner_iters=args.inner)
+        t_setup = time.perf_counter() - t0
     Jd = torch.from_numpy(J).to(dev)
     E = torch.zeros((n, n), dtype=torch.complex64, device=dev)
     # warm-up: W Arnoldi steps
@@ -218,43 +278,40 @@ def main():
     t_e2e = time.perf_counter() - t0
     e2e_value = world * n * n * args.steps / t_e2e / 1e6
     hbm, bf16, bf16s, src = peaks()
-    # roofline of the dominant kernel class
+    # rooflines per kernel class (algorithmic bytes of the timed region)
     cls_ms = prof["ms"]
-    dom = max(cls_ms, key=lambda c: cls_ms[c])
     N = n * n
-    roof = None
-    if dom == "stencil":
-        launches = prof["launches"]["stencil"]
-        per = cls_ms["stencil"] / max(launches, 1)
-        ach = 20.0 * N / (per / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "stencil_jacobi_c64" if precond == F.PRECOND_JACOBI else "stencil_c64",
-                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-                "bytes_per_cell": 20, "peak_source": src}
-    elif dom in ("cgs_dots", "cgs_update"):
-        # algorithmic bytes over the timed steps (j = 0..steps-1 in one cycle of 30)
-        js = [s % 30 for s in range(steps)]
-        if dom == "cgs_dots":
-            byts = sum((8 * (j + 1) + 8) * N for j in js)
-        else:
-            byts = sum((8 * (j + 1) + 16) * N for j in js)
-        ach = byts / (cls_ms[dom] / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_source": src}
-    elif dom == "nno":
-        flop = 318.0e6 * (N / 4096.0) * prof["launches"].get("nno_applies", steps) if False else None
-        roof = {"bound": "tensor", "kernel": "nno", "achieved": None, "peak": bf16s, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "peak_source": src}
+    roofs = {}
+    for cls, ms_c in cls_ms.items():
+        nl = prof["launches"][cls]
+        if ms_c <= 0 or nl == 0:
+            continue
+        byts = algorithmic_bytes(cls, nl, N, steps)
+        if byts is None:
+            continue
+        ach = byts / (ms_c / 1e3) / 1e9
+        r = {"bound": "hbm", "kernel": KERNEL_NAMES.get(cls, cls), "achieved": ach, "peak": hbm, "unit": "GB/s",
+             "frac": ach / hbm, "traffic": None, "launches": nl, "ms": ms_c, "peak_source": src}
+        fl = NNO_FLOP_PER_WIN.get(cls)
+        if fl:
+            r["tflops"] = fl * (N / 4096.0) * nl / (ms_c / 1e3) / 1e12
+        roofs[cls] = r
+    dom = max(roofs, key=lambda c: roofs[c]["ms"]) if roofs else None
+    roof = dict(roofs[dom]) if dom else None
     line = {"metric": METRIC, "value": value, "unit": "Mcell-it/s", "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms / max(steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64",
-            "data": "synthetic (seeded freeform eps, point source, seeded-init FNO weights)",
+            "data": "synthetic (seeded freeform eps, point source)",
             "config": {"workload": f"freeform{n}: {n}x{n} grid, lambda/dx=30, eps {{1,12.25}}, npml 20, "
                                    f"{'Schwarz-NNO FGMRES(30)' if precond == F.PRECOND_SCHWARZ else 'Jacobi-GMRES(30)'}",
                        "grid": n, "precond": args.precond, "k_coarse": kc if precond == F.PRECOND_SCHWARZ else None,
+                       "inner_iters": args.inner if precond == F.PRECOND_SCHWARZ else None,
+                       "weights": wsrc if precond == F.PRECOND_SCHWARZ else None,
+                       "setup_s": t_setup if precond == F.PRECOND_SCHWARZ else None,
                        "nno_precision": prec_nno if precond == F.PRECOND_SCHWARZ else None,
                        "l2": "inputs larger than L2 (each Krylov vector 134 MB; V, Z 8 GB)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "profile_ms": cls_ms, "gpu_launches": prof["total_launches"],
+            "roofline": roof, "rooflines": roofs, "gpu_launches": prof["total_launches"],
             "e2e": {"value": e2e_value, "unit": "Mcell-it/s", "h2d_bytes_per_step": N * 8 // args.steps,
                     "d2h_bytes_per_step": N * 8 // args.steps},
             "clocks": clk.summary(), "relres_after_steps": st["relres_true"]}

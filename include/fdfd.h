@@ -77,7 +77,8 @@ typedef struct {
 /* Two-level Schwarz set-up (Sec. 2.2, Methods, Algorithm 3 set-up). */
 typedef struct {
   int k_coarse;          /* coarse basis vectors per window; 0 = one-level */
-  int precision;         /* FDFD_PREC_BF16 or FDFD_PREC_FP8 neural operator */
+  int precision;         /* FDFD_PREC_BF16 (FDFD_PREC_FP8 is reserved and
+                            currently rejected with FDFD_EINVAL)            */
   const float* weights;  /* HOST ptr to the FNO weight blob, float32, in the
                             order: lift_w[32][15], lift_b[32], then per block
                             b = 0..3: R_re[32][32][32][16], R_im[...],
@@ -86,6 +87,11 @@ typedef struct {
                             [out][in][ky][kx] with ky rows 0..15 = modes
                             0..15 and rows 16..31 = modes -16..-1.          */
   size_t n_weights;      /* number of floats in the blob (4,199,442)       */
+  int inner_iters;       /* local solver of each window (Algorithm 3's
+                            M.solve): 0 = one neural-operator application
+                            with the residual and Robin data as inputs;
+                            m in 1..16 = m steps of NN-preconditioned FGMRES
+                            (Algorithm 1) on the window's Robin problem     */
 } schwarz_desc;
 
 typedef struct {
@@ -164,11 +170,13 @@ int  fdfd_grad_eps(fdfd_handle h, const fdfd_c64* E_dev, const fdfd_c64* lam_dev
                    float* grad_dev, int accumulate);
 
 /* ---- live profiling (CUDA events on the handle's stream) -------------- */
-#define FDFD_PROF_NCLASS 8
+#define FDFD_PROF_NCLASS 16
 /* kernel classes: 0 stencil A~x (incl. the fused Jacobi form), 1 CGS dots,
  * 2 CGS update + Givens, 3 FP64 residual, 4 solution update / misc vector,
- * 5 neural operator (all its kernels), 6 partition (restrict, prolong,
- * traces), 7 coarse space (solve and correction). */
+ * 5 neural-operator pack (restriction + inputs), 6 traces, 7 coarse solve
+ * and correction, 8 lift GEMM, 9 DFT-x GEMM, 10 DFT-y GEMM, 11 spectral
+ * mix GEMM, 12 inverse DFT-y GEMM, 13 fused inverse DFT-x + mixer +
+ * activation, 14 projection + prolongation GEMM, 15 unused. */
 typedef struct {
   double ms[FDFD_PROF_NCLASS];        /* summed device time per class      */
   long long launches[FDFD_PROF_NCLASS];/* kernel launches per class        */
@@ -199,6 +207,12 @@ int  fdfd_precond_apply(fdfd_handle h, const fdfd_c64* v, fdfd_c64* z);
  * uses; writes e_win [n][80][80].  Requires schwarz_setup. */
 int  fdfd_nno_solve(fdfd_handle h, const fdfd_c64* r_win, const fdfd_c64* g_win,
                     const int* win_id, int n, fdfd_c64* e_win);
+
+/* Local Robin operator (Eq. 1 restricted to a window, Eq. 2 on its interface
+ * sides with zero Robin data, zero ghosts on grid-edge sides): y = A_w x for
+ * n windows; x, y device [n][80][80], win_id device int [n].  Does not need
+ * schwarz_setup. */
+int  fdfd_local_apply(fdfd_handle h, const fdfd_c64* x_win, fdfd_c64* y_win, const int* win_id, int n);
 
 /* Robin traces g = u_o - u_b + j (k0 dx) sqrt(eps_b) u_b (Eq. 2, dx-scaled)
  * of a global field on every window's interface sides: g [n_win][4][80],

@@ -22,14 +22,19 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import fdfd, nno
+from . import fdfd, krylov, nno
 from .partition import Windows, restrict, prolong, traces, local_operator, local_rhs, WIN
 from .coarse import CoarseSpace
 
 
 class Schwarz:
     def __init__(self, eps, dx, wavelength, npml, weights=None, k_coarse: int = 0,
-                 local: str = "nno"):
+                 local: str = "nno", inner: int = 0):
+        """local = "nno": neural local solves -- one application of the
+        network to (residual, Robin data) when inner = 0, else `inner` steps
+        of NN-preconditioned FGMRES (Algorithm 1) on the window's Robin
+        problem; local = "exact": SuperLU local solves."""
+        self.inner = inner
         ny, nx = eps.shape
         self.eps = np.asarray(eps, dtype=np.float32)
         self.dx, self.wavelength = dx, wavelength
@@ -41,10 +46,11 @@ class Schwarz:
         self.weights = weights
         self.local = local
         self._lu = None
-        if local == "exact":
-            import scipy.sparse.linalg as spla
+        if local == "exact" or inner > 0:
             self._ops = [local_operator(self.win, w, self.A, self.eps, dx, wavelength)
                          for w in range(self.win.n)]
+        if local == "exact":
+            import scipy.sparse.linalg as spla
             self._lu = [spla.splu(op.tocsc()) for op, _ in self._ops]
         self.coarse = None
         if k_coarse > 0:
@@ -63,6 +69,16 @@ class Schwarz:
             if self.local == "exact":
                 rhs = local_rhs(r_loc[w], g_loc[w], self._ops[w][1])
                 out[w] = self._lu[w].solve(rhs).reshape(WIN, WIN)
+            elif self.inner > 0:
+                Aw, bnd = self._ops[w]
+                rhs = local_rhs(r_loc[w], g_loc[w], bnd)
+                k2e, isx, isy = self.aux(w)
+                zero_g = np.zeros((4, WIN))
+                M = lambda v, k2e=k2e, isx=isx, isy=isy: nno.solve(
+                    v.reshape(WIN, WIN), zero_g, k2e, isx, isy, self.weights).ravel()
+                x, _ = krylov.fgmres(lambda u, Aw=Aw: Aw @ u, rhs, precond=M, restart=self.inner,
+                                     tol=0.0, max_iters=self.inner)
+                out[w] = x.reshape(WIN, WIN)
             else:
                 k2e, isx, isy = self.aux(w)
                 out[w] = nno.solve(r_loc[w], g_loc[w], k2e, isx, isy, self.weights)

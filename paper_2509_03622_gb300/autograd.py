@@ -1,0 +1,55 @@
+"""Differentiable solve for inverse design (Sec. 2.2, adjoint variable method).
+
+`fdfd_field(solver, eps, J, ...)` returns E = A~(eps)^-1 b~(J) from the
+library's FGMRES solve and, on backward, runs the library's adjoint solve on
+A~^T with the same preconditioner and its dF/deps kernel; nothing of the
+solve is traced by autograd (implicit differentiation, as the paper does to
+keep the graph small for large problems).
+
+Gradient convention: for a real loss L of the complex field E, PyTorch hands
+backward grad_E = 2 conj(dL/dE) (conjugate Wirtinger, doubled).  With
+g = dL/dE = conj(grad_E)/2 and A~^T lam = g,
+    dL/deps_p = 2 Re(g . dE/deps_p) = -2 Re(lam_p (k0 dx)^2 E_p),
+which is exactly what fdfd_grad_eps computes.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import fdfd as F
+
+
+class _FieldSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, eps, J, solver, weights, opts):
+        solver.set_eps(eps.detach().contiguous())
+        if opts.get("precond", F.PRECOND_SCHWARZ) == F.PRECOND_SCHWARZ:
+            solver.schwarz_setup(weights, k_coarse=opts.get("k_coarse", 0), inner_iters=opts.get("inner", 0))
+        E = torch.zeros(J.shape, dtype=torch.complex64, device=J.device)
+        kw = {k: v for k, v in opts.items() if k in ("restart", "max_iters", "tol", "precond")}
+        rc, st = solver.solve(J, E, **kw)
+        ctx.solver, ctx.kw, ctx.stats = solver, kw, st
+        ctx.save_for_backward(E)
+        return E
+
+    @staticmethod
+    def backward(ctx, grad_E):
+        (E,) = ctx.saved_tensors
+        g = (grad_E.conj() * 0.5).to(torch.complex64).contiguous()
+        lam = torch.zeros_like(E)
+        ctx.solver.solve_adjoint(g, lam, **ctx.kw)
+        grad = torch.empty(E.shape, dtype=torch.float32, device=E.device)
+        ctx.solver.grad_eps(E, lam, grad)
+        return grad, None, None, None, None
+
+
+def fdfd_field(solver: "F.Solver", eps: torch.Tensor, J: torch.Tensor, weights=None, **opts) -> torch.Tensor:
+    """Field of the current density J in the permittivity eps (float32 CUDA
+    tensor, may require grad).  opts: restart, max_iters, tol, precond,
+    k_coarse, inner (Schwarz set-up is redone for every new eps)."""
+    return _FieldSolve.apply(eps, J, solver, weights, opts)
+
+
+def mode_overlap(E: torch.Tensor, port_x: int, mode: torch.Tensor, y0: int, dx: float) -> torch.Tensor:
+    """c = sum_port conj(m) E dx along the vertical line x = port_x."""
+    return torch.sum(torch.conj(mode) * E[y0:y0 + mode.numel(), port_x]) * dx

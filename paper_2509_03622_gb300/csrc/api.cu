@@ -12,6 +12,7 @@
 #include <complex>
 #include "ctx.cuh"
 #include "nno.cuh"
+#include "local.cuh"
 
 namespace {
 
@@ -425,6 +426,15 @@ int fdfd_nno_solve(fdfd_handle h, const fdfd_c64* r_win, const fdfd_c64* g_win, 
   if (!h->sw) return FDFD_ENOSETUP;
   int rc = schwarz_nno_solve(h, reinterpret_cast<const float2*>(r_win), reinterpret_cast<const float2*>(g_win),
                              win_id, n, reinterpret_cast<float2*>(e_win));
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return FDFD_OK;
+}
+
+int fdfd_local_apply(fdfd_handle h, const fdfd_c64* x, fdfd_c64* y, const int* win_id, int n) {
+  if (!h || !x || !y || !win_id || n < 0) return FDFD_EINVAL;
+  if (n == 0) return FDFD_OK;
+  int rc = local_apply_windows(h, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), win_id, n);
   if (rc) return rc;
   CK(cudaStreamSynchronize(h->stream));
   return FDFD_OK;

@@ -12,6 +12,7 @@
 #include <math.h>
 #include "ctx.cuh"
 #include "nno.cuh"
+#include "local.cuh"
 #include "reduce.cuh"
 
 struct CoarseData {
@@ -310,7 +311,8 @@ void coarse_free(CoarseData* c) {
   delete c;
 }
 
-int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, int k, CoarseData** out, size_t* bytes) {
+int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, int k, CoarseData** out,
+                 size_t* bytes) {
   const int nwx = h->nx / FDFD_CORE, nwy = h->ny / FDFD_CORE, n_win = nwx * nwy;
   const int nc = n_win * k;
   if (k < 1 || k > 256 || (size_t)nc * nc * 16 > ((size_t)16 << 30)) return FDFD_EINVAL;
@@ -330,15 +332,26 @@ int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, int k, CoarseD
   trials_gs_kernel<<<n_win, 256, 0, s>>>(c->Q, c->Qf, k, h->eps, h->k0dx, h->nx, h->ny, nwx, n_win);
   CKL();
   GridGeom g{h->nx, h->ny, nwx, (float)h->k2, h->eps, h->isx, h->isy};
+  float2* rhs = nullptr;
+  if (L && (rc = ca(&rhs, (size_t)n_win * 6400, bytes))) { coarse_free(c); return rc; }
   for (int m = 0; m < k; ++m) {
-    NnoInput in;
-    in.g_win = c->Qf + (size_t)m * n_win * 320;
-    NnoOutput o;
-    o.e_win = c->tmp;
-    if ((rc = nno_forward(W, work, g, in, o, n_win, s))) { coarse_free(c); return rc; }
+    const float2* qm = c->Qf + (size_t)m * n_win * 320;
+    if (L) {  // homogeneous Robin problem solved by the local NN-FGMRES
+      if ((rc = local_robin_rhs(h, qm, rhs, n_win)) ||
+          (rc = local_fgmres(h, L, W, work, nullptr, rhs, nullptr, c->tmp, nullptr))) {
+        cudaFree(rhs); coarse_free(c); return rc;
+      }
+    } else {  // one neural application with the Robin data as input
+      NnoInput in;
+      in.g_win = qm;
+      NnoOutput o;
+      o.e_win = c->tmp;
+      if ((rc = nno_forward(W, work, g, in, o, n_win, s))) { cudaFree(rhs); coarse_free(c); return rc; }
+    }
     copy_core_kernel<<<n_win, 256, 0, s>>>(c->tmp, c->Phi, m, k, h->nx, h->ny, nwx, n_win);
     CKL();
   }
+  if (rhs) { cudaStreamSynchronize(s); cudaFree(rhs); *bytes -= (size_t)n_win * 6400 * sizeof(float2); }
   assemble_C_kernel<<<dim3(n_win, 9), 256, 0, s>>>(c->C, c->Q, c->Phi, k, h->eps, h->k0dx, h->nx, h->ny, nwx, nwy);
   CKL();
   if (cudaMemsetAsync(c->N, 0, (size_t)nc * nc * sizeof(double2), s) != cudaSuccess) { coarse_free(c); return FDFD_ECUDA; }
@@ -363,7 +376,11 @@ int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u) {
   const int nwx = h->nx / FDFD_CORE, nwy = h->ny / FDFD_CORE, n_win = nwx * nwy;
   cudaStream_t s = h->stream;
   int rc;
-  if ((rc = schwarz_traces(h, u, c->ebc))) return rc;
+  {
+    ProfScope ps(h, 6, 1);
+    if ((rc = schwarz_traces(h, u, c->ebc))) return rc;
+  }
+  ProfScope ps(h, 7, 3);
   coarse_rhs_kernel<<<n_win, 64, 0, s>>>(c->rc, c->C, c->ebc, c->k, nwx, nwy);
   gemv_kernel<<<(c->nc + 7) / 8, 256, 0, s>>>(c->zc, c->N, c->rc, c->dropped, c->nc);
   correction_kernel<<<dim3(4096 / 256, n_win), 256, 0, s>>>(u, c->Phi, c->zc, c->k, h->nx, nwx);

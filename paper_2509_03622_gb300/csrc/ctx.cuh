@@ -42,6 +42,7 @@ struct fdfd_ctx {
 struct ProfScope {
   fdfd_ctx* h; int cls; int slot;
   ProfScope(fdfd_ctx* h_, int cls_, int nk) : h(h_), cls(cls_), slot(-1) {
+    if (!h) return;
     h->launches_total += nk;
     if (!h->prof_on) return;
     h->prof_launch[cls] += nk;

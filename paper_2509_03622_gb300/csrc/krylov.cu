@@ -36,10 +36,25 @@ cgs_dots_kernel(const float4* __restrict__ V, size_t ld4, int v0, int nv, const 
       }
     }
   }
-  for (int i = 0; i < nv; ++i) {
-    const double tr = block_sum<KT>((double)ar[i], sh);
-    const double ti = block_sum<KT>((double)ai[i], sh);
-    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * FDFD_MAXRESTART + i] = make_double2(tr, ti);
+  // warp sums (FP64) of all nv accumulators, then one pass over the 8 warps
+  __shared__ double2 wsum[KT / 32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    if (i < nv) {
+      double tr = (double)ar[i], ti = (double)ai[i];
+      for (int o = 16; o > 0; o >>= 1) {
+        tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        ti += __shfl_xor_sync(0xffffffffu, ti, o);
+      }
+      if (lane == 0) wsum[wid][i] = make_double2(tr, ti);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double tr = 0.0, ti = 0.0;
+    for (int q = 0; q < KT / 32; ++q) { tr += wsum[q][threadIdx.x].x; ti += wsum[q][threadIdx.x].y; }
+    partials[(size_t)blockIdx.x * FDFD_MAXRESTART + threadIdx.x] = make_double2(tr, ti);
   }
   if (last_block(counter)) {
     const int nb = gridDim.x;

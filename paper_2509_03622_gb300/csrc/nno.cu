@@ -20,6 +20,7 @@
 #include <string.h>
 #include <vector>
 #include "nno.cuh"
+#include "ctx.cuh"
 #include "tc.cuh"
 #include "reduce.cuh"
 
@@ -57,27 +58,27 @@ __global__ void __launch_bounds__(128) gemm_kernel(Op op, int* err) {
   const int b = blockIdx.y;
   const int m0 = blockIdx.x * 128;
   const int Mb = op.rows(b);
-  const uint4 z4 = make_uint4(0, 0, 0, 0);
-  // ---- operand loads (global -> canonical smem tiles) ----
+  // ---- operand loads (global -> canonical smem tiles), all in flight ----
   if (!AMN) {
     for (int c = tid; c < 128 * KC; c += 128) {
       const int t8 = c & 7, rest = c >> 3, kc = rest % KC, rg = rest / KC;
       const int m = m0 + rg * 8 + t8;
-      const uint4 v = (m < Mb) ? __ldg(op.a_src(b, m, kc * 8)) : z4;
-      *reinterpret_cast<uint4*>(sA + (rg * KC + kc) * 128 + t8 * 16) = v;
+      const bool ok = m < Mb;
+      tc::cp_async16(sA + (rg * KC + kc) * 128 + t8 * 16, op.a_src(b, ok ? m : 0, kc * 8), ok);
     }
   } else {
     for (int c = tid; c < 16 * K; c += 128) {
       const int t8 = c & 7, rest = c >> 3, mg = rest & 15, kg = rest >> 4;
       const int m = m0 + mg * 8;
-      const uint4 v = (m < Mb) ? __ldg(op.a_src(b, m, kg * 8 + t8)) : z4;
-      *reinterpret_cast<uint4*>(sA + (mg * KC + kg) * 128 + t8 * 16) = v;
+      const bool ok = m < Mb;
+      tc::cp_async16(sA + (mg * KC + kg) * 128 + t8 * 16, op.a_src(b, ok ? m : 0, kg * 8 + t8), ok);
     }
   }
   for (int c = tid; c < BN * KC; c += 128) {
     const int t8 = c & 7, rest = c >> 3, kc = rest % KC, rg = rest / KC;
-    *reinterpret_cast<uint4*>(sB + (rg * KC + kc) * 128 + t8 * 16) = __ldg(op.b_src(b, rg * 8 + t8, kc * 8));
+    tc::cp_async16(sB + (rg * KC + kc) * 128 + t8 * 16, op.b_src(b, rg * 8 + t8, kc * 8), true);
   }
+  tc::cp_async_wait_all();
   if (tid == 0) tc::mbar_init(tc::smem_u32(mbar), 1);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), TCOLS);
   tc::fence_async_smem();
@@ -245,6 +246,7 @@ struct ProjOp {  // rows = pixels, K = 32, N = 128 hidden; then 128 -> 2 and the
   const bf16* X; const bf16* P1; const float* p1b; const float* P2; float p2b0, p2b1;
   const float* rho; const double* scale; const int* win_id;
   float2* z_global; float2* e_win; int nx, nwx;
+  const double* scale_win;
   struct State { float re, im; };
   __device__ int rows(int) const { return NPIX; }
   __device__ const uint4* a_src(int b, int m, int k) const {
@@ -263,6 +265,7 @@ struct ProjOp {  // rows = pixels, K = 32, N = 128 hidden; then 128 -> 2 and the
   __device__ void epi_end(int b, int m, State& s) const {
     float f = rho[b];
     if (scale) f *= (float)(*scale);
+    if (scale_win) f *= (float)scale_win[b];
     const float2 o = make_float2((s.re + p2b0) * f, (s.im + p2b1) * f);
     if (e_win) { e_win[(size_t)b * NPIX + m] = o; return; }
     const int w = win_id ? win_id[b] : b;
@@ -300,18 +303,15 @@ __global__ void __launch_bounds__(128) g5_kernel(bf16* X, const bf16* T3, const 
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sBw + 2048 + 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.y, y0 = blockIdx.x * G5_ROWS;
-  const uint4 z4 = make_uint4(0, 0, 0, 0);
   // Gx (rows >= 80 are zero in global) and W
   for (int c = tid; c < 128 * 4; c += 128) {
     const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-    *reinterpret_cast<uint4*>(sAg + (rg * 4 + kc) * 128 + t8 * 16) =
-        __ldg(reinterpret_cast<const uint4*>(Gx + (rg * 8 + t8) * 32 + kc * 8));
+    tc::cp_async16(sAg + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
   }
   {
     const int c = tid;  // 32 rows x 4 chunks = 128
     const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-    *reinterpret_cast<uint4*>(sBw + (rg * 4 + kc) * 128 + t8 * 16) =
-        __ldg(reinterpret_cast<const uint4*>(Wb + (rg * 8 + t8) * 32 + kc * 8));
+    tc::cp_async16(sBw + (rg * 4 + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * 32 + kc * 8, true);
   }
   for (int yy = 0; yy < G5_ROWS; ++yy) {
     const int y = y0 + yy;
@@ -319,15 +319,17 @@ __global__ void __launch_bounds__(128) g5_kernel(bf16* X, const bf16* T3, const 
     for (int c = tid; c < 128 * 4; c += 128) {
       const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
       const int x = rg * 8 + t8;
-      const uint4 v = x < 80 ? __ldg(reinterpret_cast<const uint4*>(X + (((size_t)b * 80 + y) * 80 + x) * 32 + kc * 8)) : z4;
-      *reinterpret_cast<uint4*>(ax + (rg * 4 + kc) * 128 + t8 * 16) = v;
+      const bool ok = x < 80;
+      tc::cp_async16(ax + (rg * 4 + kc) * 128 + t8 * 16,
+                     X + (((size_t)b * 80 + y) * 80 + (ok ? x : 0)) * 32 + kc * 8, ok);
     }
     {
       const int c = tid, t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-      *reinterpret_cast<uint4*>(sBt + yy * 2048 + (rg * 4 + kc) * 128 + t8 * 16) =
-          __ldg(reinterpret_cast<const uint4*>(T3 + (((size_t)b * 80 + y) * 32 + rg * 8 + t8) * 32 + kc * 8));
+      tc::cp_async16(sBt + yy * 2048 + (rg * 4 + kc) * 128 + t8 * 16,
+                     T3 + (((size_t)b * 80 + y) * 32 + rg * 8 + t8) * 32 + kc * 8, true);
     }
   }
+  tc::cp_async_wait_all();
   if (tid == 0) tc::mbar_init(tc::smem_u32(mbar), 1);
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 256);
   tc::fence_async_smem();
@@ -579,31 +581,55 @@ void nno_free_work(NnoWork* w) {
 }
 
 int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInput& in, const NnoOutput& out,
-                int n, cudaStream_t s) {
+                int n, cudaStream_t s, fdfd_ctx* h) {
   if (n <= 0) return FDFD_OK;
   if (n > k->cap) return FDFD_EINVAL;
   int rc;
-  pack_kernel<<<n, 256, 0, s>>>(in, g, k->in, k->rho);
-  CKL();
-  if ((rc = launch_gemm<32, 16, false>(LiftOp{k->in, W->lift_w, W->lift_b, k->X}, NPIX / 128, n, k->err, s))) return rc;
+  {
+    ProfScope ps(h, 5, 1);
+    pack_kernel<<<n, 256, 0, s>>>(in, g, k->in, k->rho);
+    CKL();
+  }
+  {
+    ProfScope ps(h, 8, 1);
+    if ((rc = launch_gemm<32, 16, false>(LiftOp{k->in, W->lift_w, W->lift_b, k->X}, NPIX / 128, n, k->err, s))) return rc;
+  }
   static bool g5_attr = false;
   if (!g5_attr) {
     CK(cudaFuncSetAttribute(g5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
     g5_attr = true;
   }
   for (int bl = 0; bl < 4; ++bl) {
-    if ((rc = launch_gemm<32, 80, true>(G1Op{k->X, W->Fx, k->T1}, 2560 / 128, n, k->err, s))) return rc;
-    if ((rc = launch_gemm<64, 160, true>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s))) return rc;
-    if ((rc = launch_gemm<64, 64, false>(G3Op{k->Xh, W->R[bl], k->Yh, k->cap, n}, (n + 127) / 128, 512, k->err, s)))
-      return rc;
-    if ((rc = launch_gemm<160, 64, false>(G4Op{k->Yh, W->Gy, k->T3}, 512 / 128, n, k->err, s))) return rc;
-    g5_kernel<<<dim3(80 / G5_ROWS, n), 128, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], bl == 3, k->err);
-    CKL();
+    {
+      ProfScope ps(h, 9, 1);
+      if ((rc = launch_gemm<32, 80, true>(G1Op{k->X, W->Fx, k->T1}, 2560 / 128, n, k->err, s))) return rc;
+    }
+    {
+      ProfScope ps(h, 10, 1);
+      if ((rc = launch_gemm<64, 160, true>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s))) return rc;
+    }
+    {
+      ProfScope ps(h, 11, 1);
+      if ((rc = launch_gemm<64, 64, false>(G3Op{k->Xh, W->R[bl], k->Yh, k->cap, n}, (n + 127) / 128, 512, k->err, s)))
+        return rc;
+    }
+    {
+      ProfScope ps(h, 12, 1);
+      if ((rc = launch_gemm<160, 64, false>(G4Op{k->Yh, W->Gy, k->T3}, 512 / 128, n, k->err, s))) return rc;
+    }
+    {
+      ProfScope ps(h, 13, 1);
+      g5_kernel<<<dim3(80 / G5_ROWS, n), 128, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], bl == 3, k->err);
+      CKL();
+    }
   }
   ProjOp po{k->X, W->P1, W->p1b, W->P2, W->p2b[0], W->p2b[1], k->rho, out.scale, in.win_id,
-            out.z_global, out.e_win, g.nx, g.nwx};
+            out.z_global, out.e_win, g.nx, g.nwx, out.scale_win};
   po.ny_ = g.ny;
-  if ((rc = launch_gemm<128, 32, false>(po, NPIX / 128, n, k->err, s))) return rc;
+  {
+    ProfScope ps(h, 14, 1);
+    if ((rc = launch_gemm<128, 32, false>(po, NPIX / 128, n, k->err, s))) return rc;
+  }
   return FDFD_OK;
 }
 

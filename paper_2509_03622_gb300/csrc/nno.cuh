@@ -45,6 +45,7 @@ struct NnoOutput {
   float2* z_global = nullptr;        // restricted prolongation into a global field, or
   float2* e_win = nullptr;           // per-window fields [n][80][80]
   const double* scale = nullptr;     // multiply by *scale (nullptr = 1)
+  const double* scale_win = nullptr; // and by scale_win[b] per batch entry (nullptr = 1)
 };
 
 struct GridGeom {
@@ -59,9 +60,11 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
 void nno_free_weights(NnoWeights* W);
 int nno_alloc_work(NnoWork* w, int cap, size_t* bytes);
 void nno_free_work(NnoWork* w);
-// Run the neural operator on n windows (n <= work->cap).
+struct fdfd_ctx;
+// Run the neural operator on n windows (n <= work->cap); h (nullable) only
+// receives the per-stage profiling scopes.
 int nno_forward(const NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInput& in,
-                const NnoOutput& out, int n, cudaStream_t s);
+                const NnoOutput& out, int n, cudaStream_t s, fdfd_ctx* h = nullptr);
 // Direct access to the tcgen05 GEMM for self-tests: C[M][N] (fp32) =
 // A[M][K] . B[N][K]^T with A K-major (a_mn = 0, row stride K) or MN-major
 // (a_mn = 1, stored [K][M]); supported (N, K): (32,80) (64,160) (64,64)

@@ -2,17 +2,20 @@
 // guess): partition kernels, neural local solves and the coarse space.
 #include "ctx.cuh"
 #include "nno.cuh"
+#include "local.cuh"
 
 struct CoarseData;
 void coarse_free(CoarseData* c);
-int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, int k, CoarseData** out, size_t* bytes);
+int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, int k, CoarseData** out,
+                 size_t* bytes);
 int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u);
 int coarse_export(fdfd_ctx* h, CoarseData* c, double* Qh, double* Ndh);
 
 struct SchwarzData {
-  int k = 0, n_win = 0, nwx = 0, precision = 0;
+  int k = 0, n_win = 0, nwx = 0, precision = 0, inner = 0;
   NnoWeights W;
   NnoWork work;
+  LocalWork local;
   CoarseData* coarse = nullptr;
   size_t bytes = 0;
 };
@@ -67,17 +70,21 @@ static int check_err(fdfd_ctx* h) {
 
 int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd) {
   if (sd->k_coarse < 0 || sd->k_coarse > 256) return FDFD_EINVAL;
-  if (sd->precision != FDFD_PREC_BF16 && sd->precision != FDFD_PREC_FP8) return FDFD_EINVAL;
+  if (sd->precision != FDFD_PREC_BF16) return FDFD_EINVAL;  // the FP8 operator is not built
+  if (sd->inner_iters < 0 || sd->inner_iters > LOCAL_MAXM) return FDFD_EINVAL;
   SchwarzData* S = new SchwarzData();
   S->nwx = h->nx / FDFD_CORE;
   S->n_win = S->nwx * (h->ny / FDFD_CORE);
   S->precision = sd->precision;
+  S->inner = sd->inner_iters;
   int rc = nno_upload_weights(&S->W, sd->weights, sd->n_weights, &S->bytes);
   if (!rc) rc = nno_alloc_work(&S->work, S->n_win < 64 ? 64 : S->n_win, &S->bytes);
+  if (!rc && S->inner > 0) rc = local_alloc(&S->local, S->n_win, S->inner, &S->bytes);
   h->sw = S;
   if (!rc && sd->k_coarse > 0) {
     S->k = sd->k_coarse;
-    rc = coarse_setup(h, &S->W, &S->work, sd->k_coarse, &S->coarse, &S->bytes);
+    rc = coarse_setup(h, &S->W, &S->work, S->inner > 0 ? &S->local : nullptr, sd->k_coarse, &S->coarse,
+                      &S->bytes);
     if (!rc) rc = check_err(h);
   }
   if (rc) { schwarz_destroy(h); return rc; }
@@ -92,6 +99,7 @@ void schwarz_destroy(fdfd_ctx* h) {
   if (S->coarse) coarse_free(S->coarse);
   nno_free_weights(&S->W);
   nno_free_work(&S->work);
+  local_free(&S->local);
   h->bytes -= (h->bytes >= S->bytes ? S->bytes : h->bytes);
   delete S;
   h->sw = nullptr;
@@ -105,12 +113,12 @@ int schwarz_apply(fdfd_ctx* h, const float2* v, const double* scale_dev, float2*
   out.z_global = z;
   out.scale = scale_dev;
   int rc;
-  {
-    ProfScope ps(h, 5, 23);
-    if ((rc = nno_forward(&S->W, &S->work, geom(h), in, out, S->n_win, h->stream))) return rc;
-  }
+  if (S->inner > 0)
+    rc = local_fgmres(h, &S->local, &S->W, &S->work, v, nullptr, z, nullptr, scale_dev);
+  else
+    rc = nno_forward(&S->W, &S->work, geom(h), in, out, S->n_win, h->stream, h);
+  if (rc) return rc;
   if (S->coarse) {
-    ProfScope ps(h, 7, 4);
     if ((rc = coarse_apply(h, S->coarse, z))) return rc;
   }
   return FDFD_OK;

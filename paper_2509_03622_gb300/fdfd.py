@@ -35,7 +35,7 @@ class Desc(C.Structure):
 
 class SchwarzDesc(C.Structure):
     _fields_ = [("k_coarse", C.c_int), ("precision", C.c_int), ("weights", C.c_void_p),
-                ("n_weights", C.c_size_t)]
+                ("n_weights", C.c_size_t), ("inner_iters", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -57,10 +57,12 @@ class Info(C.Structure):
 
 
 class Profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_longlong * 8), ("total_launches", C.c_longlong)]
+    _fields_ = [("ms", C.c_double * 16), ("launches", C.c_longlong * 16), ("total_launches", C.c_longlong)]
 
 
-PROF_CLASSES = ["stencil", "cgs_dots", "cgs_update", "residual64", "vector_misc", "nno", "partition", "coarse"]
+PROF_CLASSES = ["stencil", "cgs_dots", "cgs_update", "residual64", "vector_misc", "nno_pack", "traces", "coarse",
+                "nno_lift", "nno_dft_x", "nno_dft_y", "nno_mix", "nno_idft_y", "nno_idft_x_mix_act", "nno_proj",
+                "unused"]
 
 _P = C.c_void_p
 _SIGS = {
@@ -78,6 +80,7 @@ _SIGS = {
     "fdfd_precond_apply": ([_P, _P, _P], C.c_int),
     "fdfd_nno_solve": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "fdfd_trace_extract": ([_P, _P, _P], C.c_int),
+    "fdfd_local_apply": ([_P, _P, _P, _P, C.c_int], C.c_int),
     "fdfd_coarse_export": ([_P, _P, _P], C.c_int),
     "fdfd_profile_start": ([_P], C.c_int),
     "fdfd_selftest_gemm": ([_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
@@ -165,10 +168,11 @@ class Solver:
     def set_eps(self, eps):
         _check(lib.fdfd_set_eps(self.h, _ptr(eps)), "fdfd_set_eps")
 
-    def schwarz_setup(self, weights_blob: np.ndarray, k_coarse: int = 0, precision: int = PREC_BF16):
+    def schwarz_setup(self, weights_blob: np.ndarray, k_coarse: int = 0, precision: int = PREC_BF16,
+                      inner_iters: int = 0):
         blob = np.ascontiguousarray(weights_blob, dtype=np.float32)
         sd = SchwarzDesc()
-        sd.k_coarse, sd.precision = k_coarse, precision
+        sd.k_coarse, sd.precision, sd.inner_iters = k_coarse, precision, inner_iters
         sd.weights = blob.ctypes.data
         sd.n_weights = blob.size
         _check(lib.schwarz_setup(self.h, C.byref(sd)), "schwarz_setup")
@@ -215,6 +219,10 @@ class Solver:
         n = r_win.shape[0]
         _check(lib.fdfd_nno_solve(self.h, _ptr(r_win), _ptr(g_win), _ptr(win_id), n, _ptr(e_win)),
                "fdfd_nno_solve")
+
+    def local_apply(self, x_win, y_win, win_id):
+        _check(lib.fdfd_local_apply(self.h, _ptr(x_win), _ptr(y_win), _ptr(win_id), x_win.shape[0]),
+               "fdfd_local_apply")
 
     def trace_extract(self, u, g):
         _check(lib.fdfd_trace_extract(self.h, _ptr(u), _ptr(g)), "fdfd_trace_extract")

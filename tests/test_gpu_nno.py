@@ -117,3 +117,41 @@ def test_precond_is_positively_homogeneous(F):
     S.precond_apply(_t(4 * v), z2)
     a, b = z1.cpu().numpy(), z2.cpu().numpy()
     assert np.linalg.norm(b - 4 * a) / np.linalg.norm(4 * a) < 1e-5
+
+
+def test_local_operator_matches_oracle(F):
+    """K2: the window Robin operator A_w (Eq. 1-2) on a batch of windows."""
+    import torch
+    S, eps, dx, w = _setup(F)
+    n = 256
+    win = OP.Windows(n, n)
+    A = OF.assemble_operator(eps, dx, LAM, 20)
+    ids = np.array([0, 5, 15, 2], dtype=np.int32)
+    x = np.stack([wl.random_field(80, 80, 20 + i) for i in range(len(ids))])
+    y = torch.empty((len(ids), 80, 80), dtype=torch.complex64, device="cuda")
+    S.local_apply(_t(x), y, _t(ids))
+    got = y.cpu().numpy()
+    for i, wi in enumerate(ids):
+        Aw, _ = OP.local_operator(win, wi, A, eps, dx, LAM)
+        ref = (Aw @ x[i].astype(complex).ravel()).reshape(80, 80)
+        assert np.linalg.norm(got[i] - ref) / np.linalg.norm(ref) < 1e-6
+
+
+@pytest.mark.parametrize("k", [0, 4])
+def test_precond_with_inner_fgmres_matches_oracle(F, k):
+    """Local solves by 2 steps of NN-preconditioned FGMRES (Algorithm 1) per
+    window, inside the (two-level) sweep."""
+    import torch
+    n = 256
+    dx = LAM / 25
+    eps = wl.rectangles_eps(n, n, seed=1000)
+    S = F.Solver(_t(eps), dx, LAM, npml=20)
+    w = wl.nno_weights(1)
+    S.schwarz_setup(wl.pack_weights(w), k_coarse=k, inner_iters=2)
+    O = OS.Schwarz(eps, dx, LAM, 20, weights=w, k_coarse=k, inner=2)
+    v = wl.random_field(n, n, 12)
+    z = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    S.precond_apply(_t(v), z)
+    ref = O.apply(v.astype(np.complex128))
+    err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < 2 * BF16_TOL, err
