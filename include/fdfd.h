@@ -208,6 +208,27 @@ int  fdfd_precond_apply(fdfd_handle h, const fdfd_c64* v, fdfd_c64* z);
 int  fdfd_nno_solve(fdfd_handle h, const fdfd_c64* r_win, const fdfd_c64* g_win,
                     const int* win_id, int n, fdfd_c64* e_win);
 
+/* fdfd_nno_solve for callers that cannot allocate device memory (the paper
+ * has no counterpart: this is an interface convenience).  Such callers are,
+ * for example, code that runs while a CUDA graph is being captured (a
+ * cudaMalloc cannot be captured), code that must stay within a memory pool
+ * it manages itself, or a latency-bound loop that cannot pay for an
+ * allocation's implicit device-wide synchronisation.  Same arguments and
+ * results as fdfd_nno_solve, but the neural operator's intermediates live in
+ * one fixed device array inside the library (about 4.3 MB, held by every
+ * GPU that loads the library until the process exits) instead of the
+ * handle's workspace, and the call allocates nothing.
+ *   - n must be <= 4 windows; larger n returns FDFD_EINVAL (with a message on
+ *     stderr) and does nothing.
+ *   - The first call on a device looks the array's device address up once;
+ *     make that first call before any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (from
+ *     several streams, threads or handles) race and corrupt each other's
+ *     results.  Serialise them.
+ *   - Requires schwarz_setup on h (FDFD_ENOSETUP otherwise); synchronous. */
+int  fdfd_nno_solve_noalloc(fdfd_handle h, const fdfd_c64* r_win, const fdfd_c64* g_win,
+                            const int* win_id, int n, fdfd_c64* e_win);
+
 /* Local Robin operator (Eq. 1 restricted to a window, Eq. 2 on its interface
  * sides with zero Robin data, zero ghosts on grid-edge sides): y = A_w x for
  * n windows; x, y device [n][80][80], win_id device int [n].  Does not need

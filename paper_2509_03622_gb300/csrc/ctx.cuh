@@ -64,4 +64,6 @@ int schwarz_nno_solve(fdfd_ctx* h, const float2* r_win, const float2* g_win, con
                       int n, float2* e_win);
 int schwarz_traces(fdfd_ctx* h, const float2* u, float2* g);
 int schwarz_export(fdfd_ctx* h, double* Q, double* Nd);
+struct NnoWeights;
+const NnoWeights* schwarz_weights(fdfd_ctx* h);  // nullptr before schwarz_setup
 int schwarz_info(fdfd_ctx* h, fdfd_info* info);

@@ -139,6 +139,8 @@ int schwarz_nno_solve(fdfd_ctx* h, const float2* r_win, const float2* g_win, con
   return check_err(h);
 }
 
+const NnoWeights* schwarz_weights(fdfd_ctx* h) { return (h && h->sw) ? &h->sw->W : nullptr; }
+
 int schwarz_export(fdfd_ctx* h, double* Q, double* Nd) {
   if (!h->sw->coarse) return FDFD_ENOSETUP;
   return coarse_export(h, h->sw->coarse, Q, Nd);

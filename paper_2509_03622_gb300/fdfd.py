@@ -81,6 +81,7 @@ _SIGS = {
     "fdfd_nno_solve": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "fdfd_trace_extract": ([_P, _P, _P], C.c_int),
     "fdfd_local_apply": ([_P, _P, _P, _P, C.c_int], C.c_int),
+    "fdfd_nno_solve_noalloc": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "fdfd_coarse_export": ([_P, _P, _P], C.c_int),
     "fdfd_profile_start": ([_P], C.c_int),
     "fdfd_selftest_gemm": ([_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
@@ -219,6 +220,12 @@ class Solver:
         n = r_win.shape[0]
         _check(lib.fdfd_nno_solve(self.h, _ptr(r_win), _ptr(g_win), _ptr(win_id), n, _ptr(e_win)),
                "fdfd_nno_solve")
+
+    def nno_solve_noalloc(self, r_win, g_win, win_id, e_win):
+        """fdfd_nno_solve without any device allocation (at most 4 windows)."""
+        n = r_win.shape[0]
+        _check(lib.fdfd_nno_solve_noalloc(self.h, _ptr(r_win), _ptr(g_win), _ptr(win_id), n, _ptr(e_win)),
+               "fdfd_nno_solve_noalloc")
 
     def local_apply(self, x_win, y_win, win_id):
         _check(lib.fdfd_local_apply(self.h, _ptr(x_win), _ptr(y_win), _ptr(win_id), x_win.shape[0]),
