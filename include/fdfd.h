@@ -41,7 +41,8 @@ extern "C" {
 /* ---- status codes ---------------------------------------------------- */
 #define FDFD_OK             0
 #define FDFD_NOT_CONVERGED  1   /* max_iters reached; stats valid            */
-#define FDFD_STAGNATED      2   /* a restart cycle made no progress          */
+#define FDFD_STAGNATED      2   /* 3 restart cycles in a row lowered the true
+                                   residual by less than 1%; stats valid      */
 #define FDFD_EINVAL        -1   /* bad argument (checked on the host)        */
 #define FDFD_ECUDA         -2   /* a CUDA call failed                        */
 #define FDFD_ENUMERIC      -3   /* NaN / Inf met in the iteration            */
@@ -156,6 +157,28 @@ int  fdfd_solve(fdfd_handle h, const fdfd_c64* J_dev, fdfd_c64* E_dev,
  * host<->device copies are part of the call. */
 int  fdfd_solve_host(fdfd_handle h, const fdfd_c64* J_host, fdfd_c64* E_host,
                      const fdfd_solve_opts* opts, fdfd_solve_stats* stats);
+
+/* ---- batching pattern (several problems in lock step; Fig. 1a) -------- */
+typedef struct fdfd_batch_ctx* fdfd_batch;
+
+/* Group n handles (any grid sizes, wavelengths, permittivities; all on the
+ * same stream) for lock-step solves.  max_windows caps the windows of one
+ * neural-operator pass (0 = min(total windows, 8192)); the batch allocates
+ * that workspace here (about 2.3 MB per window).  The handles must outlive
+ * the batch.  FDFD_EINVAL if streams differ. */
+int  fdfd_batch_create(fdfd_handle* hs, int n, int max_windows, fdfd_batch* out);
+
+/* FGMRES solves of all problems of the batch in lock step: J_dev[p], E_dev[p]
+ * are device pointers of problem p (host arrays of n pointers); stats[p]
+ * receives each problem's statistics (t_solve_ms is the batch's time).  With
+ * FDFD_PRECOND_SCHWARZ every Arnoldi step applies the neural local solves of
+ * all windows of all active problems as one batch (one launch per operator
+ * stage per chunk), using hs[0]'s weights (every handle must have been set
+ * up with the same blob and inner_iters = 0); coarse corrections are applied
+ * per problem.  Returns the most severe status over the problems. */
+int  fdfd_solve_batched(fdfd_batch b, const fdfd_c64* const* J_dev, fdfd_c64* const* E_dev,
+                        const fdfd_solve_opts* opts, fdfd_solve_stats* stats);
+void fdfd_batch_destroy(fdfd_batch b);
 
 /* Adjoint solve A~^T lam = g (Sec. 2.2, adjoint variable method): g_dev is
  * the device [ny][nx] right-hand side taken as is (no source scaling), the

@@ -14,9 +14,14 @@ which is exactly what fdfd_grad_eps computes.
 """
 from __future__ import annotations
 
+import warnings
+
 import torch
 
 from . import fdfd as F
+
+# statistics of the most recent forward and adjoint solves (for inspection)
+last_stats = {"forward": None, "adjoint": None}
 
 
 class _FieldSolve(torch.autograd.Function):
@@ -28,6 +33,9 @@ class _FieldSolve(torch.autograd.Function):
         E = torch.zeros(J.shape, dtype=torch.complex64, device=J.device)
         kw = {k: v for k, v in opts.items() if k in ("restart", "max_iters", "tol", "precond")}
         rc, st = solver.solve(J, E, **kw)
+        last_stats["forward"] = st
+        if rc != F.OK:
+            warnings.warn(f"forward solve: {F.status_string(rc)} (relres {st['relres_true']:.2e})")
         ctx.solver, ctx.kw, ctx.stats = solver, kw, st
         ctx.save_for_backward(E)
         return E
@@ -37,7 +45,10 @@ class _FieldSolve(torch.autograd.Function):
         (E,) = ctx.saved_tensors
         g = (grad_E.conj() * 0.5).to(torch.complex64).contiguous()
         lam = torch.zeros_like(E)
-        ctx.solver.solve_adjoint(g, lam, **ctx.kw)
+        rc, st = ctx.solver.solve_adjoint(g, lam, **ctx.kw)
+        last_stats["adjoint"] = st
+        if rc != F.OK:
+            warnings.warn(f"adjoint solve: {F.status_string(rc)} (relres {st['relres_true']:.2e})")
         grad = torch.empty(E.shape, dtype=torch.float32, device=E.device)
         ctx.solver.grad_eps(E, lam, grad)
         return grad, None, None, None, None

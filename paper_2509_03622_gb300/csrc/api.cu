@@ -109,7 +109,8 @@ void release(fdfd_ctx* h) {
   if (!h) return;
   schwarz_destroy(h);
   void* ptrs[] = {h->eps, h->cx, h->cy, h->cxT, h->cyT, h->cx64, h->cy64, h->cxT64, h->cyT64, h->isx, h->isy,
-                  h->V, h->Z, h->w, h->x64, h->st, h->partials, h->counter, h->hostJ, h->hostE, h->d_one};
+                  h->V, h->Z, h->w, h->x64, h->st, h->partials, h->counter, h->hostJ, h->hostE, h->d_one,
+                  h->adj};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->flag_host) cudaFreeHost(h->flag_host);
@@ -169,7 +170,7 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
   CK(cudaMemsetAsync(h->x64, 0, n * sizeof(double2), s));
   {
     ProfScope ps(h, 3, 2);
-    if ((rc = launch_residual64(h->x64, rhs, h->sb, rhs_is_source, h->eps, cx64, cy64, h->k2, h->nx, h->ny,
+    if ((rc = launch_residual64(h->x64, rhs, h->sb, rhs_is_source, 1.0, h->eps, cx64, cy64, h->k2, h->nx, h->ny,
                                 h->V, h->partials, h->counter, &h->st->resid, s)))
       return rc;
     set_bnorm_kernel<<<1, 1, 0, s>>>(h->st);
@@ -184,9 +185,22 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
     if (stats) { *stats = loc; stats->status = FDFD_OK; }
     return FDFD_OK;
   }
+  // Solve the system scaled by a power of two so that ||rs b|| is in [1, 2):
+  // right-hand sides of any magnitude (an adjoint source is often ~1e-20)
+  // then keep the FP32 sums of squares inside the preconditioner and the
+  // local solves far from underflow.  x64 holds rs x; the scaling is exact.
+  const double rs = ldexp(1.0, -ilogb(bnorm));
+  if (rs != 1.0) {
+    ProfScope ps(h, 3, 1);
+    if ((rc = launch_residual64(h->x64, rhs, h->sb, rhs_is_source, rs, h->eps, cx64, cy64, h->k2, h->nx, h->ny,
+                                h->V, h->partials, h->counter, &h->st->resid, s)))
+      return rc;
+    set_bnorm_kernel<<<1, 1, 0, s>>>(h->st);
+    CKL();
+  }
   if (o->use_x0) {
     ProfScope ps(h, 4, 1);
-    if ((rc = launch_load_field(E, h->x64, n, s))) return rc;
+    if ((rc = launch_load_field(E, h->x64, n, rs, s))) return rc;
   }
   int iters = 0, cycles = 0, status = FDFD_NOT_CONVERGED;
   double est = 1.0, relres = 1.0, prev_relres = INFINITY;
@@ -194,7 +208,7 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
   for (;;) {
     if (cycles > 0 || o->use_x0) {
       ProfScope ps(h, 3, 1);
-      if ((rc = launch_residual64(h->x64, rhs, h->sb, rhs_is_source, h->eps, cx64, cy64, h->k2, h->nx,
+      if ((rc = launch_residual64(h->x64, rhs, h->sb, rhs_is_source, rs, h->eps, cx64, cy64, h->k2, h->nx,
                                   h->ny, h->V, h->partials, h->counter, &h->st->resid, s)))
         return rc;
     }
@@ -208,7 +222,8 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
     est = relres;
     if (relres <= o->tol) { status = FDFD_OK; break; }
     if (iters >= o->max_iters) { status = FDFD_NOT_CONVERGED; break; }
-    if (relres > 0.999 * prev_relres) { if (++stalls >= 2) { status = FDFD_STAGNATED; break; } }
+    // stagnation: three cycles in a row that do not lower the true residual by 1%
+    if (relres > 0.99 * prev_relres) { if (++stalls >= 3) { status = FDFD_STAGNATED; break; } }
     else stalls = 0;
     prev_relres = relres;
     int k = 0;
@@ -259,7 +274,7 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
   }
   if (status != FDFD_ENUMERIC) {
     ProfScope ps(h, 4, 1);
-    if ((rc = launch_store_field(h->x64, E, n, s))) return rc;
+    if ((rc = launch_store_field(h->x64, E, n, 1.0 / rs, s))) return rc;
   }
   CK(cudaEventRecord(h->ev1, s));
   CK(cudaStreamSynchronize(s));
@@ -321,7 +336,7 @@ int fdfd_create(const fdfd_desc* d, fdfd_handle* out) {
       (rc = dalloc(h, &h->V, (size_t)(h->rmax + 1) * n)) || (rc = dalloc(h, &h->Z, (size_t)h->rmax * n)) ||
       (rc = dalloc(h, &h->w, n)) || (rc = dalloc(h, &h->x64, n)) || (rc = dalloc(h, &h->st, 1)) ||
       (rc = dalloc(h, &h->partials, (size_t)8192 * FDFD_MAXRESTART * 2)) || (rc = dalloc(h, &h->counter, 4)) ||
-      (rc = dalloc(h, &h->d_one, 1))) {
+      (rc = dalloc(h, &h->d_one, 1)) || (rc = dalloc(h, &h->adj, n))) {
     release(h);
     return rc;
   }
@@ -386,9 +401,44 @@ int fdfd_solve_host(fdfd_handle h, const fdfd_c64* J, fdfd_c64* E, const fdfd_so
   return rc;
 }
 
+// Adjoint solve through the symmetrised operator: with D = diag(s_x s_y)
+// (UPML factors at cell centres), D A~ is complex symmetric, so
+// A~^T = D A~ D^-1 and  A~^T lam = g  <=>  A~ mu = D^-1 g,  lam = D mu.
+// The forward machinery (and its preconditioner, built for A~) then solves
+// the adjoint exactly; the reported relres is the adjoint's own FP64 one.
 int fdfd_solve_adjoint(fdfd_handle h, const fdfd_c64* g, fdfd_c64* lam, const fdfd_solve_opts* o,
                        fdfd_solve_stats* st) {
-  return solve_impl(h, reinterpret_cast<const float2*>(g), 0, 1, reinterpret_cast<float2*>(lam), o, st);
+  if (!h || !g || !lam || !o) return FDFD_EINVAL;
+  float2* L = reinterpret_cast<float2*>(lam);
+  const float2* G = reinterpret_cast<const float2*>(g);
+  cudaStream_t s = h->stream;
+  int rc;
+  {
+    ProfScope ps(h, 4, o->use_x0 ? 2 : 1);
+    if (o->use_x0 && (rc = launch_scale_d(L, L, h->isx, h->isy, h->nx, h->n, 1, s))) return rc;
+    if ((rc = launch_scale_d(G, h->adj, h->isx, h->isy, h->nx, h->n, 1, s))) return rc;
+  }
+  fdfd_solve_stats loc{};
+  const int status = solve_impl(h, h->adj, 0, 0, L, o, &loc);
+  if (status < 0) { if (st) *st = loc; return status; }
+  {
+    ProfScope ps(h, 4, 1);
+    if ((rc = launch_scale_d(L, L, h->isx, h->isy, h->nx, h->n, 0, s))) return rc;
+  }
+  // ||g - A~^T lam|| / ||g|| in FP64
+  double r2[2];
+  for (int pass = 0; pass < 2; ++pass) {
+    ProfScope ps(h, 3, 2);
+    if (pass == 0) CK(cudaMemsetAsync(h->x64, 0, h->n * sizeof(double2), s));
+    else if ((rc = launch_load_field(L, h->x64, h->n, 1.0, s))) return rc;
+    if ((rc = launch_residual64(h->x64, G, h->sb, 0, 1.0, h->eps, h->cxT64, h->cyT64, h->k2, h->nx, h->ny, h->V,
+                                h->partials, h->counter, &h->st->resid, s)))
+      return rc;
+    if ((rc = read_double(h, &h->st->resid, &r2[pass]))) return rc;
+  }
+  loc.relres_true = r2[0] > 0 ? sqrt(r2[1] / r2[0]) : 0.0;
+  if (st) *st = loc;
+  return status;
 }
 
 int fdfd_grad_eps(fdfd_handle h, const fdfd_c64* E, const fdfd_c64* lam, float* grad, int accumulate) {

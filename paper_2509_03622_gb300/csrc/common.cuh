@@ -79,12 +79,16 @@ int launch_stencil(const float2* x, float2* y, const float* eps, const AxisCoef*
 int launch_stencil_jacobi(const float2* v, const double* vscale_dev, float2* w, const float* eps,
                           const AxisCoef* cx, const AxisCoef* cy, float k2, int nx, int ny,
                           cudaStream_t s);
-int launch_residual64(const double2* x, const float2* J, double sb, int rhs_is_source,
+int launch_residual64(const double2* x, const float2* J, double sb, int rhs_is_source, double rs,
                       const float* eps, const AxisCoef64* cx, const AxisCoef64* cy, double k2,
                       int nx, int ny, float2* r_out, double* partials, unsigned* counter,
                       double* result, cudaStream_t s);
 int launch_grad_eps(const float2* E, const float2* lam, float* grad, float k2, int n,
                     int accumulate, cudaStream_t s);
+// out = in * D^-1 (inverse = 1) or in * D (inverse = 0), D = s_x s_y at cell centres
+// (isx, isy hold 1/s); in and out may alias.
+int launch_scale_d(const float2* in, float2* out, const float2* isx, const float2* isy, int nx, size_t n,
+                   int inverse, cudaStream_t s);
 // krylov.cu
 int krylov_grid(size_t n);
 int launch_cgs_dots(const float2* V, size_t ld, int j, const float2* w, size_t n,
@@ -99,8 +103,9 @@ int launch_x_update(double2* x, const float2* Z, size_t ld, int k, size_t n, con
 int launch_x_update_jacobi(double2* x, const float2* V, size_t ld, int k, size_t n,
                            const KrylovState* st, const float* eps, const AxisCoef* cx,
                            const AxisCoef* cy, float k2, int nx, cudaStream_t s);
-int launch_store_field(const double2* x, float2* E, size_t n, cudaStream_t s);
-int launch_load_field(const float2* E, double2* x, size_t n, cudaStream_t s);
+// E = f x (complex128 -> complex64) and x = f E
+int launch_store_field(const double2* x, float2* E, size_t n, double f, cudaStream_t s);
+int launch_load_field(const float2* E, double2* x, size_t n, double f, cudaStream_t s);
 int launch_scale_copy(const float2* v, const double* scale_dev, float2* z, size_t n, cudaStream_t s);
 int launch_jacobi_apply(const float2* v, const double* scale_dev, float2* z, const float* eps,
                         const AxisCoef* cx, const AxisCoef* cy, float k2, int nx, int ny,

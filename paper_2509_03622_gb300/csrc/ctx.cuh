@@ -25,6 +25,7 @@ struct fdfd_ctx {
   double* d_one = nullptr;      // device constant 1.0 (unit scale)
   double* flag_host = nullptr;  // pinned: est, nonfinite|breakdown
   float2 *hostJ = nullptr, *hostE = nullptr;  // device staging for host-buffer solves
+  float2* adj = nullptr;                       // D^-1 g of the adjoint solve
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   size_t bytes = 0;
   SchwarzData* sw = nullptr;

@@ -214,13 +214,13 @@ __global__ void x_update_jacobi_kernel(double2* __restrict__ x, const float2* __
   }
 }
 
-__global__ void store_field_kernel(const double2* __restrict__ x, float2* __restrict__ E, size_t n) {
+__global__ void store_field_kernel(const double2* __restrict__ x, float2* __restrict__ E, size_t n, double f) {
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
-    E[c] = make_float2((float)x[c].x, (float)x[c].y);
+    E[c] = make_float2((float)(f * x[c].x), (float)(f * x[c].y));
 }
-__global__ void load_field_kernel(const float2* __restrict__ E, double2* __restrict__ x, size_t n) {
+__global__ void load_field_kernel(const float2* __restrict__ E, double2* __restrict__ x, size_t n, double f) {
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
-    x[c] = make_double2((double)E[c].x, (double)E[c].y);
+    x[c] = make_double2(f * (double)E[c].x, f * (double)E[c].y);
 }
 __global__ void scale_copy_kernel(const float2* __restrict__ v, const double* __restrict__ sc,
                                   float2* __restrict__ z, size_t n) {
@@ -320,13 +320,13 @@ int launch_x_update_jacobi(double2* x, const float2* V, size_t ld, int k, size_t
   return FDFD_OK;
 }
 
-int launch_store_field(const double2* x, float2* E, size_t n, cudaStream_t s) {
-  store_field_kernel<<<krylov_grid(n), 256, 0, s>>>(x, E, n);
+int launch_store_field(const double2* x, float2* E, size_t n, double f, cudaStream_t s) {
+  store_field_kernel<<<krylov_grid(n), 256, 0, s>>>(x, E, n, f);
   CKL();
   return FDFD_OK;
 }
-int launch_load_field(const float2* E, double2* x, size_t n, cudaStream_t s) {
-  load_field_kernel<<<krylov_grid(n), 256, 0, s>>>(E, x, n);
+int launch_load_field(const float2* E, double2* x, size_t n, double f, cudaStream_t s) {
+  load_field_kernel<<<krylov_grid(n), 256, 0, s>>>(E, x, n, f);
   CKL();
   return FDFD_OK;
 }

@@ -251,8 +251,11 @@ int local_robin_rhs(fdfd_ctx* h, const float2* g, float2* rhs, int n_win) {
 }
 
 int local_fgmres(fdfd_ctx* h, LocalWork* L, const NnoWeights* W, NnoWork* work, const float2* v_global,
-                 const float2* rhs_win, float2* z_global, float2* e_win, const double* scale) {
+                 const float2* rhs_win, float2* z_global, float2* e_win, const double* scale, int transpose) {
   const int n = L->n, nwx = h->nx / FDFD_CORE;
+  // for the adjoint solve the local problems use the transposed couplings
+  const AxisCoef* lcx = transpose ? h->cxT : h->cx;
+  const AxisCoef* lcy = transpose ? h->cyT : h->cy;
   const size_t ld = (size_t)n * NP;
   cudaStream_t s = h->stream;
   GridGeom g{h->nx, h->ny, nwx, (float)h->k2, h->eps, h->isx, h->isy};
@@ -276,8 +279,8 @@ int local_fgmres(fdfd_ctx* h, LocalWork* L, const NnoWeights* W, NnoWork* work, 
     if ((rc = nno_forward(W, work, g, in, out, n, s, h))) return rc;
     {
       ProfScope ps(h, 15, 2);
-      local_apply_kernel<<<dim3(NP / LT / 5, n), LT, 0, s>>>(L->Z + (size_t)j * ld, L->w, nullptr, h->eps, h->cx,
-                                                              h->cy, (float)h->k2, (float)h->k0dx, h->nx, h->ny, nwx);
+      local_apply_kernel<<<dim3(NP / LT / 5, n), LT, 0, s>>>(L->Z + (size_t)j * ld, L->w, nullptr, h->eps, lcx,
+                                                              lcy, (float)h->k2, (float)h->k0dx, h->nx, h->ny, nwx);
       local_cgs_kernel<<<n, LT, 0, s>>>(L->V, L->w, L->V + (size_t)(j + 1) * ld, L->st, j, ld);
       CKL();
     }

@@ -35,6 +35,6 @@ int local_robin_rhs(fdfd_ctx* h, const float2* g, float2* rhs, int n_win);
 // v_global (restricted) or from rhs_win; result prolonged (restricted, times
 // *scale) into z_global, or written whole to e_win.
 int local_fgmres(fdfd_ctx* h, LocalWork* L, const NnoWeights* W, NnoWork* work, const float2* v_global,
-                 const float2* rhs_win, float2* z_global, float2* e_win, const double* scale);
+                 const float2* rhs_win, float2* z_global, float2* e_win, const double* scale, int transpose = 0);
 // y = A_w x for n windows (x, y [n][80][80]; win_id nullable = identity).
 int local_apply_windows(fdfd_ctx* h, const float2* x, float2* y, const int* win_id, int n);

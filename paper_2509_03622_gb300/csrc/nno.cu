@@ -7,7 +7,7 @@
 //   block b (the truncated 2D DFT is done as two 1D DFT GEMMs each way):
 //     G1  DFT along x   : rows (y,c)   K = x 80        N = (kx,ri) 32   A MN-major
 //     G2  DFT along y   : rows (kx,c)  K = (ri,y) 160  N = (q,ri) 64    A MN-major
-//     G3  spectral mix  : per mode, rows = windows, K = (c,ri) 64, N = (o,ri) 64
+//     G3  spectral mix  : 4 modes per CTA, rows = windows, K = (c,ri) 64, N = (o,ri) 64
 //     G4  inverse DFT y : rows (o,kx)  K = (q,ri) 64   N = (y,ri) 160
 //     G5  fused: inverse real DFT along x + W x + bias + leaky-ReLU, per y row:
 //         D_y[x][o] = Gx[x][:] . T3_y[o][:] + X_y[x][:] . W[o][:]
@@ -43,22 +43,25 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
 // epilogue.  One elected thread issues the MMAs, the commit arrives on an
 // mbarrier, all four warps read the FP32 accumulator from TMEM.
 // ---------------------------------------------------------------------
+// Persistent form: each CTA walks the tiles blockIdx.x, +gridDim.x, ... of
+// the (batch, tile) space.  Two shared-memory stages: while tile i's MMA and
+// epilogue run, tile i+1's operands are already in flight (cp.async).  A
+// B operand that is the same for every tile (Op::kConstB: DFT matrices,
+// weights) is loaded once per CTA.
 template <int BN, int K, bool AMN, class Op>
-__global__ void __launch_bounds__(128) gemm_kernel(Op op, int* err) {
-  static_assert(K % 16 == 0 && BN % 16 == 0 && BN <= 256, "shape");
+struct GemmCfg {
+  static constexpr int KC = K / 8;
+  static constexpr uint32_t A_BYTES = 128 * K * 2, B_BYTES = BN * K * 2;
+  static constexpr uint32_t STAGE = A_BYTES + (Op::kConstB ? 0 : B_BYTES);
+  static constexpr uint32_t SMEM = 2 * STAGE + (Op::kConstB ? B_BYTES : 0) + 16;
+  static constexpr uint32_t TCOLS = tc::tmem_cols(BN);
+};
+
+template <int BN, int K, bool AMN, class Op>
+__device__ __forceinline__ void gemm_load(const Op& op, uint8_t* sA, uint8_t* sB, int b, int m0, int Mb,
+                                          bool loadB) {
   constexpr int KC = K / 8;
-  constexpr uint32_t A_BYTES = 128 * K * 2, B_BYTES = BN * K * 2;
-  constexpr uint32_t TCOLS = tc::tmem_cols(BN);
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + A_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + A_BYTES + B_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + A_BYTES + B_BYTES + 8);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int b = blockIdx.y;
-  const int m0 = blockIdx.x * 128;
-  const int Mb = op.rows(b);
-  // ---- operand loads (global -> canonical smem tiles), all in flight ----
+  const int tid = threadIdx.x;
   if (!AMN) {
     for (int c = tid; c < 128 * KC; c += 128) {
       const int t8 = c & 7, rest = c >> 3, kc = rest % KC, rg = rest / KC;
@@ -74,60 +77,129 @@ __global__ void __launch_bounds__(128) gemm_kernel(Op op, int* err) {
       tc::cp_async16(sA + (mg * KC + kg) * 128 + t8 * 16, op.a_src(b, ok ? m : 0, kg * 8 + t8), ok);
     }
   }
-  for (int c = tid; c < BN * KC; c += 128) {
-    const int t8 = c & 7, rest = c >> 3, kc = rest % KC, rg = rest / KC;
-    tc::cp_async16(sB + (rg * KC + kc) * 128 + t8 * 16, op.b_src(b, rg * 8 + t8, kc * 8), true);
+  if (loadB)
+    for (int c = tid; c < BN * KC; c += 128) {
+      const int t8 = c & 7, rest = c >> 3, kc = rest % KC, rg = rest / KC;
+      tc::cp_async16(sB + (rg * KC + kc) * 128 + t8 * 16, op.b_src(b, rg * 8 + t8, kc * 8), true);
+    }
+}
+
+template <int BN, int K, bool AMN, class Op>
+__global__ void __launch_bounds__(128) gemm_kernel(Op op, int tiles_per_batch, int total, int* err) {
+  static_assert(K % 16 == 0 && BN % 16 == 0 && BN <= 256, "shape");
+  typedef GemmCfg<BN, K, AMN, Op> Cfg;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* stage[2] = {smem, smem + Cfg::STAGE};
+  uint8_t* sBc = smem + 2 * Cfg::STAGE;  // constant B (if kConstB)
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + Cfg::SMEM - 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Cfg::SMEM - 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int tile = blockIdx.x;
+  if (tile >= total) return;
+  auto sB_of = [&](int st) { return Op::kConstB ? sBc : stage[st] + Cfg::A_BYTES; };
+  {
+    const int b = tile / tiles_per_batch, m0 = (tile % tiles_per_batch) * 128;
+    gemm_load<BN, K, AMN>(op, stage[0], sB_of(0), b, m0, op.rows(b), true);
   }
-  tc::cp_async_wait_all();
+  asm volatile("cp.async.commit_group;" ::: "memory");
   if (tid == 0) tc::mbar_init(tc::smem_u32(mbar), 1);
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), TCOLS);
-  tc::fence_async_smem();
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), Cfg::TCOLS);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  if (tid == 0) {
-    constexpr uint32_t idesc = tc::idesc_bf16(BN, AMN, false);
-    const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+  constexpr uint32_t idesc = tc::idesc_bf16(BN, AMN, false);
+  for (int i = 0; tile < total; tile += gridDim.x, ++i) {
+    const int st = i & 1;
+    const int b = tile / tiles_per_batch, m0 = (tile % tiles_per_batch) * 128;
+    const int Mb = op.rows(b);
+    const int next = tile + gridDim.x;
+    if (next < total) {  // prefetch the next tile into the other stage
+      const int nb = next / tiles_per_batch;
+      gemm_load<BN, K, AMN>(op, stage[st ^ 1], sB_of(st ^ 1), nb, (next % tiles_per_batch) * 128, op.rows(nb),
+                            !Op::kConstB);
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 1;" ::: "memory");
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t a0 = tc::smem_u32(stage[st]), b0 = tc::smem_u32(sB_of(st));
 #pragma unroll
-    for (int s = 0; s < K / 16; ++s)
-      tc::mma_bf16(tmem, tc::make_desc(a0 + s * 256, 128, K * 16), tc::make_desc(b0 + s * 256, 128, K * 16), idesc,
-                   s > 0);
-    tc::mma_commit(tc::smem_u32(mbar));
-  }
-  if (!tc::mbar_wait(tc::smem_u32(mbar), 0, WAIT_LIMIT)) atomicExch(err, 1);
-  tc::fence_after();
-  // ---- epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows ----
-  const int m = m0 + warp * 32 + lane;
-  const bool valid = m < Mb;
-  typename Op::State st;
-  op.epi_begin(st);
+      for (int s = 0; s < K / 16; ++s)
+        tc::mma_bf16(tmem, tc::make_desc(a0 + s * 256, 128, K * 16), tc::make_desc(b0 + s * 256, 128, K * 16),
+                     idesc, s > 0);
+      tc::mma_commit(tc::smem_u32(mbar));
+    }
+    if (!tc::mbar_wait(tc::smem_u32(mbar), (uint32_t)(i & 1), WAIT_LIMIT)) atomicExch(err, 1);
+    tc::fence_after();
+    // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows
+    const int m = m0 + warp * 32 + lane;
+    const bool valid = m < Mb;
+    typename Op::State sst;
+    op.epi_begin(sst);
+    if constexpr (Op::kUnroll) {
+#pragma unroll
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (valid) op.epi(b, m, c0, v, sst);
+      }
+    } else {
 #pragma unroll 1
-  for (int c0 = 0; c0 < BN; c0 += 16) {
-    float v[16];
-    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    if (valid) op.epi(b, m, c0, v, st);
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (valid) op.epi(b, m, c0, v, sst);
+      }
+    }
+    if (valid) op.epi_end(b, m, sst);
+    tc::fence_before();
+    __syncthreads();  // accumulator and stage st are free again
   }
-  if (valid) op.epi_end(b, m, st);
-  tc::fence_before();
-  __syncthreads();
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (warp == 0) {
     tc::fence_after();
-    tc::tmem_free(tmem, TCOLS);
+    tc::tmem_free(tmem, Cfg::TCOLS);
   }
+}
+
+constexpr int SM_SMEM = 233472;  // shared memory per SM (228 KB)
+
+// Grid of a persistent kernel: SMs x resident CTAs per SM, the latter from
+// shared memory (1 KB reserved per CTA), threads, registers and the 512
+// TMEM columns per SM (a CTA that cannot get its columns would only wait in
+// tcgen05.alloc).
+int persistent_grid(const void* kern, int threads, size_t smem, uint32_t tcols) {
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncAttributes fa;
+  int regs = 64;
+  if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && fa.numRegs > 0) regs = fa.numRegs;
+  int per_sm = (int)(SM_SMEM / (smem + 1024));
+  per_sm = per_sm < 2048 / threads ? per_sm : 2048 / threads;
+  const int by_regs = 65536 / (regs * threads);
+  per_sm = per_sm < by_regs ? per_sm : by_regs;
+  const int by_tmem = (int)(512 / tcols);
+  per_sm = per_sm < by_tmem ? per_sm : by_tmem;
+  if (per_sm < 1) per_sm = 1;
+  return nsm * per_sm;
 }
 
 template <int BN, int K, bool AMN, class Op>
 int launch_gemm(const Op& op, int tiles, int batches, int* err, cudaStream_t s) {
-  const size_t smem = 128 * K * 2 + BN * K * 2 + 16;
+  typedef GemmCfg<BN, K, AMN, Op> Cfg;
   auto kern = gemm_kernel<BN, K, AMN, Op>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  static int grid_cap = 0;
+  if (grid_cap == 0) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess)
       return FDFD_ECUDA;
-    attr_set = true;
+    grid_cap = persistent_grid((const void*)kern, 128, Cfg::SMEM, Cfg::TCOLS);
   }
-  kern<<<dim3(tiles, batches), 128, smem, s>>>(op, err);
+  const int total = tiles * batches;
+  const int grid = total < grid_cap ? total : grid_cap;
+  kern<<<grid, 128, Cfg::SMEM, s>>>(op, tiles, total, err);
   CKL();
   return FDFD_OK;
 }
@@ -138,6 +210,8 @@ struct NoState {};
 // Stage operators
 // ---------------------------------------------------------------------
 struct LiftOp {  // rows = pixels, K = 16 inputs, N = 32 channels
+  static constexpr bool kConstB = true;
+  static constexpr bool kUnroll = false;
   const bf16* in; const bf16* w; const float* bias; bf16* X;
   typedef NoState State;
   __device__ int rows(int) const { return NPIX; }
@@ -158,6 +232,8 @@ struct LiftOp {  // rows = pixels, K = 16 inputs, N = 32 channels
 };
 
 struct G1Op {  // DFT along x: rows (y,c), K = x (A MN-major from X), N = (kx,ri)
+  static constexpr bool kConstB = true;
+  static constexpr bool kUnroll = false;
   const bf16* X; const bf16* Fx; bf16* T1;
   typedef NoState State;
   __device__ int rows(int) const { return 80 * 32; }
@@ -180,6 +256,8 @@ struct G1Op {  // DFT along x: rows (y,c), K = x (A MN-major from X), N = (kx,ri
 };
 
 struct G2Op {  // DFT along y: rows (kx,c), K = (ri,y) (A MN-major from T1), N = (q,ri)
+  static constexpr bool kConstB = true;
+  static constexpr bool kUnroll = false;
   const bf16* T1; const bf16* Fy; bf16* Xh; int cap;
   typedef NoState State;
   __device__ int rows(int) const { return 512; }
@@ -199,30 +277,10 @@ struct G2Op {  // DFT along y: rows (kx,c), K = (ri,y) (A MN-major from T1), N =
   __device__ void epi_end(int, int, State&) const {}
 };
 
-struct G3Op {  // spectral mix per mode: rows = windows, K = (c,ri), N = (o,ri)
-  const bf16* Xh; const bf16* R; bf16* Yh; int cap; int nwin;
-  typedef NoState State;
-  __device__ static int mode_of(int bidx) { return (bidx & 31) * 16 + (bidx >> 5); }  // q fastest, kx outer
-  __device__ int rows(int) const { return nwin; }
-  __device__ const uint4* a_src(int bidx, int m, int k) const {
-    return reinterpret_cast<const uint4*>(Xh + ((size_t)mode_of(bidx) * cap + m) * 64 + k);
-  }
-  __device__ const uint4* b_src(int bidx, int n, int k) const {
-    return reinterpret_cast<const uint4*>(R + ((size_t)mode_of(bidx) * 64 + n) * 64 + k);
-  }
-  __device__ void epi_begin(State&) const {}
-  __device__ void epi(int bidx, int w, int c0, const float* v, State&) const {
-    const int md = mode_of(bidx), q = md >> 4, kx = md & 15;
-#pragma unroll
-    for (int i = 0; i < 16; i += 2) {
-      const int o = (c0 + i) >> 1;
-      *reinterpret_cast<uint32_t*>(Yh + (((size_t)w * 512) + o * 16 + kx) * 64 + q * 2) = pack2(v[i], v[i + 1]);
-    }
-  }
-  __device__ void epi_end(int, int, State&) const {}
-};
 
 struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
+  static constexpr bool kConstB = true;
+  static constexpr bool kUnroll = false;
   const bf16* Yh; const bf16* Gy; bf16* T3;
   typedef NoState State;
   __device__ int rows(int) const { return 512; }
@@ -243,7 +301,9 @@ struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
 };
 
 struct ProjOp {  // rows = pixels, K = 32, N = 128 hidden; then 128 -> 2 and the output
-  const bf16* X; const bf16* P1; const float* p1b; const float* P2; float p2b0, p2b1;
+  static constexpr bool kConstB = true;
+  static constexpr bool kUnroll = true;  // constants below become constant-bank operands
+  const bf16* X; const bf16* P1; float p2b0, p2b1;
   const float* rho; const double* scale; const int* win_id;
   float2* z_global; float2* e_win; int nx, nwx;
   const double* scale_win;
@@ -258,123 +318,111 @@ struct ProjOp {  // rows = pixels, K = 32, N = 128 hidden; then 128 -> 2 and the
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const float h = leaky(v[i] + p1b[c0 + i]);
-      s.re += P2[c0 + i] * h;
-      s.im += P2[128 + c0 + i] * h;
+      s.re = fmaf(P2[c0 + i], h, s.re);
+      s.im = fmaf(P2[128 + c0 + i], h, s.im);
     }
   }
   __device__ void epi_end(int b, int m, State& s) const {
+    int w = win_id ? win_id[b] : b;
+    int gnx = nx, gny = ny_, gnwx = nwx;
+    const double* sc = scale;
+    float2* zg = z_global;
+    if (ptab) {  // multi-problem batch
+      const int2 e = wtab[b];
+      const ProbGeom& P = ptab[e.x];
+      w = e.y; gnx = P.nx; gny = P.ny; gnwx = P.nwx; sc = P.scale; zg = P.z;
+    }
     float f = rho[b];
-    if (scale) f *= (float)(*scale);
+    if (sc) f *= (float)(*sc);
     if (scale_win) f *= (float)scale_win[b];
     const float2 o = make_float2((s.re + p2b0) * f, (s.im + p2b1) * f);
     if (e_win) { e_win[(size_t)b * NPIX + m] = o; return; }
-    const int w = win_id ? win_id[b] : b;
-    const int a = w % nwx, bb = w / nwx;
-    const int ny_unused = 0; (void)ny_unused;
+    // restricted prolongation: only the window's 64 x 64 core is written
+    const int a = w % gnwx, bb = w / gnwx;
     const int y = m / 80, x = m % 80;
-    // window origin (shifted inward at the grid edge) and its core
-    const int gx0 = min(max(FDFD_CORE * a - FDFD_OVL, 0), nx - FDFD_WIN);
-    const int gx = gx0 + x;
+    const int gx = min(max(FDFD_CORE * a - FDFD_OVL, 0), gnx - FDFD_WIN) + x;
+    const int gy = min(max(FDFD_CORE * bb - FDFD_OVL, 0), gny - FDFD_WIN) + y;
     if (gx < FDFD_CORE * a || gx >= FDFD_CORE * a + FDFD_CORE) return;
-    // rows: the grid height enters through the window table of the caller
-    const int gy0 = win_y0(bb);
-    const int gy = gy0 + y;
     if (gy < FDFD_CORE * bb || gy >= FDFD_CORE * bb + FDFD_CORE) return;
-    z_global[(size_t)gy * nx + gx] = o;
+    zg[(size_t)gy * gnx + gx] = o;
   }
   int ny_;
-  __device__ int win_y0(int bb) const { return min(max(FDFD_CORE * bb - FDFD_OVL, 0), ny_ - FDFD_WIN); }
+  const int2* wtab;
+  const ProbGeom* ptab;
+  float p1b[128];  // hidden bias
+  float P2[256];   // [2][128] output weights
 };
 
-// Fused G5: per (window, 8 rows): D_y[x][o] = Gx[x][:] T3_y[o][:]^T + X_y[x][:] W[o][:]^T,
-// then + bias, leaky-ReLU (not after the last block), written back to X.
-constexpr int G5_ROWS = 8;
-constexpr uint32_t G5_TILE = 128 * 32 * 2;  // one [128][32] bf16 tile
-constexpr uint32_t G5_SMEM = G5_TILE * (1 + G5_ROWS) + 32 * 32 * 2 * (G5_ROWS + 1) + 16;
+// G3 with 4 modes per CTA: unit = (kx, q-group of 4, tile of 128 windows);
+// D_m[w][(o,ri)] = Xh_m[w][(c,ri')] R'_m[(o,ri)][(c,ri')]^T for the 4 modes
+// m = (q0..q0+3, kx), accumulators side by side in TMEM (4 x 64 columns), so
+// the epilogue writes 16 contiguous bytes (4 q x re/im) per (window, o).
+constexpr int G3_Q = 4;
+constexpr uint32_t G3_A = 128 * 64 * 2, G3_B = 64 * 64 * 2;
+constexpr uint32_t G3_SMEM = G3_Q * (G3_A + G3_B) + 16;
 
-__global__ void __launch_bounds__(128) g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb,
-                                                 const float* bias, int last, int* err) {
+__global__ void __launch_bounds__(128) g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int cap, int nwin,
+                                                 int wtiles, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sAg = smem;                                   // Gx, [128][32]
-  uint8_t* sAx = smem + G5_TILE;                         // 8 x [128][32]
-  uint8_t* sBt = sAx + G5_TILE * G5_ROWS;                // 8 x [32][32]
-  uint8_t* sBw = sBt + 2048 * G5_ROWS;                   // [32][32]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sBw + 2048);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sBw + 2048 + 8);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + G3_Q * G3_A;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + G3_SMEM - 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G3_SMEM - 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int b = blockIdx.y, y0 = blockIdx.x * G5_ROWS;
-  // Gx (rows >= 80 are zero in global) and W
-  for (int c = tid; c < 128 * 4; c += 128) {
-    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-    tc::cp_async16(sAg + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
-  }
-  {
-    const int c = tid;  // 32 rows x 4 chunks = 128
-    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-    tc::cp_async16(sBw + (rg * 4 + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * 32 + kc * 8, true);
-  }
-  for (int yy = 0; yy < G5_ROWS; ++yy) {
-    const int y = y0 + yy;
-    uint8_t* ax = sAx + yy * G5_TILE;
-    for (int c = tid; c < 128 * 4; c += 128) {
-      const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-      const int x = rg * 8 + t8;
-      const bool ok = x < 80;
-      tc::cp_async16(ax + (rg * 4 + kc) * 128 + t8 * 16,
-                     X + (((size_t)b * 80 + y) * 80 + (ok ? x : 0)) * 32 + kc * 8, ok);
+  const int u = blockIdx.x;
+  const int wt = u % wtiles, qg = (u / wtiles) % (32 / G3_Q), kx = u / (wtiles * (32 / G3_Q));
+  const int w0 = wt * 128;
+  for (int mq = 0; mq < G3_Q; ++mq) {
+    const int md = (qg * G3_Q + mq) * 16 + kx;
+    for (int c = tid; c < 128 * 8; c += 128) {
+      const int t8 = c & 7, rest = c >> 3, kc = rest & 7, rg = rest >> 3;
+      const int w = w0 + rg * 8 + t8;
+      const bool ok = w < nwin;
+      tc::cp_async16(sA + mq * G3_A + (rg * 8 + kc) * 128 + t8 * 16,
+                     Xh + ((size_t)md * cap + (ok ? w : 0)) * 64 + kc * 8, ok);
     }
-    {
-      const int c = tid, t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-      tc::cp_async16(sBt + yy * 2048 + (rg * 4 + kc) * 128 + t8 * 16,
-                     T3 + (((size_t)b * 80 + y) * 32 + rg * 8 + t8) * 32 + kc * 8, true);
+    for (int c = tid; c < 64 * 8; c += 128) {
+      const int t8 = c & 7, rest = c >> 3, kc = rest & 7, rg = rest >> 3;
+      tc::cp_async16(sB + mq * G3_B + (rg * 8 + kc) * 128 + t8 * 16,
+                     R + ((size_t)md * 64 + rg * 8 + t8) * 64 + kc * 8, true);
     }
   }
   tc::cp_async_wait_all();
   if (tid == 0) tc::mbar_init(tc::smem_u32(mbar), 1);
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 256);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 64 * G3_Q);
   tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
   if (tid == 0) {
-    constexpr uint32_t idesc = tc::idesc_bf16(32, false, false);
-    const uint32_t ag = tc::smem_u32(sAg), ax0 = tc::smem_u32(sAx), bt0 = tc::smem_u32(sBt), bw = tc::smem_u32(sBw);
-    for (int yy = 0; yy < G5_ROWS; ++yy) {
-      const uint32_t d = tmem + yy * 32;
-      for (int s = 0; s < 2; ++s)
-        tc::mma_bf16(d, tc::make_desc(ag + s * 256, 128, 512), tc::make_desc(bt0 + yy * 2048 + s * 256, 128, 512),
+    constexpr uint32_t idesc = tc::idesc_bf16(64, false, false);
+    for (int mq = 0; mq < G3_Q; ++mq) {
+      const uint32_t a0 = tc::smem_u32(sA + mq * G3_A), b0 = tc::smem_u32(sB + mq * G3_B);
+      for (int s = 0; s < 4; ++s)
+        tc::mma_bf16(tmem + mq * 64, tc::make_desc(a0 + s * 256, 128, 1024), tc::make_desc(b0 + s * 256, 128, 1024),
                      idesc, s > 0);
-      for (int s = 0; s < 2; ++s)
-        tc::mma_bf16(d, tc::make_desc(ax0 + yy * G5_TILE + s * 256, 128, 512), tc::make_desc(bw + s * 256, 128, 512),
-                     idesc, 1);
     }
     tc::mma_commit(tc::smem_u32(mbar));
   }
   if (!tc::mbar_wait(tc::smem_u32(mbar), 0, WAIT_LIMIT)) atomicExch(err, 1);
   tc::fence_after();
-  if (warp < 3) {
-    const int x = warp * 32 + lane;
-    float bs[32];
+  const int w = w0 + warp * 32 + lane;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int oc = 0; oc < 4; ++oc) {  // 8 output channels (16 columns) per pass
+    float v[G3_Q][16];
 #pragma unroll
-    for (int o = 0; o < 32; ++o) bs[o] = bias[o];
-    for (int yy = 0; yy < G5_ROWS; ++yy) {
-      float v[32];
-      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + yy * 32, v);
-      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + yy * 32 + 16, v + 16);
-      if (x < 80) {
-        uint32_t p[16];
+    for (int mq = 0; mq < G3_Q; ++mq) tc::tmem_ld16(trow + mq * 64 + oc * 16, v[mq]);
+    if (w < nwin) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          float a = v[2 * i] + bs[2 * i], c = v[2 * i + 1] + bs[2 * i + 1];
-          if (!last) { a = leaky(a); c = leaky(c); }
-          p[i] = pack2(a, c);
-        }
-        uint4* dst = reinterpret_cast<uint4*>(X + (((size_t)b * 80 + y0 + yy) * 80 + x) * 32);
-        dst[0] = make_uint4(p[0], p[1], p[2], p[3]);
-        dst[1] = make_uint4(p[4], p[5], p[6], p[7]);
-        dst[2] = make_uint4(p[8], p[9], p[10], p[11]);
-        dst[3] = make_uint4(p[12], p[13], p[14], p[15]);
+      for (int oo = 0; oo < 8; ++oo) {
+        const int o = oc * 8 + oo;
+        uint4 q;
+        q.x = pack2(v[0][2 * oo], v[0][2 * oo + 1]);
+        q.y = pack2(v[1][2 * oo], v[1][2 * oo + 1]);
+        q.z = pack2(v[2][2 * oo], v[2][2 * oo + 1]);
+        q.w = pack2(v[3][2 * oo], v[3][2 * oo + 1]);
+        *reinterpret_cast<uint4*>(Yh + (((size_t)w * 512) + o * 16 + kx) * 64 + qg * G3_Q * 2) = q;
       }
     }
   }
@@ -382,16 +430,144 @@ __global__ void __launch_bounds__(128) g5_kernel(bf16* X, const bf16* T3, const 
   __syncthreads();
   if (warp == 0) {
     tc::fence_after();
-    tc::tmem_free(tmem, 256);
+    tc::tmem_free(tmem, 64 * G3_Q);
   }
 }
 
-// Restriction + input packing (K3): rho per window, 16 bf16 channels per pixel.
+// Fused G5, persistent over units (window, 4 rows):
+//   D_y[x][o] = Gx[x][:] T3_y[o][:]^T + X_y[x][:] W[o][:]^T
+// then + bias, leaky-ReLU (not after the last block), written back to X.
+// The MMA has M = 128 rows but only x < 80 are real: the X tiles of a stage
+// are packed 80 rows apart, so rows 80..127 of one tile read the next tile
+// (or the stage's slack), and the corresponding accumulator rows are never
+// read back.  Gx and W are loaded once per CTA; the next unit's X and T3
+// tiles are prefetched into the other stage while the current unit runs.
+// 8 warps: warps w and w+4 share TMEM lanes 32(w%4).. and split the rows.
+constexpr int G5_ROWS = 4;
+constexpr int G5_THREADS = 256;
+constexpr uint32_t G5_XT = 80 * 32 * 2;                              // one packed [80][32] X tile
+constexpr uint32_t G5_STAGE = G5_ROWS * G5_XT + 48 * 64 + G5_ROWS * 2048;  // X tiles + slack + T3 tiles
+constexpr uint32_t G5_GX = 128 * 32 * 2;
+constexpr uint32_t G5_SMEM = G5_GX + 2048 + 2 * G5_STAGE + 16;
+
+__device__ __forceinline__ void g5_load(uint8_t* stg, const bf16* X, const bf16* T3, int b, int y0) {
+  const int tid = threadIdx.x;
+  for (int c = tid; c < G5_ROWS * 80 * 4; c += G5_THREADS) {
+    const int yy = c / 320, r = c % 320;
+    const int t8 = r & 7, rest = r >> 3, kc = rest & 3, rg = rest >> 2;
+    tc::cp_async16(stg + yy * G5_XT + (rg * 4 + kc) * 128 + t8 * 16,
+                   X + (((size_t)b * 80 + y0 + yy) * 80 + rg * 8 + t8) * 32 + kc * 8, true);
+  }
+  for (int c = tid; c < G5_ROWS * 128; c += G5_THREADS) {
+    const int yy = c >> 7, r = c & 127;
+    const int t8 = r & 7, rest = r >> 3, kc = rest & 3, rg = rest >> 2;
+    tc::cp_async16(stg + G5_ROWS * G5_XT + 48 * 64 + yy * 2048 + (rg * 4 + kc) * 128 + t8 * 16,
+                   T3 + (((size_t)b * 80 + y0 + yy) * 32 + rg * 8 + t8) * 32 + kc * 8, true);
+  }
+}
+
+__global__ void __launch_bounds__(G5_THREADS) g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb,
+                                                        const float* bias, int last, int total, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sAg = smem;                       // Gx, [128][32] (rows >= 80 zero)
+  uint8_t* sBw = smem + G5_GX;               // W, [32][32]
+  uint8_t* stage[2] = {smem + G5_GX + 2048, smem + G5_GX + 2048 + G5_STAGE};
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + G5_SMEM - 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G5_SMEM - 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int UPW = 80 / G5_ROWS;  // units per window
+  int u = blockIdx.x;
+  if (u >= total) return;
+  for (int c = tid; c < 128 * 4; c += G5_THREADS) {
+    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
+    tc::cp_async16(sAg + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
+  }
+  if (tid < 128) {
+    const int t8 = tid & 7, rest = tid >> 3, kc = rest & 3, rg = rest >> 2;
+    tc::cp_async16(sBw + (rg * 4 + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * 32 + kc * 8, true);
+  }
+  g5_load(stage[0], X, T3, u / UPW, (u % UPW) * G5_ROWS);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  float bs[32];
+#pragma unroll
+  for (int o = 0; o < 32; ++o) bs[o] = bias[o];
+  if (tid == 0) tc::mbar_init(tc::smem_u32(mbar), 1);
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 32 * G5_ROWS);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  constexpr uint32_t idesc = tc::idesc_bf16(32, false, false);
+  const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter, row half
+  for (int i = 0; u < total; u += gridDim.x, ++i) {
+    const int st = i & 1;
+    const int b = u / UPW, y0 = (u % UPW) * G5_ROWS;
+    const int next = u + gridDim.x;
+    if (next < total) g5_load(stage[st ^ 1], X, T3, next / UPW, (next % UPW) * G5_ROWS);
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 1;" ::: "memory");
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t ag = tc::smem_u32(sAg), bw = tc::smem_u32(sBw), ax0 = tc::smem_u32(stage[st]);
+      const uint32_t bt0 = ax0 + G5_ROWS * G5_XT + 48 * 64;
+      for (int yy = 0; yy < G5_ROWS; ++yy) {
+        const uint32_t d = tmem + yy * 32;
+        for (int s = 0; s < 2; ++s)
+          tc::mma_bf16(d, tc::make_desc(ag + s * 256, 128, 512), tc::make_desc(bt0 + yy * 2048 + s * 256, 128, 512),
+                       idesc, s > 0);
+        for (int s = 0; s < 2; ++s)
+          tc::mma_bf16(d, tc::make_desc(ax0 + yy * G5_XT + s * 256, 128, 512),
+                       tc::make_desc(bw + s * 256, 128, 512), idesc, 1);
+      }
+      tc::mma_commit(tc::smem_u32(mbar));
+    }
+    if (!tc::mbar_wait(tc::smem_u32(mbar), (uint32_t)(i & 1), WAIT_LIMIT)) atomicExch(err, 1);
+    tc::fence_after();
+    if (quarter < 3) {
+      const int x = quarter * 32 + lane;
+      for (int yy = half * (G5_ROWS / 2); yy < (half + 1) * (G5_ROWS / 2); ++yy) {
+        float v[32];
+        tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + yy * 32, v);
+        tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + yy * 32 + 16, v + 16);
+        if (x < 80) {
+          uint32_t p[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            float a = v[2 * q] + bs[2 * q], c = v[2 * q + 1] + bs[2 * q + 1];
+            if (!last) { a = leaky(a); c = leaky(c); }
+            p[q] = pack2(a, c);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(X + (((size_t)b * 80 + y0 + yy) * 80 + x) * 32);
+          dst[0] = make_uint4(p[0], p[1], p[2], p[3]);
+          dst[1] = make_uint4(p[4], p[5], p[6], p[7]);
+          dst[2] = make_uint4(p[8], p[9], p[10], p[11]);
+          dst[3] = make_uint4(p[12], p[13], p[14], p[15]);
+        }
+      }
+    }
+    tc::fence_before();
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_free(tmem, 32 * G5_ROWS);
+  }
+}
+
 __global__ void __launch_bounds__(256) pack_kernel(NnoInput in, GridGeom g, bf16* out, float* rho_out) {
   __shared__ double sh[8];
   __shared__ float s_inv;
   const int b = blockIdx.x;
-  const int w = in.win_id ? in.win_id[b] : b;
+  int w = in.win_id ? in.win_id[b] : b;
+  if (in.ptab) {  // multi-problem batch: this entry's problem supplies geometry and input
+    const int2 e = in.wtab[b];
+    const ProbGeom P = in.ptab[e.x];
+    w = e.y;
+    g.nx = P.nx; g.ny = P.ny; g.nwx = P.nwx; g.k2 = P.k2; g.eps = P.eps; g.isx = P.isx; g.isy = P.isy;
+    in.v_global = P.v;
+  }
   const int a = w % g.nwx, bb = w / g.nwx;
   const int x0 = min(max(FDFD_CORE * a - FDFD_OVL, 0), g.nx - FDFD_WIN);
   const int y0 = min(max(FDFD_CORE * bb - FDFD_OVL, 0), g.ny - FDFD_WIN);
@@ -437,6 +613,8 @@ __global__ void __launch_bounds__(256) pack_kernel(NnoInput in, GridGeom g, bf16
 
 // Self-test operator: plain row-major C = A B^T.
 struct TestOp {
+  static constexpr bool kConstB = false;
+  static constexpr bool kUnroll = false;
   const bf16* A; const bf16* B; float* C; int M, N, K, amn;
   typedef NoState State;
   __device__ int rows(int) const { return M; }
@@ -540,8 +718,10 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
   if ((rc = up(&W->P1, to_bf16(std::vector<float>(p, p + 128 * 32)), bytes))) return rc;
   p += 128 * 32;
   if ((rc = up(&W->p1b, std::vector<float>(p, p + 128), bytes))) return rc;
+  memcpy(W->hp1b, p, sizeof(W->hp1b));
   p += 128;
   if ((rc = up(&W->P2, std::vector<float>(p, p + 256), bytes))) return rc;
+  memcpy(W->hP2, p, sizeof(W->hP2));
   p += 256;
   W->p2b[0] = p[0];
   W->p2b[1] = p[1];
@@ -594,11 +774,14 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     ProfScope ps(h, 8, 1);
     if ((rc = launch_gemm<32, 16, false>(LiftOp{k->in, W->lift_w, W->lift_b, k->X}, NPIX / 128, n, k->err, s))) return rc;
   }
-  static bool g5_attr = false;
-  if (!g5_attr) {
+  static int g5_cap = 0;
+  if (!g5_cap) {
+    CK(cudaFuncSetAttribute(g3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G3_SMEM));
     CK(cudaFuncSetAttribute(g5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
-    g5_attr = true;
+    g5_cap = persistent_grid((const void*)g5_kernel, G5_THREADS, G5_SMEM, 32 * G5_ROWS);
   }
+  const int g5_total = n * (80 / G5_ROWS);
+  const int g5_grid = g5_total < g5_cap ? g5_total : g5_cap;
   for (int bl = 0; bl < 4; ++bl) {
     {
       ProfScope ps(h, 9, 1);
@@ -610,8 +793,9 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     }
     {
       ProfScope ps(h, 11, 1);
-      if ((rc = launch_gemm<64, 64, false>(G3Op{k->Xh, W->R[bl], k->Yh, k->cap, n}, (n + 127) / 128, 512, k->err, s)))
-        return rc;
+      const int wtiles = (n + 127) / 128;
+      g3_kernel<<<wtiles * (32 / G3_Q) * 16, 128, G3_SMEM, s>>>(k->Xh, W->R[bl], k->Yh, k->cap, n, wtiles, k->err);
+      CKL();
     }
     {
       ProfScope ps(h, 12, 1);
@@ -619,13 +803,17 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     }
     {
       ProfScope ps(h, 13, 1);
-      g5_kernel<<<dim3(80 / G5_ROWS, n), 128, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], bl == 3, k->err);
+      g5_kernel<<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], bl == 3, g5_total, k->err);
       CKL();
     }
   }
-  ProjOp po{k->X, W->P1, W->p1b, W->P2, W->p2b[0], W->p2b[1], k->rho, out.scale, in.win_id,
+  ProjOp po{k->X, W->P1, W->p2b[0], W->p2b[1], k->rho, out.scale, in.win_id,
             out.z_global, out.e_win, g.nx, g.nwx, out.scale_win};
   po.ny_ = g.ny;
+  po.wtab = in.wtab;
+  po.ptab = in.ptab;
+  memcpy(po.p1b, W->hp1b, sizeof(po.p1b));
+  memcpy(po.P2, W->hP2, sizeof(po.P2));
   {
     ProfScope ps(h, 14, 1);
     if ((rc = launch_gemm<128, 32, false>(po, NPIX / 128, n, k->err, s))) return rc;

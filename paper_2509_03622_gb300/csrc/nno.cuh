@@ -18,6 +18,8 @@ struct NnoWeights {
   float* p1b = nullptr;     // [128]
   float* P2 = nullptr;      // [2][128]
   float p2b[2] = {0.f, 0.f};
+  float hp1b[128] = {};     // host copies of p1b and P2: the projection epilogue
+  float hP2[256] = {};      // takes them as kernel parameters (constant bank)
 };
 
 struct NnoWork {
@@ -32,12 +34,28 @@ struct NnoWork {
   int* err = nullptr;       // bounded-wait failure flag
 };
 
+// One problem of a multi-problem window batch (batching pattern).
+struct ProbGeom {
+  int nx, ny, nwx;
+  float k2;
+  const float* eps;
+  const float2* isx;
+  const float2* isy;
+  const float2* v;       // preconditioner input field of this problem
+  float2* z;             // output field (restricted prolongation)
+  const double* scale;   // output scale (device scalar)
+};
+
 // Where the packed inputs come from.
 struct NnoInput {
   const float2* v_global = nullptr;  // residual source: global field (restricted per window), or
   const float2* r_win = nullptr;     //   per-window residuals [n][80][80], or neither (zero)
   const float2* g_win = nullptr;     // Robin data [n][4][80] (nullptr = zero)
   const int* win_id = nullptr;       // window of each batch entry (nullptr = identity)
+  // multi-problem batch: entry b is window wtab[b].y of problem ptab[wtab[b].x]
+  // (geometry, input and output then come from the table)
+  const int2* wtab = nullptr;
+  const ProbGeom* ptab = nullptr;
 };
 
 // Where the output goes.

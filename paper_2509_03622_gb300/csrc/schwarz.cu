@@ -105,7 +105,7 @@ void schwarz_destroy(fdfd_ctx* h) {
   h->sw = nullptr;
 }
 
-int schwarz_apply(fdfd_ctx* h, const float2* v, const double* scale_dev, float2* z, int /*transpose*/) {
+int schwarz_apply(fdfd_ctx* h, const float2* v, const double* scale_dev, float2* z, int transpose) {
   SchwarzData* S = h->sw;
   NnoInput in;
   in.v_global = v;
@@ -114,7 +114,7 @@ int schwarz_apply(fdfd_ctx* h, const float2* v, const double* scale_dev, float2*
   out.scale = scale_dev;
   int rc;
   if (S->inner > 0)
-    rc = local_fgmres(h, &S->local, &S->W, &S->work, v, nullptr, z, nullptr, scale_dev);
+    rc = local_fgmres(h, &S->local, &S->W, &S->work, v, nullptr, z, nullptr, scale_dev, transpose);
   else
     rc = nno_forward(&S->W, &S->work, geom(h), in, out, S->n_win, h->stream, h);
   if (rc) return rc;
@@ -140,6 +140,14 @@ int schwarz_nno_solve(fdfd_ctx* h, const float2* r_win, const float2* g_win, con
 }
 
 const NnoWeights* schwarz_weights(fdfd_ctx* h) { return (h && h->sw) ? &h->sw->W : nullptr; }
+
+int schwarz_inner_iters(fdfd_ctx* h) { return (h && h->sw) ? h->sw->inner : 0; }
+
+// Coarse correction of a one-level sweep result z (no-op without a coarse space).
+int schwarz_coarse(fdfd_ctx* h, float2* z) {
+  if (!h->sw || !h->sw->coarse) return FDFD_OK;
+  return coarse_apply(h, h->sw->coarse, z);
+}
 
 int schwarz_export(fdfd_ctx* h, double* Q, double* Nd) {
   if (!h->sw->coarse) return FDFD_ENOSETUP;

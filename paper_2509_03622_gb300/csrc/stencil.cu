@@ -125,12 +125,13 @@ __global__ void jacobi_apply(const float2* __restrict__ v, const double* __restr
   }
 }
 
-// FP64 residual r = b - A~ x with FP64 coefficients, x in FP64; b = j sb J
-// (source form) or b = J (adjoint right-hand side).  Writes r rounded to
-// complex64 and reduces ||r||^2 (FP64) into *result.
+// FP64 residual r = rs b - A~ x with FP64 coefficients, x in FP64; b = j sb J
+// (source form) or b = J (adjoint right-hand side); rs rescales the system
+// (a power of two, so exactly).  Writes r rounded to complex64 and reduces
+// ||r||^2 (FP64) into *result.
 constexpr int RT = 256;
 __global__ void __launch_bounds__(RT)
-residual64(const double2* __restrict__ x, const float2* __restrict__ J, double sb, int src,
+residual64(const double2* __restrict__ x, const float2* __restrict__ J, double sb, int src, double rs,
            const float* __restrict__ eps, const AxisCoef64* __restrict__ cx,
            const AxisCoef64* __restrict__ cy, double k2, int nx, int ny,
            float2* __restrict__ r_out, double* __restrict__ partials, unsigned* counter,
@@ -148,8 +149,8 @@ residual64(const double2* __restrict__ x, const float2* __restrict__ J, double s
     if (j > 0) Ax = zadd(Ax, zmul(b.lo, x[c - nx]));
     if (j + 1 < ny) Ax = zadd(Ax, zmul(b.hi, x[c + nx]));
     const float2 Jc = J[c];
-    const double2 bc = src ? make_double2(-sb * (double)Jc.y, sb * (double)Jc.x)
-                           : make_double2((double)Jc.x, (double)Jc.y);
+    const double2 bc = src ? make_double2(-sb * rs * (double)Jc.y, sb * rs * (double)Jc.x)
+                           : make_double2(rs * (double)Jc.x, rs * (double)Jc.y);
     const double2 r = zsub(bc, Ax);
     r_out[c] = make_float2((float)r.x, (float)r.y);
     acc += r.x * r.x + r.y * r.y;
@@ -173,7 +174,27 @@ __global__ void grad_eps_kernel(const float2* __restrict__ E, const float2* __re
   }
 }
 
+__global__ void scale_d_kernel(const float2* in, float2* out, const float2* __restrict__ isx,
+                               const float2* __restrict__ isy, int nx, size_t n, int inverse) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const float2 dinv = cmul(isx[c % nx], isy[c / nx]);  // 1 / (s_x s_y)
+    float2 f = dinv;
+    if (!inverse) {
+      const float m = dinv.x * dinv.x + dinv.y * dinv.y;
+      f = make_float2(dinv.x / m, -dinv.y / m);
+    }
+    out[c] = cmul(in[c], f);
+  }
+}
+
 }  // namespace
+
+int launch_scale_d(const float2* in, float2* out, const float2* isx, const float2* isy, int nx, size_t n,
+                   int inverse, cudaStream_t s) {
+  scale_d_kernel<<<krylov_grid(n), 256, 0, s>>>(in, out, isx, isy, nx, n, inverse);
+  CKL();
+  return FDFD_OK;
+}
 
 int launch_stencil(const float2* x, float2* y, const float* eps, const AxisCoef* cx,
                    const AxisCoef* cy, float k2, int nx, int ny, cudaStream_t s) {
@@ -203,11 +224,11 @@ int launch_jacobi_apply(const float2* v, const double* vscale, float2* z, const 
   return FDFD_OK;
 }
 
-int launch_residual64(const double2* x, const float2* J, double sb, int rhs_is_source,
+int launch_residual64(const double2* x, const float2* J, double sb, int rhs_is_source, double rs,
                       const float* eps, const AxisCoef64* cx, const AxisCoef64* cy, double k2,
                       int nx, int ny, float2* r_out, double* partials, unsigned* counter,
                       double* result, cudaStream_t s) {
-  residual64<<<krylov_grid((size_t)nx * ny), RT, 0, s>>>(x, J, sb, rhs_is_source, eps, cx, cy, k2,
+  residual64<<<krylov_grid((size_t)nx * ny), RT, 0, s>>>(x, J, sb, rhs_is_source, rs, eps, cx, cy, k2,
                                                           nx, ny, r_out, partials, counter, result);
   CKL();
   return FDFD_OK;

@@ -81,6 +81,9 @@ _SIGS = {
     "fdfd_nno_solve": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "fdfd_trace_extract": ([_P, _P, _P], C.c_int),
     "fdfd_local_apply": ([_P, _P, _P, _P, C.c_int], C.c_int),
+    "fdfd_batch_create": ([C.POINTER(_P), C.c_int, C.c_int, C.POINTER(_P)], C.c_int),
+    "fdfd_solve_batched": ([_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(SolveOpts), C.POINTER(SolveStats)], C.c_int),
+    "fdfd_batch_destroy": ([_P], None),
     "fdfd_nno_solve_noalloc": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "fdfd_coarse_export": ([_P, _P, _P], C.c_int),
     "fdfd_profile_start": ([_P], C.c_int),
@@ -251,3 +254,34 @@ class Solver:
         Nd = np.zeros((nw, k, k, 2), dtype=np.float64)
         _check(lib.fdfd_coarse_export(self.h, Q.ctypes.data, Nd.ctypes.data), "fdfd_coarse_export")
         return Q[..., 0] + 1j * Q[..., 1], Nd[..., 0] + 1j * Nd[..., 1]
+
+
+class Batch:
+    """Lock-step solves of several problems (fdfd_batch_create ... destroy)."""
+
+    def __init__(self, solvers, max_windows: int = 0):
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        b = C.c_void_p()
+        _check(lib.fdfd_batch_create(arr, len(self.solvers), max_windows, C.byref(b)), "fdfd_batch_create")
+        self.b = b
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib.fdfd_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, Js, Es, restart=30, max_iters=1000, tol=1e-6, precond=PRECOND_SCHWARZ, use_x0=False):
+        n = len(self.solvers)
+        jp = (C.c_void_p * n)(*[_ptr(J).value for J in Js])
+        ep = (C.c_void_p * n)(*[_ptr(E).value for E in Es])
+        st = (SolveStats * n)()
+        o = Solver._opts(restart, max_iters, tol, precond, use_x0)
+        rc = _check(lib.fdfd_solve_batched(self.b, jp, ep, C.byref(o), st), "fdfd_solve_batched")
+        return rc, [s.as_dict() for s in st]

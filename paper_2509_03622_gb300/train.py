@@ -189,6 +189,105 @@ def boundary_rhs(t, g, P):
     return out
 
 
+def dense_operator(t, P):
+    """Dense A_w [B][6400][6400] of the local Robin problems (same stencil as
+    local_apply), for exact training targets."""
+    B = P["eps"].shape[0]
+    n = WIN * WIN
+    dev = P["eps"].device
+    A = t.zeros(B, n, n, dtype=t.complex64, device=dev)
+    idx = t.arange(n, device=dev)
+    lx, ly = idx % WIN, idx // WIN
+    xlo, xhi, ylo, yhi = P["xlo"], P["xhi"], P["ylo"], P["yhi"]
+    k2 = (P["k0dx"] ** 2)[:, None]
+    epsf = P["eps"].reshape(B, n)
+    kd = P["k0dx"][:, None] * t.sqrt(epsf)
+    f = 1 - 1j * kd
+    dg = -(xlo + xhi)[:, lx] - (ylo + yhi)[:, ly] + k2 * epsf
+    rb = P["robin"]
+    dg = dg + t.where((lx == 0)[None] & rb[:, 0:1], xlo[:, lx] * f, t.zeros_like(dg))
+    dg = dg + t.where((lx == WIN - 1)[None] & rb[:, 1:2], xhi[:, lx] * f, t.zeros_like(dg))
+    dg = dg + t.where((ly == 0)[None] & rb[:, 2:3], ylo[:, ly] * f, t.zeros_like(dg))
+    dg = dg + t.where((ly == WIN - 1)[None] & rb[:, 3:4], yhi[:, ly] * f, t.zeros_like(dg))
+    A[:, idx, idx] = dg
+    m = lx > 0
+    A[:, idx[m], idx[m] - 1] = xlo[:, lx[m]]
+    m = lx < WIN - 1
+    A[:, idx[m], idx[m] + 1] = xhi[:, lx[m]]
+    m = ly > 0
+    A[:, idx[m], idx[m] - WIN] = ylo[:, ly[m]]
+    m = ly < WIN - 1
+    A[:, idx[m], idx[m] + WIN] = yhi[:, ly[m]]
+    return A
+
+
+def expand(P, reps):
+    """Repeat each window's parameters `reps` times (several right-hand sides per window)."""
+    return {k: v.repeat_interleave(reps, 0) for k, v in P.items()}
+
+
+def train_data(minutes, windows, rhs_per_win, lr, seed, out, log_every, device, init, c_res=0.3):
+    """Supervised training on exact local solutions (LU of the dense local
+    operator, several right-hand sides per factorisation) plus the residual
+    loss; second step trained on the residual of the first (Algorithm 2)."""
+    import torch as t
+    from paper_2509_03622_gb300 import workloads as wl
+    dev = t.device(device)
+    t.manual_seed(seed)
+    t.backends.cuda.matmul.allow_tf32 = True
+    w0 = wl.unpack_weights(np.load(init)) if init else wl.nno_weights(seed)
+    model = build_model(t, w0).to(dev)
+    opt = t.optim.Adam(model.parameters(), lr=lr)
+    S = Sampler(t, dev, windows)
+    t0, it, hist = time.time(), 0, []
+    R = rhs_per_win
+    while time.time() - t0 < minutes * 60:
+        frac = (time.time() - t0) / (minutes * 60)
+        for gp in opt.param_groups:
+            gp["lr"] = lr * 0.5 * (1 + math.cos(math.pi * min(frac, 1.0)))
+        P = S.batch()
+        with t.no_grad():
+            A = dense_operator(t, P)
+            LU, piv = t.linalg.lu_factor(A)
+            del A
+        Pe = expand(P, R)
+        Bt = windows * R
+        sig = t.rand(Bt, device=dev) * 6.0
+        r = S.smooth_noise((Bt, WIN, WIN), sig) if hasattr(S, "smooth_noise") else None
+        g = t.randn(Bt, 4, WIN, dtype=t.complex64, device=dev)
+        kindr = t.rand(Bt, device=dev)
+        r = t.where((kindr < 0.25)[:, None, None], t.zeros_like(r), r)
+        g = t.where((kindr > 0.5)[:, None, None], t.zeros_like(g), g)
+        g = g * Pe["robin"][:, :, None]
+        rhs = r + boundary_rhs(t, g, Pe)
+        with t.no_grad():
+            b = rhs.reshape(windows, R, WIN * WIN).transpose(1, 2)
+            xs = t.linalg.lu_solve(LU, piv, b).transpose(1, 2).reshape(Bt, WIN, WIN)
+        nx_ = (xs.abs() ** 2).sum((1, 2)).clamp(min=1e-30)
+        nr_ = (rhs.abs() ** 2).sum((1, 2)).clamp(min=1e-30)
+        opt.zero_grad()
+        e1 = solve(t, model, r, g, Pe)
+        l1 = ((e1 - xs).abs() ** 2).sum((1, 2)) / nx_
+        res1 = rhs - local_apply(t, e1, Pe)
+        p1 = (res1.abs() ** 2).sum((1, 2)) / nr_
+        res1d = res1.detach()
+        e2 = solve(t, model, res1d, t.zeros_like(g), Pe)
+        tgt2 = (xs - e1.detach())
+        l2 = ((e2 - tgt2).abs() ** 2).sum((1, 2)) / (tgt2.abs() ** 2).sum((1, 2)).clamp(min=1e-30)
+        loss = (l1.clamp(max=4.0).mean() + l2.clamp(max=4.0).mean() + c_res * p1.clamp(max=4.0).mean()) / (2 + c_res)
+        loss.backward()
+        t.nn.utils.clip_grad_norm_(model.parameters(), 1.0)
+        opt.step()
+        it += 1
+        hist.append((float(l1.mean()), float(l2.mean()), float(p1.mean())))
+        if it % log_every == 0:
+            h = np.mean(hist[-log_every:], axis=0)
+            print(f"it {it} t {time.time() - t0:.0f}s field-err1 {h[0]:.4f} field-err2 {h[1]:.4f} "
+                  f"resid1 {h[2]:.4f}", flush=True)
+    np.save(out, wl.pack_weights(model.export()))
+    print(f"saved {out} after {it} iterations")
+
+
 def pack(t, r, g, P):
     rho = t.sqrt((r.abs() ** 2).sum((1, 2)) + (g.abs() ** 2).sum((1, 2))) / WIN
     inv = t.where(rho > 0, 1.0 / rho, t.zeros_like(rho))
@@ -285,6 +384,12 @@ if __name__ == "__main__":
     ap.add_argument("--device", default="cuda")
     ap.add_argument("--init", default=None, help="start from a saved weight blob")
     ap.add_argument("--log-every", type=int, default=200)
+    ap.add_argument("--mode", default="physics", choices=["physics", "data"])
+    ap.add_argument("--windows", type=int, default=4, help="data mode: windows factored per step")
+    ap.add_argument("--rhs", type=int, default=16, help="data mode: right-hand sides per window")
     a = ap.parse_args()
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
-    train(a.minutes, a.batch, a.recur, a.lr, a.seed, a.out, a.log_every, a.device, a.init)
+    if a.mode == "data":
+        train_data(a.minutes, a.windows, a.rhs, a.lr, a.seed, a.out, a.log_every, a.device, a.init)
+    else:
+        train(a.minutes, a.batch, a.recur, a.lr, a.seed, a.out, a.log_every, a.device, a.init)

@@ -1,0 +1,93 @@
+"""Solve-level parity: the field returned by fdfd_solve (Schwarz neural-
+operator FGMRES, inner NN-FGMRES local solves, FP64 refinement at restarts)
+matches the FP64 oracle's sparse direct solve to 1e-5 relative L2; at larger
+sizes the reported FP64 residual equals the oracle's own CSR residual of the
+returned field."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fdfd as OF
+from paper_2509_03622_gb300 import workloads as wl
+
+LAM = 1.55e-6
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _weights():
+    p = os.path.join(ROOT, "paper_2509_03622_gb300", "weights", "nno_trained.npy")
+    return np.load(p) if os.path.exists(p) else wl.pack_weights(wl.nno_weights(0))
+
+
+@pytest.mark.parametrize("case", ["rect128", "free128"])
+def test_solve_matches_direct_oracle(case):
+    import torch
+    from paper_2509_03622_gb300 import fdfd as F
+    n = 128
+    if case == "rect128":
+        eps, dx = wl.rectangles_eps(n, n, n_rect=6, seed=1001), LAM / 25
+    else:
+        eps, dx = wl.freeform_eps(n, n, seed=2128), LAM / 30
+    J = wl.point_source(n, n)
+    S = F.Solver(torch.from_numpy(eps).cuda(), dx, LAM, npml=20)
+    S.schwarz_setup(_weights(), k_coarse=0, inner_iters=16)
+    E = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    rc, st = S.solve(torch.from_numpy(J).cuda(), E, restart=30, max_iters=2000, tol=1e-7)
+    assert rc == F.OK, st
+    Eo = OF.solve_direct(eps, J, dx, LAM, 20)
+    err = np.linalg.norm(E.cpu().numpy() - Eo) / np.linalg.norm(Eo)
+    assert err < 1e-5, (err, st)
+    assert st["relres_true"] <= 1e-7
+    # the FP64 iterate met the tolerance; the returned complex64 field adds
+    # at most its own rounding (the relres of the exact field rounded to complex64)
+    A = OF.assemble_operator(eps, dx, LAM, 20)
+    b = OF.source_rhs(J, dx, LAM)
+    rr = OF.relres(A, E.cpu().numpy().ravel(), b)
+    floor = OF.relres(A, Eo.astype(np.complex64).astype(np.complex128).ravel(), b)
+    assert rr <= 1e-7 + 2 * floor, (rr, floor)
+
+
+@pytest.mark.parametrize("precond", [1, 2])
+def test_solve_is_scale_invariant(precond):
+    """A right-hand side scaled by 2^-70 (the size of a typical adjoint source)
+    gives the same iterates: the field scaled by exactly 2^-70 (entries that
+    the scaling pushes into the FP32 subnormal range lose bits on output)."""
+    import torch
+    from paper_2509_03622_gb300 import fdfd as F
+    n = 128
+    eps, dx = wl.freeform_eps(n, n, seed=2128), LAM / 30
+    S = F.Solver(torch.from_numpy(eps).cuda(), dx, LAM, npml=20)
+    if precond == 2:
+        S.schwarz_setup(_weights(), k_coarse=0, inner_iters=4)
+    J = torch.from_numpy(wl.point_source(n, n)).cuda()
+    out = []
+    for f in (1.0, 2.0 ** -70):
+        E = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+        rc, st = S.solve(J * f, E, restart=30, max_iters=40, tol=1e-12, precond=precond)
+        out.append((E.cpu().numpy(), st))
+    (E1, s1), (E2, s2) = out
+    assert s1["iters"] == s2["iters"] == 40 and s1["relres_true"] == s2["relres_true"]
+    big = np.abs(E1) > 1e-10 * np.abs(E1).max()
+    assert np.array_equal((E2 * np.float32(2.0 ** 70))[big], E1[big])
+    assert np.max(np.abs(E2 * np.float32(2.0 ** 70) - E1)) <= 1e-9 * np.abs(E1).max()
+
+
+def test_reported_residual_is_true_residual_1024():
+    """At 1024^2 (256 windows, the precision-pattern workload) after a fixed
+    number of steps: the FP64 relres the solver reports equals the oracle's
+    CSR relres of the returned complex64 field."""
+    import torch
+    from paper_2509_03622_gb300 import fdfd as F
+    n, dx = 1024, LAM / 30
+    eps = wl.freeform_eps(n, n, seed=3024)
+    J = wl.point_source(n, n)
+    S = F.Solver(torch.from_numpy(eps).cuda(), dx, LAM, npml=20)
+    S.schwarz_setup(_weights(), k_coarse=0, inner_iters=2)
+    E = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+    rc, st = S.solve(torch.from_numpy(J).cuda(), E, restart=30, max_iters=45, tol=1e-9)
+    assert rc == F.NOT_CONVERGED and st["iters"] == 45
+    A = OF.assemble_operator(eps, dx, LAM, 20)
+    rr = OF.relres(A, E.cpu().numpy().ravel(), OF.source_rhs(J, dx, LAM))
+    assert abs(rr - st["relres_true"]) <= 1e-4 * rr

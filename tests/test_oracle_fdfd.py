@@ -80,6 +80,20 @@ def test_greens_function_hankel_second_order():
     assert 3.0 < e20 / e40 < 5.5 and 3.0 < e40 / e80 < 5.5
 
 
+def test_pml_operator_symmetrised_by_stretch_factors():
+    """With D = diag(s_x s_y) at cell centres, D A~ is complex symmetric
+    (the stretched Laplacian is -G^T S^-1 G per axis), so A~^T = D A~ D^-1:
+    the adjoint of the PML operator is a diagonal similarity of it."""
+    n, dx = 48, LAM / 25
+    eps = wl.rectangles_eps(n, n, npml=8, n_rect=4, seed=2)
+    A = fdfd.assemble_operator(eps, dx, LAM, npml=(8, 5, 6, 9))
+    sxn, _, syn, _ = fdfd.pml_factors(n, n, dx, LAM, (8, 5, 6, 9))
+    import scipy.sparse as sp
+    DA = sp.diags(np.outer(syn, sxn).ravel()) @ A
+    assert abs(DA - DA.T).max() < 1e-12 * abs(DA).max()
+    assert abs(A - A.T).max() > 1e-3  # A~ itself is not symmetric in the PML
+
+
 def test_reciprocity_heterogeneous():
     n = 96
     dx = LAM / 25

@@ -72,3 +72,16 @@ def test_fno_twin_matches_oracle():
     back = wl.unpack_weights(wl.pack_weights(model.export()))
     for k in w:
         assert np.array_equal(back[k], w[k])
+
+
+def test_dense_operator_matches_stencil():
+    """The dense local operator used for exact training targets equals the
+    matrix-free local_apply (and hence the oracle's A_w)."""
+    S = T.Sampler(torch, torch.device("cpu"), 2)
+    torch.manual_seed(3)
+    P = S.batch()
+    A = T.dense_operator(torch, P)
+    e = torch.randn(2, 80, 80, dtype=torch.complex64)
+    y1 = (A @ e.reshape(2, -1, 1)).reshape(2, 80, 80)
+    y2 = T.local_apply(torch, e, P)
+    assert torch.allclose(y1, y2, rtol=1e-4, atol=1e-5 * y2.abs().max())
