@@ -97,9 +97,10 @@ WIN_BYTES = {
     "nno_dft_y": 160 * 512 * 2 + 512 * 64 * 2,
     "nno_mix": 512 * 64 * 2 * 2,              # spectrum in and out (weights amortised)
     "nno_idft_y": 512 * 64 * 2 + 80 * 32 * 32 * 2,
-    "nno_idft_x_mix_act": 6400 * 64 * 2 + 80 * 32 * 32 * 2,
+    "nno_idft_x_mix_act": 6400 * 64 * 2 + 80 * 32 * 32 * 2,   # + T1 out in blocks 0..2 (below)
     "nno_proj": 6400 * 64 + 4096 * 8,         # activation in, core field out
 }
+G5_T1_BYTES = 160 * 512 * 2                   # next block's half-spectrum, written by blocks 0..2
 # Useful FLOPs per window of each stage (padding excluded).
 NNO_FLOP_PER_WIN = {
     "nno_lift": 6400 * 32 * 15 * 2, "nno_dft_x": 2560 * 32 * 80 * 2, "nno_dft_y": 512 * 64 * 160 * 2,
@@ -109,8 +110,8 @@ NNO_FLOP_PER_WIN = {
 KERNEL_NAMES = {"stencil": "stencil_c64", "cgs_dots": "cgs_dots_kernel", "cgs_update": "cgs_update_kernel",
                 "residual64": "residual64", "nno_pack": "pack_kernel", "nno_lift": "gemm_kernel<32,16> (LiftOp)",
                 "nno_dft_x": "gemm_kernel<32,80,MN> (G1Op)", "nno_dft_y": "gemm_kernel<64,160,MN> (G2Op)",
-                "nno_mix": "gemm_kernel<64,64> (G3Op)", "nno_idft_y": "gemm_kernel<160,64> (G4Op)",
-                "nno_idft_x_mix_act": "g5_kernel", "nno_proj": "gemm_kernel<128,32> (ProjOp)"}
+                "nno_mix": "g3_kernel", "nno_idft_y": "gemm_kernel<160,64> (G4Op)",
+                "nno_idft_x_mix_act": "g5_kernel", "nno_proj": "proj_kernel", "rhs_norm": "residual64 (x = 0)"}
 
 
 def algorithmic_bytes(cls, launches, N, steps):
@@ -124,9 +125,12 @@ def algorithmic_bytes(cls, launches, N, steps):
         return float(sum((8 * (j + 1) + extra) * N for j in js))
     if cls == "residual64":
         return 36.0 * N * launches
+    if cls == "rhs_norm":
+        return 16.0 * N * launches
     if cls in WIN_BYTES:
         per = WIN_BYTES[cls] * nwin + (512 * 64 * 64 * 2 if cls == "nno_mix" else 0)
-        return float(per) * launches
+        extra = G5_T1_BYTES * nwin * (launches * 3 // 4) if cls == "nno_idft_x_mix_act" else 0
+        return float(per) * launches + extra
     return None
 
 
@@ -269,6 +273,15 @@ def main():
         dist.barrier()
     steps = st["iters"]
     value = world * n * n * steps / (ms / 1e3) / 1e6
+    # the same steps replayed as CUDA graphs (profiling off), for comparison
+    S.use_graphs = True
+    S.solve(Jd, E, restart=30, max_iters=min(args.steps, 30), tol=1e-30, precond=precond)  # capture
+    torch.cuda.synchronize()
+    ev0.record(S.stream)
+    S.solve(Jd, E, restart=30, max_iters=args.steps, tol=1e-30, precond=precond)
+    ev1.record(S.stream)
+    torch.cuda.synchronize()
+    ms_graph = ev0.elapsed_time(ev1)
     # end to end through the host-buffer entry point
     Jh = np.ascontiguousarray(J.astype(np.complex64))
     Eh = np.zeros_like(Jh)
@@ -314,7 +327,9 @@ def main():
             "roofline": roof, "rooflines": roofs, "gpu_launches": prof["total_launches"],
             "e2e": {"value": e2e_value, "unit": "Mcell-it/s", "h2d_bytes_per_step": N * 8 // args.steps,
                     "d2h_bytes_per_step": N * 8 // args.steps},
-            "clocks": clk.summary(), "relres_after_steps": st["relres_true"]}
+            "clocks": clk.summary(), "relres_after_steps": st["relres_true"],
+            "graphs": {"ms_per_step": ms_graph / max(steps, 1),
+                       "note": "same solve with each Arnoldi step replayed as a CUDA graph, unprofiled"}}
     if rank == 0 and not args.no_cpu:
         w = wl.nno_weights(0) if precond == F.PRECOND_SCHWARZ else None
         it = 3 if precond == F.PRECOND_SCHWARZ else 20

@@ -101,6 +101,12 @@ typedef struct {
   double tol;            /* true relative residual ||b~ - A~ E||/||b~||   */
   int    precond;        /* FDFD_PRECOND_*                                 */
   int    use_x0;         /* 1: start from the contents of E               */
+  int    use_graphs;     /* 1: replay each Arnoldi step (preconditioner,
+                            matvec, orthogonalisation) as a CUDA graph,
+                            captured once per handle, restart length,
+                            preconditioner and direction; results are
+                            identical to eager launches.  Ignored while
+                            live profiling is on (fdfd_profile_start). */
 } fdfd_solve_opts;
 
 typedef struct {
@@ -117,6 +123,8 @@ typedef struct {
   int k_coarse;          /* 0 if no coarse space set up                   */
   int n_coarse;          /* n_win * k_coarse                               */
   size_t workspace_bytes;/* device memory held by the handle              */
+  int graphs_cached;     /* Arnoldi-step graph sets currently captured     */
+  int graphs_ok;         /* 0 once a capture failed (eager launches only)  */
 } fdfd_info;
 
 /* ---- handle life cycle ----------------------------------------------- */
@@ -193,13 +201,15 @@ int  fdfd_grad_eps(fdfd_handle h, const fdfd_c64* E_dev, const fdfd_c64* lam_dev
                    float* grad_dev, int accumulate);
 
 /* ---- live profiling (CUDA events on the handle's stream) -------------- */
-#define FDFD_PROF_NCLASS 16
+#define FDFD_PROF_NCLASS 18
 /* kernel classes: 0 stencil A~x (incl. the fused Jacobi form), 1 CGS dots,
  * 2 CGS update + Givens, 3 FP64 residual, 4 solution update / misc vector,
  * 5 neural-operator pack (restriction + inputs), 6 traces, 7 coarse solve
  * and correction, 8 lift GEMM, 9 DFT-x GEMM, 10 DFT-y GEMM, 11 spectral
  * mix GEMM, 12 inverse DFT-y GEMM, 13 fused inverse DFT-x + mixer +
- * activation, 14 projection + prolongation GEMM, 15 unused. */
+ * activation (+ the next block's DFT-x), 14 projection + prolongation,
+ * 15 local Robin operator and Krylov update of the inner NN-FGMRES,
+ * 16 FP64 right-hand-side norm (residual of x = 0), 17 unused. */
 typedef struct {
   double ms[FDFD_PROF_NCLASS];        /* summed device time per class      */
   long long launches[FDFD_PROF_NCLASS];/* kernel launches per class        */

@@ -14,6 +14,14 @@
 #include "nno.cuh"
 #include "local.cuh"
 
+void graphs_invalidate(fdfd_ctx* h) {
+  for (auto& g : h->graphs) {
+    for (auto& e : g.exec)
+      if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+    g.key = -1;
+  }
+}
+
 namespace {
 
 constexpr double MU0 = 1.25663706212e-6;    // vacuum permeability (CODATA 2018)
@@ -107,6 +115,7 @@ int setup_coefs(fdfd_ctx* h) {
 
 void release(fdfd_ctx* h) {
   if (!h) return;
+  graphs_invalidate(h);
   schwarz_destroy(h);
   void* ptrs[] = {h->eps, h->cx, h->cy, h->cxT, h->cyT, h->cx64, h->cy64, h->cxT64, h->cyT64, h->isx, h->isy,
                   h->V, h->Z, h->w, h->x64, h->st, h->partials, h->counter, h->hostJ, h->hostE, h->d_one,
@@ -121,6 +130,7 @@ void release(fdfd_ctx* h) {
   }
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
 
@@ -148,6 +158,54 @@ __global__ void set_bnorm_kernel(KrylovState* st) {
   st->breakdown = 0;
 }
 
+// CUDA graphs of the m Arnoldi steps for `key`, captured on first use (the
+// capture only records launches; nothing runs).  Kernels counted during the
+// capture are booked per replay instead.  Returns nullptr (eager launches)
+// if any capture fails, and stops trying for this handle.
+template <class Step>
+fdfd_ctx::StepGraphs* step_graphs(fdfd_ctx* h, int key, int m, Step& issue_step) {
+  for (auto& g : h->graphs)
+    if (g.key == key) return &g;
+  fdfd_ctx::StepGraphs& g = h->graphs[h->graph_next];
+  h->graph_next = (h->graph_next + 1) % 4;
+  for (auto& e : g.exec)
+    if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+  g.key = -1;
+  // capture on the handle's private stream (the caller's may be the legacy
+  // default stream, which cannot be captured); replays go to the caller's
+  cudaStream_t user = h->stream;
+  h->stream = h->cap_stream;
+  for (int j = 0; j < m; ++j) {
+    const long long before = h->launches_total;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      h->graphs_ok = false;
+      break;
+    }
+    const int rc = issue_step(j);
+    const cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+    g.nk[j] = h->launches_total - before;
+    h->launches_total = before;
+    if (rc || ce != cudaSuccess || !graph || cudaGraphInstantiate(&g.exec[j], graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      h->graphs_ok = false;
+      break;
+    }
+    cudaGraphDestroy(graph);
+  }
+  h->stream = user;
+  cudaGetLastError();
+  if (!h->graphs_ok) {
+    for (auto& e : g.exec)
+      if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+    return nullptr;
+  }
+  g.key = key;
+  return &g;
+}
+
 // One FGMRES(restart) solve of A~ x = rhs (or A~^T x = rhs).
 int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose, float2* E,
                const fdfd_solve_opts* o, fdfd_solve_stats* stats) {
@@ -169,8 +227,8 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
   // ||b|| via the residual of x = 0
   CK(cudaMemsetAsync(h->x64, 0, n * sizeof(double2), s));
   {
-    ProfScope ps(h, 3, 2);
-    if ((rc = launch_residual64(h->x64, rhs, h->sb, rhs_is_source, 1.0, h->eps, cx64, cy64, h->k2, h->nx, h->ny,
+    ProfScope ps(h, 16, 2);
+    if ((rc = launch_residual64(nullptr, rhs, h->sb, rhs_is_source, 1.0, h->eps, cx64, cy64, h->k2, h->nx, h->ny,
                                 h->V, h->partials, h->counter, &h->st->resid, s)))
       return rc;
     set_bnorm_kernel<<<1, 1, 0, s>>>(h->st);
@@ -191,8 +249,8 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
   // local solves far from underflow.  x64 holds rs x; the scaling is exact.
   const double rs = ldexp(1.0, -ilogb(bnorm));
   if (rs != 1.0) {
-    ProfScope ps(h, 3, 1);
-    if ((rc = launch_residual64(h->x64, rhs, h->sb, rhs_is_source, rs, h->eps, cx64, cy64, h->k2, h->nx, h->ny,
+    ProfScope ps(h, 16, 2);
+    if ((rc = launch_residual64(nullptr, rhs, h->sb, rhs_is_source, rs, h->eps, cx64, cy64, h->k2, h->nx, h->ny,
                                 h->V, h->partials, h->counter, &h->st->resid, s)))
       return rc;
     set_bnorm_kernel<<<1, 1, 0, s>>>(h->st);
@@ -202,6 +260,39 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
     ProfScope ps(h, 4, 1);
     if ((rc = launch_load_field(E, h->x64, n, rs, s))) return rc;
   }
+  // one Arnoldi step j: z_j = M v_j, w = A~ z_j, CGS against v_0..v_j, v_{j+1}
+  auto issue_step = [&](int j) -> int {
+    int r;
+    cudaStream_t s = h->stream;  // the private capture stream while a graph is recorded
+    float2* vj = h->V + (size_t)j * n;
+    float2* zj = h->Z + (size_t)j * n;
+    const double* scj = &h->st->vscale[j];
+    if (o->precond == FDFD_PRECOND_JACOBI) {
+      ProfScope ps(h, 0, 1);
+      r = launch_stencil_jacobi(vj, scj, h->w, h->eps, cx, cy, k2, h->nx, h->ny, s);
+    } else {
+      if (o->precond == FDFD_PRECOND_NONE) {
+        ProfScope ps(h, 4, 1);
+        r = launch_scale_copy(vj, scj, zj, n, s);
+      } else {
+        r = schwarz_apply(h, vj, scj, zj, transpose);
+      }
+      if (r) return r;
+      ProfScope ps(h, 0, 1);
+      r = launch_stencil(zj, h->w, h->eps, cx, cy, k2, h->nx, h->ny, s);
+    }
+    if (r) return r;
+    {
+      ProfScope ps(h, 1, (j + 16) / 16);
+      if ((r = launch_cgs_dots(h->V, n, j, h->w, n, h->st, h->partials, h->counter, s))) return r;
+    }
+    ProfScope ps(h, 2, (j + 16) / 16);
+    return launch_cgs_update(h->V, n, j, h->w, h->V + (size_t)(j + 1) * n, n, h->st, h->partials, h->counter, m,
+                             s);
+  };
+  fdfd_ctx::StepGraphs* G = nullptr;
+  if (o->use_graphs && !h->prof_on && h->graphs_ok)
+    G = step_graphs(h, o->precond + 3 * transpose + 6 * m, m, issue_step);
   int iters = 0, cycles = 0, status = FDFD_NOT_CONVERGED;
   double est = 1.0, relres = 1.0, prev_relres = INFINITY;
   int stalls = 0;
@@ -228,33 +319,11 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
     prev_relres = relres;
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      float2* vj = h->V + (size_t)j * n;
-      float2* zj = h->Z + (size_t)j * n;
-      const double* scj = &h->st->vscale[j];
-      if (o->precond == FDFD_PRECOND_JACOBI) {
-        ProfScope ps(h, 0, 1);
-        rc = launch_stencil_jacobi(vj, scj, h->w, h->eps, cx, cy, k2, h->nx, h->ny, s);
-      } else {
-        if (o->precond == FDFD_PRECOND_NONE) {
-          ProfScope ps(h, 4, 1);
-          rc = launch_scale_copy(vj, scj, zj, n, s);
-        } else {
-          rc = schwarz_apply(h, vj, scj, zj, transpose);
-        }
-        if (rc) return rc;
-        ProfScope ps(h, 0, 1);
-        rc = launch_stencil(zj, h->w, h->eps, cx, cy, k2, h->nx, h->ny, s);
-      }
-      if (rc) return rc;
-      {
-        ProfScope ps(h, 1, (j + 32) / 32);
-        if ((rc = launch_cgs_dots(h->V, n, j, h->w, n, h->st, h->partials, h->counter, s))) return rc;
-      }
-      {
-        ProfScope ps(h, 2, (j + 32) / 32);
-        if ((rc = launch_cgs_update(h->V, n, j, h->w, h->V + (size_t)(j + 1) * n, n, h->st, h->partials,
-                                    h->counter, m, s)))
-          return rc;
+      if (G) {
+        CK(cudaGraphLaunch(G->exec[j], s));
+        h->launches_total += G->nk[j];
+      } else if ((rc = issue_step(j))) {
+        return rc;
       }
       ++iters;
       k = j + 1;
@@ -345,7 +414,8 @@ int fdfd_create(const fdfd_desc* d, fdfd_handle* out) {
       cudaMemset(h->st, 0, sizeof(KrylovState)) != cudaSuccess ||
       cudaMemcpy(h->d_one, &kOne, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMallocHost((void**)&h->flag_host, 4 * sizeof(double)) != cudaSuccess ||
-      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+      cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     release(h);
     return FDFD_ECUDA;
   }
@@ -357,12 +427,14 @@ int fdfd_set_eps(fdfd_handle h, const float* eps_dev) {
   if (!h || !eps_dev) return FDFD_EINVAL;
   CK(cudaMemcpyAsync(h->eps, eps_dev, h->n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  graphs_invalidate(h);
   schwarz_destroy(h);
   return FDFD_OK;
 }
 
 int schwarz_setup(fdfd_handle h, const schwarz_desc* sd) {
   if (!h || !sd) return FDFD_EINVAL;
+  graphs_invalidate(h);
   schwarz_destroy(h);
   return schwarz_create(h, sd);
 }
@@ -376,6 +448,8 @@ int fdfd_get_info(fdfd_handle h, fdfd_info* info) {
   info->nwy = h->ny / FDFD_CORE;
   info->n_win = info->nwx * info->nwy;
   info->workspace_bytes = h->bytes;
+  for (auto& g : h->graphs) info->graphs_cached += g.key >= 0;
+  info->graphs_ok = h->graphs_ok;
   if (h->sw) schwarz_info(h, info);
   return FDFD_OK;
 }
@@ -429,9 +503,8 @@ int fdfd_solve_adjoint(fdfd_handle h, const fdfd_c64* g, fdfd_c64* lam, const fd
   double r2[2];
   for (int pass = 0; pass < 2; ++pass) {
     ProfScope ps(h, 3, 2);
-    if (pass == 0) CK(cudaMemsetAsync(h->x64, 0, h->n * sizeof(double2), s));
-    else if ((rc = launch_load_field(L, h->x64, h->n, 1.0, s))) return rc;
-    if ((rc = launch_residual64(h->x64, G, h->sb, 0, 1.0, h->eps, h->cxT64, h->cyT64, h->k2, h->nx, h->ny, h->V,
+    if (pass == 1 && (rc = launch_load_field(L, h->x64, h->n, 1.0, s))) return rc;
+    if ((rc = launch_residual64(pass ? h->x64 : nullptr, G, h->sb, 0, 1.0, h->eps, h->cxT64, h->cyT64, h->k2, h->nx, h->ny, h->V,
                                 h->partials, h->counter, &h->st->resid, s)))
       return rc;
     if ((rc = read_double(h, &h->st->resid, &r2[pass]))) return rc;

@@ -111,7 +111,7 @@ extern "C" int fdfd_solve_batched(fdfd_batch bt, const fdfd_c64* const* Jp, fdfd
     fdfd_ctx* h = bt->hs[p];
     CK(cudaMemsetAsync(h->x64, 0, h->n * sizeof(double2), s));
     ProfScope ps_(h0, 3, 2);
-    if ((rc = launch_residual64(h->x64, Jf(p), h->sb, 1, 1.0, h->eps, h->cx64, h->cy64, h->k2, h->nx, h->ny, h->V,
+    if ((rc = launch_residual64(nullptr, Jf(p), h->sb, 1, 1.0, h->eps, h->cx64, h->cy64, h->k2, h->nx, h->ny, h->V,
                                 h->partials, h->counter, &h->st->resid, s)))
       return rc;
     bnorm_kernel<<<1, 1, 0, s>>>(h->st);
@@ -129,7 +129,7 @@ extern "C" int fdfd_solve_batched(fdfd_batch bt, const fdfd_c64* const* Jp, fdfd
       fdfd_ctx* h = bt->hs[p];
       ps[p].rs = ldexp(1.0, -ilogb(bn));
       if (ps[p].rs != 1.0) {  // ||rs b|| and, from x = 0, the first residual
-        if ((rc = launch_residual64(h->x64, Jf(p), h->sb, 1, ps[p].rs, h->eps, h->cx64, h->cy64, h->k2, h->nx,
+        if ((rc = launch_residual64(nullptr, Jf(p), h->sb, 1, ps[p].rs, h->eps, h->cx64, h->cy64, h->k2, h->nx,
                                     h->ny, h->V, h->partials, h->counter, &h->st->resid, s)))
           return rc;
         bnorm_kernel<<<1, 1, 0, s>>>(h->st);

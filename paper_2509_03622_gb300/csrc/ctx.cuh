@@ -36,7 +36,20 @@ struct fdfd_ctx {
   int* prof_cls = nullptr;          // class of each recorded pair
   long long prof_launch[FDFD_PROF_NCLASS] = {0};
   long long launches_total = 0;
+  // CUDA graphs of the Arnoldi steps (key = precond + 3 transpose + 6 restart)
+  struct StepGraphs {
+    int key = -1;
+    cudaGraphExec_t exec[FDFD_MAXRESTART] = {};
+    long long nk[FDFD_MAXRESTART] = {};  // kernels in each graph
+  };
+  StepGraphs graphs[4];
+  cudaStream_t cap_stream = nullptr;     // private stream the graphs are captured on
+  int graph_next = 0;
+  bool graphs_ok = true;                 // false after a failed capture
 };
+
+// Drop every captured step graph (buffers or the preconditioner changed).
+void graphs_invalidate(fdfd_ctx* h);
 
 #define PROF_POOL 16384
 // Bracket `nk` kernel launches of class `cls` issued by `body`.

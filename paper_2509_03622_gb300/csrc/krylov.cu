@@ -24,15 +24,31 @@ cgs_dots_kernel(const float4* __restrict__ V, size_t ld4, int v0, int nv, const 
   float ar[NV], ai[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) { ar[i] = 0.f; ai[i] = 0.f; }
-  for (size_t c = blockIdx.x * (size_t)KT + threadIdx.x; c < n4; c += (size_t)gridDim.x * KT) {
-    const float4 q = __ldg(w + c);
+  // two float4 of w per thread and iteration; the loads of each group of
+  // four vectors are issued together (8 x 16 B in flight per thread)
+  const size_t stride = (size_t)gridDim.x * KT;
+  for (size_t c0 = blockIdx.x * (size_t)KT + threadIdx.x; c0 < n4; c0 += 2 * stride) {
+    const size_t c1 = c0 + stride;
+    const bool has1 = c1 < n4;
+    const float4 q0 = __ldg(w + c0);
+    const float4 q1 = has1 ? __ldg(w + c1) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      if (i < nv) {
-        const float4 v = __ldg(V + (size_t)(v0 + i) * ld4 + c);
-        // conj(v) * w for both complex entries of the float4
-        ar[i] += v.x * q.x + v.y * q.y + v.z * q.z + v.w * q.w;
-        ai[i] += v.x * q.y - v.y * q.x + v.z * q.w - v.w * q.z;
+    for (int g = 0; g < NV; g += 4) {
+      float4 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const bool on = g + i < nv;
+        const float4* vi = V + (size_t)(v0 + g + i) * ld4;
+        a[i] = on ? __ldg(vi + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        b[i] = (on && has1) ? __ldg(vi + c1) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        // conj(v) * w for both complex entries of each float4
+        ar[g + i] += a[i].x * q0.x + a[i].y * q0.y + a[i].z * q0.z + a[i].w * q0.w
+                   + b[i].x * q1.x + b[i].y * q1.y + b[i].z * q1.z + b[i].w * q1.w;
+        ai[g + i] += a[i].x * q0.y - a[i].y * q0.x + a[i].z * q0.w - a[i].w * q0.z
+                   + b[i].x * q1.y - b[i].y * q1.x + b[i].z * q1.w - b[i].w * q1.z;
       }
     }
   }
@@ -125,22 +141,43 @@ cgs_update_kernel(const float4* __restrict__ V, size_t ld4, int v0, int nv, floa
   }
   __syncthreads();
   float acc = 0.f;
-  for (size_t c = blockIdx.x * (size_t)KT + threadIdx.x; c < n4; c += (size_t)gridDim.x * KT) {
-    float4 q = w[c];
+  // two float4 per thread and iteration; each group of four vectors' loads
+  // is issued together (8 x 16 B in flight per thread)
+  const size_t stride = (size_t)gridDim.x * KT;
+  for (size_t c0 = blockIdx.x * (size_t)KT + threadIdx.x; c0 < n4; c0 += 2 * stride) {
+    const size_t c1 = c0 + stride;
+    const bool has1 = c1 < n4;
+    float4 q[2] = {w[c0], has1 ? w[c1] : make_float4(0.f, 0.f, 0.f, 0.f)};
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      if (i < nv) {
-        const float4 v = __ldg(V + (size_t)(v0 + i) * ld4 + c);
-        const float2 h = coef[i];
-        q.x -= h.x * v.x - h.y * v.y; q.y -= h.x * v.y + h.y * v.x;
-        q.z -= h.x * v.z - h.y * v.w; q.w -= h.x * v.w + h.y * v.z;
+    for (int g = 0; g < NV; g += 4) {
+      float4 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const bool on = g + i < nv;
+        const float4* vi = V + (size_t)(v0 + g + i) * ld4;
+        a[i] = on ? __ldg(vi + c0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        b[i] = (on && has1) ? __ldg(vi + c1) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 h = coef[g + i < NV ? g + i : 0];
+        const float hx = g + i < nv ? h.x : 0.f, hy = g + i < nv ? h.y : 0.f;
+        q[0].x -= hx * a[i].x - hy * a[i].y; q[0].y -= hx * a[i].y + hy * a[i].x;
+        q[0].z -= hx * a[i].z - hy * a[i].w; q[0].w -= hx * a[i].w + hy * a[i].z;
+        q[1].x -= hx * b[i].x - hy * b[i].y; q[1].y -= hx * b[i].y + hy * b[i].x;
+        q[1].z -= hx * b[i].z - hy * b[i].w; q[1].w -= hx * b[i].w + hy * b[i].z;
       }
     }
     if (final_chunk) {
-      vnext[c] = q;
-      acc += q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+      vnext[c0] = q[0];
+      acc += q[0].x * q[0].x + q[0].y * q[0].y + q[0].z * q[0].z + q[0].w * q[0].w;
+      if (has1) {
+        vnext[c1] = q[1];
+        acc += q[1].x * q[1].x + q[1].y * q[1].y + q[1].z * q[1].z + q[1].w * q[1].w;
+      }
     } else {
-      w[c] = q;
+      w[c0] = q[0];
+      if (has1) w[c1] = q[1];
     }
   }
   if (!final_chunk) return;
@@ -232,7 +269,17 @@ __global__ void scale_copy_kernel(const float2* __restrict__ v, const double* __
 template <int NV>
 int dots_nv(const float2* V, size_t ld, int v0, int nv, const float2* w, size_t n, KrylovState* st,
             double* partials, unsigned* counter, cudaStream_t s) {
-  cgs_dots_kernel<NV><<<krylov_grid(n), KT, 0, s>>>(
+  static int resident = 0;  // one wave of resident blocks: fewer partial sums to combine
+  if (!resident) {
+    int per_sm = 0, dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgs_dots_kernel<NV>, KT, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    resident = nsm * per_sm;
+  }
+  const int grid = krylov_grid(n) < resident ? krylov_grid(n) : resident;
+  cgs_dots_kernel<NV><<<grid, KT, 0, s>>>(
       reinterpret_cast<const float4*>(V), ld / 2, v0, nv, reinterpret_cast<const float4*>(w), n / 2, st,
       reinterpret_cast<double2*>(partials), counter);
   CKL();
@@ -267,12 +314,12 @@ int krylov_grid(size_t n) {
 int launch_cgs_dots(const float2* V, size_t ld, int j, const float2* w, size_t n, KrylovState* st,
                     double* partials, unsigned* counter, cudaStream_t s) {
   int rc = FDFD_OK;
-  for (int v0 = 0; v0 <= j && rc == FDFD_OK; v0 += 32) {
-    const int nv = (j + 1 - v0) < 32 ? (j + 1 - v0) : 32;
+  // at most 16 vectors per pass: more would cost occupancy (registers) than
+  // the extra read of w saves
+  for (int v0 = 0; v0 <= j && rc == FDFD_OK; v0 += 16) {
+    const int nv = (j + 1 - v0) < 16 ? (j + 1 - v0) : 16;
     if (nv <= 8) rc = dots_nv<8>(V, ld, v0, nv, w, n, st, partials, counter, s);
-    else if (nv <= 16) rc = dots_nv<16>(V, ld, v0, nv, w, n, st, partials, counter, s);
-    else if (nv <= 24) rc = dots_nv<24>(V, ld, v0, nv, w, n, st, partials, counter, s);
-    else rc = dots_nv<32>(V, ld, v0, nv, w, n, st, partials, counter, s);
+    else rc = dots_nv<16>(V, ld, v0, nv, w, n, st, partials, counter, s);
   }
   return rc;
 }
@@ -282,13 +329,11 @@ int launch_cgs_update(const float2* V, size_t ld, int j, float2* w, float2* vnex
                       cudaStream_t s) {
   int rc = FDFD_OK;
   const int ldH = restart + 1;
-  for (int v0 = 0; v0 <= j && rc == FDFD_OK; v0 += 32) {
-    const int nv = (j + 1 - v0) < 32 ? (j + 1 - v0) : 32;
-    const int fin = (v0 + 32 > j);
+  for (int v0 = 0; v0 <= j && rc == FDFD_OK; v0 += 16) {  // 16 vectors per pass, as for the dots
+    const int nv = (j + 1 - v0) < 16 ? (j + 1 - v0) : 16;
+    const int fin = (v0 + 16 > j);
     if (nv <= 8) rc = update_nv<8>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
-    else if (nv <= 16) rc = update_nv<16>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
-    else if (nv <= 24) rc = update_nv<24>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
-    else rc = update_nv<32>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
+    else rc = update_nv<16>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
   }
   return rc;
 }

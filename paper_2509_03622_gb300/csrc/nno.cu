@@ -6,11 +6,13 @@
 //   lift   : [6400 px][16] x [32][16]^T                           (GEMM)
 //   block b (the truncated 2D DFT is done as two 1D DFT GEMMs each way):
 //     G1  DFT along x   : rows (y,c)   K = x 80        N = (kx,ri) 32   A MN-major
+//         (block 0 only as its own GEMM; blocks 1..3 inside the previous G5)
 //     G2  DFT along y   : rows (kx,c)  K = (ri,y) 160  N = (q,ri) 64    A MN-major
 //     G3  spectral mix  : 4 modes per CTA, rows = windows, K = (c,ri) 64, N = (o,ri) 64
 //     G4  inverse DFT y : rows (o,kx)  K = (q,ri) 64   N = (y,ri) 160
 //     G5  fused: inverse real DFT along x + W x + bias + leaky-ReLU, per y row:
 //         D_y[x][o] = Gx[x][:] . T3_y[o][:] + X_y[x][:] . W[o][:]
+//         then the next block's G1 on the new rows (warp-specialised, bulk copies)
 //   proj   : [6400 px][32] x [128][32]^T, leaky, 128 -> 2, times rho,
 //            written to the window's core in the global field (restricted
 //            prolongation) or to a per-window array.
@@ -37,31 +39,52 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// tiled activation layout: [window*80 + y][x/8][c/8][x%8][c%8] (bf16 elements)
+__device__ __forceinline__ size_t xt_off(size_t wy, int x, int c) {
+  return wy * 2560 + (size_t)((x >> 3) * 256 + (c >> 3) * 64 + (x & 7) * 8 + (c & 7));
+}
+// tiled inverse-y spectrum: [window*80 + y][o/8][k/8][o%8][k%8], k = (kx,ri)
+__device__ __forceinline__ size_t t3_off(size_t wy, int o, int k) {
+  return wy * 1024 + (size_t)((o >> 3) * 256 + (k >> 3) * 64 + (o & 7) * 8 + (k & 7));
+}
+
 // ---------------------------------------------------------------------
-// Generic tile GEMM: D[128 x BN] = A[128 x K] . B[BN x K]^T for tile
-// blockIdx.x of batch blockIdx.y; Op supplies operand addresses and the
-// epilogue.  One elected thread issues the MMAs, the commit arrives on an
-// mbarrier, all four warps read the FP32 accumulator from TMEM.
-// ---------------------------------------------------------------------
-// Persistent form: each CTA walks the tiles blockIdx.x, +gridDim.x, ... of
-// the (batch, tile) space.  Two shared-memory stages: while tile i's MMA and
-// epilogue run, tile i+1's operands are already in flight (cp.async).  A
-// B operand that is the same for every tile (Op::kConstB: DFT matrices,
+// Generic tile GEMM: D[128 x BN] = A[128 x K] . B[BN x K]^T per tile of the
+// (batch, tile) space; Op supplies operand addresses and the epilogue.
+// Warp-specialised and persistent (one CTA per SM walks tiles blockIdx.x,
+// +gridDim.x, ...):
+//   warps 0-3  producers: cp.async gathers of the A tile (and B when it
+//              varies) into a ring of Cfg::S stages; each thread's copies
+//              arrive on the stage's `full` barrier when they land
+//              (cp.async.mbarrier.arrive.noinc, 128 arrivals per phase);
+//   warps 4-7  epilogue: warp w reads TMEM lanes 32(w%4).. of one of two
+//              accumulator buffers, so tile i's epilogue overlaps tile i+1's
+//              MMAs;
+//   warp 8     one thread issues the MMAs, commits free the stage and fill
+//              the accumulator.
+// A B operand that is the same for every tile (Op::kConstB: DFT matrices,
 // weights) is loaded once per CTA.
+// ---------------------------------------------------------------------
 template <int BN, int K, bool AMN, class Op>
 struct GemmCfg {
   static constexpr int KC = K / 8;
   static constexpr uint32_t A_BYTES = 128 * K * 2, B_BYTES = BN * K * 2;
   static constexpr uint32_t STAGE = A_BYTES + (Op::kConstB ? 0 : B_BYTES);
-  static constexpr uint32_t SMEM = 2 * STAGE + (Op::kConstB ? B_BYTES : 0) + 16;
+  static constexpr uint32_t CONSTB = Op::kConstB ? B_BYTES : 0;
+  static constexpr int S0 = (int)((200u * 1024u - CONSTB) / STAGE);
+  static constexpr int S = S0 > 8 ? 8 : S0;
+  static constexpr uint32_t OFF_BAR = S * STAGE + CONSTB;
+  static constexpr uint32_t SMEM = OFF_BAR + (2 * S + 4) * 8 + 16;
   static constexpr uint32_t TCOLS = tc::tmem_cols(BN);
+  static_assert(S >= 2, "stages");
 };
+constexpr int GEMM_THREADS = 288;
 
 template <int BN, int K, bool AMN, class Op>
 __device__ __forceinline__ void gemm_load(const Op& op, uint8_t* sA, uint8_t* sB, int b, int m0, int Mb,
                                           bool loadB) {
   constexpr int KC = K / 8;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x;  // 0..127: the producer warps
   if (!AMN) {
     for (int c = tid; c < 128 * KC; c += 128) {
       const int t8 = c & 7, rest = c >> 3, kc = rest % KC, rg = rest / KC;
@@ -85,82 +108,103 @@ __device__ __forceinline__ void gemm_load(const Op& op, uint8_t* sA, uint8_t* sB
 }
 
 template <int BN, int K, bool AMN, class Op>
-__global__ void __launch_bounds__(128) gemm_kernel(Op op, int tiles_per_batch, int total, int* err) {
+__global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_per_batch, int total, int* err) {
   static_assert(K % 16 == 0 && BN % 16 == 0 && BN <= 256, "shape");
   typedef GemmCfg<BN, K, AMN, Op> Cfg;
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* stage[2] = {smem, smem + Cfg::STAGE};
-  uint8_t* sBc = smem + 2 * Cfg::STAGE;  // constant B (if kConstB)
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + Cfg::SMEM - 16);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Cfg::SMEM - 8);
+  const uint32_t sbase = tc::smem_u32(smem);
+  const uint32_t bar = sbase + Cfg::OFF_BAR;
+  auto full = [&](int s) { return bar + 8u * s; };
+  auto empty = [&](int s) { return bar + 8u * (Cfg::S + s); };
+  auto acc_full = [&](int a) { return bar + 8u * (2 * Cfg::S + a); };
+  auto acc_empty = [&](int a) { return bar + 8u * (2 * Cfg::S + 2 + a); };
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + Cfg::OFF_BAR + (2 * Cfg::S + 4) * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + Cfg::OFF_BAR + (2 * Cfg::S + 4) * 8 + 4);
+  uint8_t* sBc = smem + Cfg::S * Cfg::STAGE;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int tile = blockIdx.x;
-  if (tile >= total) return;
-  auto sB_of = [&](int st) { return Op::kConstB ? sBc : stage[st] + Cfg::A_BYTES; };
-  {
-    const int b = tile / tiles_per_batch, m0 = (tile % tiles_per_batch) * 128;
-    gemm_load<BN, K, AMN>(op, stage[0], sB_of(0), b, m0, op.rows(b), true);
+  if ((int)blockIdx.x >= total) return;
+  if (Op::kConstB && tid < 128) {
+    for (int c = tid; c < BN * Cfg::KC; c += 128) {
+      const int t8 = c & 7, rest = c >> 3, kc = rest % Cfg::KC, rg = rest / Cfg::KC;
+      tc::cp_async16(sBc + (rg * Cfg::KC + kc) * 128 + t8 * 16, op.b_src(0, rg * 8 + t8, kc * 8), true);
+    }
+    tc::cp_async_wait_all();
   }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  if (tid == 0) tc::mbar_init(tc::smem_u32(mbar), 1);
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), Cfg::TCOLS);
+  if (tid == 0) {
+    for (int s = 0; s < Cfg::S; ++s) { tc::mbar_init(full(s), 128); tc::mbar_init(empty(s), 1); }
+    for (int a = 0; a < 2; ++a) { tc::mbar_init(acc_full(a), 1); tc::mbar_init(acc_empty(a), 4); }
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 4) tc::tmem_alloc(tc::smem_u32(tslot), 2 * Cfg::TCOLS);
+  tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  constexpr uint32_t idesc = tc::idesc_bf16(BN, AMN, false);
-  for (int i = 0; tile < total; tile += gridDim.x, ++i) {
-    const int st = i & 1;
-    const int b = tile / tiles_per_batch, m0 = (tile % tiles_per_batch) * 128;
-    const int Mb = op.rows(b);
-    const int next = tile + gridDim.x;
-    if (next < total) {  // prefetch the next tile into the other stage
-      const int nb = next / tiles_per_batch;
-      gemm_load<BN, K, AMN>(op, stage[st ^ 1], sB_of(st ^ 1), nb, (next % tiles_per_batch) * 128, op.rows(nb),
-                            !Op::kConstB);
+  auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
+
+  if (warp < 4) {  // ---------------- producers ----------------
+    int it = 0;
+    for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x, ++it) {
+      const int s = it % Cfg::S;
+      if (it >= Cfg::S && !tc::mbar_wait(empty(s), ((it / Cfg::S) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+      const int b = tile / tiles_per_batch, m0 = (tile % tiles_per_batch) * 128;
+      uint8_t* st = smem + s * Cfg::STAGE;
+      gemm_load<BN, K, AMN>(op, st, st + Cfg::A_BYTES, b, m0, op.rows(b), !Op::kConstB);
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full(s)) : "memory");
     }
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 1;" ::: "memory");
-    tc::fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t a0 = tc::smem_u32(stage[st]), b0 = tc::smem_u32(sB_of(st));
+    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may outlive the CTA
+  } else if (warp == 8) {  // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16(BN, AMN, false);
+      int it = 0;
+      for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x, ++it) {
+        const int s = it % Cfg::S, a = it & 1;
+        if (!tc::mbar_wait(full(s), (it / Cfg::S) & 1, WAIT_LIMIT)) { fail(); break; }
+        if (it >= 2 && !tc::mbar_wait(acc_empty(a), ((it >> 1) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+        tc::fence_async_smem();  // the producers' cp.async data -> async proxy
+        tc::fence_after();
+        const uint32_t a0 = sbase + s * Cfg::STAGE;
+        const uint32_t b0 = Op::kConstB ? sbase + Cfg::S * Cfg::STAGE : a0 + Cfg::A_BYTES;
 #pragma unroll
-      for (int s = 0; s < K / 16; ++s)
-        tc::mma_bf16(tmem, tc::make_desc(a0 + s * 256, 128, K * 16), tc::make_desc(b0 + s * 256, 128, K * 16),
-                     idesc, s > 0);
-      tc::mma_commit(tc::smem_u32(mbar));
-    }
-    if (!tc::mbar_wait(tc::smem_u32(mbar), (uint32_t)(i & 1), WAIT_LIMIT)) atomicExch(err, 1);
-    tc::fence_after();
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows
-    const int m = m0 + warp * 32 + lane;
-    const bool valid = m < Mb;
-    typename Op::State sst;
-    op.epi_begin(sst);
-    if constexpr (Op::kUnroll) {
-#pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        if (valid) op.epi(b, m, c0, v, sst);
+        for (int k = 0; k < K / 16; ++k)
+          tc::mma_bf16(tmem + a * Cfg::TCOLS, tc::make_desc(a0 + k * 256, 128, K * 16),
+                       tc::make_desc(b0 + k * 256, 128, K * 16), idesc, k > 0);
+        tc::mma_commit(empty(s));
+        tc::mma_commit(acc_full(a));
       }
-    } else {
+    }
+  } else {  // ---------------- epilogue (warps 4-7) ----------------
+    const int q = warp & 3;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
+      const int a = it & 1;
+      if (*abort_flag || !tc::mbar_wait(acc_full(a), (it >> 1) & 1, WAIT_LIMIT)) { fail(); break; }
+      tc::fence_after();
+      const int b = tile / tiles_per_batch, m0 = (tile % tiles_per_batch) * 128;
+      const int m = m0 + q * 32 + lane;
+      const bool valid = m < op.rows(b);
+      typename Op::State sst;
+      op.epi_begin(sst);
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 16) {
         float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * Cfg::TCOLS + (uint32_t)c0, v);
         if (valid) op.epi(b, m, c0, v, sst);
       }
+      if (valid) op.epi_end(b, m, sst);
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty(a));
     }
-    if (valid) op.epi_end(b, m, sst);
-    tc::fence_before();
-    __syncthreads();  // accumulator and stage st are free again
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  if (warp == 0) {
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 4) {
+    __syncwarp();
     tc::fence_after();
-    tc::tmem_free(tmem, Cfg::TCOLS);
+    tc::tmem_free(tmem, 2 * Cfg::TCOLS);
   }
 }
 
@@ -195,11 +239,11 @@ int launch_gemm(const Op& op, int tiles, int batches, int* err, cudaStream_t s) 
   if (grid_cap == 0) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess)
       return FDFD_ECUDA;
-    grid_cap = persistent_grid((const void*)kern, 128, Cfg::SMEM, Cfg::TCOLS);
+    grid_cap = persistent_grid((const void*)kern, GEMM_THREADS, Cfg::SMEM, 2 * Cfg::TCOLS);
   }
   const int total = tiles * batches;
   const int grid = total < grid_cap ? total : grid_cap;
-  kern<<<grid, 128, Cfg::SMEM, s>>>(op, tiles, total, err);
+  kern<<<grid, GEMM_THREADS, Cfg::SMEM, s>>>(op, tiles, total, err);
   CKL();
   return FDFD_OK;
 }
@@ -211,7 +255,6 @@ struct NoState {};
 // ---------------------------------------------------------------------
 struct LiftOp {  // rows = pixels, K = 16 inputs, N = 32 channels
   static constexpr bool kConstB = true;
-  static constexpr bool kUnroll = false;
   const bf16* in; const bf16* w; const float* bias; bf16* X;
   typedef NoState State;
   __device__ int rows(int) const { return NPIX; }
@@ -224,22 +267,21 @@ struct LiftOp {  // rows = pixels, K = 16 inputs, N = 32 channels
     uint32_t p[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) p[i] = pack2(v[2 * i] + bias[c0 + 2 * i], v[2 * i + 1] + bias[c0 + 2 * i + 1]);
-    uint4* dst = reinterpret_cast<uint4*>(X + ((size_t)b * NPIX + m) * 32 + c0);
-    dst[0] = make_uint4(p[0], p[1], p[2], p[3]);
-    dst[1] = make_uint4(p[4], p[5], p[6], p[7]);
+    bf16* dst = X + xt_off((size_t)b * 80 + m / 80, m % 80, c0);
+    *reinterpret_cast<uint4*>(dst) = make_uint4(p[0], p[1], p[2], p[3]);
+    *reinterpret_cast<uint4*>(dst + 64) = make_uint4(p[4], p[5], p[6], p[7]);
   }
   __device__ void epi_end(int, int, State&) const {}
 };
 
 struct G1Op {  // DFT along x: rows (y,c), K = x (A MN-major from X), N = (kx,ri)
   static constexpr bool kConstB = true;
-  static constexpr bool kUnroll = false;
   const bf16* X; const bf16* Fx; bf16* T1;
   typedef NoState State;
   __device__ int rows(int) const { return 80 * 32; }
   __device__ const uint4* a_src(int b, int m, int k) const {  // 8 consecutive c at (y, x = k)
     const int y = m >> 5, c = m & 31;
-    return reinterpret_cast<const uint4*>(X + (((size_t)b * 80 + y) * 80 + k) * 32 + c);
+    return reinterpret_cast<const uint4*>(X + xt_off((size_t)b * 80 + y, k, c));
   }
   __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(Fx + n * 80 + k); }
   __device__ void epi_begin(State&) const {}
@@ -257,7 +299,6 @@ struct G1Op {  // DFT along x: rows (y,c), K = x (A MN-major from X), N = (kx,ri
 
 struct G2Op {  // DFT along y: rows (kx,c), K = (ri,y) (A MN-major from T1), N = (q,ri)
   static constexpr bool kConstB = true;
-  static constexpr bool kUnroll = false;
   const bf16* T1; const bf16* Fy; bf16* Xh; int cap;
   typedef NoState State;
   __device__ int rows(int) const { return 512; }
@@ -280,7 +321,6 @@ struct G2Op {  // DFT along y: rows (kx,c), K = (ri,y) (A MN-major from T1), N =
 
 struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
   static constexpr bool kConstB = true;
-  static constexpr bool kUnroll = false;
   const bf16* Yh; const bf16* Gy; bf16* T3;
   typedef NoState State;
   __device__ int rows(int) const { return 512; }
@@ -294,69 +334,19 @@ struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
 #pragma unroll
     for (int i = 0; i < 16; i += 2) {
       const int y = (c0 + i) >> 1;
-      *reinterpret_cast<uint32_t*>(T3 + (((size_t)b * 80 + y) * 32 + o) * 32 + kx * 2) = pack2(v[i], v[i + 1]);
+      *reinterpret_cast<uint32_t*>(T3 + t3_off((size_t)b * 80 + y, o, kx * 2)) = pack2(v[i], v[i + 1]);
     }
   }
   __device__ void epi_end(int, int, State&) const {}
-};
-
-struct ProjOp {  // rows = pixels, K = 32, N = 128 hidden; then 128 -> 2 and the output
-  static constexpr bool kConstB = true;
-  static constexpr bool kUnroll = true;  // constants below become constant-bank operands
-  const bf16* X; const bf16* P1; float p2b0, p2b1;
-  const float* rho; const double* scale; const int* win_id;
-  float2* z_global; float2* e_win; int nx, nwx;
-  const double* scale_win;
-  struct State { float re, im; };
-  __device__ int rows(int) const { return NPIX; }
-  __device__ const uint4* a_src(int b, int m, int k) const {
-    return reinterpret_cast<const uint4*>(X + ((size_t)b * NPIX + m) * 32 + k);
-  }
-  __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(P1 + n * 32 + k); }
-  __device__ void epi_begin(State& s) const { s.re = 0.f; s.im = 0.f; }
-  __device__ void epi(int, int, int c0, const float* v, State& s) const {
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const float h = leaky(v[i] + p1b[c0 + i]);
-      s.re = fmaf(P2[c0 + i], h, s.re);
-      s.im = fmaf(P2[128 + c0 + i], h, s.im);
-    }
-  }
-  __device__ void epi_end(int b, int m, State& s) const {
-    int w = win_id ? win_id[b] : b;
-    int gnx = nx, gny = ny_, gnwx = nwx;
-    const double* sc = scale;
-    float2* zg = z_global;
-    if (ptab) {  // multi-problem batch
-      const int2 e = wtab[b];
-      const ProbGeom& P = ptab[e.x];
-      w = e.y; gnx = P.nx; gny = P.ny; gnwx = P.nwx; sc = P.scale; zg = P.z;
-    }
-    float f = rho[b];
-    if (sc) f *= (float)(*sc);
-    if (scale_win) f *= (float)scale_win[b];
-    const float2 o = make_float2((s.re + p2b0) * f, (s.im + p2b1) * f);
-    if (e_win) { e_win[(size_t)b * NPIX + m] = o; return; }
-    // restricted prolongation: only the window's 64 x 64 core is written
-    const int a = w % gnwx, bb = w / gnwx;
-    const int y = m / 80, x = m % 80;
-    const int gx = min(max(FDFD_CORE * a - FDFD_OVL, 0), gnx - FDFD_WIN) + x;
-    const int gy = min(max(FDFD_CORE * bb - FDFD_OVL, 0), gny - FDFD_WIN) + y;
-    if (gx < FDFD_CORE * a || gx >= FDFD_CORE * a + FDFD_CORE) return;
-    if (gy < FDFD_CORE * bb || gy >= FDFD_CORE * bb + FDFD_CORE) return;
-    zg[(size_t)gy * gnx + gx] = o;
-  }
-  int ny_;
-  const int2* wtab;
-  const ProbGeom* ptab;
-  float p1b[128];  // hidden bias
-  float P2[256];   // [2][128] output weights
 };
 
 // G3 with 4 modes per CTA: unit = (kx, q-group of 4, tile of 128 windows);
 // D_m[w][(o,ri)] = Xh_m[w][(c,ri')] R'_m[(o,ri)][(c,ri')]^T for the 4 modes
 // m = (q0..q0+3, kx), accumulators side by side in TMEM (4 x 64 columns), so
 // the epilogue writes 16 contiguous bytes (4 q x re/im) per (window, o).
+// One CTA per unit, two resident per SM (shared memory and TMEM), CTAs in
+// the order (window tile, q-group, kx): a warp-specialised persistent form
+// of this kernel measured slower on GB300, so this one stays.
 constexpr int G3_Q = 4;
 constexpr uint32_t G3_A = 128 * 64 * 2, G3_B = 64 * 64 * 2;
 constexpr uint32_t G3_SMEM = G3_Q * (G3_A + G3_B) + 16;
@@ -434,125 +424,449 @@ __global__ void __launch_bounds__(128) g3_kernel(const bf16* Xh, const bf16* R, 
   }
 }
 
-// Fused G5, persistent over units (window, 4 rows):
-//   D_y[x][o] = Gx[x][:] T3_y[o][:]^T + X_y[x][:] W[o][:]^T
-// then + bias, leaky-ReLU (not after the last block), written back to X.
-// The MMA has M = 128 rows but only x < 80 are real: the X tiles of a stage
-// are packed 80 rows apart, so rows 80..127 of one tile read the next tile
-// (or the stage's slack), and the corresponding accumulator rows are never
-// read back.  Gx and W are loaded once per CTA; the next unit's X and T3
-// tiles are prefetched into the other stage while the current unit runs.
-// 8 warps: warps w and w+4 share TMEM lanes 32(w%4).. and split the rows.
+// Fused G5, warp-specialised and persistent over units (window, 4 rows y0..y0+3):
+//   D_y[x][o] = Gx[x][:] T3_y[o][:]^T + X_y[x][:] W[o][:]^T,  + bias, leaky-ReLU
+// (not after the last block), written back to X; for blocks 0..2 the same
+// kernel also runs the NEXT block's DFT along x on the rows it just made
+// (G1: T1[(ri,y)][(kx,c)] = sum_x Fx[(kx,ri)][x] X_y[x][c]), so X is not
+// read again for it.
+// Roles: warp 0 lane 0 = producer (one bulk copy of the 4 X rows, 20 KB, and
+// one of the 4 T3 rows, 8 KB, per unit into a G5_STAGES-deep ring, completion
+// by transaction count), warp 1 lane 0 = MMA issuer, warps 4..11 = epilogue
+// (warp w reads TMEM lanes 32(w%4)..).  Two accumulator sets in TMEM (G5:
+// 4 x 32 columns, G1: 32 columns) let the epilogue of unit i overlap the
+// MMAs of unit i+1.  The G5 MMA has M = 128 rows of which x < 80 are real:
+// rows 80..127 of one X tile read the next tile (or, for the last row of a
+// stage, the following buffer); those accumulator rows are never read.
+// X and T3 are stored tiled (core-matrix order), so one row is one
+// contiguous K-major operand tile.
 constexpr int G5_ROWS = 4;
-constexpr int G5_THREADS = 256;
-constexpr uint32_t G5_XT = 80 * 32 * 2;                              // one packed [80][32] X tile
-constexpr uint32_t G5_STAGE = G5_ROWS * G5_XT + 48 * 64 + G5_ROWS * 2048;  // X tiles + slack + T3 tiles
-constexpr uint32_t G5_GX = 128 * 32 * 2;
-constexpr uint32_t G5_SMEM = G5_GX + 2048 + 2 * G5_STAGE + 16;
+constexpr int G5_STAGES = 4;
+constexpr int G5_THREADS = 384;
+constexpr uint32_t G5_XT = 80 * 32 * 2;                          // one tiled [80][32] X row
+constexpr uint32_t G5_XB = G5_ROWS * G5_XT;                      // 20480
+constexpr uint32_t G5_TB = G5_ROWS * 2048;                       // 8192
+constexpr uint32_t G5_STAGE = G5_XB + G5_TB;                     // 28672
+constexpr uint32_t G5_A1 = 128 * 80 * 2;                         // G1 A tile, MN-major (yy,c) x x
+constexpr uint32_t G5_OFF_A1 = G5_STAGES * G5_STAGE;             // after the ring (absorbs the over-read)
+constexpr uint32_t G5_OFF_GX = G5_OFF_A1 + 2 * G5_A1;
+constexpr uint32_t G5_OFF_W = G5_OFF_GX + 128 * 32 * 2;
+constexpr uint32_t G5_OFF_FX = G5_OFF_W + 32 * 32 * 2;
+constexpr uint32_t G5_OFF_BAR = G5_OFF_FX + 32 * 80 * 2;
+constexpr uint32_t G5_NBAR = 2 * G5_STAGES + 8;
+constexpr uint32_t G5_SMEM = G5_OFF_BAR + G5_NBAR * 8 + 16;
+static_assert(G5_SMEM <= 227 * 1024, "g5 shared memory");
 
-__device__ __forceinline__ void g5_load(uint8_t* stg, const bf16* X, const bf16* T3, int b, int y0) {
-  const int tid = threadIdx.x;
-  for (int c = tid; c < G5_ROWS * 80 * 4; c += G5_THREADS) {
-    const int yy = c / 320, r = c % 320;
-    const int t8 = r & 7, rest = r >> 3, kc = rest & 3, rg = rest >> 2;
-    tc::cp_async16(stg + yy * G5_XT + (rg * 4 + kc) * 128 + t8 * 16,
-                   X + (((size_t)b * 80 + y0 + yy) * 80 + rg * 8 + t8) * 32 + kc * 8, true);
-  }
-  for (int c = tid; c < G5_ROWS * 128; c += G5_THREADS) {
-    const int yy = c >> 7, r = c & 127;
-    const int t8 = r & 7, rest = r >> 3, kc = rest & 3, rg = rest >> 2;
-    tc::cp_async16(stg + G5_ROWS * G5_XT + 48 * 64 + yy * 2048 + (rg * 4 + kc) * 128 + t8 * 16,
-                   T3 + (((size_t)b * 80 + y0 + yy) * 32 + rg * 8 + t8) * 32 + kc * 8, true);
-  }
-}
-
-__global__ void __launch_bounds__(G5_THREADS) g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb,
-                                                        const float* bias, int last, int total, int* err) {
+__global__ void __launch_bounds__(G5_THREADS, 1)
+g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* bias, const bf16* Fx, bf16* T1,
+          int last, int total, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sAg = smem;                       // Gx, [128][32] (rows >= 80 zero)
-  uint8_t* sBw = smem + G5_GX;               // W, [32][32]
-  uint8_t* stage[2] = {smem + G5_GX + 2048, smem + G5_GX + 2048 + G5_STAGE};
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + G5_SMEM - 16);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G5_SMEM - 8);
+  const uint32_t sbase = tc::smem_u32(smem);
+  const uint32_t bar = sbase + G5_OFF_BAR;
+  // barriers: full[s], empty[s], g5_full[2], g1_full[2], a1_full[2], acc_empty[2]
+  auto full = [&](int s) { return bar + 8u * s; };
+  auto empty = [&](int s) { return bar + 8u * (G5_STAGES + s); };
+  auto g5_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + a); };
+  auto g1_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + 2 + a); };
+  auto a1_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + 4 + a); };
+  auto acc_empty = [&](int a) { return bar + 8u * (2 * G5_STAGES + 6 + a); };
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G5_OFF_BAR + G5_NBAR * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + G5_OFF_BAR + G5_NBAR * 8 + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int UPW = 80 / G5_ROWS;  // units per window
-  int u = blockIdx.x;
-  if (u >= total) return;
+  constexpr int UPW = 80 / G5_ROWS;
+  if ((int)blockIdx.x >= total) return;
+  // constant operands: Gx [128][32], W [32][32], Fx [32][80] (K-major tiles)
   for (int c = tid; c < 128 * 4; c += G5_THREADS) {
     const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-    tc::cp_async16(sAg + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
+    tc::cp_async16(smem + G5_OFF_GX + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
   }
-  if (tid < 128) {
-    const int t8 = tid & 7, rest = tid >> 3, kc = rest & 3, rg = rest >> 2;
-    tc::cp_async16(sBw + (rg * 4 + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * 32 + kc * 8, true);
+  for (int c = tid; c < 32 * 4; c += G5_THREADS) {
+    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
+    tc::cp_async16(smem + G5_OFF_W + (rg * 4 + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * 32 + kc * 8, true);
   }
-  g5_load(stage[0], X, T3, u / UPW, (u % UPW) * G5_ROWS);
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  float bs[32];
-#pragma unroll
-  for (int o = 0; o < 32; ++o) bs[o] = bias[o];
-  if (tid == 0) tc::mbar_init(tc::smem_u32(mbar), 1);
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 32 * G5_ROWS);
+  if (!last)
+    for (int c = tid; c < 32 * 10; c += G5_THREADS) {
+      const int t8 = c & 7, rest = c >> 3, kc = rest % 10, rg = rest / 10;
+      tc::cp_async16(smem + G5_OFF_FX + (rg * 10 + kc) * 128 + t8 * 16, Fx + (rg * 8 + t8) * 80 + kc * 8, true);
+    }
+  tc::cp_async_wait_all();
+  if (tid == 0) {
+    for (int s = 0; s < G5_STAGES; ++s) { tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); }
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(g5_full(a), 1); tc::mbar_init(g1_full(a), 1);
+      tc::mbar_init(a1_full(a), 8); tc::mbar_init(acc_empty(a), 8);
+    }
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  constexpr uint32_t idesc = tc::idesc_bf16(32, false, false);
-  const int quarter = warp & 3, half = warp >> 2;  // TMEM lane quarter, row half
-  for (int i = 0; u < total; u += gridDim.x, ++i) {
-    const int st = i & 1;
-    const int b = u / UPW, y0 = (u % UPW) * G5_ROWS;
-    const int next = u + gridDim.x;
-    if (next < total) g5_load(stage[st ^ 1], X, T3, next / UPW, (next % UPW) * G5_ROWS);
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 1;" ::: "memory");
-    tc::fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t ag = tc::smem_u32(sAg), bw = tc::smem_u32(sBw), ax0 = tc::smem_u32(stage[st]);
-      const uint32_t bt0 = ax0 + G5_ROWS * G5_XT + 48 * 64;
-      for (int yy = 0; yy < G5_ROWS; ++yy) {
-        const uint32_t d = tmem + yy * 32;
-        for (int s = 0; s < 2; ++s)
-          tc::mma_bf16(d, tc::make_desc(ag + s * 256, 128, 512), tc::make_desc(bt0 + yy * 2048 + s * 256, 128, 512),
-                       idesc, s > 0);
-        for (int s = 0; s < 2; ++s)
-          tc::mma_bf16(d, tc::make_desc(ax0 + yy * G5_XT + s * 256, 128, 512),
-                       tc::make_desc(bw + s * 256, 128, 512), idesc, 1);
+  auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- producer ----------------
+      int it = 0;
+      for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
+        const int s = it % G5_STAGES;
+        if (it >= G5_STAGES && !tc::mbar_wait(empty(s), ((it / G5_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+        const size_t wy = (size_t)(u / UPW) * 80 + (u % UPW) * G5_ROWS;
+        tc::mbar_arrive_tx(full(s), G5_STAGE);
+        tc::bulk_g2s(sbase + s * G5_STAGE, X + wy * 2560, G5_XB, full(s));
+        tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
       }
-      tc::mma_commit(tc::smem_u32(mbar));
+      // every copy issued must have landed before the CTA may exit
+      for (int j = (it > G5_STAGES ? it - G5_STAGES : 0); j < it; ++j)
+        if (!tc::mbar_wait(full(j % G5_STAGES), (j / G5_STAGES) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
     }
-    if (!tc::mbar_wait(tc::smem_u32(mbar), (uint32_t)(i & 1), WAIT_LIMIT)) atomicExch(err, 1);
-    tc::fence_after();
-    if (quarter < 3) {
-      const int x = quarter * 32 + lane;
-      for (int yy = half * (G5_ROWS / 2); yy < (half + 1) * (G5_ROWS / 2); ++yy) {
-        float v[32];
-        tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + yy * 32, v);
-        tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + yy * 32 + 16, v + 16);
-        if (x < 80) {
-          uint32_t p[16];
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer ----------------
+      constexpr uint32_t id5 = tc::idesc_bf16(32, false, false);
+      constexpr uint32_t id1 = tc::idesc_bf16(32, true, false);
+      const uint32_t ag = sbase + G5_OFF_GX, bw = sbase + G5_OFF_W, bfx = sbase + G5_OFF_FX;
+      auto issue_g1 = [&](int j) -> bool {  // next block's DFT along x for unit j
+        const int a = j & 1;
+        if (!tc::mbar_wait(a1_full(a), (j >> 1) & 1, WAIT_LIMIT)) return false;
+        tc::fence_after();
+        const uint32_t a1 = sbase + G5_OFF_A1 + a * G5_A1;
+        for (int s = 0; s < 5; ++s)
+          tc::mma_bf16(tmem + a * 256 + 128, tc::make_desc(a1 + s * 256, 128, 1280),
+                       tc::make_desc(bfx + s * 256, 128, 1280), id1, s > 0);
+        tc::mma_commit(g1_full(a));
+        return true;
+      };
+      int it = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
+        const int s = it % G5_STAGES, a = it & 1;
+        if (!tc::mbar_wait(full(s), (it / G5_STAGES) & 1, WAIT_LIMIT)) { ok = false; break; }
+        if (it >= 2 && !tc::mbar_wait(acc_empty(a), ((it >> 1) - 1) & 1, WAIT_LIMIT)) { ok = false; break; }
+        tc::fence_after();
+        const uint32_t ax = sbase + s * G5_STAGE, bt = ax + G5_XB;
+        for (int yy = 0; yy < G5_ROWS; ++yy) {
+          const uint32_t d = tmem + a * 256 + yy * 32;
+          for (int k = 0; k < 2; ++k)
+            tc::mma_bf16(d, tc::make_desc(ag + k * 256, 128, 512), tc::make_desc(bt + yy * 2048 + k * 256, 128, 512),
+                         id5, k > 0);
+          for (int k = 0; k < 2; ++k)
+            tc::mma_bf16(d, tc::make_desc(ax + yy * G5_XT + k * 256, 128, 512), tc::make_desc(bw + k * 256, 128, 512),
+                         id5, 1);
+        }
+        tc::mma_commit(empty(s));
+        tc::mma_commit(g5_full(a));
+        if (!last && it >= 1 && !issue_g1(it - 1)) { ok = false; break; }
+      }
+      if (ok && !last && it >= 1 && !*abort_flag && !issue_g1(it - 1)) ok = false;
+      if (!ok) fail();
+    }
+  } else if (warp >= 4) {  // ---------------- epilogue ----------------
+    const int ew = warp - 4, q = ew & 3, hf = ew >> 2;
+    float bs[32];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            float a = v[2 * q] + bs[2 * q], c = v[2 * q + 1] + bs[2 * q + 1];
-            if (!last) { a = leaky(a); c = leaky(c); }
-            p[q] = pack2(a, c);
+    for (int o = 0; o < 32; ++o) bs[o] = bias[o];
+    int it = 0;
+    for (int u = blockIdx.x; u < total; u += gridDim.x, ++it) {
+      const int a = it & 1;
+      if (*abort_flag || !tc::mbar_wait(g5_full(a), (it >> 1) & 1, WAIT_LIMIT)) { fail(); break; }
+      tc::fence_after();
+      const size_t wy0 = (size_t)(u / UPW) * 80 + (u % UPW) * G5_ROWS;
+      uint8_t* a1 = smem + G5_OFF_A1 + a * G5_A1;
+      if (q < 3) {
+        const int x = q * 32 + lane;
+        for (int yy = hf * 2; yy < hf * 2 + 2; ++yy) {
+          float v[32];
+          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * 256 + yy * 32, v);
+          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * 256 + yy * 32 + 16, v + 16);
+          if (x < 80) {
+            uint32_t p[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              float e0 = v[2 * i] + bs[2 * i], e1 = v[2 * i + 1] + bs[2 * i + 1];
+              if (!last) { e0 = leaky(e0); e1 = leaky(e1); }
+              p[i] = pack2(e0, e1);
+            }
+            bf16* dst = X + xt_off(wy0 + yy, x, 0);
+#pragma unroll
+            for (int cg = 0; cg < 4; ++cg)
+              *reinterpret_cast<uint4*>(dst + cg * 64) = make_uint4(p[4 * cg], p[4 * cg + 1], p[4 * cg + 2], p[4 * cg + 3]);
+            if (!last)
+#pragma unroll
+              for (int cg = 0; cg < 4; ++cg)
+                *reinterpret_cast<uint4*>(a1 + ((yy * 4 + cg) * 10 + (x >> 3)) * 128 + (x & 7) * 16) =
+                    make_uint4(p[4 * cg], p[4 * cg + 1], p[4 * cg + 2], p[4 * cg + 3]);
           }
-          uint4* dst = reinterpret_cast<uint4*>(X + (((size_t)b * 80 + y0 + yy) * 80 + x) * 32);
-          dst[0] = make_uint4(p[0], p[1], p[2], p[3]);
-          dst[1] = make_uint4(p[4], p[5], p[6], p[7]);
-          dst[2] = make_uint4(p[8], p[9], p[10], p[11]);
-          dst[3] = make_uint4(p[12], p[13], p[14], p[15]);
         }
       }
+      if (!last) {
+        tc::fence_async_smem();  // A1 written by this warp -> visible to the tensor core
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(a1_full(a));
+        if (!tc::mbar_wait(g1_full(a), (it >> 1) & 1, WAIT_LIMIT)) { fail(); break; }
+        tc::fence_after();
+        // lanes (yy = q, c = lane), columns (kx,ri) hf*16 .. hf*16+15
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * 256 + 128 + hf * 16, v);
+        const int y = (int)(wy0 % 80) + q;
+        bf16* base = T1 + (wy0 / 80) * (size_t)(160 * 512);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int col = hf * 16 + i, kx = col >> 1, ri = col & 1;
+          base[(ri * 80 + y) * 512 + kx * 32 + lane] = __float2bfloat16_rn(v[i]);
+        }
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty(a));
     }
-    tc::fence_before();
-    __syncthreads();
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  tc::fence_before();
+  __syncthreads();
   if (warp == 0) {
+    __syncwarp();
     tc::fence_after();
-    tc::tmem_free(tmem, 32 * G5_ROWS);
+    tc::tmem_free(tmem, 512);
+  }
+}
+
+// Projection, warp-specialised and persistent over units (window, 128
+// consecutive pixels; the tiled activation makes that one contiguous 8 KB
+// operand tile):
+//   H[p][h]  = X[p][:] P1[h][:]^T + p1b[h]     (MMA 1; the bias enters as a
+//              K-column of ones in A against p1b in B)
+//   O[p][.]  = leaky(H[p][:]) P2[.][:]^T       (MMA 2, N = 16 of which 2 used)
+//   z        = (O + p2b) * rho * scale, written to the window's core in the
+//              global field (restricted prolongation) or to a per-window array.
+// Roles: warp 0 producer (bulk copies into a PJ_STAGES ring), warp 1 issues
+// the first MMA and warp 2 the second (separate threads, so neither waits
+// for the other's operands), warps 4..11 epilogue (leaky-ReLU of H in packed BF16
+// into the second MMA's A tile, then the output).  Four TMEM accumulators of
+// 128 columns (MMA 2 reuses the first 16 columns of its unit's accumulator
+// once H has been read).  The epilogue is two groups of four warps taking
+// alternate units, each software-pipelined: it prepares its next unit's
+// second operand while the previous unit's second MMA runs.
+constexpr int PJ_STAGES = 6;
+constexpr int PJ_THREADS = 384;
+constexpr uint32_t PJ_AT = 128 * 32 * 2;                  // X tile
+constexpr uint32_t PJ_A2 = 128 * 128 * 2;                 // leaky(H) tile, K-major
+constexpr int PJ_NA2 = 4;                                 // leaky(H) buffers (2 per epilogue group)
+constexpr uint32_t PJ_OFF_A2 = PJ_STAGES * PJ_AT;
+constexpr uint32_t PJ_OFF_B1 = PJ_OFF_A2 + PJ_NA2 * PJ_A2;  // [128 h][48 k]: P1 | p1b | 0
+constexpr uint32_t PJ_OFF_ONE = PJ_OFF_B1 + 128 * 48 * 2; // [128 p][16 k]: 1 | 0
+constexpr uint32_t PJ_OFF_B2 = PJ_OFF_ONE + 128 * 16 * 2; // [16 n][128 h]: P2 rows 0, 1
+constexpr uint32_t PJ_OFF_BAR = PJ_OFF_B2 + 16 * 128 * 2;
+constexpr int PJ_ACC = 4;
+constexpr uint32_t PJ_NBAR = 2 * PJ_STAGES + 4 * PJ_ACC;
+constexpr uint32_t PJ_SMEM = PJ_OFF_BAR + PJ_NBAR * 8 + 16;
+static_assert(PJ_SMEM <= 227 * 1024, "proj shared memory");
+
+struct ProjArgs {
+  const bf16* X; const bf16* P1; const float* p1b; const float* P2; float p2b0, p2b1;
+  const float* rho; const double* scale; const int* win_id; const double* scale_win;
+  float2* z_global; float2* e_win; int nx, ny, nwx;
+  const int2* wtab; const ProbGeom* ptab;
+};
+
+__global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int total, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const uint32_t sbase = tc::smem_u32(smem);
+  const uint32_t bar = sbase + PJ_OFF_BAR;
+  auto full = [&](int s) { return bar + 8u * s; };
+  auto empty = [&](int s) { return bar + 8u * (PJ_STAGES + s); };
+  auto m1_full = [&](int a) { return bar + 8u * (2 * PJ_STAGES + a); };
+  auto m2_full = [&](int a) { return bar + 8u * (2 * PJ_STAGES + PJ_ACC + a); };
+  auto a2_full = [&](int a) { return bar + 8u * (2 * PJ_STAGES + 2 * PJ_ACC + a); };
+  auto acc_empty = [&](int a) { return bar + 8u * (2 * PJ_STAGES + 3 * PJ_ACC + a); };
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + PJ_OFF_BAR + PJ_NBAR * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + PJ_OFF_BAR + PJ_NBAR * 8 + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int UPW = NPIX / 128;  // 50 units per window
+  if ((int)blockIdx.x >= total) return;
+  // constant operands
+  for (int c = tid; c < 128 * 4; c += PJ_THREADS) {  // P1 -> B1 k-groups 0..3
+    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
+    tc::cp_async16(smem + PJ_OFF_B1 + (rg * 6 + kc) * 128 + t8 * 16, P.P1 + (rg * 8 + t8) * 32 + kc * 8, true);
+  }
+  for (int c = tid; c < 128 * 16; c += PJ_THREADS) {  // B1 k = 32..47: p1b then zeros
+    const int n = c >> 4, k = 32 + (c & 15);
+    *reinterpret_cast<bf16*>(smem + PJ_OFF_B1 + tc::kmaj_off(n, k, 48)) =
+        __float2bfloat16_rn(k == 32 ? P.p1b[n] : 0.f);
+  }
+  for (int c = tid; c < 128 * 16; c += PJ_THREADS) {  // ones column of A
+    const int r = c >> 4, k = c & 15;
+    *reinterpret_cast<bf16*>(smem + PJ_OFF_ONE + tc::kmaj_off(r, k, 16)) = __float2bfloat16_rn(k == 0 ? 1.f : 0.f);
+  }
+  for (int c = tid; c < 16 * 128; c += PJ_THREADS) {  // B2: rows 0, 1 = P2
+    const int n = c >> 7, k = c & 127;
+    *reinterpret_cast<bf16*>(smem + PJ_OFF_B2 + tc::kmaj_off(n, k, 128)) =
+        __float2bfloat16_rn(n < 2 ? P.P2[n * 128 + k] : 0.f);
+  }
+  tc::cp_async_wait_all();
+  if (tid == 0) {
+    for (int s = 0; s < PJ_STAGES; ++s) { tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); }
+    for (int a = 0; a < PJ_ACC; ++a) {
+      tc::mbar_init(m1_full(a), 1); tc::mbar_init(m2_full(a), 1);
+      tc::mbar_init(a2_full(a), 4); tc::mbar_init(acc_empty(a), 4);
+    }
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int it = 0;
+      for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
+        const int s = it % PJ_STAGES;
+        if (it >= PJ_STAGES && !tc::mbar_wait(empty(s), ((it / PJ_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+        tc::mbar_arrive_tx(full(s), PJ_AT);
+        tc::bulk_g2s(sbase + s * PJ_AT, P.X + (size_t)(u / UPW) * (NPIX * 32) + (size_t)(u % UPW) * (128 * 32), PJ_AT,
+                     full(s));
+      }
+      for (int j = (it > PJ_STAGES ? it - PJ_STAGES : 0); j < it; ++j)
+        if (!tc::mbar_wait(full(j % PJ_STAGES), (j / PJ_STAGES) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA 1 issuer: H = X P1^T + p1b, runs ahead by PJ_ACC units
+      constexpr uint32_t id1 = tc::idesc_bf16(128, false, false);
+      const uint32_t b1 = sbase + PJ_OFF_B1, one = sbase + PJ_OFF_ONE;
+      int it = 0;
+      for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
+        const int s = it % PJ_STAGES, a = it % PJ_ACC;
+        if (!tc::mbar_wait(full(s), (it / PJ_STAGES) & 1, WAIT_LIMIT)) { fail(); break; }
+        if (it >= PJ_ACC && !tc::mbar_wait(acc_empty(a), ((it / PJ_ACC) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+        tc::fence_after();
+        const uint32_t ax = sbase + s * PJ_AT, d = tmem + a * 128;
+        tc::mma_bf16(d, tc::make_desc(ax, 128, 512), tc::make_desc(b1, 128, 768), id1, 0);
+        tc::mma_bf16(d, tc::make_desc(ax + 256, 128, 512), tc::make_desc(b1 + 256, 128, 768), id1, 1);
+        tc::mma_bf16(d, tc::make_desc(one, 128, 256), tc::make_desc(b1 + 512, 128, 768), id1, 1);
+        tc::mma_commit(empty(s));
+        tc::mma_commit(m1_full(a));
+      }
+    }
+  } else if (warp == 2) {
+    if (lane == 0) {  // MMA 2 issuer: O = leaky(H) P2^T, as soon as a unit's A2 tile is ready
+      constexpr uint32_t id2 = tc::idesc_bf16(16, false, false);
+      const uint32_t b2 = sbase + PJ_OFF_B2;
+      int j = 0;
+      for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++j) {
+        const int a = j % PJ_ACC;
+        if (!tc::mbar_wait(a2_full(a), (j / PJ_ACC) & 1, WAIT_LIMIT)) { fail(); break; }
+        tc::fence_after();
+        const uint32_t a2 = sbase + PJ_OFF_A2 + (j % PJ_NA2) * PJ_A2;
+        for (int k = 0; k < 8; ++k)
+          tc::mma_bf16(tmem + a * 128, tc::make_desc(a2 + k * 256, 128, 2048), tc::make_desc(b2 + k * 256, 128, 2048),
+                       id2, k > 0);
+        tc::mma_commit(m2_full(a));
+      }
+    }
+  } else if (warp >= 4) {  // epilogue: group grp takes units it = grp, grp + 2, ...
+    const int q = warp & 3, grp = (warp - 4) >> 2;
+    const int px = q * 32 + lane;
+    const __nv_bfloat162 slope = __floats2bfloat162_rn(LEAK, LEAK);
+    // leaky(H) of unit j into its A2 buffer
+    auto stage1 = [&](int j) -> bool {
+      const int a = j % PJ_ACC;
+      if (*abort_flag || !tc::mbar_wait(m1_full(a), (j / PJ_ACC) & 1, WAIT_LIMIT)) return false;
+      tc::fence_after();
+      uint8_t* a2 = smem + PJ_OFF_A2 + (j % PJ_NA2) * PJ_A2;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {  // 32 hidden units per round
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * 128 + g * 32, v);
+        uint32_t p[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          h2 = __hmax2(h2, __hmul2(h2, slope));
+          p[i] = *reinterpret_cast<uint32_t*>(&h2);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          *reinterpret_cast<uint4*>(a2 + ((px >> 3) * 16 + g * 4 + t) * 128 + (px & 7) * 16) =
+              make_uint4(p[4 * t], p[4 * t + 1], p[4 * t + 2], p[4 * t + 3]);
+      }
+      tc::fence_before();
+      tc::fence_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(a2_full(a));
+      return true;
+    };
+    // per-unit output parameters, loaded one unit ahead of their use
+    struct OutP { float2* dst; float rho; double sc, sw; int ld, x0, y0, cx0, cy0; };
+    auto prep = [&](int u) -> OutP {
+      OutP o;
+      const int b = u / UPW;
+      int w = P.win_id ? P.win_id[b] : b;
+      int gnx = P.nx, gny = P.ny, gnwx = P.nwx;
+      const double* sc = P.scale;
+      o.dst = P.z_global;
+      if (P.ptab) {
+        const int2 e = P.wtab[b];
+        const ProbGeom& G = P.ptab[e.x];
+        w = e.y; gnx = G.nx; gny = G.ny; gnwx = G.nwx; sc = G.scale; o.dst = G.z;
+      }
+      o.rho = P.rho[b];  // raw loads; combined at first use in stage2
+      o.sc = sc ? *sc : 1.0;
+      o.sw = P.scale_win ? P.scale_win[b] : 1.0;
+      if (P.e_win) {  // per-window output: x0 = -1 marks it
+        o.dst = P.e_win + (size_t)b * NPIX;
+        o.x0 = -1; o.ld = 80; o.y0 = o.cx0 = o.cy0 = 0;
+      } else {
+        const int wa = w % gnwx, wb = w / gnwx;
+        o.ld = gnx;
+        o.x0 = min(max(FDFD_CORE * wa - FDFD_OVL, 0), gnx - FDFD_WIN);
+        o.y0 = min(max(FDFD_CORE * wb - FDFD_OVL, 0), gny - FDFD_WIN);
+        o.cx0 = FDFD_CORE * wa; o.cy0 = FDFD_CORE * wb;
+      }
+      return o;
+    };
+    // output of unit j (its 128 pixels of window entry u / UPW)
+    auto stage2 = [&](int j, int u, const OutP& o) -> bool {
+      const int a = j % PJ_ACC;
+      if (!tc::mbar_wait(m2_full(a), (j / PJ_ACC) & 1, WAIT_LIMIT)) return false;
+      tc::fence_after();
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * 128, v);
+      const int m = (u % UPW) * 128 + px;
+      const float f = o.rho * (float)o.sc * (float)o.sw;
+      const float2 val = make_float2((v[0] + P.p2b0) * f, (v[1] + P.p2b1) * f);
+      if (o.x0 < 0) {
+        o.dst[m] = val;
+      } else {  // restricted prolongation: only the window's 64 x 64 core
+        const int gx = o.x0 + m % 80, gy = o.y0 + m / 80;
+        if (gx >= o.cx0 && gx < o.cx0 + FDFD_CORE && gy >= o.cy0 && gy < o.cy0 + FDFD_CORE)
+          o.dst[(size_t)gy * o.ld + gx] = val;
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty(a));
+      return true;
+    };
+    int it = grp, prev = -1, prev_u = -1;
+    OutP prev_o{};
+    for (int u = blockIdx.x + grp * gridDim.x; u < total; u += 2 * gridDim.x, it += 2) {
+      const OutP cur = prep(u);
+      if (!stage1(it)) { fail(); prev = -1; break; }
+      if (prev >= 0 && !stage2(prev, prev_u, prev_o)) { fail(); prev = -1; break; }
+      prev = it; prev_u = u; prev_o = cur;
+    }
+    if (prev >= 0 && !*abort_flag && !stage2(prev, prev_u, prev_o)) fail();
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc::fence_after();
+    tc::tmem_free(tmem, 512);
   }
 }
 
@@ -614,7 +928,6 @@ __global__ void __launch_bounds__(256) pack_kernel(NnoInput in, GridGeom g, bf16
 // Self-test operator: plain row-major C = A B^T.
 struct TestOp {
   static constexpr bool kConstB = false;
-  static constexpr bool kUnroll = false;
   const bf16* A; const bf16* B; float* C; int M, N, K, amn;
   typedef NoState State;
   __device__ int rows(int) const { return M; }
@@ -718,10 +1031,8 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
   if ((rc = up(&W->P1, to_bf16(std::vector<float>(p, p + 128 * 32)), bytes))) return rc;
   p += 128 * 32;
   if ((rc = up(&W->p1b, std::vector<float>(p, p + 128), bytes))) return rc;
-  memcpy(W->hp1b, p, sizeof(W->hp1b));
   p += 128;
   if ((rc = up(&W->P2, std::vector<float>(p, p + 256), bytes))) return rc;
-  memcpy(W->hP2, p, sizeof(W->hP2));
   p += 256;
   W->p2b[0] = p[0];
   W->p2b[1] = p[1];
@@ -778,15 +1089,15 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
   if (!g5_cap) {
     CK(cudaFuncSetAttribute(g3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G3_SMEM));
     CK(cudaFuncSetAttribute(g5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
-    g5_cap = persistent_grid((const void*)g5_kernel, G5_THREADS, G5_SMEM, 32 * G5_ROWS);
+    g5_cap = persistent_grid((const void*)g5_kernel, G5_THREADS, G5_SMEM, 512);
   }
   const int g5_total = n * (80 / G5_ROWS);
   const int g5_grid = g5_total < g5_cap ? g5_total : g5_cap;
+  {  // block 0's DFT along x; blocks 1..3 get theirs from the previous block's G5 kernel
+    ProfScope ps(h, 9, 1);
+    if ((rc = launch_gemm<32, 80, true>(G1Op{k->X, W->Fx, k->T1}, 2560 / 128, n, k->err, s))) return rc;
+  }
   for (int bl = 0; bl < 4; ++bl) {
-    {
-      ProfScope ps(h, 9, 1);
-      if ((rc = launch_gemm<32, 80, true>(G1Op{k->X, W->Fx, k->T1}, 2560 / 128, n, k->err, s))) return rc;
-    }
     {
       ProfScope ps(h, 10, 1);
       if ((rc = launch_gemm<64, 160, true>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s))) return rc;
@@ -803,20 +1114,23 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     }
     {
       ProfScope ps(h, 13, 1);
-      g5_kernel<<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], bl == 3, g5_total, k->err);
+      g5_kernel<<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], W->Fx, k->T1,
+                                                     bl == 3, g5_total, k->err);
       CKL();
     }
   }
-  ProjOp po{k->X, W->P1, W->p2b[0], W->p2b[1], k->rho, out.scale, in.win_id,
-            out.z_global, out.e_win, g.nx, g.nwx, out.scale_win};
-  po.ny_ = g.ny;
-  po.wtab = in.wtab;
-  po.ptab = in.ptab;
-  memcpy(po.p1b, W->hp1b, sizeof(po.p1b));
-  memcpy(po.P2, W->hP2, sizeof(po.P2));
   {
+    static int pj_cap = 0;
+    if (!pj_cap) {
+      CK(cudaFuncSetAttribute(proj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PJ_SMEM));
+      pj_cap = persistent_grid((const void*)proj_kernel, PJ_THREADS, PJ_SMEM, 512);
+    }
+    ProjArgs pa{k->X, W->P1, W->p1b, W->P2, W->p2b[0], W->p2b[1], k->rho, out.scale, in.win_id, out.scale_win,
+                out.z_global, out.e_win, g.nx, g.ny, g.nwx, in.wtab, in.ptab};
+    const int pj_total = n * (NPIX / 128);
     ProfScope ps(h, 14, 1);
-    if ((rc = launch_gemm<128, 32, false>(po, NPIX / 128, n, k->err, s))) return rc;
+    proj_kernel<<<pj_total < pj_cap ? pj_total : pj_cap, PJ_THREADS, PJ_SMEM, s>>>(pa, pj_total, k->err);
+    CKL();
   }
   return FDFD_OK;
 }

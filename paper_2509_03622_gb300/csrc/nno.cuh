@@ -18,18 +18,16 @@ struct NnoWeights {
   float* p1b = nullptr;     // [128]
   float* P2 = nullptr;      // [2][128]
   float p2b[2] = {0.f, 0.f};
-  float hp1b[128] = {};     // host copies of p1b and P2: the projection epilogue
-  float hP2[256] = {};      // takes them as kernel parameters (constant bank)
 };
 
 struct NnoWork {
   int cap = 0;              // windows per batch
   bf16* in = nullptr;       // [cap][6400][16]  packed inputs (channel-last)
-  bf16* X = nullptr;        // [cap][6400][32]  activations (channel-last, in place)
+  bf16* X = nullptr;        // [cap][80 y][x/8][c/8][x%8][c%8]  activations, tiled (in place)
   bf16* T1 = nullptr;       // [cap][160 (ri,y)][512 (kx,c)]
   bf16* Xh = nullptr;       // [512 mode][cap][64 (c,ri)]
   bf16* Yh = nullptr;       // [cap][512 (o,kx)][64 (q,ri)]
-  bf16* T3 = nullptr;       // [cap][80 y][32 o][32 (kx,ri)]
+  bf16* T3 = nullptr;       // [cap][80 y][o/8][k/8][o%8][k%8]  k = (kx,ri), tiled
   float* rho = nullptr;     // [cap]
   int* err = nullptr;       // bounded-wait failure flag
 };

@@ -127,8 +127,10 @@ __global__ void jacobi_apply(const float2* __restrict__ v, const double* __restr
 
 // FP64 residual r = rs b - A~ x with FP64 coefficients, x in FP64; b = j sb J
 // (source form) or b = J (adjoint right-hand side); rs rescales the system
-// (a power of two, so exactly).  Writes r rounded to complex64 and reduces
-// ||r||^2 (FP64) into *result.
+// (a power of two, so exactly); x == nullptr means x = 0.  Writes r rounded
+// to complex64 and reduces ||r||^2 (FP64) into *result.  FP64 arithmetic is
+// scarce on this GPU, so cells whose coefficients are all real (everywhere
+// outside the PML) take a real-coefficient path with the same roundings.
 constexpr int RT = 256;
 __global__ void __launch_bounds__(RT)
 residual64(const double2* __restrict__ x, const float2* __restrict__ J, double sb, int src, double rs,
@@ -140,14 +142,26 @@ residual64(const double2* __restrict__ x, const float2* __restrict__ J, double s
   double acc = 0.0;
   const size_t n = (size_t)nx * ny;
   for (size_t c = blockIdx.x * (size_t)RT + threadIdx.x; c < n; c += (size_t)gridDim.x * RT) {
-    const int i = (int)(c % nx), j = (int)(c / nx);
-    const AxisCoef64 a = cx[i], b = cy[j];
-    const double2 xc = x[c];
-    double2 Ax = zmul(make_double2(a.dg.x + b.dg.x + k2 * (double)eps[c], a.dg.y + b.dg.y), xc);
-    if (i > 0) Ax = zadd(Ax, zmul(a.lo, x[c - 1]));
-    if (i + 1 < nx) Ax = zadd(Ax, zmul(a.hi, x[c + 1]));
-    if (j > 0) Ax = zadd(Ax, zmul(b.lo, x[c - nx]));
-    if (j + 1 < ny) Ax = zadd(Ax, zmul(b.hi, x[c + nx]));
+    double2 Ax = make_double2(0.0, 0.0);
+    if (x) {
+      const int i = (int)(c % nx), j = (int)(c / nx);
+      const AxisCoef64 a = cx[i], b = cy[j];
+      const double2 xc = x[c];
+      const double2 z = make_double2(0.0, 0.0);
+      const double2 xl = i > 0 ? x[c - 1] : z, xr = i + 1 < nx ? x[c + 1] : z;
+      const double2 xd = j > 0 ? x[c - nx] : z, xu = j + 1 < ny ? x[c + nx] : z;
+      const double dre = a.dg.x + b.dg.x + k2 * (double)eps[c];
+      if (a.lo.y == 0.0 && a.hi.y == 0.0 && b.lo.y == 0.0 && b.hi.y == 0.0 && a.dg.y + b.dg.y == 0.0) {
+        Ax.x = dre * xc.x + a.lo.x * xl.x + a.hi.x * xr.x + b.lo.x * xd.x + b.hi.x * xu.x;
+        Ax.y = dre * xc.y + a.lo.x * xl.y + a.hi.x * xr.y + b.lo.x * xd.y + b.hi.x * xu.y;
+      } else {
+        Ax = zmul(make_double2(dre, a.dg.y + b.dg.y), xc);
+        Ax = zadd(Ax, zmul(a.lo, xl));
+        Ax = zadd(Ax, zmul(a.hi, xr));
+        Ax = zadd(Ax, zmul(b.lo, xd));
+        Ax = zadd(Ax, zmul(b.hi, xu));
+      }
+    }
     const float2 Jc = J[c];
     const double2 bc = src ? make_double2(-sb * rs * (double)Jc.y, sb * rs * (double)Jc.x)
                            : make_double2(rs * (double)Jc.x, rs * (double)Jc.y);

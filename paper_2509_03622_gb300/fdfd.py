@@ -40,7 +40,7 @@ class SchwarzDesc(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("restart", C.c_int), ("max_iters", C.c_int), ("tol", C.c_double),
-                ("precond", C.c_int), ("use_x0", C.c_int)]
+                ("precond", C.c_int), ("use_x0", C.c_int), ("use_graphs", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -53,16 +53,17 @@ class SolveStats(C.Structure):
 
 class Info(C.Structure):
     _fields_ = [("n_win", C.c_int), ("nwx", C.c_int), ("nwy", C.c_int), ("k_coarse", C.c_int),
-                ("n_coarse", C.c_int), ("workspace_bytes", C.c_size_t)]
+                ("n_coarse", C.c_int), ("workspace_bytes", C.c_size_t), ("graphs_cached", C.c_int),
+                ("graphs_ok", C.c_int)]
 
 
 class Profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 16), ("launches", C.c_longlong * 16), ("total_launches", C.c_longlong)]
+    _fields_ = [("ms", C.c_double * 18), ("launches", C.c_longlong * 18), ("total_launches", C.c_longlong)]
 
 
 PROF_CLASSES = ["stencil", "cgs_dots", "cgs_update", "residual64", "vector_misc", "nno_pack", "traces", "coarse",
                 "nno_lift", "nno_dft_x", "nno_dft_y", "nno_mix", "nno_idft_y", "nno_idft_x_mix_act", "nno_proj",
-                "unused"]
+                "local_krylov", "rhs_norm", "unused"]
 
 _P = C.c_void_p
 _SIGS = {
@@ -181,10 +182,13 @@ class Solver:
         sd.n_weights = blob.size
         _check(lib.schwarz_setup(self.h, C.byref(sd)), "schwarz_setup")
 
-    @staticmethod
-    def _opts(restart, max_iters, tol, precond, use_x0):
+    # replay each Arnoldi step as a CUDA graph (set False for eager launches)
+    use_graphs = True
+
+    def _opts(self, restart, max_iters, tol, precond, use_x0):
         o = SolveOpts()
         o.restart, o.max_iters, o.tol, o.precond, o.use_x0 = restart, max_iters, tol, precond, int(use_x0)
+        o.use_graphs = int(self.use_graphs)
         return o
 
     def solve(self, J, E, restart=30, max_iters=1000, tol=1e-6, precond=PRECOND_SCHWARZ, use_x0=False):
@@ -282,6 +286,6 @@ class Batch:
         jp = (C.c_void_p * n)(*[_ptr(J).value for J in Js])
         ep = (C.c_void_p * n)(*[_ptr(E).value for E in Es])
         st = (SolveStats * n)()
-        o = Solver._opts(restart, max_iters, tol, precond, use_x0)
+        o = self.solvers[0]._opts(restart, max_iters, tol, precond, use_x0)
         rc = _check(lib.fdfd_solve_batched(self.b, jp, ep, C.byref(o), st), "fdfd_solve_batched")
         return rc, [s.as_dict() for s in st]

@@ -91,3 +91,29 @@ def test_reported_residual_is_true_residual_1024():
     A = OF.assemble_operator(eps, dx, LAM, 20)
     rr = OF.relres(A, E.cpu().numpy().ravel(), OF.source_rhs(J, dx, LAM))
     assert abs(rr - st["relres_true"]) <= 1e-4 * rr
+
+
+@pytest.mark.parametrize("precond,inner", [(2, 0), (2, 2), (1, 0)])
+def test_graph_replay_equals_eager(precond, inner):
+    """Arnoldi steps replayed as CUDA graphs give bitwise the same iterates as
+    eager launches (batching pattern: launch-bound small grids)."""
+    import torch
+    from paper_2509_03622_gb300 import fdfd as F
+    n = 192
+    eps, dx = wl.freeform_eps(n, n, seed=2192), LAM / 30
+    S = F.Solver(torch.from_numpy(eps).cuda(), dx, LAM, npml=20)
+    if precond == 2:
+        S.schwarz_setup(_weights(), k_coarse=0, inner_iters=inner)
+    J = torch.from_numpy(wl.point_source(n, n)).cuda()
+    out = []
+    for graphs in (False, True, True):  # eager, first capture, replay of the cached graphs
+        S.use_graphs = graphs
+        E = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+        rc, st = S.solve(J, E, restart=12, max_iters=30, tol=1e-12, precond=precond)
+        out.append((E.cpu().numpy(), st))
+    info = S.info()
+    assert info["graphs_ok"] == 1 and info["graphs_cached"] >= 1
+    for E, st in out[1:]:
+        assert st["iters"] == out[0][1]["iters"] == 30
+        assert st["relres_true"] == out[0][1]["relres_true"]
+        assert np.array_equal(E, out[0][0])
