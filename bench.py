@@ -92,7 +92,7 @@ class Clocks:
 # channels = 64 B per pixel, complex64 fields = 8 B per cell).
 WIN_BYTES = {
     "nno_pack": 6400 * (8 + 4 + 32),          # residual + eps in, 16 bf16 channels out
-    "nno_lift": 6400 * (32 + 64),             # inputs in, activation out
+    "nno_lift": 6400 * (32 + 64) + 160 * 512 * 2,   # inputs in, activation and block 0's T1 out
     "nno_dft_x": 6400 * 64 + 160 * 512 * 2,   # activation in, half-spectrum along x out
     "nno_dft_y": 160 * 512 * 2 + 512 * 64 * 2,
     "nno_mix": 512 * 64 * 2 * 2,              # spectrum in and out (weights amortised)
@@ -103,12 +103,12 @@ WIN_BYTES = {
 G5_T1_BYTES = 160 * 512 * 2                   # next block's half-spectrum, written by blocks 0..2
 # Useful FLOPs per window of each stage (padding excluded).
 NNO_FLOP_PER_WIN = {
-    "nno_lift": 6400 * 32 * 15 * 2, "nno_dft_x": 2560 * 32 * 80 * 2, "nno_dft_y": 512 * 64 * 160 * 2,
+    "nno_lift": 6400 * 32 * 15 * 2 + 2560 * 32 * 80 * 2, "nno_dft_x": 2560 * 32 * 80 * 2, "nno_dft_y": 512 * 64 * 160 * 2,
     "nno_mix": 512 * 64 * 64 * 2, "nno_idft_y": 512 * 160 * 64 * 2, "nno_idft_x_mix_act": 80 * 80 * 32 * 64 * 2,
     "nno_proj": 6400 * (128 * 32 + 2 * 128) * 2,
 }
 KERNEL_NAMES = {"stencil": "stencil_c64", "cgs_dots": "cgs_dots_kernel", "cgs_update": "cgs_update_kernel",
-                "residual64": "residual64", "nno_pack": "pack_kernel", "nno_lift": "gemm_kernel<32,16> (LiftOp)",
+                "residual64": "residual64", "nno_pack": "pack_kernel", "nno_lift": "g5_kernel<lift> (lift + block-0 DFT-x)",
                 "nno_dft_x": "gemm_kernel<32,80,MN> (G1Op)", "nno_dft_y": "gemm_kernel<64,160,MN> (G2Op)",
                 "nno_mix": "g3_kernel", "nno_idft_y": "gemm_kernel<160,64> (G4Op)",
                 "nno_idft_x_mix_act": "g5_kernel", "nno_proj": "proj_kernel", "rhs_norm": "residual64 (x = 0)"}
@@ -217,6 +217,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tts", action="store_true", help="also time a full solve to 1e-6")
+    ap.add_argument("--nno-precision", default="bf16", choices=["bf16", "fp8"],
+                    help="neural-operator activations: BF16, or E4M3 with per-channel scales")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -239,7 +241,7 @@ def main():
     S = F.Solver(torch.from_numpy(eps).to(dev), dx, lam, npml=20)
     precond = F.PRECOND_SCHWARZ if args.precond == "schwarz" else F.PRECOND_JACOBI
     kc = args.k_coarse if args.k_coarse >= 0 else (8 if n <= 1024 else 0)
-    prec_nno = "bf16"
+    prec_nno = args.nno_precision
     if precond == F.PRECOND_SCHWARZ:
         blob, wsrc = load_weights(args.weights)
         t0 = time.perf_counter()
@@ -328,6 +330,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "Mcell-it/s", "h2d_bytes_per_step": N * 8 // args.steps,
                     "d2h_bytes_per_step": N * 8 // args.steps},
             "clocks": clk.summary(), "relres_after_steps": st["relres_true"],
+            "class_ms_per_step": {c: v / max(steps, 1) for c, v in cls_ms.items() if v > 0},
             "graphs": {"ms_per_step": ms_graph / max(steps, 1),
                        "note": "same solve with each Arnoldi step replayed as a CUDA graph, unprofiled"}}
     if rank == 0 and not args.no_cpu:

@@ -78,8 +78,16 @@ typedef struct {
 /* Two-level Schwarz set-up (Sec. 2.2, Methods, Algorithm 3 set-up). */
 typedef struct {
   int k_coarse;          /* coarse basis vectors per window; 0 = one-level */
-  int precision;         /* FDFD_PREC_BF16 (FDFD_PREC_FP8 is reserved and
-                            currently rejected with FDFD_EINVAL)            */
+  int precision;         /* FDFD_PREC_BF16: BF16 activations and weights,
+                            FP32 accumulation.  FDFD_PREC_FP8: the
+                            activation entering each Fourier block and the
+                            projection is stored as E4M3 with power-of-two
+                            per-channel scales (calibrated at set-up on a
+                            seeded random residual, 4x headroom below the
+                            E4M3 maximum, saturating), converted to BF16 in
+                            shared memory for the tensor cores, the scales
+                            folded into the weights that read it; halves
+                            the activation traffic (precision pattern).    */
   const float* weights;  /* HOST ptr to the FNO weight blob, float32, in the
                             order: lift_w[32][15], lift_b[32], then per block
                             b = 0..3: R_re[32][32][32][16], R_im[...],

@@ -28,6 +28,12 @@ struct CoarseData {
   float2* ebc = nullptr;     // [n_win][320]
   float2* tmp = nullptr;     // [n_win][6400] window fields during set-up
   int* dropped = nullptr;    // [nc]
+  // FP32 copies used by the per-iteration apply (the correction is part of a
+  // flexible preconditioner, and FP64 arithmetic is scarce on this GPU)
+  float2* Cf = nullptr;      // [n_win][9][320][k]
+  float2* Nf = nullptr;      // [nc][nc] inverse normal matrix
+  float2* rcf = nullptr;     // [nc]
+  float2* zcf = nullptr;     // [nc]
 };
 
 namespace {
@@ -238,53 +244,61 @@ __global__ void gj_col_kernel(const double2* A, int n, int p, double2* pcol) {
 }
 
 // r_c[(w,m)] = -sum_{i adjacent to w} sum_slot conj(C[i][j(w)][slot][m]) e_bc[i][slot]
-__global__ void coarse_rhs_kernel(double2* rc, const double2* C, const float2* ebc, int k, int nwx, int nwy) {
-  const int w = blockIdx.x;
+// FP32 apply: r_c[w][m] = -sum C[i][d][sl][m]^H e_bc[i][sl] over the window and
+// its 8 neighbours (warp per basis vector m, lanes over the 9 x 320 terms)
+__global__ void __launch_bounds__(256) coarse_rhs32_kernel(float2* rc, const float2* C, const float2* ebc, int k,
+                                                           int nwx, int nwy) {
+  const int w = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int aw = w % nwx, bw = w / nwx;
-  for (int m = threadIdx.x; m < k; m += blockDim.x) {
-    double sr = 0.0, si = 0.0;
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int ai = aw - dx, bi = bw - dy;
-        if (ai < 0 || ai >= nwx || bi < 0 || bi >= nwy) continue;
-        const int i = bi * nwx + ai;
-        const double2* c = C + (((size_t)i * 9 + (dy + 1) * 3 + dx + 1) * 320) * k + m;
-        const float2* e = ebc + (size_t)i * 320;
-        for (int sl = 0; sl < 320; ++sl) {
-          const double2 a = c[(size_t)sl * k];
-          const double er = e[sl].x, ei = e[sl].y;
-          sr += a.x * er + a.y * ei;
-          si += a.x * ei - a.y * er;
-        }
-      }
-    rc[w * k + m] = make_double2(-sr, -si);
+  for (int m = warp; m < k; m += blockDim.x / 32) {
+    float sr = 0.f, si = 0.f;
+    for (int t = lane; t < 9 * 320; t += 32) {
+      const int d = t / 320, sl = t % 320, dy = d / 3 - 1, dx = d % 3 - 1;
+      const int ai = aw - dx, bi = bw - dy;
+      if (ai < 0 || ai >= nwx || bi < 0 || bi >= nwy) continue;
+      const int i = bi * nwx + ai;
+      const float2 a = C[(((size_t)i * 9 + d) * 320 + sl) * k + m];
+      const float2 e = ebc[(size_t)i * 320 + sl];
+      sr += a.x * e.x + a.y * e.y;
+      si += a.x * e.y - a.y * e.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) rc[w * k + m] = make_float2(-sr, -si);
   }
 }
 
-// z = Ninv r_c (one warp per row, FP64)
-__global__ void gemv_kernel(double2* z, const double2* A, const double2* x, const int* dropped, int n) {
+// z = Ninv r_c in FP32 (one warp per row)
+__global__ void gemv32_kernel(float2* z, const float2* A, const float2* x, const int* dropped, int n) {
   const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
   if (row >= n) return;
-  double sr = 0.0, si = 0.0;
-  const double2* a = A + (size_t)row * n;
+  float sr = 0.f, si = 0.f;
+  const float2* a = A + (size_t)row * n;
   for (int j = lane; j < n; j += 32) {
     if (dropped[j]) continue;
-    const double2 p = zmul(a[j], x[j]);
+    const float2 p = cmul(a[j], x[j]);
     sr += p.x; si += p.y;
   }
   for (int o = 16; o > 0; o >>= 1) {
     sr += __shfl_xor_sync(0xffffffffu, sr, o);
     si += __shfl_xor_sync(0xffffffffu, si, o);
   }
-  if (lane == 0) z[row] = dropped[row] ? make_double2(0.0, 0.0) : make_double2(sr, si);
+  if (lane == 0) z[row] = dropped[row] ? make_float2(0.f, 0.f) : make_float2(sr, si);
+}
+
+__global__ void to_f32_kernel(float2* dst, const double2* src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = make_float2((float)src[i].x, (float)src[i].y);
 }
 
 // u[core(w)] += sum_m z[w,m] Phi[w][m]
-__global__ void correction_kernel(float2* u, const float2* Phi, const double2* z, int k, int nx, int nwx) {
+__global__ void correction_kernel(float2* u, const float2* Phi, const float2* z, int k, int nx, int nwx) {
   const int w = blockIdx.y;
   const int a = w % nwx, b = w / nwx;
   __shared__ float2 zw[256];
-  for (int m = threadIdx.x; m < k; m += blockDim.x) zw[m] = make_float2((float)z[w * k + m].x, (float)z[w * k + m].y);
+  for (int m = threadIdx.x; m < k; m += blockDim.x) zw[m] = z[w * k + m];
   __syncthreads();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= 4096) return;
@@ -306,7 +320,8 @@ int ca(T** p, size_t n, size_t* bytes) {
 
 void coarse_free(CoarseData* c) {
   if (!c) return;
-  void* ptrs[] = {c->Q, c->Qf, c->Phi, c->C, c->N, c->Nd, c->rc, c->zc, c->ebc, c->tmp, c->dropped};
+  void* ptrs[] = {c->Q, c->Qf, c->Phi, c->C, c->N, c->Nd, c->rc, c->zc, c->ebc, c->tmp, c->dropped,
+                  c->Cf, c->Nf, c->rcf, c->zcf};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete c;
 }
@@ -324,7 +339,9 @@ int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, 
       (rc = ca(&c->N, (size_t)nc * nc, bytes)) || (rc = ca(&c->Nd, (size_t)n_win * k * k, bytes)) ||
       (rc = ca(&c->rc, (size_t)nc, bytes)) || (rc = ca(&c->zc, (size_t)nc, bytes)) ||
       (rc = ca(&c->ebc, (size_t)n_win * 320, bytes)) || (rc = ca(&c->tmp, (size_t)n_win * 6400, bytes)) ||
-      (rc = ca(&c->dropped, (size_t)nc, bytes))) {
+      (rc = ca(&c->dropped, (size_t)nc, bytes)) || (rc = ca(&c->Cf, (size_t)n_win * 9 * 320 * k, bytes)) ||
+      (rc = ca(&c->Nf, (size_t)nc * nc, bytes)) || (rc = ca(&c->rcf, (size_t)nc, bytes)) ||
+      (rc = ca(&c->zcf, (size_t)nc, bytes))) {
     coarse_free(c);
     return rc;
   }
@@ -366,6 +383,8 @@ int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, 
     gj_row_kernel<<<(nc + 255) / 256, 256, 0, s>>>(c->N, nc, p, c->rc);
     gj_elim_kernel<<<gb, 256, 0, s>>>(c->N, nc, p, c->rc, c->zc);
   }
+  to_f32_kernel<<<1024, 256, 0, s>>>(c->Cf, c->C, (size_t)n_win * 9 * 320 * k);
+  to_f32_kernel<<<1024, 256, 0, s>>>(c->Nf, c->N, (size_t)nc * nc);
   CKL();
   CK(cudaStreamSynchronize(s));
   *out = c;
@@ -381,9 +400,9 @@ int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u) {
     if ((rc = schwarz_traces(h, u, c->ebc))) return rc;
   }
   ProfScope ps(h, 7, 3);
-  coarse_rhs_kernel<<<n_win, 64, 0, s>>>(c->rc, c->C, c->ebc, c->k, nwx, nwy);
-  gemv_kernel<<<(c->nc + 7) / 8, 256, 0, s>>>(c->zc, c->N, c->rc, c->dropped, c->nc);
-  correction_kernel<<<dim3(4096 / 256, n_win), 256, 0, s>>>(u, c->Phi, c->zc, c->k, h->nx, nwx);
+  coarse_rhs32_kernel<<<n_win, 256, 0, s>>>(c->rcf, c->Cf, c->ebc, c->k, nwx, nwy);
+  gemv32_kernel<<<(c->nc + 7) / 8, 256, 0, s>>>(c->zcf, c->Nf, c->rcf, c->dropped, c->nc);
+  correction_kernel<<<dim3(4096 / 256, n_win), 256, 0, s>>>(u, c->Phi, c->zcf, c->k, h->nx, nwx);
   CKL();
   return FDFD_OK;
 }

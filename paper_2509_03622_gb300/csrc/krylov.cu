@@ -290,7 +290,18 @@ template <int NV>
 int update_nv(const float2* V, size_t ld, int v0, int nv, float2* w, float2* vnext, size_t n,
               KrylovState* st, double* partials, unsigned* counter, int j, int ldH, int fin,
               cudaStream_t s) {
-  cgs_update_kernel<NV><<<krylov_grid(n), KT, 0, s>>>(
+  static int resident = 0;  // one wave of resident blocks (as for the dots)
+  if (!resident) {
+    int per_sm = 0, dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cgs_update_kernel<NV>, KT, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    resident = nsm * per_sm;
+  }
+  const int grid = krylov_grid(n) < resident ? krylov_grid(n) : resident;
+  cgs_update_kernel<NV><<<grid, KT, 0, s>>>(
       reinterpret_cast<const float4*>(V), ld / 2, v0, nv, reinterpret_cast<float4*>(w),
       reinterpret_cast<float4*>(vnext), n / 2, st, partials, counter, j, ldH, fin);
   CKL();

@@ -3,10 +3,10 @@
 //
 // Per window (80 x 80, width 32, 4 Fourier blocks, 512 retained modes):
 //   pack   : restriction, RMS normalisation, 15 input channels   (SIMT)
-//   lift   : [6400 px][16] x [32][16]^T                           (GEMM)
+//   lift   : [6400 px][16] x [32][16]^T, then block 0's G1, in the G5 pipeline
 //   block b (the truncated 2D DFT is done as two 1D DFT GEMMs each way):
 //     G1  DFT along x   : rows (y,c)   K = x 80        N = (kx,ri) 32   A MN-major
-//         (block 0 only as its own GEMM; blocks 1..3 inside the previous G5)
+//         (inside the kernel that produced the block's input rows)
 //     G2  DFT along y   : rows (kx,c)  K = (ri,y) 160  N = (q,ri) 64    A MN-major
 //     G3  spectral mix  : 4 modes per CTA, rows = windows, K = (c,ri) 64, N = (o,ri) 64
 //     G4  inverse DFT y : rows (o,kx)  K = (q,ri) 64   N = (y,ri) 160
@@ -21,6 +21,7 @@
 #include <math.h>
 #include <string.h>
 #include <vector>
+#include <cuda_fp8.h>
 #include "nno.cuh"
 #include "ctx.cuh"
 #include "tc.cuh"
@@ -42,6 +43,10 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
 // tiled activation layout: [window*80 + y][x/8][c/8][x%8][c%8] (bf16 elements)
 __device__ __forceinline__ size_t xt_off(size_t wy, int x, int c) {
   return wy * 2560 + (size_t)((x >> 3) * 256 + (c >> 3) * 64 + (x & 7) * 8 + (c & 7));
+}
+// tiled packed inputs: [window*80 + y][x/8][k/8][x%8][k%8] (16 input channels)
+__device__ __forceinline__ size_t in_off(size_t wy, int x, int k) {
+  return wy * 1280 + (size_t)((x >> 3) * 128 + (k >> 3) * 64 + (x & 7) * 8 + (k & 7));
 }
 // tiled inverse-y spectrum: [window*80 + y][o/8][k/8][o%8][k%8], k = (kx,ri)
 __device__ __forceinline__ size_t t3_off(size_t wy, int o, int k) {
@@ -65,12 +70,16 @@ __device__ __forceinline__ size_t t3_off(size_t wy, int o, int k) {
 // A B operand that is the same for every tile (Op::kConstB: DFT matrices,
 // weights) is loaded once per CTA.
 // ---------------------------------------------------------------------
-template <int BN, int K, bool AMN, class Op>
+// KS > 1 splits K into KS consecutive stages accumulating into one tile
+// (smaller stages, a deeper ring for the same shared memory).
+template <int BN, int K, bool AMN, class Op, int KS = 1>
 struct GemmCfg {
+  static constexpr int KH = K / KS;  // K per stage
   static constexpr int KC = K / 8;
-  static constexpr uint32_t A_BYTES = 128 * K * 2, B_BYTES = BN * K * 2;
-  static constexpr uint32_t STAGE = A_BYTES + (Op::kConstB ? 0 : B_BYTES);
+  static constexpr uint32_t A_BYTES = 128 * KH * 2, B_BYTES = BN * K * 2;
+  static constexpr uint32_t STAGE = A_BYTES + (Op::kConstB ? 0 : BN * KH * 2);
   static constexpr uint32_t CONSTB = Op::kConstB ? B_BYTES : 0;
+  static_assert(K % (16 * KS) == 0, "K split");
   static constexpr int S0 = (int)((200u * 1024u - CONSTB) / STAGE);
   static constexpr int S = S0 > 8 ? 8 : S0;
   static constexpr uint32_t OFF_BAR = S * STAGE + CONSTB;
@@ -80,9 +89,10 @@ struct GemmCfg {
 };
 constexpr int GEMM_THREADS = 288;
 
+// Columns k0 .. k0+K-1 of the A tile (and of B when it varies) into a stage.
 template <int BN, int K, bool AMN, class Op>
 __device__ __forceinline__ void gemm_load(const Op& op, uint8_t* sA, uint8_t* sB, int b, int m0, int Mb,
-                                          bool loadB) {
+                                          bool loadB, int k0 = 0) {
   constexpr int KC = K / 8;
   const int tid = threadIdx.x;  // 0..127: the producer warps
   if (!AMN) {
@@ -90,27 +100,27 @@ __device__ __forceinline__ void gemm_load(const Op& op, uint8_t* sA, uint8_t* sB
       const int t8 = c & 7, rest = c >> 3, kc = rest % KC, rg = rest / KC;
       const int m = m0 + rg * 8 + t8;
       const bool ok = m < Mb;
-      tc::cp_async16(sA + (rg * KC + kc) * 128 + t8 * 16, op.a_src(b, ok ? m : 0, kc * 8), ok);
+      tc::cp_async16(sA + (rg * KC + kc) * 128 + t8 * 16, op.a_src(b, ok ? m : 0, k0 + kc * 8), ok);
     }
   } else {
     for (int c = tid; c < 16 * K; c += 128) {
       const int t8 = c & 7, rest = c >> 3, mg = rest & 15, kg = rest >> 4;
       const int m = m0 + mg * 8;
       const bool ok = m < Mb;
-      tc::cp_async16(sA + (mg * KC + kg) * 128 + t8 * 16, op.a_src(b, ok ? m : 0, kg * 8 + t8), ok);
+      tc::cp_async16(sA + (mg * KC + kg) * 128 + t8 * 16, op.a_src(b, ok ? m : 0, k0 + kg * 8 + t8), ok);
     }
   }
   if (loadB)
     for (int c = tid; c < BN * KC; c += 128) {
       const int t8 = c & 7, rest = c >> 3, kc = rest % KC, rg = rest / KC;
-      tc::cp_async16(sB + (rg * KC + kc) * 128 + t8 * 16, op.b_src(b, rg * 8 + t8, kc * 8), true);
+      tc::cp_async16(sB + (rg * KC + kc) * 128 + t8 * 16, op.b_src(b, rg * 8 + t8, k0 + kc * 8), true);
     }
 }
 
-template <int BN, int K, bool AMN, class Op>
+template <int BN, int K, bool AMN, class Op, int KS>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_per_batch, int total, int* err) {
   static_assert(K % 16 == 0 && BN % 16 == 0 && BN <= 256, "shape");
-  typedef GemmCfg<BN, K, AMN, Op> Cfg;
+  typedef GemmCfg<BN, K, AMN, Op, KS> Cfg;
   extern __shared__ __align__(1024) uint8_t smem[];
   const uint32_t sbase = tc::smem_u32(smem);
   const uint32_t bar = sbase + Cfg::OFF_BAR;
@@ -145,35 +155,46 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_
   auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
 
   if (warp < 4) {  // ---------------- producers ----------------
-    int it = 0;
-    for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x, ++it) {
-      const int s = it % Cfg::S;
-      if (it >= Cfg::S && !tc::mbar_wait(empty(s), ((it / Cfg::S) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+    int it = 0;  // stage fills: KS per tile
+    for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x) {
       const int b = tile / tiles_per_batch, m0 = (tile % tiles_per_batch) * 128;
-      uint8_t* st = smem + s * Cfg::STAGE;
-      gemm_load<BN, K, AMN>(op, st, st + Cfg::A_BYTES, b, m0, op.rows(b), !Op::kConstB);
-      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full(s)) : "memory");
+      for (int part = 0; part < KS && !*abort_flag; ++part, ++it) {
+        const int s = it % Cfg::S;
+        if (it >= Cfg::S && !tc::mbar_wait(empty(s), ((it / Cfg::S) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+        uint8_t* st = smem + s * Cfg::STAGE;
+        gemm_load<BN, Cfg::KH, AMN>(op, st, st + Cfg::A_BYTES, b, m0, op.rows(b), !Op::kConstB, part * Cfg::KH);
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full(s)) : "memory");
+      }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");  // no copy may outlive the CTA
   } else if (warp == 8) {  // ---------------- MMA issuer ----------------
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_bf16(BN, AMN, false);
-      int it = 0;
-      for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x, ++it) {
-        const int s = it % Cfg::S, a = it & 1;
-        if (!tc::mbar_wait(full(s), (it / Cfg::S) & 1, WAIT_LIMIT)) { fail(); break; }
-        if (it >= 2 && !tc::mbar_wait(acc_empty(a), ((it >> 1) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
-        tc::fence_async_smem();  // the producers' cp.async data -> async proxy
-        tc::fence_after();
-        const uint32_t a0 = sbase + s * Cfg::STAGE;
-        const uint32_t b0 = Op::kConstB ? sbase + Cfg::S * Cfg::STAGE : a0 + Cfg::A_BYTES;
+      int it = 0, t = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < total && !*abort_flag && ok; tile += gridDim.x, ++t) {
+        const int a = t & 1;
+        if (t >= 2 && !tc::mbar_wait(acc_empty(a), ((t >> 1) - 1) & 1, WAIT_LIMIT)) { ok = false; break; }
+        for (int part = 0; part < KS; ++part, ++it) {
+          const int s = it % Cfg::S;
+          if (!tc::mbar_wait(full(s), (it / Cfg::S) & 1, WAIT_LIMIT)) { ok = false; break; }
+          tc::fence_async_smem();  // the producers' cp.async data -> async proxy
+          tc::fence_after();
+          const uint32_t a0 = sbase + s * Cfg::STAGE;
+          // constant B holds all K: this part's K-steps start at part * KH / 16
+          const uint32_t b0 = Op::kConstB ? sbase + Cfg::S * Cfg::STAGE + part * (Cfg::KH / 16) * 256
+                                          : a0 + Cfg::A_BYTES;
+          const uint32_t bsbo = Op::kConstB ? K * 16 : Cfg::KH * 16;
 #pragma unroll
-        for (int k = 0; k < K / 16; ++k)
-          tc::mma_bf16(tmem + a * Cfg::TCOLS, tc::make_desc(a0 + k * 256, 128, K * 16),
-                       tc::make_desc(b0 + k * 256, 128, K * 16), idesc, k > 0);
-        tc::mma_commit(empty(s));
+          for (int k = 0; k < Cfg::KH / 16; ++k)
+            tc::mma_bf16(tmem + a * Cfg::TCOLS, tc::make_desc(a0 + k * 256, 128, Cfg::KH * 16),
+                         tc::make_desc(b0 + k * 256, 128, bsbo), idesc, (part > 0) || (k > 0));
+          tc::mma_commit(empty(s));
+        }
+        if (!ok) break;
         tc::mma_commit(acc_full(a));
       }
+      if (!ok) fail();
     }
   } else {  // ---------------- epilogue (warps 4-7) ----------------
     const int q = warp & 3;
@@ -231,10 +252,10 @@ int persistent_grid(const void* kern, int threads, size_t smem, uint32_t tcols) 
   return nsm * per_sm;
 }
 
-template <int BN, int K, bool AMN, class Op>
+template <int BN, int K, bool AMN, class Op, int KS = 1>
 int launch_gemm(const Op& op, int tiles, int batches, int* err, cudaStream_t s) {
-  typedef GemmCfg<BN, K, AMN, Op> Cfg;
-  auto kern = gemm_kernel<BN, K, AMN, Op>;
+  typedef GemmCfg<BN, K, AMN, Op, KS> Cfg;
+  auto kern = gemm_kernel<BN, K, AMN, Op, KS>;
   static int grid_cap = 0;
   if (grid_cap == 0) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess)
@@ -253,50 +274,6 @@ struct NoState {};
 // ---------------------------------------------------------------------
 // Stage operators
 // ---------------------------------------------------------------------
-struct LiftOp {  // rows = pixels, K = 16 inputs, N = 32 channels
-  static constexpr bool kConstB = true;
-  const bf16* in; const bf16* w; const float* bias; bf16* X;
-  typedef NoState State;
-  __device__ int rows(int) const { return NPIX; }
-  __device__ const uint4* a_src(int b, int m, int k) const {
-    return reinterpret_cast<const uint4*>(in + ((size_t)b * NPIX + m) * 16 + k);
-  }
-  __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(w + n * 16 + k); }
-  __device__ void epi_begin(State&) const {}
-  __device__ void epi(int b, int m, int c0, const float* v, State&) const {
-    uint32_t p[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) p[i] = pack2(v[2 * i] + bias[c0 + 2 * i], v[2 * i + 1] + bias[c0 + 2 * i + 1]);
-    bf16* dst = X + xt_off((size_t)b * 80 + m / 80, m % 80, c0);
-    *reinterpret_cast<uint4*>(dst) = make_uint4(p[0], p[1], p[2], p[3]);
-    *reinterpret_cast<uint4*>(dst + 64) = make_uint4(p[4], p[5], p[6], p[7]);
-  }
-  __device__ void epi_end(int, int, State&) const {}
-};
-
-struct G1Op {  // DFT along x: rows (y,c), K = x (A MN-major from X), N = (kx,ri)
-  static constexpr bool kConstB = true;
-  const bf16* X; const bf16* Fx; bf16* T1;
-  typedef NoState State;
-  __device__ int rows(int) const { return 80 * 32; }
-  __device__ const uint4* a_src(int b, int m, int k) const {  // 8 consecutive c at (y, x = k)
-    const int y = m >> 5, c = m & 31;
-    return reinterpret_cast<const uint4*>(X + xt_off((size_t)b * 80 + y, k, c));
-  }
-  __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(Fx + n * 80 + k); }
-  __device__ void epi_begin(State&) const {}
-  __device__ void epi(int b, int m, int c0, const float* v, State&) const {
-    const int y = m >> 5, c = m & 31;
-    bf16* base = T1 + (size_t)b * 160 * 512;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int col = c0 + i, kx = col >> 1, ri = col & 1;
-      base[(ri * 80 + y) * 512 + kx * 32 + c] = __float2bfloat16_rn(v[i]);
-    }
-  }
-  __device__ void epi_end(int, int, State&) const {}
-};
-
 struct G2Op {  // DFT along y: rows (kx,c), K = (ri,y) (A MN-major from T1), N = (q,ri)
   static constexpr bool kConstB = true;
   const bf16* T1; const bf16* Fy; bf16* Xh; int cap;
@@ -446,20 +423,51 @@ constexpr int G5_THREADS = 384;
 constexpr uint32_t G5_XT = 80 * 32 * 2;                          // one tiled [80][32] X row
 constexpr uint32_t G5_XB = G5_ROWS * G5_XT;                      // 20480
 constexpr uint32_t G5_TB = G5_ROWS * 2048;                       // 8192
-constexpr uint32_t G5_STAGE = G5_XB + G5_TB;                     // 28672
+constexpr uint32_t G5_X8B = G5_ROWS * 2560;                      // 10240: the rows in FP8 (staging)
+constexpr uint32_t G5_STAGE = G5_XB + G5_TB + G5_X8B;            // 38912
 constexpr uint32_t G5_A1 = 128 * 80 * 2;                         // G1 A tile, MN-major (yy,c) x x
 constexpr uint32_t G5_OFF_A1 = G5_STAGES * G5_STAGE;             // after the ring (absorbs the over-read)
 constexpr uint32_t G5_OFF_GX = G5_OFF_A1 + 2 * G5_A1;
 constexpr uint32_t G5_OFF_W = G5_OFF_GX + 128 * 32 * 2;
 constexpr uint32_t G5_OFF_FX = G5_OFF_W + 32 * 32 * 2;
 constexpr uint32_t G5_OFF_BAR = G5_OFF_FX + 32 * 80 * 2;
-constexpr uint32_t G5_NBAR = 2 * G5_STAGES + 8;
+constexpr uint32_t G5_NBAR = 3 * G5_STAGES + 8;
 constexpr uint32_t G5_SMEM = G5_OFF_BAR + G5_NBAR * 8 + 16;
 static_assert(G5_SMEM <= 227 * 1024, "g5 shared memory");
 
+// FP8 tiled activation layout: [window*80 + y][x/8][c/16][x%8][c%16] (bytes)
+__device__ __forceinline__ size_t x8_off(size_t wy, int x, int c) {
+  return wy * 2560 + (size_t)((x >> 3) * 256 + (c >> 4) * 128 + (x & 7) * 16 + (c & 15));
+}
+// 16 E4M3 values (one 16-byte chunk) -> 16 BF16 values (two 16-byte chunks);
+// exact: every E4M3 value is representable in BF16.
+__device__ __forceinline__ void e4m3x16_to_bf16(uint4 q, uint4& lo, uint4& hi) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  uint32_t o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const __nv_fp8x2_storage_t pr = (__nv_fp8x2_storage_t)((w[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu);
+    const __half2 h = __half2(__nv_cvt_fp8x2_to_halfraw2(pr, __NV_E4M3));
+    const float2 f = __half22float2(h);
+    o[i] = pack2(f.x, f.y);
+  }
+  lo = make_uint4(o[0], o[1], o[2], o[3]);
+  hi = make_uint4(o[4], o[5], o[6], o[7]);
+}
+// x * qinv for 2 channels -> 2 E4M3 (saturating)
+__device__ __forceinline__ uint32_t to_e4m3x2(float a, float b) {
+  return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+}
+
+template <bool LIFT, bool FP8>
 __global__ void __launch_bounds__(G5_THREADS, 1)
 g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* bias, const bf16* Fx, bf16* T1,
-          int last, int total, int* err) {
+          const float* qinv, int last, int total, int* err) {
+  // LIFT: T3 is the tiled packed input and Wb the lift weights [32][16]; the
+  // unit's MMA is the lift (K = 16), no activation, then block 0's DFT along x.
+  // FP8: X holds E4M3 activations (x8_off layout).  The unit's input rows
+  // are bulk-copied as FP8 and converted to BF16 by warps 2-3 (the scale is
+  // folded into Wb); the output rows are written as E4M3 times qinv[c].
   extern __shared__ __align__(1024) uint8_t smem[];
   const uint32_t sbase = tc::smem_u32(smem);
   const uint32_t bar = sbase + G5_OFF_BAR;
@@ -470,19 +478,23 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   auto g1_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + 2 + a); };
   auto a1_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + 4 + a); };
   auto acc_empty = [&](int a) { return bar + 8u * (2 * G5_STAGES + 6 + a); };
+  auto conv_full = [&](int s) { return bar + 8u * (2 * G5_STAGES + 8 + s); };  // FP8 rows converted
+  constexpr bool CONV = FP8 && !LIFT;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G5_OFF_BAR + G5_NBAR * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + G5_OFF_BAR + G5_NBAR * 8 + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int UPW = 80 / G5_ROWS;
   if ((int)blockIdx.x >= total) return;
-  // constant operands: Gx [128][32], W [32][32], Fx [32][80] (K-major tiles)
-  for (int c = tid; c < 128 * 4; c += G5_THREADS) {
-    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-    tc::cp_async16(smem + G5_OFF_GX + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
-  }
-  for (int c = tid; c < 32 * 4; c += G5_THREADS) {
-    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-    tc::cp_async16(smem + G5_OFF_W + (rg * 4 + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * 32 + kc * 8, true);
+  // constant operands: Gx [128][32], W [32][32] (lift: [32][16]), Fx [32][80] (K-major tiles)
+  if (!LIFT)
+    for (int c = tid; c < 128 * 4; c += G5_THREADS) {
+      const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
+      tc::cp_async16(smem + G5_OFF_GX + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
+    }
+  constexpr int WK = LIFT ? 2 : 4;  // k-groups of the mixer / lift weights
+  for (int c = tid; c < 32 * WK; c += G5_THREADS) {
+    const int t8 = c & 7, rest = c >> 3, kc = rest % WK, rg = rest / WK;
+    tc::cp_async16(smem + G5_OFF_W + (rg * WK + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * (8 * WK) + kc * 8, true);
   }
   if (!last)
     for (int c = tid; c < 32 * 10; c += G5_THREADS) {
@@ -496,6 +508,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       tc::mbar_init(g5_full(a), 1); tc::mbar_init(g1_full(a), 1);
       tc::mbar_init(a1_full(a), 8); tc::mbar_init(acc_empty(a), 8);
     }
+    for (int s = 0; s < G5_STAGES; ++s) tc::mbar_init(conv_full(s), 2);
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -514,9 +527,19 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
         const int s = it % G5_STAGES;
         if (it >= G5_STAGES && !tc::mbar_wait(empty(s), ((it / G5_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
         const size_t wy = (size_t)(u / UPW) * 80 + (u % UPW) * G5_ROWS;
-        tc::mbar_arrive_tx(full(s), G5_STAGE);
-        tc::bulk_g2s(sbase + s * G5_STAGE, X + wy * 2560, G5_XB, full(s));
-        tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
+        if (LIFT) {  // 4 rows of packed inputs
+          tc::mbar_arrive_tx(full(s), G5_ROWS * 2560);
+          tc::bulk_g2s(sbase + s * G5_STAGE, T3 + wy * 1280, G5_ROWS * 2560, full(s));
+        } else if (FP8) {  // FP8 rows into the staging area, the inverse-y spectrum as usual
+          tc::mbar_arrive_tx(full(s), G5_X8B + G5_TB);
+          tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB + G5_TB, reinterpret_cast<const uint8_t*>(X) + wy * 2560, G5_X8B,
+                       full(s));
+          tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
+        } else {
+          tc::mbar_arrive_tx(full(s), G5_XB + G5_TB);
+          tc::bulk_g2s(sbase + s * G5_STAGE, X + wy * 2560, G5_XB, full(s));
+          tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
+        }
       }
       // every copy issued must have landed before the CTA may exit
       for (int j = (it > G5_STAGES ? it - G5_STAGES : 0); j < it; ++j)
@@ -542,12 +565,16 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       bool ok = true;
       for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
         const int s = it % G5_STAGES, a = it & 1;
-        if (!tc::mbar_wait(full(s), (it / G5_STAGES) & 1, WAIT_LIMIT)) { ok = false; break; }
+        if (!tc::mbar_wait(CONV ? conv_full(s) : full(s), (it / G5_STAGES) & 1, WAIT_LIMIT)) { ok = false; break; }
         if (it >= 2 && !tc::mbar_wait(acc_empty(a), ((it >> 1) - 1) & 1, WAIT_LIMIT)) { ok = false; break; }
         tc::fence_after();
         const uint32_t ax = sbase + s * G5_STAGE, bt = ax + G5_XB;
         for (int yy = 0; yy < G5_ROWS; ++yy) {
           const uint32_t d = tmem + a * 256 + yy * 32;
+          if (LIFT) {  // lift: [x][16 inputs] . [32][16]^T
+            tc::mma_bf16(d, tc::make_desc(ax + yy * 2560, 128, 256), tc::make_desc(bw, 128, 256), id5, 0);
+            continue;
+          }
           for (int k = 0; k < 2; ++k)
             tc::mma_bf16(d, tc::make_desc(ag + k * 256, 128, 512), tc::make_desc(bt + yy * 2048 + k * 256, 128, 512),
                          id5, k > 0);
@@ -562,8 +589,33 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       if (ok && !last && it >= 1 && !*abort_flag && !issue_g1(it - 1)) ok = false;
       if (!ok) fail();
     }
+  } else if (warp < 4) {  // ---------------- FP8 -> BF16 converters (warps 2-3) ----------------
+    if (CONV) {
+      const int ct = tid - 64;  // 0..63
+      int it = 0;
+      for (int u = blockIdx.x; u < total; u += gridDim.x, ++it) {
+        const int s = it % G5_STAGES;
+        if (*abort_flag || !tc::mbar_wait(full(s), (it / G5_STAGES) & 1, WAIT_LIMIT)) { fail(); break; }
+        const uint8_t* src = smem + s * G5_STAGE + G5_XB + G5_TB;
+        uint8_t* dst = smem + s * G5_STAGE;
+        for (int c = ct; c < G5_ROWS * 160; c += 64) {  // 16-byte FP8 chunks, row by row
+          const int yy = c / 160, r = c % 160, x8 = r >> 4, c16 = (r >> 3) & 1, xr = r & 7;
+          uint4 lo, hi;
+          e4m3x16_to_bf16(*reinterpret_cast<const uint4*>(src + yy * 2560 + r * 16), lo, hi);
+          uint8_t* d = dst + yy * G5_XT + (x8 * 4 + 2 * c16) * 128 + xr * 16;
+          *reinterpret_cast<uint4*>(d) = lo;
+          *reinterpret_cast<uint4*>(d + 128) = hi;
+        }
+        tc::fence_async_smem();
+        __syncwarp();
+        if ((tid & 31) == 0) tc::mbar_arrive(conv_full(s));
+      }
+    }
   } else if (warp >= 4) {  // ---------------- epilogue ----------------
     const int ew = warp - 4, q = ew & 3, hf = ew >> 2;
+    float qi[32];
+#pragma unroll
+    for (int o = 0; o < 32; ++o) qi[o] = FP8 ? qinv[o] : 1.f;
     float bs[32];
 #pragma unroll
     for (int o = 0; o < 32; ++o) bs[o] = bias[o];
@@ -585,13 +637,33 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
               float e0 = v[2 * i] + bs[2 * i], e1 = v[2 * i + 1] + bs[2 * i + 1];
-              if (!last) { e0 = leaky(e0); e1 = leaky(e1); }
+              if (!LIFT && !last) { e0 = leaky(e0); e1 = leaky(e1); }
               p[i] = pack2(e0, e1);
             }
-            bf16* dst = X + xt_off(wy0 + yy, x, 0);
+            if (FP8) {  // E4M3 activations, 2 x 16 channels
+              uint32_t q8[8];
 #pragma unroll
-            for (int cg = 0; cg < 4; ++cg)
-              *reinterpret_cast<uint4*>(dst + cg * 64) = make_uint4(p[4 * cg], p[4 * cg + 1], p[4 * cg + 2], p[4 * cg + 3]);
+              for (int i = 0; i < 8; ++i) {
+                float e[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                  const int c = 4 * i + t;
+                  float ev = v[c] + bs[c];
+                  if (!LIFT && !last) ev = leaky(ev);
+                  e[t] = ev * qi[c];
+                }
+                q8[i] = to_e4m3x2(e[0], e[1]) | (to_e4m3x2(e[2], e[3]) << 16);
+              }
+              uint8_t* d8 = reinterpret_cast<uint8_t*>(X) + x8_off(wy0 + yy, x, 0);
+              *reinterpret_cast<uint4*>(d8) = make_uint4(q8[0], q8[1], q8[2], q8[3]);
+              *reinterpret_cast<uint4*>(d8 + 128) = make_uint4(q8[4], q8[5], q8[6], q8[7]);
+            } else {
+              bf16* dst = X + xt_off(wy0 + yy, x, 0);
+#pragma unroll
+              for (int cg = 0; cg < 4; ++cg)
+                *reinterpret_cast<uint4*>(dst + cg * 64) =
+                    make_uint4(p[4 * cg], p[4 * cg + 1], p[4 * cg + 2], p[4 * cg + 3]);
+            }
             if (!last)
 #pragma unroll
               for (int cg = 0; cg < 4; ++cg)
@@ -648,17 +720,19 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
 // alternate units, each software-pipelined: it prepares its next unit's
 // second operand while the previous unit's second MMA runs.
 constexpr int PJ_STAGES = 6;
+constexpr uint32_t PJ_A8 = 128 * 32;                      // the X tile in FP8 (staging)
 constexpr int PJ_THREADS = 384;
-constexpr uint32_t PJ_AT = 128 * 32 * 2;                  // X tile
+constexpr uint32_t PJ_AT = 128 * 32 * 2;                  // X tile (BF16)
+constexpr uint32_t PJ_ST = PJ_AT + PJ_A8;                 // stage: BF16 tile + FP8 staging
 constexpr uint32_t PJ_A2 = 128 * 128 * 2;                 // leaky(H) tile, K-major
 constexpr int PJ_NA2 = 4;                                 // leaky(H) buffers (2 per epilogue group)
-constexpr uint32_t PJ_OFF_A2 = PJ_STAGES * PJ_AT;
+constexpr uint32_t PJ_OFF_A2 = PJ_STAGES * PJ_ST;
 constexpr uint32_t PJ_OFF_B1 = PJ_OFF_A2 + PJ_NA2 * PJ_A2;  // [128 h][48 k]: P1 | p1b | 0
 constexpr uint32_t PJ_OFF_ONE = PJ_OFF_B1 + 128 * 48 * 2; // [128 p][16 k]: 1 | 0
 constexpr uint32_t PJ_OFF_B2 = PJ_OFF_ONE + 128 * 16 * 2; // [16 n][128 h]: P2 rows 0, 1
 constexpr uint32_t PJ_OFF_BAR = PJ_OFF_B2 + 16 * 128 * 2;
 constexpr int PJ_ACC = 4;
-constexpr uint32_t PJ_NBAR = 2 * PJ_STAGES + 4 * PJ_ACC;
+constexpr uint32_t PJ_NBAR = 3 * PJ_STAGES + 4 * PJ_ACC;
 constexpr uint32_t PJ_SMEM = PJ_OFF_BAR + PJ_NBAR * 8 + 16;
 static_assert(PJ_SMEM <= 227 * 1024, "proj shared memory");
 
@@ -669,6 +743,9 @@ struct ProjArgs {
   const int2* wtab; const ProbGeom* ptab;
 };
 
+// FP8: X holds E4M3 activations; the tile is bulk-copied as FP8, converted to
+// BF16 by warp 3 and multiplied by P1 diag(s) (P.P1 then points at it).
+template <bool FP8>
 __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int total, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const uint32_t sbase = tc::smem_u32(smem);
@@ -679,6 +756,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int tot
   auto m2_full = [&](int a) { return bar + 8u * (2 * PJ_STAGES + PJ_ACC + a); };
   auto a2_full = [&](int a) { return bar + 8u * (2 * PJ_STAGES + 2 * PJ_ACC + a); };
   auto acc_empty = [&](int a) { return bar + 8u * (2 * PJ_STAGES + 3 * PJ_ACC + a); };
+  auto conv_full = [&](int s) { return bar + 8u * (2 * PJ_STAGES + 4 * PJ_ACC + s); };
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + PJ_OFF_BAR + PJ_NBAR * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + PJ_OFF_BAR + PJ_NBAR * 8 + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -705,7 +783,9 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int tot
   }
   tc::cp_async_wait_all();
   if (tid == 0) {
-    for (int s = 0; s < PJ_STAGES; ++s) { tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); }
+    for (int s = 0; s < PJ_STAGES; ++s) {
+      tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); tc::mbar_init(conv_full(s), 1);
+    }
     for (int a = 0; a < PJ_ACC; ++a) {
       tc::mbar_init(m1_full(a), 1); tc::mbar_init(m2_full(a), 1);
       tc::mbar_init(a2_full(a), 4); tc::mbar_init(acc_empty(a), 4);
@@ -727,9 +807,16 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int tot
       for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
         const int s = it % PJ_STAGES;
         if (it >= PJ_STAGES && !tc::mbar_wait(empty(s), ((it / PJ_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
-        tc::mbar_arrive_tx(full(s), PJ_AT);
-        tc::bulk_g2s(sbase + s * PJ_AT, P.X + (size_t)(u / UPW) * (NPIX * 32) + (size_t)(u % UPW) * (128 * 32), PJ_AT,
-                     full(s));
+        if (FP8) {
+          tc::mbar_arrive_tx(full(s), PJ_A8);
+          tc::bulk_g2s(sbase + s * PJ_ST + PJ_AT,
+                       reinterpret_cast<const uint8_t*>(P.X) + (size_t)(u / UPW) * (NPIX * 32) + (size_t)(u % UPW) * PJ_A8,
+                       PJ_A8, full(s));
+        } else {
+          tc::mbar_arrive_tx(full(s), PJ_AT);
+          tc::bulk_g2s(sbase + s * PJ_ST, P.X + (size_t)(u / UPW) * (NPIX * 32) + (size_t)(u % UPW) * (128 * 32),
+                       PJ_AT, full(s));
+        }
       }
       for (int j = (it > PJ_STAGES ? it - PJ_STAGES : 0); j < it; ++j)
         if (!tc::mbar_wait(full(j % PJ_STAGES), (j / PJ_STAGES) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
@@ -741,10 +828,10 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int tot
       int it = 0;
       for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
         const int s = it % PJ_STAGES, a = it % PJ_ACC;
-        if (!tc::mbar_wait(full(s), (it / PJ_STAGES) & 1, WAIT_LIMIT)) { fail(); break; }
+        if (!tc::mbar_wait(FP8 ? conv_full(s) : full(s), (it / PJ_STAGES) & 1, WAIT_LIMIT)) { fail(); break; }
         if (it >= PJ_ACC && !tc::mbar_wait(acc_empty(a), ((it / PJ_ACC) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
         tc::fence_after();
-        const uint32_t ax = sbase + s * PJ_AT, d = tmem + a * 128;
+        const uint32_t ax = sbase + s * PJ_ST, d = tmem + a * 128;
         tc::mma_bf16(d, tc::make_desc(ax, 128, 512), tc::make_desc(b1, 128, 768), id1, 0);
         tc::mma_bf16(d, tc::make_desc(ax + 256, 128, 512), tc::make_desc(b1 + 256, 128, 768), id1, 1);
         tc::mma_bf16(d, tc::make_desc(one, 128, 256), tc::make_desc(b1 + 512, 128, 768), id1, 1);
@@ -766,6 +853,27 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int tot
           tc::mma_bf16(tmem + a * 128, tc::make_desc(a2 + k * 256, 128, 2048), tc::make_desc(b2 + k * 256, 128, 2048),
                        id2, k > 0);
         tc::mma_commit(m2_full(a));
+      }
+    }
+  } else if (warp == 3) {
+    if (FP8) {  // FP8 -> BF16 converter
+      int it = 0;
+      for (int u = blockIdx.x; u < total; u += gridDim.x, ++it) {
+        const int s = it % PJ_STAGES;
+        if (*abort_flag || !tc::mbar_wait(full(s), (it / PJ_STAGES) & 1, WAIT_LIMIT)) { fail(); break; }
+        const uint8_t* src = smem + s * PJ_ST + PJ_AT;
+        uint8_t* dst = smem + s * PJ_ST;
+        for (int c = lane; c < 256; c += 32) {  // chunk = (pixel group, 16 channels, pixel)
+          const int g = c >> 4, c16 = (c >> 3) & 1, xr = c & 7;
+          uint4 lo, hi;
+          e4m3x16_to_bf16(*reinterpret_cast<const uint4*>(src + c * 16), lo, hi);
+          uint8_t* d = dst + (g * 4 + 2 * c16) * 128 + xr * 16;
+          *reinterpret_cast<uint4*>(d) = lo;
+          *reinterpret_cast<uint4*>(d + 128) = hi;
+        }
+        tc::fence_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(conv_full(s));
       }
     }
   } else if (warp >= 4) {  // epilogue: group grp takes units it = grp, grp + 2, ...
@@ -919,9 +1027,11 @@ __global__ void __launch_bounds__(256) pack_kernel(NnoInput in, GridGeom g, bf16
     }
     const float2 sx = g.isx[gx], sy = g.isy[gy];
     c[11] = sx.x; c[12] = sx.y; c[13] = sy.x; c[14] = sy.y; c[15] = 0.f;
-    uint4* dst = reinterpret_cast<uint4*>(out + ((size_t)b * NPIX + p) * 16);
-    dst[0] = make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), pack2(c[6], c[7]));
-    dst[1] = make_uint4(pack2(c[8], c[9]), pack2(c[10], c[11]), pack2(c[12], c[13]), pack2(c[14], c[15]));
+    bf16* dst = out + in_off((size_t)b * 80 + y, x, 0);  // tiled: one row = one K-major tile
+    *reinterpret_cast<uint4*>(dst) =
+        make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), pack2(c[6], c[7]));
+    *reinterpret_cast<uint4*>(dst + 64) =
+        make_uint4(pack2(c[8], c[9]), pack2(c[10], c[11]), pack2(c[12], c[13]), pack2(c[14], c[15]));
   }
 }
 
@@ -1040,12 +1150,13 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
 }
 
 void nno_free_weights(NnoWeights* W) {
-  void* ptrs[] = {W->lift_w, W->lift_b, W->Fx, W->Fy, W->Gy, W->Gx, W->P1, W->p1b, W->P2};
+  void* ptrs[] = {W->lift_w, W->lift_b, W->Fx, W->Fy, W->Gy, W->Gx, W->P1, W->p1b, W->P2, W->qinv, W->P18};
   for (void* q : ptrs) if (q) cudaFree(q);
   for (int b = 0; b < 4; ++b) {
     if (W->R[b]) cudaFree(W->R[b]);
     if (W->W[b]) cudaFree(W->W[b]);
     if (W->bias[b]) cudaFree(W->bias[b]);
+    if (W->W8[b]) cudaFree(W->W8[b]);
   }
   *W = NnoWeights();
 }
@@ -1071,36 +1182,69 @@ void nno_free_work(NnoWork* w) {
   *w = NnoWork();
 }
 
+// max |x| per channel of the BF16 tiled activations of n windows (calibration)
+__global__ void absmax_kernel(const bf16* X, size_t n_elem, unsigned* out) {
+  __shared__ unsigned m[32];
+  if (threadIdx.x < 32) m[threadIdx.x] = 0u;
+  __syncthreads();
+  for (size_t e8 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e8 < n_elem / 8; e8 += (size_t)gridDim.x * blockDim.x) {
+    const uint4 q = reinterpret_cast<const uint4*>(X)[e8];
+    const bf16* v = reinterpret_cast<const bf16*>(&q);
+    const int cg = (int)((e8 >> 3) & 3);  // chunk -> c/8 (xt_off: 64 elements per c-group)
+    for (int i = 0; i < 8; ++i) {
+      const float a = fabsf(__bfloat162float(v[i]));
+      atomicMax(&m[cg * 8 + i], __float_as_uint(a));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) atomicMax(&out[threadIdx.x], m[threadIdx.x]);
+}
+
 int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInput& in, const NnoOutput& out,
-                int n, cudaStream_t s, fdfd_ctx* h) {
+                int n, cudaStream_t s, fdfd_ctx* h, unsigned* calib) {
   if (n <= 0) return FDFD_OK;
   if (n > k->cap) return FDFD_EINVAL;
+  if (calib && W->fp8) return FDFD_EINVAL;  // calibration runs on the BF16 path
   int rc;
+  auto record = [&](int b) -> int {  // calibration: channel maxima of the activation entering block b
+    if (!calib) return FDFD_OK;
+    absmax_kernel<<<256, 256, 0, s>>>(k->X, (size_t)n * NPIX * 32, calib + 32 * b);
+    CKL();
+    return FDFD_OK;
+  };
   {
     ProfScope ps(h, 5, 1);
     pack_kernel<<<n, 256, 0, s>>>(in, g, k->in, k->rho);
     CKL();
   }
-  {
-    ProfScope ps(h, 8, 1);
-    if ((rc = launch_gemm<32, 16, false>(LiftOp{k->in, W->lift_w, W->lift_b, k->X}, NPIX / 128, n, k->err, s))) return rc;
-  }
   static int g5_cap = 0;
   if (!g5_cap) {
     CK(cudaFuncSetAttribute(g3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G3_SMEM));
-    CK(cudaFuncSetAttribute(g5_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
-    g5_cap = persistent_grid((const void*)g5_kernel, G5_THREADS, G5_SMEM, 512);
+    CK(cudaFuncSetAttribute(g5_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
+    CK(cudaFuncSetAttribute(g5_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
+    CK(cudaFuncSetAttribute(g5_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
+    CK(cudaFuncSetAttribute(g5_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
+    g5_cap = persistent_grid((const void*)g5_kernel<false, false>, G5_THREADS, G5_SMEM, 512);
   }
   const int g5_total = n * (80 / G5_ROWS);
   const int g5_grid = g5_total < g5_cap ? g5_total : g5_cap;
-  {  // block 0's DFT along x; blocks 1..3 get theirs from the previous block's G5 kernel
-    ProfScope ps(h, 9, 1);
-    if ((rc = launch_gemm<32, 80, true>(G1Op{k->X, W->Fx, k->T1}, 2560 / 128, n, k->err, s))) return rc;
+  {  // lift 15 -> 32 and block 0's DFT along x, in the G5 pipeline; blocks 1..3
+     // get their DFT along x from the previous block's G5 kernel
+    ProfScope ps(h, 8, 1);
+    if (W->fp8)
+      g5_kernel<true, true><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->in, nullptr, W->lift_w, W->lift_b, W->Fx,
+                                                                  k->T1, W->qinv, 0, g5_total, k->err);
+    else
+      g5_kernel<true, false><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->in, nullptr, W->lift_w, W->lift_b, W->Fx,
+                                                                   k->T1, nullptr, 0, g5_total, k->err);
+    CKL();
   }
+  if ((rc = record(0))) return rc;
   for (int bl = 0; bl < 4; ++bl) {
     {
       ProfScope ps(h, 10, 1);
-      if ((rc = launch_gemm<64, 160, true>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s))) return rc;
+      if ((rc = launch_gemm<64, 160, true, G2Op, 2>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s)))
+        return rc;
     }
     {
       ProfScope ps(h, 11, 1);
@@ -1114,24 +1258,84 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     }
     {
       ProfScope ps(h, 13, 1);
-      g5_kernel<<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], W->Fx, k->T1,
-                                                     bl == 3, g5_total, k->err);
+      if (W->fp8)
+        g5_kernel<false, true><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W8[bl], W->bias[bl], W->Fx,
+                                                                     k->T1, W->qinv + 32 * (bl + 1), bl == 3,
+                                                                     g5_total, k->err);
+      else
+        g5_kernel<false, false><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], W->Fx,
+                                                                      k->T1, nullptr, bl == 3, g5_total, k->err);
       CKL();
     }
+    if ((rc = record(bl + 1))) return rc;
   }
   {
     static int pj_cap = 0;
     if (!pj_cap) {
-      CK(cudaFuncSetAttribute(proj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PJ_SMEM));
-      pj_cap = persistent_grid((const void*)proj_kernel, PJ_THREADS, PJ_SMEM, 512);
+      CK(cudaFuncSetAttribute(proj_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PJ_SMEM));
+      CK(cudaFuncSetAttribute(proj_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PJ_SMEM));
+      pj_cap = persistent_grid((const void*)proj_kernel<false>, PJ_THREADS, PJ_SMEM, 512);
     }
-    ProjArgs pa{k->X, W->P1, W->p1b, W->P2, W->p2b[0], W->p2b[1], k->rho, out.scale, in.win_id, out.scale_win,
+    ProjArgs pa{k->X, W->fp8 ? W->P18 : W->P1, W->p1b, W->P2, W->p2b[0], W->p2b[1], k->rho, out.scale, in.win_id, out.scale_win,
                 out.z_global, out.e_win, g.nx, g.ny, g.nwx, in.wtab, in.ptab};
     const int pj_total = n * (NPIX / 128);
     ProfScope ps(h, 14, 1);
-    proj_kernel<<<pj_total < pj_cap ? pj_total : pj_cap, PJ_THREADS, PJ_SMEM, s>>>(pa, pj_total, k->err);
+    const int pj_grid = pj_total < pj_cap ? pj_total : pj_cap;
+    if (W->fp8) proj_kernel<true><<<pj_grid, PJ_THREADS, PJ_SMEM, s>>>(pa, pj_total, k->err);
+    else proj_kernel<false><<<pj_grid, PJ_THREADS, PJ_SMEM, s>>>(pa, pj_total, k->err);
     CKL();
   }
+  return FDFD_OK;
+}
+
+int nno_enable_fp8(NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInput& in, int n,
+                   const float* blob, size_t nfloats, size_t* bytes, cudaStream_t s) {
+  if (W->fp8 || n <= 0 || n > work->cap) return FDFD_EINVAL;
+  unsigned* calib = nullptr;
+  if (cudaMalloc((void**)&calib, 5 * 32 * sizeof(unsigned)) != cudaSuccess) return FDFD_ENOMEM;
+  int rc = FDFD_OK;
+  std::vector<unsigned> mx(5 * 32, 0u);
+  if (cudaMemsetAsync(calib, 0, 5 * 32 * sizeof(unsigned), s) != cudaSuccess) rc = FDFD_ECUDA;
+  NnoOutput out;  // outputs are not needed: a scratch per-window array
+  float2* scratch = nullptr;
+  if (!rc && cudaMalloc((void**)&scratch, (size_t)n * NPIX * sizeof(float2)) != cudaSuccess) rc = FDFD_ENOMEM;
+  out.e_win = scratch;
+  if (!rc) rc = nno_forward(W, work, g, in, out, n, s, nullptr, calib);
+  if (!rc && (cudaMemcpyAsync(mx.data(), calib, mx.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess))
+    rc = FDFD_ECUDA;
+  cudaFree(calib);
+  if (scratch) cudaFree(scratch);
+  if (rc) return rc;
+  // power-of-two scales with 4x headroom below the E4M3 maximum (448)
+  float sc[5][32], qi[5][32];
+  for (int b = 0; b < 5; ++b)
+    for (int c = 0; c < 32; ++c) {
+      float m;
+      memcpy(&m, &mx[b * 32 + c], sizeof(float));
+      const float want = (m > 0.f && isfinite(m)) ? 4.f * m / 448.f : 1.f;
+      sc[b][c] = ldexpf(1.f, (int)ceilf(log2f(want)));
+      qi[b][c] = 1.f / sc[b][c];
+    }
+  const size_t blk = 2 * 32 * 32 * 512 + 32 * 32 + 32;
+  const size_t expect = 32 * 15 + 32 + 4 * blk + 128 * 32 + 128 + 2 * 128 + 2;
+  if (!blob || nfloats != expect) return FDFD_EINVAL;
+  for (int b = 0; b < 4; ++b) {  // W[b] diag(s[b]): block b reads the activation with scale s[b]
+    const float* w = blob + 32 * 15 + 32 + b * blk + 2 * 32 * 32 * 512;
+    std::vector<float> ws(32 * 32);
+    for (int o = 0; o < 32; ++o)
+      for (int c = 0; c < 32; ++c) ws[o * 32 + c] = w[o * 32 + c] * sc[b][c];
+    if ((rc = up(&W->W8[b], to_bf16(ws), bytes))) return rc;
+  }
+  {
+    const float* p1 = blob + 32 * 15 + 32 + 4 * blk;
+    std::vector<float> ps(128 * 32);
+    for (int hh = 0; hh < 128; ++hh)
+      for (int c = 0; c < 32; ++c) ps[hh * 32 + c] = p1[hh * 32 + c] * sc[4][c];
+    if ((rc = up(&W->P18, to_bf16(ps), bytes))) return rc;
+  }
+  if ((rc = up(&W->qinv, std::vector<float>(&qi[0][0], &qi[0][0] + 5 * 32), bytes))) return rc;
+  W->fp8 = true;
   return FDFD_OK;
 }
 

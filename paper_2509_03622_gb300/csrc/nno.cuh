@@ -18,6 +18,14 @@ struct NnoWeights {
   float* p1b = nullptr;     // [128]
   float* P2 = nullptr;      // [2][128]
   float p2b[2] = {0.f, 0.f};
+  // FP8 activations (precision pattern): the activation entering block b
+  // (b = 0..3) and the projection (b = 4) is stored as E4M3 q with
+  // x = q * s[b][c] (power-of-two per-channel scales from a calibration pass);
+  // the scales are folded into the weights that read it.
+  bool fp8 = false;
+  float* qinv = nullptr;    // [5][32]  1 / s[b][c], used by the writers
+  bf16* W8[4] = {};         // [32 o][32 c]  W[b] diag(s[b])
+  bf16* P18 = nullptr;      // [128][32]     P1 diag(s[4])
 };
 
 struct NnoWork {
@@ -80,7 +88,14 @@ struct fdfd_ctx;
 // Run the neural operator on n windows (n <= work->cap); h (nullable) only
 // receives the per-stage profiling scopes.
 int nno_forward(const NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInput& in,
-                const NnoOutput& out, int n, cudaStream_t s, fdfd_ctx* h = nullptr);
+                const NnoOutput& out, int n, cudaStream_t s, fdfd_ctx* h = nullptr,
+                unsigned* calib = nullptr);
+// Switch W to FP8 activations: calibrate the per-channel scales on a BF16
+// forward of `n` windows of `in` (max |x| per channel at the five activation
+// points, with 4x headroom, rounded up to a power of two) and upload the
+// scale-folded weights.  `blob` is the weight blob W was made from.
+int nno_enable_fp8(NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInput& in, int n,
+                   const float* blob, size_t nfloats, size_t* bytes, cudaStream_t s);
 // Direct access to the tcgen05 GEMM for self-tests: C[M][N] (fp32) =
 // A[M][K] . B[N][K]^T with A K-major (a_mn = 0, row stride K) or MN-major
 // (a_mn = 1, stored [K][M]); supported (N, K): (32,80) (64,160) (64,64)

@@ -61,6 +61,19 @@ static GridGeom geom(fdfd_ctx* h) {
   return GridGeom{h->nx, h->ny, h->nx / FDFD_CORE, (float)h->k2, h->eps, h->isx, h->isy};
 }
 
+// Seeded uniform complex field in [-1, 1)^2 (counter-based splitmix64), the
+// residual-like input of the FP8 calibration forward.
+__global__ void fill_uniform_kernel(float2* v, size_t n, unsigned long long seed) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const float a = (float)(uint32_t)(z >> 32) * (1.f / 4294967296.f), b = (float)(uint32_t)z * (1.f / 4294967296.f);
+    v[i] = make_float2(2.f * a - 1.f, 2.f * b - 1.f);
+  }
+}
+
 static int check_err(fdfd_ctx* h) {
   int e = 0;
   CK(cudaMemcpyAsync(&e, h->sw->work.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -70,7 +83,7 @@ static int check_err(fdfd_ctx* h) {
 
 int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd) {
   if (sd->k_coarse < 0 || sd->k_coarse > 256) return FDFD_EINVAL;
-  if (sd->precision != FDFD_PREC_BF16) return FDFD_EINVAL;  // the FP8 operator is not built
+  if (sd->precision != FDFD_PREC_BF16 && sd->precision != FDFD_PREC_FP8) return FDFD_EINVAL;
   if (sd->inner_iters < 0 || sd->inner_iters > LOCAL_MAXM) return FDFD_EINVAL;
   SchwarzData* S = new SchwarzData();
   S->nwx = h->nx / FDFD_CORE;
@@ -79,6 +92,12 @@ int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd) {
   S->inner = sd->inner_iters;
   int rc = nno_upload_weights(&S->W, sd->weights, sd->n_weights, &S->bytes);
   if (!rc) rc = nno_alloc_work(&S->work, S->n_win < 64 ? 64 : S->n_win, &S->bytes);
+  if (!rc && sd->precision == FDFD_PREC_FP8) {  // calibrate the activation scales on a random residual
+    fill_uniform_kernel<<<1024, 256, 0, h->stream>>>(h->w, h->n, 0x5EEDull);
+    NnoInput in;
+    in.v_global = h->w;
+    rc = nno_enable_fp8(&S->W, &S->work, geom(h), in, S->n_win, sd->weights, sd->n_weights, &S->bytes, h->stream);
+  }
   if (!rc && S->inner > 0) rc = local_alloc(&S->local, S->n_win, S->inner, &S->bytes);
   h->sw = S;
   if (!rc && sd->k_coarse > 0) {
