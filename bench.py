@@ -331,6 +331,7 @@ def main():
                     "d2h_bytes_per_step": N * 8 // args.steps},
             "clocks": clk.summary(), "relres_after_steps": st["relres_true"],
             "class_ms_per_step": {c: v / max(steps, 1) for c, v in cls_ms.items() if v > 0},
+            "autotuned": {k: v for k, v in S.info().items() if k.startswith("tuned_")},
             "graphs": {"ms_per_step": ms_graph / max(steps, 1),
                        "note": "same solve with each Arnoldi step replayed as a CUDA graph, unprofiled"}}
     if rank == 0 and not args.no_cpu:

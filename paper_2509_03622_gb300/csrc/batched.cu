@@ -59,7 +59,10 @@ extern "C" int fdfd_batch_create(fdfd_handle* hs, int n, int max_windows, fdfd_b
   b->hs.assign(hs, hs + n);
   b->cap = max_windows > 0 ? (max_windows < total ? max_windows : total) : (total < 8192 ? total : 8192);
   int rc = FDFD_OK;
-  if (schwarz_weights(hs[0])) rc = nno_alloc_work(&b->work, b->cap, &b->bytes);
+  if (schwarz_weights(hs[0])) {
+    rc = nno_alloc_work(&b->work, b->cap, &b->bytes);
+    if (!rc) rc = nno_autotune(schwarz_weights(hs[0]), &b->work, b->cap, hs[0]->stream);
+  }
   if (!rc) {
     if (cudaMalloc((void**)&b->wtab_d, (size_t)total * sizeof(int2)) != cudaSuccess ||
         cudaMalloc((void**)&b->ptab_d, (size_t)n * sizeof(ProbGeom)) != cudaSuccess ||

@@ -321,20 +321,22 @@ struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
 // D_m[w][(o,ri)] = Xh_m[w][(c,ri')] R'_m[(o,ri)][(c,ri')]^T for the 4 modes
 // m = (q0..q0+3, kx), accumulators side by side in TMEM (4 x 64 columns), so
 // the epilogue writes 16 contiguous bytes (4 q x re/im) per (window, o).
-// One CTA per unit, two resident per SM (shared memory and TMEM), CTAs in
-// the order (window tile, q-group, kx): a warp-specialised persistent form
-// of this kernel measured slower on GB300, so this one stays.
-constexpr int G3_Q = 4;
+// One CTA per unit, several resident per SM (shared memory and TMEM), CTAs
+// in the order (window tile, q-group, kx): a warp-specialised persistent
+// form of this kernel measured slower on GB300, so this one stays.  The
+// number of modes per CTA (2 or 4) is chosen by nno_autotune.
 constexpr uint32_t G3_A = 128 * 64 * 2, G3_B = 64 * 64 * 2;
-constexpr uint32_t G3_SMEM = G3_Q * (G3_A + G3_B) + 16;
+template <int G3_Q>
+constexpr uint32_t g3_smem() { return G3_Q * (G3_A + G3_B) + 16; }
 
+template <int G3_Q>
 __global__ void __launch_bounds__(128) g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int cap, int nwin,
                                                  int wtiles, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;
   uint8_t* sB = smem + G3_Q * G3_A;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + G3_SMEM - 16);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G3_SMEM - 8);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + g3_smem<G3_Q>() - 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + g3_smem<G3_Q>() - 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int u = blockIdx.x;
   const int wt = u % wtiles, qg = (u / wtiles) % (32 / G3_Q), kx = u / (wtiles * (32 / G3_Q));
@@ -385,11 +387,16 @@ __global__ void __launch_bounds__(128) g3_kernel(const bf16* Xh, const bf16* R, 
       for (int oo = 0; oo < 8; ++oo) {
         const int o = oc * 8 + oo;
         uint4 q;
-        q.x = pack2(v[0][2 * oo], v[0][2 * oo + 1]);
-        q.y = pack2(v[1][2 * oo], v[1][2 * oo + 1]);
-        q.z = pack2(v[2][2 * oo], v[2][2 * oo + 1]);
-        q.w = pack2(v[3][2 * oo], v[3][2 * oo + 1]);
-        *reinterpret_cast<uint4*>(Yh + (((size_t)w * 512) + o * 16 + kx) * 64 + qg * G3_Q * 2) = q;
+        if constexpr (G3_Q == 4) {
+          q.x = pack2(v[0][2 * oo], v[0][2 * oo + 1]);
+          q.y = pack2(v[1][2 * oo], v[1][2 * oo + 1]);
+          q.z = pack2(v[2][2 * oo], v[2][2 * oo + 1]);
+          q.w = pack2(v[3][2 * oo], v[3][2 * oo + 1]);
+          *reinterpret_cast<uint4*>(Yh + (((size_t)w * 512) + o * 16 + kx) * 64 + qg * G3_Q * 2) = q;
+        } else {
+          *reinterpret_cast<uint2*>(Yh + (((size_t)w * 512) + o * 16 + kx) * 64 + qg * G3_Q * 2) =
+              make_uint2(pack2(v[0][2 * oo], v[0][2 * oo + 1]), pack2(v[1][2 * oo], v[1][2 * oo + 1]));
+        }
       }
     }
   }
@@ -1200,6 +1207,62 @@ __global__ void absmax_kernel(const bf16* X, size_t n_elem, unsigned* out) {
   if (threadIdx.x < 32) atomicMax(&out[threadIdx.x], m[threadIdx.x]);
 }
 
+int launch_g3(NnoWork* k, const bf16* R, int n, int modes, cudaStream_t s) {
+  static bool init = false;
+  if (!init) {
+    CK(cudaFuncSetAttribute(g3_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g3_smem<2>()));
+    CK(cudaFuncSetAttribute(g3_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g3_smem<4>()));
+    init = true;
+  }
+  const int wtiles = (n + 127) / 128;
+  if (modes == 2)
+    g3_kernel<2><<<wtiles * 16 * 16, 128, g3_smem<2>(), s>>>(k->Xh, R, k->Yh, k->cap, n, wtiles, k->err);
+  else
+    g3_kernel<4><<<wtiles * 8 * 16, 128, g3_smem<4>(), s>>>(k->Xh, R, k->Yh, k->cap, n, wtiles, k->err);
+  CKL();
+  return FDFD_OK;
+}
+
+int launch_g2(NnoWork* k, const NnoWeights* W, int n, int split, cudaStream_t s) {
+  if (split == 2) return launch_gemm<64, 160, true, G2Op, 2>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s);
+  return launch_gemm<64, 160, true, G2Op, 1>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s);
+}
+
+int nno_autotune(const NnoWeights* W, NnoWork* k, int n, cudaStream_t s) {
+  if (n <= 0 || n > k->cap) return FDFD_EINVAL;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  // inputs of the timed stages: zeroed half-spectra (timing only)
+  CK(cudaMemsetAsync(k->T1, 0, (size_t)n * 160 * 512 * 2, s));
+  CK(cudaMemsetAsync(k->Xh, 0, (size_t)512 * k->cap * 64 * 2, s));
+  auto best_of = [&](auto&& run, const int* opts, int nopt) -> int {
+    int best = opts[0];
+    float best_ms = 1e30f;
+    for (int i = 0; i < nopt; ++i) {
+      if (run(opts[i])) return -1;  // warm-up (and the first-use set-up)
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3; ++r)
+        if (run(opts[i])) return -1;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return -1;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; best = opts[i]; }
+    }
+    return best;
+  };
+  const int g3opts[2] = {4, 2}, g2opts[2] = {2, 1};
+  const int g3 = best_of([&](int m) { return launch_g3(k, W->R[0], n, m, s); }, g3opts, 2);
+  const int g2 = best_of([&](int sp) { return launch_g2(k, W, n, sp, s); }, g2opts, 2);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (g3 < 0 || g2 < 0) return FDFD_ECUDA;
+  k->g3_modes = g3;
+  k->g2_split = g2;
+  return FDFD_OK;
+}
+
 int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInput& in, const NnoOutput& out,
                 int n, cudaStream_t s, fdfd_ctx* h, unsigned* calib) {
   if (n <= 0) return FDFD_OK;
@@ -1219,7 +1282,6 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
   }
   static int g5_cap = 0;
   if (!g5_cap) {
-    CK(cudaFuncSetAttribute(g3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G3_SMEM));
     CK(cudaFuncSetAttribute(g5_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
     CK(cudaFuncSetAttribute(g5_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
     CK(cudaFuncSetAttribute(g5_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
@@ -1243,14 +1305,11 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
   for (int bl = 0; bl < 4; ++bl) {
     {
       ProfScope ps(h, 10, 1);
-      if ((rc = launch_gemm<64, 160, true, G2Op, 2>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s)))
-        return rc;
+      if ((rc = launch_g2(k, W, n, k->g2_split, s))) return rc;
     }
     {
       ProfScope ps(h, 11, 1);
-      const int wtiles = (n + 127) / 128;
-      g3_kernel<<<wtiles * (32 / G3_Q) * 16, 128, G3_SMEM, s>>>(k->Xh, W->R[bl], k->Yh, k->cap, n, wtiles, k->err);
-      CKL();
+      if ((rc = launch_g3(k, W->R[bl], n, k->g3_modes, s))) return rc;
     }
     {
       ProfScope ps(h, 12, 1);

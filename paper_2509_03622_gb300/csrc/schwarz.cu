@@ -92,6 +92,7 @@ int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd) {
   S->inner = sd->inner_iters;
   int rc = nno_upload_weights(&S->W, sd->weights, sd->n_weights, &S->bytes);
   if (!rc) rc = nno_alloc_work(&S->work, S->n_win < 64 ? 64 : S->n_win, &S->bytes);
+  if (!rc) rc = nno_autotune(&S->W, &S->work, S->n_win, h->stream);
   if (!rc && sd->precision == FDFD_PREC_FP8) {  // calibrate the activation scales on a random residual
     fill_uniform_kernel<<<1024, 256, 0, h->stream>>>(h->w, h->n, 0x5EEDull);
     NnoInput in;
@@ -176,5 +177,7 @@ int schwarz_export(fdfd_ctx* h, double* Q, double* Nd) {
 int schwarz_info(fdfd_ctx* h, fdfd_info* info) {
   info->k_coarse = h->sw->k;
   info->n_coarse = h->sw->k * h->sw->n_win;
+  info->tuned_mix_modes = h->sw->work.g3_modes;
+  info->tuned_dfty_split = h->sw->work.g2_split;
   return FDFD_OK;
 }
