@@ -101,6 +101,13 @@ WIN_BYTES = {
     "nno_proj": 6400 * 64 + 4096 * 8,         # activation in, core field out
 }
 G5_T1_BYTES = 160 * 512 * 2                   # next block's half-spectrum, written by blocks 0..2
+# DRAM bytes (read + write) per window of one launch, from ncu captures of the
+# same kernels on freeform1536 (576 windows, above L2), scaled by the windows
+# of the benched launch; kernel -> (bytes per window, summary under profiles/).
+MEASURED_TRAFFIC = {
+    "nno_idft_x_mix_act": (601.5e6 / 576, "profiles/g5_kernel_freeform1536.md"),  # a block-0..2 launch
+    "nno_proj": (250.7e6 / 576, "profiles/proj_kernel_freeform1536.md"),
+}
 # Useful FLOPs per window of each stage (padding excluded).
 NNO_FLOP_PER_WIN = {
     "nno_lift": 6400 * 32 * 15 * 2 + 2560 * 32 * 80 * 2, "nno_dft_x": 2560 * 32 * 80 * 2, "nno_dft_y": 512 * 64 * 160 * 2,
@@ -156,10 +163,10 @@ def make_problem(n, seed_off=0):
     return eps, J, dx, lam
 
 
-def cpu_oracle_rate(n_sample, iters, precond, weights=None, k_coarse=0):
+def cpu_oracle_rate(n_sample, iters, precond, weights=None, k_coarse=0, inner=0, budget_s=None):
     """Mcell-it/s of the FP64 oracle FGMRES (as it stands) on an n_sample^2
-    grid of the same recipe, `iters` Arnoldi steps."""
-    import numpy as np
+    grid of the same recipe, `iters` Arnoldi steps (or, with budget_s, as
+    many as fit in about that many seconds after a 2-step probe)."""
     from oracle import fdfd as OF, krylov as OK
     eps, J, dx, lam = make_problem(n_sample)
     t0 = time.perf_counter()
@@ -170,33 +177,52 @@ def cpu_oracle_rate(n_sample, iters, precond, weights=None, k_coarse=0):
         M = lambda v: v / d
     else:
         from oracle import schwarz as OS
-        M = OS.Schwarz(eps, dx, lam, 20, weights=weights, k_coarse=k_coarse)
+        M = OS.Schwarz(eps, dx, lam, 20, weights=weights, k_coarse=k_coarse, inner=inner)
     t1 = time.perf_counter()
+    if budget_s:
+        OK.fgmres(lambda v: A @ v, b, precond=M, restart=30, tol=1e-14, max_iters=2)
+        per = (time.perf_counter() - t1) / 2
+        iters = int(max(2, min(60, budget_s / max(per, 1e-6))))
+        t1 = time.perf_counter()
     OK.fgmres(lambda v: A @ v, b, precond=M, restart=30, tol=1e-14, max_iters=iters)
     t2 = time.perf_counter()
-    return n_sample * n_sample * iters / (t2 - t1) / 1e6, t2 - t1, t1 - t0
+    return n_sample * n_sample * iters / (t2 - t1) / 1e6, t2 - t1, iters
+
+
+def workload_name(n, precond):
+    return (f"freeform{n}: {n}x{n} grid, lambda/dx=30, eps {{1,12.25}}, npml 20, "
+            f"{'Schwarz-NNO FGMRES(30)' if precond == 'schwarz' else 'Jacobi-GMRES(30)'}")
+
+
+def oracle_preconditioner(args):
+    """The oracle counterpart of the arm's preconditioner configuration."""
+    from paper_2509_03622_gb300 import workloads as wl
+    if args.precond != "schwarz":
+        return None, 0, 0
+    blob, _ = load_weights(args.weights)
+    kc = args.k_coarse if args.k_coarse >= 0 else (8 if args.n <= 1024 else 0)
+    return wl.unpack_weights(blob), kc, args.inner
 
 
 def run_reference(args):
-    import numpy as np
-    from paper_2509_03622_gb300 import workloads as wl
     n_s = args.cpu_sample
-    w = wl.nno_weights(0) if args.precond == "schwarz" else None
-    k = 4 if args.precond == "schwarz" else 0
+    w, k, inner = oracle_preconditioner(args)
     tot_t, tot_cells = 0.0, 0.0
     for _ in range(args.warmup):
         pass  # the oracle has no device state to warm
     for _ in range(args.steps):
-        rate, t, _ = cpu_oracle_rate(n_s, 1, args.precond, w, k)
+        rate, t, _ = cpu_oracle_rate(n_s, 1, args.precond, w, k, inner)
         tot_t += t
         tot_cells += n_s * n_s
     v = tot_cells / tot_t / 1e6
     cores = os.cpu_count()
-    sample = f"{n_s}x{n_s} grid of the same freeform recipe, 1 FGMRES step per bench step ({args.precond})"
+    sample = (f"{n_s}x{n_s} grid of the same freeform recipe and preconditioner configuration, "
+              f"1 FGMRES step per bench step ({args.precond})")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mcell-it/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"freeform{n_s} oracle sample", "grid": n_s},
+            "data": "synthetic", "config": {"workload": workload_name(args.n, args.precond), "grid": args.n,
+                                            "sample_grid": n_s},
             "cpu_baseline": {"value": v, "unit": "Mcell-it/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "Mcell-it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -206,7 +232,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precond", default="schwarz", choices=["schwarz", "jacobi"])
@@ -311,14 +337,22 @@ def main():
         if fl:
             r["tflops"] = fl * (N / 4096.0) * nl / (ms_c / 1e3) / 1e12
         roofs[cls] = r
+    for cls, (per_win, src_file) in MEASURED_TRAFFIC.items():
+        if cls in roofs and precond == F.PRECOND_SCHWARZ and prec_nno == "bf16":
+            nl = roofs[cls]["launches"]
+            tr = per_win * (N / 4096.0)
+            if cls == "nno_idft_x_mix_act":  # the last block writes no next-block spectrum
+                last = (WIN_BYTES[cls]) / (WIN_BYTES[cls] + G5_T1_BYTES)
+                tr *= ((nl - nl // 4) + (nl // 4) * last) / nl
+            roofs[cls]["traffic"] = tr
+            roofs[cls]["traffic_source"] = src_file + " (scaled by windows)"
     dom = max(roofs, key=lambda c: roofs[c]["ms"]) if roofs else None
     roof = dict(roofs[dom]) if dom else None
     line = {"metric": METRIC, "value": value, "unit": "Mcell-it/s", "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms / max(steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic (seeded freeform eps, point source)",
-            "config": {"workload": f"freeform{n}: {n}x{n} grid, lambda/dx=30, eps {{1,12.25}}, npml 20, "
-                                   f"{'Schwarz-NNO FGMRES(30)' if precond == F.PRECOND_SCHWARZ else 'Jacobi-GMRES(30)'}",
+            "config": {"workload": workload_name(n, args.precond),
                        "grid": n, "precond": args.precond, "k_coarse": kc if precond == F.PRECOND_SCHWARZ else None,
                        "inner_iters": args.inner if precond == F.PRECOND_SCHWARZ else None,
                        "weights": wsrc if precond == F.PRECOND_SCHWARZ else None,
@@ -335,12 +369,12 @@ def main():
             "graphs": {"ms_per_step": ms_graph / max(steps, 1),
                        "note": "same solve with each Arnoldi step replayed as a CUDA graph, unprofiled"}}
     if rank == 0 and not args.no_cpu:
-        w = wl.nno_weights(0) if precond == F.PRECOND_SCHWARZ else None
-        it = 3 if precond == F.PRECOND_SCHWARZ else 20
+        w, kc_o, inner_o = oracle_preconditioner(args)
         ns = args.cpu_sample if precond == F.PRECOND_SCHWARZ else 1024
-        rate, t, _ = cpu_oracle_rate(ns, it, args.precond, w, 4 if w is not None else 0)
+        rate, t, it = cpu_oracle_rate(ns, 0, args.precond, w, kc_o, inner_o, budget_s=10.0)
         line["cpu_baseline"] = {"value": rate, "unit": "Mcell-it/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"{ns}x{ns} grid, same recipe, {it} FGMRES steps ({args.precond}), {t:.1f} s"}
+                                "sample": f"{ns}x{ns} grid, same recipe and preconditioner configuration, "
+                                          f"{it} FGMRES steps ({args.precond}), {t:.1f} s"}
     if args.tts and rank == 0:
         E.zero_()
         rc, st2 = S.solve(Jd, E, restart=30, max_iters=3000, tol=1e-6, precond=precond)
