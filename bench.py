@@ -117,7 +117,7 @@ NNO_FLOP_PER_WIN = {
 KERNEL_NAMES = {"stencil": "stencil_c64", "cgs_dots": "cgs_dots_kernel", "cgs_update": "cgs_update_kernel",
                 "residual64": "residual64", "nno_pack": "pack_kernel", "nno_lift": "g5_kernel<lift> (lift + block-0 DFT-x)",
                 "nno_dft_x": "gemm_kernel<32,80,MN> (G1Op)", "nno_dft_y": "gemm_kernel<64,160,MN> (G2Op)",
-                "nno_mix": "g3_kernel", "nno_idft_y": "gemm_kernel<160,64> (G4Op)",
+                "nno_mix": "spectral mixing (autotuned: g3_kernel, or G3Op GEMM + mix_transpose_kernel)", "nno_idft_y": "gemm_kernel<160,64> (G4Op)",
                 "nno_idft_x_mix_act": "g5_kernel", "nno_proj": "proj_kernel", "rhs_norm": "residual64 (x = 0)"}
 
 

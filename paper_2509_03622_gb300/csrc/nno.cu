@@ -8,7 +8,8 @@
 //     G1  DFT along x   : rows (y,c)   K = x 80        N = (kx,ri) 32   A MN-major
 //         (inside the kernel that produced the block's input rows)
 //     G2  DFT along y   : rows (kx,c)  K = (ri,y) 160  N = (q,ri) 64    A MN-major
-//     G3  spectral mix  : 4 modes per CTA, rows = windows, K = (c,ri) 64, N = (o,ri) 64
+//     G3  spectral mix  : rows = windows, K = (c,ri) 64, N = (o,ri) 64, 4 or 2 modes per CTA
+//         writing window-major, or one mode per tile + a transpose (autotuned)
 //     G4  inverse DFT y : rows (o,kx)  K = (q,ri) 64   N = (y,ri) 160
 //     G5  fused: inverse real DFT along x + W x + bias + leaky-ReLU, per y row:
 //         D_y[x][o] = Gx[x][:] . T3_y[o][:] + X_y[x][:] . W[o][:]
@@ -295,6 +296,26 @@ struct G2Op {  // DFT along y: rows (kx,c), K = (ri,y) (A MN-major from T1), N =
   __device__ void epi_end(int, int, State&) const {}
 };
 
+
+struct G3Op {  // spectral mixing, one mode per tile: rows = windows, K = (c,ri) 64, N = (o,ri) 64
+  static constexpr bool kConstB = false;
+  const bf16* Xh; const bf16* R; bf16* Ym; int cap, nwin;
+  typedef NoState State;
+  __device__ int rows(int) const { return nwin; }
+  __device__ const uint4* a_src(int md, int w, int k) const {
+    return reinterpret_cast<const uint4*>(Xh + ((size_t)md * cap + w) * 64 + k);
+  }
+  __device__ const uint4* b_src(int md, int n, int k) const {
+    return reinterpret_cast<const uint4*>(R + ((size_t)md * 64 + n) * 64 + k);
+  }
+  __device__ void epi_begin(State&) const {}
+  __device__ void epi(int md, int w, int c0, const float* v, State&) const {  // 32 contiguous bytes per thread
+    uint4* dst = reinterpret_cast<uint4*>(Ym + ((size_t)md * cap + w) * 64 + c0);
+    dst[0] = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+    dst[1] = make_uint4(pack2(v[8], v[9]), pack2(v[10], v[11]), pack2(v[12], v[13]), pack2(v[14], v[15]));
+  }
+  __device__ void epi_end(int, int, State&) const {}
+};
 
 struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
   static constexpr bool kConstB = true;
@@ -1207,15 +1228,59 @@ __global__ void absmax_kernel(const bf16* X, size_t n_elem, unsigned* out) {
   if (threadIdx.x < 32) atomicMax(&out[threadIdx.x], m[threadIdx.x]);
 }
 
-int launch_g3(NnoWork* k, const bf16* R, int n, int modes, cudaStream_t s) {
+// Mode-major mixed spectrum Ym[mode][w][(o,ri)] -> window-major
+// Yw[w][(o,kx)][(q,ri)], mode = q*16 + kx.  Per window (blocks stride over
+// windows): its 512 mode rows (128 B, read whole by 8 threads each) into
+// shared memory with rows padded to 136 B (34 words, so the reads below hit
+// distinct banks), then every thread assembles whole 128-byte output rows.
+constexpr int TP_THREADS = 256;
+constexpr int TP_ROW = 136;
+constexpr int TP_SMEM = 512 * TP_ROW;
+__global__ void __launch_bounds__(TP_THREADS) mix_transpose_kernel(const bf16* Ym, bf16* Yw, int cap, int nwin) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  for (int w = blockIdx.x; w < nwin; w += gridDim.x) {
+    for (int c = threadIdx.x; c < 512 * 8; c += TP_THREADS) {
+      const int m = c >> 3, part = c & 7;
+      const uint4 q = *reinterpret_cast<const uint4*>(Ym + ((size_t)m * cap + w) * 64 + part * 8);
+      uint32_t* d = reinterpret_cast<uint32_t*>(sm + m * TP_ROW + part * 16);
+      d[0] = q.x; d[1] = q.y; d[2] = q.z; d[3] = q.w;
+    }
+    __syncthreads();
+    for (int row = threadIdx.x; row < 512; row += TP_THREADS) {  // row = (o, kx), kx fastest
+      const int o = row >> 4, kx = row & 15;
+      uint4* dst = reinterpret_cast<uint4*>(Yw + ((size_t)w * 512 + row) * 64);
+#pragma unroll
+      for (int qg = 0; qg < 8; ++qg) {
+        uint32_t v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)  // (re, im) of mode (q, kx), output channel o
+          v[t] = *reinterpret_cast<const uint32_t*>(sm + ((qg * 4 + t) * 16 + kx) * TP_ROW + o * 4);
+        dst[qg] = make_uint4(v[0], v[1], v[2], v[3]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Spectral mixing into the window-major layout G4 reads; returns where it is.
+// modes = 4 or 2: modes per CTA of g3_kernel, writing it directly; modes = 1:
+// one mode per tile in the generic pipeline (contiguous mode-major rows),
+// then the transpose into the Xh buffer, which the mixing no longer needs.
+int launch_g3(NnoWork* k, const bf16* R, int n, int modes, cudaStream_t s, const bf16** yw = nullptr) {
   static bool init = false;
   if (!init) {
     CK(cudaFuncSetAttribute(g3_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g3_smem<2>()));
     CK(cudaFuncSetAttribute(g3_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g3_smem<4>()));
+    CK(cudaFuncSetAttribute(mix_transpose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM));
     init = true;
   }
   const int wtiles = (n + 127) / 128;
-  if (modes == 2)
+  if (yw) *yw = modes == 1 ? k->Xh : k->Yh;
+  if (modes == 1) {
+    int rc = launch_gemm<64, 64, false, G3Op>(G3Op{k->Xh, R, k->Yh, k->cap, n}, wtiles, 512, k->err, s);
+    if (rc) return rc;
+    mix_transpose_kernel<<<n < 456 ? n : 456, TP_THREADS, TP_SMEM, s>>>(k->Yh, k->Xh, k->cap, n);
+  } else if (modes == 2)
     g3_kernel<2><<<wtiles * 16 * 16, 128, g3_smem<2>(), s>>>(k->Xh, R, k->Yh, k->cap, n, wtiles, k->err);
   else
     g3_kernel<4><<<wtiles * 8 * 16, 128, g3_smem<4>(), s>>>(k->Xh, R, k->Yh, k->cap, n, wtiles, k->err);
@@ -1252,8 +1317,8 @@ int nno_autotune(const NnoWeights* W, NnoWork* k, int n, cudaStream_t s) {
     }
     return best;
   };
-  const int g3opts[2] = {4, 2}, g2opts[2] = {2, 1};
-  const int g3 = best_of([&](int m) { return launch_g3(k, W->R[0], n, m, s); }, g3opts, 2);
+  const int g3opts[3] = {4, 2, 1}, g2opts[2] = {2, 1};
+  const int g3 = best_of([&](int m) { return launch_g3(k, W->R[0], n, m, s); }, g3opts, 3);
   const int g2 = best_of([&](int sp) { return launch_g2(k, W, n, sp, s); }, g2opts, 2);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1302,18 +1367,19 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     CKL();
   }
   if ((rc = record(0))) return rc;
+  const bf16* yw = k->Yh;  // window-major mixed spectrum (where launch_g3 put it)
   for (int bl = 0; bl < 4; ++bl) {
     {
       ProfScope ps(h, 10, 1);
       if ((rc = launch_g2(k, W, n, k->g2_split, s))) return rc;
     }
     {
-      ProfScope ps(h, 11, 1);
-      if ((rc = launch_g3(k, W->R[bl], n, k->g3_modes, s))) return rc;
+      ProfScope ps(h, 11, k->g3_modes == 1 ? 2 : 1);
+      if ((rc = launch_g3(k, W->R[bl], n, k->g3_modes, s, &yw))) return rc;
     }
     {
       ProfScope ps(h, 12, 1);
-      if ((rc = launch_gemm<160, 64, false>(G4Op{k->Yh, W->Gy, k->T3}, 512 / 128, n, k->err, s))) return rc;
+      if ((rc = launch_gemm<160, 64, false>(G4Op{yw, W->Gy, k->T3}, 512 / 128, n, k->err, s))) return rc;
     }
     {
       ProfScope ps(h, 13, 1);

@@ -38,7 +38,8 @@ struct NnoWork {
   bf16* T3 = nullptr;       // [cap][80 y][o/8][k/8][o%8][k%8]  k = (kx,ri), tiled
   float* rho = nullptr;     // [cap]
   int* err = nullptr;       // bounded-wait failure flag
-  int g3_modes = 4;         // modes per spectral-mixing CTA (2 or 4), set by nno_autotune
+  int g3_modes = 4;         // spectral mixing: modes per CTA (4 or 2), or 1 = one mode per
+                            // tile + transpose through the Xh buffer; set by nno_autotune
   int g2_split = 2;         // K split of the DFT-y GEMM (1 or 2), set by nno_autotune
 };
 
