@@ -154,6 +154,22 @@ def load_weights(path=None):
     return wl.pack_weights(wl.nno_weights(0)), "seeded init (seed 0)"
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The job's time is its slowest rank's: MAX all-reduce of a per-rank float."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, cells: int, steps: int, seconds: float) -> float:
+    """Whole-job Mcell-iterations/s: every rank solves its own replica of `cells`."""
+    return world * cells * steps / seconds / 1e6
+
+
 def make_problem(n, seed_off=0):
     from paper_2509_03622_gb300 import workloads as wl
     lam = 1.55e-6
@@ -293,14 +309,11 @@ def main():
         ev1.record(S.stream)
         prof = S.profile_stop()
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     steps = st["iters"]
-    value = world * n * n * steps / (ms / 1e3) / 1e6
+    value = job_rate(world, n * n, steps, ms / 1e3)
     # the same steps replayed as CUDA graphs (profiling off), for comparison
     S.use_graphs = True
     S.solve(Jd, E, restart=30, max_iters=min(args.steps, 30), tol=1e-30, precond=precond)  # capture
@@ -316,8 +329,8 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     S.solve_host(Jh, Eh, restart=30, max_iters=args.steps, tol=1e-30, precond=precond)
-    t_e2e = time.perf_counter() - t0
-    e2e_value = world * n * n * args.steps / t_e2e / 1e6
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_value = job_rate(world, n * n, args.steps, t_e2e)
     hbm, bf16, bf16s, src = peaks()
     # rooflines per kernel class (algorithmic bytes of the timed region)
     cls_ms = prof["ms"]
