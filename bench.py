@@ -91,8 +91,8 @@ class Clocks:
 # operator stage: what it must read and write once (bf16 activations of 32
 # channels = 64 B per pixel, complex64 fields = 8 B per cell).
 WIN_BYTES = {
-    "nno_pack": 6400 * (8 + 4 + 32),          # residual + eps in, 16 bf16 channels out
-    "nno_lift": 6400 * (32 + 64) + 160 * 512 * 2,   # inputs in, activation and block 0's T1 out
+    "nno_pack": 6400 * 8,                     # residual in (window RMS)
+    "nno_lift": 6400 * (8 + 4 + 64) + 160 * 512 * 2,  # residual + eps in, activation and block 0's T1 out
     "nno_dft_x": 6400 * 64 + 160 * 512 * 2,   # activation in, half-spectrum along x out
     "nno_dft_y": 160 * 512 * 2 + 512 * 64 * 2,
     "nno_mix": 512 * 64 * 2 * 2,              # spectrum in and out (weights amortised)
@@ -115,7 +115,8 @@ NNO_FLOP_PER_WIN = {
     "nno_proj": 6400 * (128 * 32 + 2 * 128) * 2,
 }
 KERNEL_NAMES = {"stencil": "stencil_c64", "cgs_dots": "cgs_dots_kernel", "cgs_update": "cgs_update_kernel",
-                "residual64": "residual64", "nno_pack": "pack_kernel", "nno_lift": "g5_kernel<lift> (lift + block-0 DFT-x)",
+                "residual64": "residual64", "nno_pack": "rho_kernel (window RMS)",
+                "nno_lift": "g5_kernel<lift> (input channels + lift + block-0 DFT-x)",
                 "nno_dft_x": "gemm_kernel<32,80,MN> (G1Op)", "nno_dft_y": "gemm_kernel<64,160,MN> (G2Op)",
                 "nno_mix": "spectral mixing (autotuned: g3_kernel, or G3Op GEMM + mix_transpose_kernel)", "nno_idft_y": "gemm_kernel<160,64> (G4Op)",
                 "nno_idft_x_mix_act": "g5_kernel", "nno_proj": "proj_kernel", "rhs_norm": "residual64 (x = 0)"}

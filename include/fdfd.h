@@ -183,7 +183,7 @@ typedef struct fdfd_batch_ctx* fdfd_batch;
 /* Group n handles (any grid sizes, wavelengths, permittivities; all on the
  * same stream) for lock-step solves.  max_windows caps the windows of one
  * neural-operator pass (0 = min(total windows, 8192)); the batch allocates
- * that workspace here (about 2.3 MB per window).  The handles must outlive
+ * that workspace here (about 0.9 MB per window).  The handles must outlive
  * the batch.  FDFD_EINVAL if streams differ. */
 int  fdfd_batch_create(fdfd_handle* hs, int n, int max_windows, fdfd_batch* out);
 
@@ -259,7 +259,7 @@ int  fdfd_nno_solve(fdfd_handle h, const fdfd_c64* r_win, const fdfd_c64* g_win,
  * it manages itself, or a latency-bound loop that cannot pay for an
  * allocation's implicit device-wide synchronisation.  Same arguments and
  * results as fdfd_nno_solve, but the neural operator's intermediates live in
- * one fixed device array inside the library (about 4.3 MB, held by every
+ * one fixed device array inside the library (about 3.5 MB, held by every
  * GPU that loads the library until the process exits) instead of the
  * handle's workspace, and the call allocates nothing.
  *   - n must be <= 4 windows; larger n returns FDFD_EINVAL (with a message on

@@ -2,8 +2,10 @@
 // tcgen05 tensor cores, batched over windows.
 //
 // Per window (80 x 80, width 32, 4 Fourier blocks, 512 retained modes):
-//   pack   : restriction, RMS normalisation, 15 input channels   (SIMT)
-//   lift   : [6400 px][16] x [32][16]^T, then block 0's G1, in the G5 pipeline
+//   rho    : window RMS (residual and Robin data)                 (SIMT)
+//   lift   : restriction + the 15 input channels over rho, built in shared
+//            memory by the kernel's own warps, [6400 px][16] x [32][16]^T,
+//            then block 0's G1, in the G5 pipeline
 //   block b (the truncated 2D DFT is done as two 1D DFT GEMMs each way):
 //     G1  DFT along x   : rows (y,c)   K = x 80        N = (kx,ri) 32   A MN-major
 //         (inside the kernel that produced the block's input rows)
@@ -487,11 +489,74 @@ __device__ __forceinline__ uint32_t to_e4m3x2(float a, float b) {
   return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
 }
 
+// Where a batch entry's window and its inputs are (restriction, Sec. 2.1 inputs).
+struct WinSrc {
+  int x0, y0, nx;
+  float k2;
+  const float* eps;
+  const float2* isx;
+  const float2* isy;
+  const float2* v;   // global field (restricted), or
+  const float2* r;   // this entry's [80][80] residual, or neither (zero)
+  const float2* g;   // this entry's Robin data [4][80] or nullptr
+};
+__device__ __forceinline__ WinSrc win_src(const NnoInput& in, GridGeom g, int b) {
+  int w = in.win_id ? in.win_id[b] : b;
+  const float2* v = in.v_global;
+  if (in.ptab) {  // multi-problem batch: this entry's problem supplies geometry and input
+    const int2 e = in.wtab[b];
+    const ProbGeom P = in.ptab[e.x];
+    w = e.y;
+    g.nx = P.nx; g.ny = P.ny; g.nwx = P.nwx; g.k2 = P.k2; g.eps = P.eps; g.isx = P.isx; g.isy = P.isy;
+    v = P.v;
+  }
+  WinSrc ws;
+  const int a = w % g.nwx, bb = w / g.nwx;
+  ws.x0 = min(max(FDFD_CORE * a - FDFD_OVL, 0), g.nx - FDFD_WIN);
+  ws.y0 = min(max(FDFD_CORE * bb - FDFD_OVL, 0), g.ny - FDFD_WIN);
+  ws.nx = g.nx; ws.k2 = g.k2; ws.eps = g.eps; ws.isx = g.isx; ws.isy = g.isy;
+  ws.v = v;
+  ws.r = (!v && in.r_win) ? in.r_win + (size_t)b * NPIX : nullptr;
+  ws.g = in.g_win ? in.g_win + (size_t)b * 320 : nullptr;
+  return ws;
+}
+__device__ __forceinline__ float2 win_residual(const WinSrc& ws, int y, int x) {
+  if (ws.v) return ws.v[(size_t)(ws.y0 + y) * ws.nx + ws.x0 + x];
+  if (ws.r) return ws.r[y * 80 + x];
+  return make_float2(0.f, 0.f);
+}
+// The 15 input channels of pixel (y, x), as BF16 pairs: (k0 dx)^2 eps, the
+// residual and the four Robin sides over rho (broadcast along their normals),
+// 1/s_x, 1/s_y.
+__device__ __forceinline__ void win_channels(const WinSrc& ws, int y, int x, float inv, uint4& lo, uint4& hi) {
+  const int gx = ws.x0 + x, gy = ws.y0 + y;
+  const float2 r = win_residual(ws, y, x);
+  float c[16];
+  c[0] = ws.k2 * ws.eps[(size_t)gy * ws.nx + gx];
+  c[1] = r.x * inv; c[2] = r.y * inv;
+  if (ws.g) {
+    const float2 gl = ws.g[0 * 80 + y], gr = ws.g[1 * 80 + y], gb = ws.g[2 * 80 + x], gt = ws.g[3 * 80 + x];
+    c[3] = gl.x * inv; c[4] = gl.y * inv; c[5] = gr.x * inv; c[6] = gr.y * inv;
+    c[7] = gb.x * inv; c[8] = gb.y * inv; c[9] = gt.x * inv; c[10] = gt.y * inv;
+  } else {
+#pragma unroll
+    for (int i = 3; i <= 10; ++i) c[i] = 0.f;
+  }
+  const float2 sx = ws.isx[gx], sy = ws.isy[gy];
+  c[11] = sx.x; c[12] = sx.y; c[13] = sy.x; c[14] = sy.y; c[15] = 0.f;
+  lo = make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), pack2(c[6], c[7]));
+  hi = make_uint4(pack2(c[8], c[9]), pack2(c[10], c[11]), pack2(c[12], c[13]), pack2(c[14], c[15]));
+}
+
+struct LiftSrc { NnoInput in; GridGeom g; const float* rho; };
+
 template <bool LIFT, bool FP8>
 __global__ void __launch_bounds__(G5_THREADS, 1)
 g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* bias, const bf16* Fx, bf16* T1,
-          const float* qinv, int last, int total, int* err) {
-  // LIFT: T3 is the tiled packed input and Wb the lift weights [32][16]; the
+          const float* qinv, int last, int total, int* err, LiftSrc lsrc) {
+  // LIFT: warps 0, 2, 3 build each unit's 4 rows of the 16 input channels
+  // (restriction, RMS normalisation by the window's rho) directly in the
+  // stage as the lift's K-major A tile; Wb is the lift weights [32][16]; the
   // unit's MMA is the lift (K = 16), no activation, then block 0's DFT along x.
   // FP8: X holds E4M3 activations (x8_off layout).  The unit's input rows
   // are bulk-copied as FP8 and converted to BF16 by warps 2-3 (the scale is
@@ -548,17 +613,47 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   const uint32_t tmem = *tslot;
   auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
 
-  if (warp == 0) {
+  if (LIFT && (warp == 0 || warp == 2 || warp == 3)) {  // ---------------- input builders ----------------
+    // Builder bw (0..2) fills the stages of units it = bw, bw + 3, ...: three
+    // units are built at once, each warp issuing all loads of a half unit
+    // before its shared-memory stores.
+    const int bw = warp == 0 ? 0 : warp - 1;
+    for (int u = blockIdx.x + bw * gridDim.x, it = bw; u < total && !*abort_flag; u += 3 * gridDim.x, it += 3) {
+      const int s = it % G5_STAGES;
+      if (it >= G5_STAGES && !tc::mbar_wait(empty(s), ((it / G5_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+      const int b = u / UPW, y0r = (u % UPW) * G5_ROWS;
+      const WinSrc ws = win_src(lsrc.in, lsrc.g, b);
+      const float rho = lsrc.rho[b];
+      const float inv = rho > 0.f ? 1.f / rho : 0.f;
+      uint8_t* st = smem + s * G5_STAGE;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint4 lo[5], hi[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          const int p = lane + 32 * (5 * h + j);  // 320 pixels = 4 rows x 80
+          win_channels(ws, y0r + p / 80, p % 80, inv, lo[j], hi[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          const int p = lane + 32 * (5 * h + j), yy = p / 80, x = p % 80;
+          uint8_t* d = st + yy * 2560 + (x >> 3) * 256 + (x & 7) * 16;  // tiled [x/8][k/8][x%8][k%8]
+          *reinterpret_cast<uint4*>(d) = lo[j];
+          *reinterpret_cast<uint4*>(d + 128) = hi[j];
+        }
+      }
+      tc::fence_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(full(s));
+    }
+  } else if (warp == 0) {
     if (lane == 0) {  // ---------------- producer ----------------
       int it = 0;
       for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
         const int s = it % G5_STAGES;
         if (it >= G5_STAGES && !tc::mbar_wait(empty(s), ((it / G5_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
         const size_t wy = (size_t)(u / UPW) * 80 + (u % UPW) * G5_ROWS;
-        if (LIFT) {  // 4 rows of packed inputs
-          tc::mbar_arrive_tx(full(s), G5_ROWS * 2560);
-          tc::bulk_g2s(sbase + s * G5_STAGE, T3 + wy * 1280, G5_ROWS * 2560, full(s));
-        } else if (FP8) {  // FP8 rows into the staging area, the inverse-y spectrum as usual
+        if (FP8) {  // FP8 rows into the staging area, the inverse-y spectrum as usual
           tc::mbar_arrive_tx(full(s), G5_X8B + G5_TB);
           tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB + G5_TB, reinterpret_cast<const uint8_t*>(X) + wy * 2560, G5_X8B,
                        full(s));
@@ -1006,61 +1101,21 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int tot
   }
 }
 
-__global__ void __launch_bounds__(256) pack_kernel(NnoInput in, GridGeom g, bf16* out, float* rho_out) {
+// Window RMS rho (residual and Robin data together, over the 6400 pixels):
+// the inputs are divided by it and the network's output multiplied by it.
+__global__ void __launch_bounds__(256) rho_kernel(NnoInput in, GridGeom g, float* rho_out) {
   __shared__ double sh[8];
-  __shared__ float s_inv;
   const int b = blockIdx.x;
-  int w = in.win_id ? in.win_id[b] : b;
-  if (in.ptab) {  // multi-problem batch: this entry's problem supplies geometry and input
-    const int2 e = in.wtab[b];
-    const ProbGeom P = in.ptab[e.x];
-    w = e.y;
-    g.nx = P.nx; g.ny = P.ny; g.nwx = P.nwx; g.k2 = P.k2; g.eps = P.eps; g.isx = P.isx; g.isy = P.isy;
-    in.v_global = P.v;
-  }
-  const int a = w % g.nwx, bb = w / g.nwx;
-  const int x0 = min(max(FDFD_CORE * a - FDFD_OVL, 0), g.nx - FDFD_WIN);
-  const int y0 = min(max(FDFD_CORE * bb - FDFD_OVL, 0), g.ny - FDFD_WIN);
-  auto r_at = [&](int p) -> float2 {
-    if (in.v_global) return in.v_global[(size_t)(y0 + p / 80) * g.nx + x0 + p % 80];
-    if (in.r_win) return in.r_win[(size_t)b * NPIX + p];
-    return make_float2(0.f, 0.f);
-  };
-  const float2* gw = in.g_win ? in.g_win + (size_t)b * 320 : nullptr;
+  const WinSrc ws = win_src(in, g, b);
   float acc = 0.f;
-  for (int p = threadIdx.x; p < NPIX; p += 256) { const float2 r = r_at(p); acc += r.x * r.x + r.y * r.y; }
-  if (gw)
-    for (int t = threadIdx.x; t < 320; t += 256) { const float2 q = gw[t]; acc += q.x * q.x + q.y * q.y; }
-  const double tot = block_sum<256>((double)acc, sh);
-  if (threadIdx.x == 0) {
-    const float rho = (float)sqrt(tot / NPIX);
-    rho_out[b] = rho;
-    s_inv = rho > 0.f ? 1.f / rho : 0.f;
-  }
-  __syncthreads();
-  const float inv = s_inv;
   for (int p = threadIdx.x; p < NPIX; p += 256) {
-    const int y = p / 80, x = p % 80, gx = x0 + x, gy = y0 + y;
-    const float2 r = r_at(p);
-    float c[16];
-    c[0] = g.k2 * g.eps[(size_t)gy * g.nx + gx];
-    c[1] = r.x * inv; c[2] = r.y * inv;
-    if (gw) {
-      const float2 gl = gw[0 * 80 + y], gr = gw[1 * 80 + y], gb = gw[2 * 80 + x], gt = gw[3 * 80 + x];
-      c[3] = gl.x * inv; c[4] = gl.y * inv; c[5] = gr.x * inv; c[6] = gr.y * inv;
-      c[7] = gb.x * inv; c[8] = gb.y * inv; c[9] = gt.x * inv; c[10] = gt.y * inv;
-    } else {
-#pragma unroll
-      for (int i = 3; i <= 10; ++i) c[i] = 0.f;
-    }
-    const float2 sx = g.isx[gx], sy = g.isy[gy];
-    c[11] = sx.x; c[12] = sx.y; c[13] = sy.x; c[14] = sy.y; c[15] = 0.f;
-    bf16* dst = out + in_off((size_t)b * 80 + y, x, 0);  // tiled: one row = one K-major tile
-    *reinterpret_cast<uint4*>(dst) =
-        make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), pack2(c[6], c[7]));
-    *reinterpret_cast<uint4*>(dst + 64) =
-        make_uint4(pack2(c[8], c[9]), pack2(c[10], c[11]), pack2(c[12], c[13]), pack2(c[14], c[15]));
+    const float2 r = win_residual(ws, p / 80, p % 80);
+    acc += r.x * r.x + r.y * r.y;
   }
+  if (ws.g)
+    for (int t = threadIdx.x; t < 320; t += 256) { const float2 q = ws.g[t]; acc += q.x * q.x + q.y * q.y; }
+  const double tot = block_sum<256>((double)acc, sh);
+  if (threadIdx.x == 0) rho_out[b] = (float)sqrt(tot / NPIX);
 }
 
 // Self-test operator: plain row-major C = A B^T.
@@ -1193,7 +1248,7 @@ int nno_alloc_work(NnoWork* w, int cap, size_t* bytes) {
   w->cap = cap;
   const size_t c = (size_t)cap;
   struct { void** p; size_t n; } a[] = {
-      {(void**)&w->in, c * NPIX * 16 * 2}, {(void**)&w->X, c * NPIX * 32 * 2}, {(void**)&w->T1, c * 160 * 512 * 2},
+      {(void**)&w->X, c * NPIX * 32 * 2}, {(void**)&w->T1, c * 160 * 512 * 2},
       {(void**)&w->Xh, 512 * c * 64 * 2},  {(void**)&w->Yh, c * 512 * 64 * 2}, {(void**)&w->T3, c * 80 * 32 * 32 * 2},
       {(void**)&w->rho, c * 4},             {(void**)&w->err, 16}};
   for (auto& e : a) {
@@ -1205,7 +1260,7 @@ int nno_alloc_work(NnoWork* w, int cap, size_t* bytes) {
 }
 
 void nno_free_work(NnoWork* w) {
-  void* ptrs[] = {w->in, w->X, w->T1, w->Xh, w->Yh, w->T3, w->rho, w->err};
+  void* ptrs[] = {w->X, w->T1, w->Xh, w->Yh, w->T3, w->rho, w->err};
   for (void* q : ptrs) if (q) cudaFree(q);
   *w = NnoWork();
 }
@@ -1342,7 +1397,7 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
   };
   {
     ProfScope ps(h, 5, 1);
-    pack_kernel<<<n, 256, 0, s>>>(in, g, k->in, k->rho);
+    rho_kernel<<<n, 256, 0, s>>>(in, g, k->rho);
     CKL();
   }
   static int g5_cap = 0;
@@ -1355,15 +1410,16 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
   }
   const int g5_total = n * (80 / G5_ROWS);
   const int g5_grid = g5_total < g5_cap ? g5_total : g5_cap;
+  const LiftSrc lsrc{in, g, k->rho};
   {  // lift 15 -> 32 and block 0's DFT along x, in the G5 pipeline; blocks 1..3
      // get their DFT along x from the previous block's G5 kernel
     ProfScope ps(h, 8, 1);
     if (W->fp8)
-      g5_kernel<true, true><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->in, nullptr, W->lift_w, W->lift_b, W->Fx,
-                                                                  k->T1, W->qinv, 0, g5_total, k->err);
+      g5_kernel<true, true><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, nullptr, nullptr, W->lift_w, W->lift_b, W->Fx,
+                                                                  k->T1, W->qinv, 0, g5_total, k->err, lsrc);
     else
-      g5_kernel<true, false><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->in, nullptr, W->lift_w, W->lift_b, W->Fx,
-                                                                   k->T1, nullptr, 0, g5_total, k->err);
+      g5_kernel<true, false><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, nullptr, nullptr, W->lift_w, W->lift_b, W->Fx,
+                                                                   k->T1, nullptr, 0, g5_total, k->err, lsrc);
     CKL();
   }
   if ((rc = record(0))) return rc;
@@ -1386,10 +1442,11 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
       if (W->fp8)
         g5_kernel<false, true><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W8[bl], W->bias[bl], W->Fx,
                                                                      k->T1, W->qinv + 32 * (bl + 1), bl == 3,
-                                                                     g5_total, k->err);
+                                                                     g5_total, k->err, LiftSrc{});
       else
         g5_kernel<false, false><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], W->Fx,
-                                                                      k->T1, nullptr, bl == 3, g5_total, k->err);
+                                                                      k->T1, nullptr, bl == 3, g5_total, k->err,
+                                                                      LiftSrc{});
       CKL();
     }
     if ((rc = record(bl + 1))) return rc;

@@ -30,7 +30,6 @@ struct NnoWeights {
 
 struct NnoWork {
   int cap = 0;              // windows per batch
-  bf16* in = nullptr;       // [cap][6400][16]  packed inputs (channel-last)
   bf16* X = nullptr;        // [cap][80 y][x/8][c/8][x%8][c%8]  activations, tiled (in place)
   bf16* T1 = nullptr;       // [cap][160 (ri,y)][512 (kx,c)]
   bf16* Xh = nullptr;       // [512 mode][cap][64 (c,ri)]

@@ -6,7 +6,7 @@
 //
 // Instead of the handle's per-call workspace, the intermediates of the
 // neural operator live in one file-scope device array of fixed size
-// (NOALLOC_MAX_WINDOWS windows, about 4.3 MB), which every GPU that loads
+// (NOALLOC_MAX_WINDOWS windows, about 3.5 MB), which every GPU that loads
 // the library holds until the process exits.  In host code the array's name
 // is only a host-side stand-in, so its device address is looked up once per
 // device with cudaGetSymbolAddress (on the first call made on that device)
@@ -20,7 +20,6 @@
 namespace {
 
 constexpr size_t NW = NOALLOC_MAX_WINDOWS;
-constexpr size_t B_IN = NW * 6400 * 16 * 2;
 constexpr size_t B_X = NW * 6400 * 32 * 2;
 constexpr size_t B_T1 = NW * 160 * 512 * 2;
 constexpr size_t B_XH = 512 * NW * 64 * 2;
@@ -28,7 +27,7 @@ constexpr size_t B_YH = NW * 512 * 64 * 2;
 constexpr size_t B_T3 = NW * 80 * 32 * 32 * 2;
 constexpr size_t B_RHO = 256;
 constexpr size_t B_ERR = 256;
-constexpr size_t SCRATCH_BYTES = B_IN + B_X + B_T1 + B_XH + B_YH + B_T3 + B_RHO + B_ERR;
+constexpr size_t SCRATCH_BYTES = B_X + B_T1 + B_XH + B_YH + B_T3 + B_RHO + B_ERR;
 
 static __device__ __align__(256) unsigned char g_nno_scratch[SCRATCH_BYTES];
 
@@ -70,7 +69,6 @@ extern "C" int fdfd_nno_solve_noalloc(fdfd_handle h, const fdfd_c64* r_win, cons
   NnoWork k;
   k.cap = NOALLOC_MAX_WINDOWS;
   size_t off = 0;
-  k.in = reinterpret_cast<bf16*>(base + off); off += B_IN;
   k.X = reinterpret_cast<bf16*>(base + off); off += B_X;
   k.T1 = reinterpret_cast<bf16*>(base + off); off += B_T1;
   k.Xh = reinterpret_cast<bf16*>(base + off); off += B_XH;
