@@ -118,7 +118,7 @@ KERNEL_NAMES = {"stencil": "stencil_c64", "cgs_dots": "cgs_dots_kernel", "cgs_up
                 "residual64": "residual64", "nno_pack": "rho_kernel (window RMS)",
                 "nno_lift": "g5_kernel<lift> (input channels + lift + block-0 DFT-x)",
                 "nno_dft_x": "gemm_kernel<32,80,MN> (G1Op)", "nno_dft_y": "gemm_kernel<64,160,MN> (G2Op)",
-                "nno_mix": "spectral mixing (autotuned: g3_kernel, or G3Op GEMM + mix_transpose_kernel)", "nno_idft_y": "gemm_kernel<160,64> (G4Op)",
+                "nno_mix": "g3_kernel (spectral mixing)", "nno_idft_y": "gemm_kernel<160,64> (G4Op)",
                 "nno_idft_x_mix_act": "g5_kernel", "nno_proj": "proj_kernel", "rhs_norm": "residual64 (x = 0)"}
 
 

@@ -133,9 +133,8 @@ typedef struct {
   size_t workspace_bytes;/* device memory held by the handle              */
   int graphs_cached;     /* Arnoldi-step graph sets currently captured     */
   int graphs_ok;         /* 0 once a capture failed (eager launches only)  */
-  int tuned_mix_modes;   /* autotuned at set-up: spectral modes per mixing
-                            CTA (2 or 4) and K split of the DFT-y GEMM    */
-  int tuned_dfty_split;
+  int tuned_dfty_split;  /* autotuned at set-up: K split of the DFT-y GEMM
+                            (1 or 2)                                      */
 } fdfd_info;
 
 /* ---- handle life cycle ----------------------------------------------- */

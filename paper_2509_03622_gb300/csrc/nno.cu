@@ -292,32 +292,12 @@ struct G2Op {  // DFT along y: rows (kx,c), K = (ri,y) (A MN-major from T1), N =
 #pragma unroll
     for (int i = 0; i < 16; i += 2) {
       const int q = (c0 + i) >> 1;
-      *reinterpret_cast<uint32_t*>(Xh + (((size_t)(q * 16 + kx)) * cap + b) * 64 + c * 2) = pack2(v[i], v[i + 1]);
+      *reinterpret_cast<uint32_t*>(Xh + xh_off(q * 16 + kx, b, c * 2, xh_rows(cap))) = pack2(v[i], v[i + 1]);
     }
   }
   __device__ void epi_end(int, int, State&) const {}
 };
 
-
-struct G3Op {  // spectral mixing, one mode per tile: rows = windows, K = (c,ri) 64, N = (o,ri) 64
-  static constexpr bool kConstB = false;
-  const bf16* Xh; const bf16* R; bf16* Ym; int cap, nwin;
-  typedef NoState State;
-  __device__ int rows(int) const { return nwin; }
-  __device__ const uint4* a_src(int md, int w, int k) const {
-    return reinterpret_cast<const uint4*>(Xh + ((size_t)md * cap + w) * 64 + k);
-  }
-  __device__ const uint4* b_src(int md, int n, int k) const {
-    return reinterpret_cast<const uint4*>(R + ((size_t)md * 64 + n) * 64 + k);
-  }
-  __device__ void epi_begin(State&) const {}
-  __device__ void epi(int md, int w, int c0, const float* v, State&) const {  // 32 contiguous bytes per thread
-    uint4* dst = reinterpret_cast<uint4*>(Ym + ((size_t)md * cap + w) * 64 + c0);
-    dst[0] = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
-    dst[1] = make_uint4(pack2(v[8], v[9]), pack2(v[10], v[11]), pack2(v[12], v[13]), pack2(v[14], v[15]));
-  }
-  __device__ void epi_end(int, int, State&) const {}
-};
 
 struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
   static constexpr bool kConstB = true;
@@ -340,94 +320,152 @@ struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
   __device__ void epi_end(int, int, State&) const {}
 };
 
-// G3 with 4 modes per CTA: unit = (kx, q-group of 4, tile of 128 windows);
-// D_m[w][(o,ri)] = Xh_m[w][(c,ri')] R'_m[(o,ri)][(c,ri')]^T for the 4 modes
-// m = (q0..q0+3, kx), accumulators side by side in TMEM (4 x 64 columns), so
-// the epilogue writes 16 contiguous bytes (4 q x re/im) per (window, o).
-// One CTA per unit, several resident per SM (shared memory and TMEM), CTAs
-// in the order (window tile, q-group, kx): a warp-specialised persistent
-// form of this kernel measured slower on GB300, so this one stays.  The
-// number of modes per CTA (2 or 4) is chosen by nno_autotune.
-constexpr uint32_t G3_A = 128 * 64 * 2, G3_B = 64 * 64 * 2;
-template <int G3_Q>
-constexpr uint32_t g3_smem() { return G3_Q * (G3_A + G3_B) + 16; }
+constexpr uint32_t G3_A = 128 * 64 * 2, G3_B = 64 * 64 * 2;  // spectrum tile, one mode's weights
 
-template <int G3_Q>
-__global__ void __launch_bounds__(128) g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int cap, int nwin,
-                                                 int wtiles, int* err) {
+// G3, spectral mixing (Fig. 2's per-mode weights): for every retained mode
+// m = (q, kx), D_m[w][(o,ri)] = Xh_m[w][(c,ri')] R_m[(o,ri)][(c,ri')]^T over
+// the windows w, persistent and warp-specialised, one CTA per SM.
+// Item = (tile of 128 windows, kx, group of G3_Q = 8 modes q0..q0+7).  Per
+// mode, warp 0 bulk-copies the tile of the spectrum (up to 16 KB: the tile's
+// windows are contiguous 128-byte rows, already in the 128-byte swizzled
+// operand layout) and the mode's weights (8 KB, same layout) into a ring of
+// G3_STAGES stages; warp 1 accumulates the 8 modes side by side in
+// TMEM (8 x 64 columns); warps 2..5 (TMEM lanes 32 (warp % 4) ..) write, per
+// (window, o), the 8 modes' (re, im) pairs as one 32-byte store: a whole
+// sector of the window-major output row (o, kx).  Half-sector writes
+// (4 modes per item, two accumulator sets) measured 2.3x slower on GB300.
+// Items are ordered mode group fastest, so the CTAs running at the same time
+// complete the same output rows.
+constexpr int G3_Q = 8;
+constexpr int G3_STAGES = 8;
+constexpr uint32_t G3_STAGE = G3_A + G3_B;  // 24 KB
+constexpr uint32_t G3_OFF_BAR = G3_STAGES * G3_STAGE;
+constexpr int G3_THREADS = 192;
+constexpr uint32_t G3_SMEM = G3_OFF_BAR + (2 * G3_STAGES + 2) * 8 + 16;
+
+__device__ __forceinline__ void st_global_v8(void* p, uint4 lo, uint4 hi) {  // one 32-byte store
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(lo.x), "r"(lo.y), "r"(lo.z),
+               "r"(lo.w), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(G3_THREADS, 1)
+g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int rows, int nwin, int wtiles, int* err) {
+  constexpr int Q = G3_Q, NACC = 1, NQG = 32 / Q;
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + G3_Q * G3_A;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + g3_smem<G3_Q>() - 16);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + g3_smem<G3_Q>() - 8);
+  const uint32_t sbase = tc::smem_u32(smem);
+  const uint32_t bar = sbase + G3_OFF_BAR;
+  auto full = [&](int s) { return bar + 8u * s; };
+  auto empty = [&](int s) { return bar + 8u * (G3_STAGES + s); };
+  auto acc_full = [&](int a) { return bar + 8u * (2 * G3_STAGES + a); };
+  auto acc_empty = [&](int a) { return bar + 8u * (2 * G3_STAGES + NACC + a); };
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G3_OFF_BAR + (2 * G3_STAGES + 2 * NACC) * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int u = blockIdx.x;
-  const int wt = u % wtiles, qg = (u / wtiles) % (32 / G3_Q), kx = u / (wtiles * (32 / G3_Q));
-  const int w0 = wt * 128;
-  for (int mq = 0; mq < G3_Q; ++mq) {
-    const int md = (qg * G3_Q + mq) * 16 + kx;
-    for (int c = tid; c < 128 * 8; c += 128) {
-      const int t8 = c & 7, rest = c >> 3, kc = rest & 7, rg = rest >> 3;
-      const int w = w0 + rg * 8 + t8;
-      const bool ok = w < nwin;
-      tc::cp_async16(sA + mq * G3_A + (rg * 8 + kc) * 128 + t8 * 16,
-                     Xh + ((size_t)md * cap + (ok ? w : 0)) * 64 + kc * 8, ok);
-    }
-    for (int c = tid; c < 64 * 8; c += 128) {
-      const int t8 = c & 7, rest = c >> 3, kc = rest & 7, rg = rest >> 3;
-      tc::cp_async16(sB + mq * G3_B + (rg * 8 + kc) * 128 + t8 * 16,
-                     R + ((size_t)md * 64 + rg * 8 + t8) * 64 + kc * 8, true);
-    }
+  const int total = wtiles * 16 * NQG;
+  if ((int)blockIdx.x >= total) return;
+  if (sbase & 1023) {  // the swizzled operand tiles need 1024-byte alignment
+    if (tid == 0) atomicExch(err, 1);
+    return;
   }
-  tc::cp_async_wait_all();
-  if (tid == 0) tc::mbar_init(tc::smem_u32(mbar), 1);
-  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 64 * G3_Q);
-  tc::fence_async_smem();
+  if (tid == 0) {
+    for (int s = 0; s < G3_STAGES; ++s) { tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); }
+    for (int a = 0; a < NACC; ++a) { tc::mbar_init(acc_full(a), 1); tc::mbar_init(acc_empty(a), 4); }
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tc::smem_u32(tslot), 512);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  if (tid == 0) {
-    constexpr uint32_t idesc = tc::idesc_bf16(64, false, false);
-    for (int mq = 0; mq < G3_Q; ++mq) {
-      const uint32_t a0 = tc::smem_u32(sA + mq * G3_A), b0 = tc::smem_u32(sB + mq * G3_B);
-      for (int s = 0; s < 4; ++s)
-        tc::mma_bf16(tmem + mq * 64, tc::make_desc(a0 + s * 256, 128, 1024), tc::make_desc(b0 + s * 256, 128, 1024),
-                     idesc, s > 0);
-    }
-    tc::mma_commit(tc::smem_u32(mbar));
-  }
-  if (!tc::mbar_wait(tc::smem_u32(mbar), 0, WAIT_LIMIT)) atomicExch(err, 1);
-  tc::fence_after();
-  const int w = w0 + warp * 32 + lane;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-  for (int oc = 0; oc < 4; ++oc) {  // 8 output channels (16 columns) per pass
-    float v[G3_Q][16];
-#pragma unroll
-    for (int mq = 0; mq < G3_Q; ++mq) tc::tmem_ld16(trow + mq * 64 + oc * 16, v[mq]);
-    if (w < nwin) {
-#pragma unroll
-      for (int oo = 0; oo < 8; ++oo) {
-        const int o = oc * 8 + oo;
-        uint4 q;
-        if constexpr (G3_Q == 4) {
-          q.x = pack2(v[0][2 * oo], v[0][2 * oo + 1]);
-          q.y = pack2(v[1][2 * oo], v[1][2 * oo + 1]);
-          q.z = pack2(v[2][2 * oo], v[2][2 * oo + 1]);
-          q.w = pack2(v[3][2 * oo], v[3][2 * oo + 1]);
-          *reinterpret_cast<uint4*>(Yh + (((size_t)w * 512) + o * 16 + kx) * 64 + qg * G3_Q * 2) = q;
-        } else {
-          *reinterpret_cast<uint2*>(Yh + (((size_t)w * 512) + o * 16 + kx) * 64 + qg * G3_Q * 2) =
-              make_uint2(pack2(v[0][2 * oo], v[0][2 * oo + 1]), pack2(v[1][2 * oo], v[1][2 * oo + 1]));
+  auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- producer ----------------
+      int it = 0;
+      bool ok = true;
+      for (int i = blockIdx.x; i < total && ok && !*abort_flag; i += gridDim.x) {
+        const int qg = i % NQG, kx = (i / NQG) % 16, w0 = (i / (NQG * 16)) * 128;
+        const uint32_t abytes = (uint32_t)min(128, rows - w0) * 128;  // rows: a multiple of 8
+        for (int mq = 0; mq < Q; ++mq, ++it) {
+          const int s = it % G3_STAGES;
+          if (it >= G3_STAGES && !tc::mbar_wait(empty(s), ((it / G3_STAGES) - 1) & 1, WAIT_LIMIT)) {
+            ok = false;
+            break;
+          }
+          const int md = (qg * Q + mq) * 16 + kx;
+          tc::mbar_arrive_tx(full(s), abytes + G3_B);
+          tc::bulk_g2s(sbase + s * G3_STAGE, Xh + xh_off(md, w0, 0, rows), abytes, full(s));
+          tc::bulk_g2s(sbase + s * G3_STAGE + G3_A, R + (size_t)md * 4096, G3_B, full(s));
         }
       }
+      if (!ok) fail();
+      // every copy issued must have landed before the CTA may exit
+      for (int j = (it > G3_STAGES ? it - G3_STAGES : 0); j < it; ++j)
+        if (!tc::mbar_wait(full(j % G3_STAGES), (j / G3_STAGES) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer ----------------
+      constexpr uint32_t idesc = tc::idesc_bf16(64, false, false);
+      int it = 0, t = 0;
+      bool ok = true;
+      for (int i = blockIdx.x; i < total && ok && !*abort_flag; i += gridDim.x, ++t) {
+        const int a = t % NACC;
+        if (t >= NACC && !tc::mbar_wait(acc_empty(a), ((t / NACC) - 1) & 1, WAIT_LIMIT)) { ok = false; break; }
+        tc::fence_after();
+        for (int mq = 0; mq < Q; ++mq, ++it) {
+          const int s = it % G3_STAGES;
+          if (!tc::mbar_wait(full(s), (it / G3_STAGES) & 1, WAIT_LIMIT)) { ok = false; break; }
+          tc::fence_after();
+          const uint32_t a0 = sbase + s * G3_STAGE, b0 = a0 + G3_A;
+          for (int k = 0; k < 4; ++k)
+            tc::mma_bf16(tmem + a * (Q * 64) + mq * 64, tc::make_desc_sw128(a0 + k * 32, 1024),
+                         tc::make_desc_sw128(b0 + k * 32, 1024), idesc, k > 0);
+          tc::mma_commit(empty(s));
+        }
+        if (!ok) break;
+        tc::mma_commit(acc_full(a));
+      }
+      if (!ok) fail();
+    }
+  } else {  // ---------------- epilogue (warps 2..5; TMEM lanes 32 (warp % 4) ..) ----------------
+    const int qw = warp & 3;
+    int t = 0;
+    for (int i = blockIdx.x; i < total; i += gridDim.x, ++t) {
+      const int a = t % NACC;
+      if (*abort_flag || !tc::mbar_wait(acc_full(a), (t / NACC) & 1, WAIT_LIMIT)) { fail(); break; }
+      tc::fence_after();
+      const int qg = i % NQG, kx = (i / NQG) % 16, w = (i / (NQG * 16)) * 128 + qw * 32 + lane;
+      const uint32_t trow = tmem + ((uint32_t)(qw * 32) << 16) + a * (Q * 64);
+      for (int oc = 0; oc < 4; ++oc) {  // 8 output channels (16 columns) per pass
+        float v[Q][16];
+#pragma unroll
+        for (int mq = 0; mq < Q; ++mq) tc::tmem_ld16(trow + mq * 64 + oc * 16, v[mq]);
+        if (w < nwin) {
+#pragma unroll
+          for (int oo = 0; oo < 8; ++oo) {
+            uint4 q4[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              q4[h] = make_uint4(pack2(v[4 * h][2 * oo], v[4 * h][2 * oo + 1]),
+                                 pack2(v[4 * h + 1][2 * oo], v[4 * h + 1][2 * oo + 1]),
+                                 pack2(v[4 * h + 2][2 * oo], v[4 * h + 2][2 * oo + 1]),
+                                 pack2(v[4 * h + 3][2 * oo], v[4 * h + 3][2 * oo + 1]));
+            st_global_v8(Yh + (((size_t)w * 512) + (oc * 8 + oo) * 16 + kx) * 64 + qg * Q * 2, q4[0], q4[1]);
+          }
+        }
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty(a));
     }
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     tc::fence_after();
-    tc::tmem_free(tmem, 64 * G3_Q);
+    tc::tmem_free(tmem, 512);
   }
 }
 
@@ -1202,17 +1240,15 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
     const float* Rr = p;
     const float* Ri = p + 32 * 32 * 512;
     p += 2 * 32 * 32 * 512;
-    std::vector<float> R(512 * 64 * 64);
+    std::vector<float> R(512 * 64 * 64);  // tiled per mode (r_off)
     for (int q = 0; q < 32; ++q)
       for (int kx = 0; kx < 16; ++kx) {
         const int md = q * 16 + kx;
         for (int o = 0; o < 32; ++o)
           for (int c = 0; c < 32; ++c) {
             const float rr = Rr[((o * 32 + c) * 32 + q) * 16 + kx], ri = Ri[((o * 32 + c) * 32 + q) * 16 + kx];
-            float* row_re = &R[((size_t)md * 64 + o * 2 + 0) * 64];
-            float* row_im = &R[((size_t)md * 64 + o * 2 + 1) * 64];
-            row_re[c * 2 + 0] = rr; row_re[c * 2 + 1] = -ri;
-            row_im[c * 2 + 0] = ri; row_im[c * 2 + 1] = rr;
+            R[r_off(md, o * 2, c * 2)] = rr; R[r_off(md, o * 2, c * 2 + 1)] = -ri;
+            R[r_off(md, o * 2 + 1, c * 2)] = ri; R[r_off(md, o * 2 + 1, c * 2 + 1)] = rr;
           }
       }
     if ((rc = up(&W->R[bl], to_bf16(R), bytes))) return rc;
@@ -1249,7 +1285,7 @@ int nno_alloc_work(NnoWork* w, int cap, size_t* bytes) {
   const size_t c = (size_t)cap;
   struct { void** p; size_t n; } a[] = {
       {(void**)&w->X, c * NPIX * 32 * 2}, {(void**)&w->T1, c * 160 * 512 * 2},
-      {(void**)&w->Xh, 512 * c * 64 * 2},  {(void**)&w->Yh, c * 512 * 64 * 2}, {(void**)&w->T3, c * 80 * 32 * 32 * 2},
+      {(void**)&w->Xh, 512 * (size_t)xh_rows(cap) * 64 * 2},  {(void**)&w->Yh, c * 512 * 64 * 2}, {(void**)&w->T3, c * 80 * 32 * 32 * 2},
       {(void**)&w->rho, c * 4},             {(void**)&w->err, 16}};
   for (auto& e : a) {
     if (cudaMalloc(e.p, e.n) != cudaSuccess) return FDFD_ENOMEM;
@@ -1283,62 +1319,16 @@ __global__ void absmax_kernel(const bf16* X, size_t n_elem, unsigned* out) {
   if (threadIdx.x < 32) atomicMax(&out[threadIdx.x], m[threadIdx.x]);
 }
 
-// Mode-major mixed spectrum Ym[mode][w][(o,ri)] -> window-major
-// Yw[w][(o,kx)][(q,ri)], mode = q*16 + kx.  Per window (blocks stride over
-// windows): its 512 mode rows (128 B, read whole by 8 threads each) into
-// shared memory with rows padded to 136 B (34 words, so the reads below hit
-// distinct banks), then every thread assembles whole 128-byte output rows.
-constexpr int TP_THREADS = 256;
-constexpr int TP_ROW = 136;
-constexpr int TP_SMEM = 512 * TP_ROW;
-__global__ void __launch_bounds__(TP_THREADS) mix_transpose_kernel(const bf16* Ym, bf16* Yw, int cap, int nwin) {
-  extern __shared__ __align__(16) uint8_t sm[];
-  for (int w = blockIdx.x; w < nwin; w += gridDim.x) {
-    for (int c = threadIdx.x; c < 512 * 8; c += TP_THREADS) {
-      const int m = c >> 3, part = c & 7;
-      const uint4 q = *reinterpret_cast<const uint4*>(Ym + ((size_t)m * cap + w) * 64 + part * 8);
-      uint32_t* d = reinterpret_cast<uint32_t*>(sm + m * TP_ROW + part * 16);
-      d[0] = q.x; d[1] = q.y; d[2] = q.z; d[3] = q.w;
-    }
-    __syncthreads();
-    for (int row = threadIdx.x; row < 512; row += TP_THREADS) {  // row = (o, kx), kx fastest
-      const int o = row >> 4, kx = row & 15;
-      uint4* dst = reinterpret_cast<uint4*>(Yw + ((size_t)w * 512 + row) * 64);
-#pragma unroll
-      for (int qg = 0; qg < 8; ++qg) {
-        uint32_t v[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t)  // (re, im) of mode (q, kx), output channel o
-          v[t] = *reinterpret_cast<const uint32_t*>(sm + ((qg * 4 + t) * 16 + kx) * TP_ROW + o * 4);
-        dst[qg] = make_uint4(v[0], v[1], v[2], v[3]);
-      }
-    }
-    __syncthreads();
+// Spectral mixing of all n windows into the window-major layout G4 reads.
+int launch_g3(NnoWork* k, const bf16* R, int n, cudaStream_t s) {
+  static int g3_cap = 0;
+  if (!g3_cap) {
+    CK(cudaFuncSetAttribute(g3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G3_SMEM));
+    g3_cap = persistent_grid((const void*)g3_kernel, G3_THREADS, G3_SMEM, 512);
   }
-}
-
-// Spectral mixing into the window-major layout G4 reads; returns where it is.
-// modes = 4 or 2: modes per CTA of g3_kernel, writing it directly; modes = 1:
-// one mode per tile in the generic pipeline (contiguous mode-major rows),
-// then the transpose into the Xh buffer, which the mixing no longer needs.
-int launch_g3(NnoWork* k, const bf16* R, int n, int modes, cudaStream_t s, const bf16** yw = nullptr) {
-  static bool init = false;
-  if (!init) {
-    CK(cudaFuncSetAttribute(g3_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g3_smem<2>()));
-    CK(cudaFuncSetAttribute(g3_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g3_smem<4>()));
-    CK(cudaFuncSetAttribute(mix_transpose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM));
-    init = true;
-  }
-  const int wtiles = (n + 127) / 128;
-  if (yw) *yw = modes == 1 ? k->Xh : k->Yh;
-  if (modes == 1) {
-    int rc = launch_gemm<64, 64, false, G3Op>(G3Op{k->Xh, R, k->Yh, k->cap, n}, wtiles, 512, k->err, s);
-    if (rc) return rc;
-    mix_transpose_kernel<<<n < 456 ? n : 456, TP_THREADS, TP_SMEM, s>>>(k->Yh, k->Xh, k->cap, n);
-  } else if (modes == 2)
-    g3_kernel<2><<<wtiles * 16 * 16, 128, g3_smem<2>(), s>>>(k->Xh, R, k->Yh, k->cap, n, wtiles, k->err);
-  else
-    g3_kernel<4><<<wtiles * 8 * 16, 128, g3_smem<4>(), s>>>(k->Xh, R, k->Yh, k->cap, n, wtiles, k->err);
+  const int wtiles = (n + 127) / 128, total = wtiles * 16 * (32 / G3_Q);
+  g3_kernel<<<total < g3_cap ? total : g3_cap, G3_THREADS, G3_SMEM, s>>>(k->Xh, R, k->Yh, xh_rows(k->cap), n, wtiles,
+                                                                          k->err);
   CKL();
   return FDFD_OK;
 }
@@ -1355,7 +1345,7 @@ int nno_autotune(const NnoWeights* W, NnoWork* k, int n, cudaStream_t s) {
   CK(cudaEventCreate(&e1));
   // inputs of the timed stages: zeroed half-spectra (timing only)
   CK(cudaMemsetAsync(k->T1, 0, (size_t)n * 160 * 512 * 2, s));
-  CK(cudaMemsetAsync(k->Xh, 0, (size_t)512 * k->cap * 64 * 2, s));
+  CK(cudaMemsetAsync(k->Xh, 0, (size_t)512 * xh_rows(k->cap) * 64 * 2, s));
   auto best_of = [&](auto&& run, const int* opts, int nopt) -> int {
     int best = opts[0];
     float best_ms = 1e30f;
@@ -1372,13 +1362,11 @@ int nno_autotune(const NnoWeights* W, NnoWork* k, int n, cudaStream_t s) {
     }
     return best;
   };
-  const int g3opts[3] = {4, 2, 1}, g2opts[2] = {2, 1};
-  const int g3 = best_of([&](int m) { return launch_g3(k, W->R[0], n, m, s); }, g3opts, 3);
+  const int g2opts[2] = {2, 1};
   const int g2 = best_of([&](int sp) { return launch_g2(k, W, n, sp, s); }, g2opts, 2);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (g3 < 0 || g2 < 0) return FDFD_ECUDA;
-  k->g3_modes = g3;
+  if (g2 < 0) return FDFD_ECUDA;
   k->g2_split = g2;
   return FDFD_OK;
 }
@@ -1423,19 +1411,18 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     CKL();
   }
   if ((rc = record(0))) return rc;
-  const bf16* yw = k->Yh;  // window-major mixed spectrum (where launch_g3 put it)
   for (int bl = 0; bl < 4; ++bl) {
     {
       ProfScope ps(h, 10, 1);
       if ((rc = launch_g2(k, W, n, k->g2_split, s))) return rc;
     }
     {
-      ProfScope ps(h, 11, k->g3_modes == 1 ? 2 : 1);
-      if ((rc = launch_g3(k, W->R[bl], n, k->g3_modes, s, &yw))) return rc;
+      ProfScope ps(h, 11, 1);
+      if ((rc = launch_g3(k, W->R[bl], n, s))) return rc;
     }
     {
       ProfScope ps(h, 12, 1);
-      if ((rc = launch_gemm<160, 64, false>(G4Op{yw, W->Gy, k->T3}, 512 / 128, n, k->err, s))) return rc;
+      if ((rc = launch_gemm<160, 64, false>(G4Op{k->Yh, W->Gy, k->T3}, 512 / 128, n, k->err, s))) return rc;
     }
     {
       ProfScope ps(h, 13, 1);

@@ -9,7 +9,8 @@ struct NnoWeights {
   float* lift_b = nullptr;  // [32]
   bf16* Fx = nullptr;       // [32 (kx,ri)][80 x]           forward DFT along x
   bf16* Fy = nullptr;       // [64 (q,ri)][160 (ri',y)]     forward DFT along y (realified)
-  bf16* R[4] = {};          // [512 mode][64 (o,ri)][64 (c,ri')]  realified spectral weights
+  bf16* R[4] = {};          // [512 mode][64 (o,ri)][64 (c,ri')]  realified spectral weights,
+                            // rows swizzled like Xh (r_off)
   bf16* Gy = nullptr;       // [160 (y,ri)][64 (q,ri')]     inverse DFT along y (1/80)
   bf16* Gx = nullptr;       // [128 x][32 (kx,ri)]          inverse real DFT along x (1/80), rows >= 80 zero
   bf16* W[4] = {};          // [32 o][32 c]
@@ -28,17 +29,32 @@ struct NnoWeights {
   bf16* P18 = nullptr;      // [128][32]     P1 diag(s[4])
 };
 
+// Rows of the spectrum per mode: the windows rounded up to a whole 8-row
+// group of the tiled layout.
+__host__ __device__ constexpr int xh_rows(int cap) { return (cap + 7) & ~7; }
+// Spectrum: element (mode md, window w, k = (c,ri)).  Each window's 64
+// values of a mode are one 128-byte row (written whole by the DFT-y
+// epilogue) with its 16-byte chunk k/8 stored at chunk (k/8) ^ (w % 8): the
+// 128-byte swizzled K-major operand layout, so a tile of up to 128
+// consecutive windows of one mode is one contiguous bulk copy that the
+// tensor core reads as it lands.
+__host__ __device__ constexpr size_t xh_off(int md, int w, int k, int rows) {
+  return ((size_t)md * rows + w) * 64 + ((((k >> 3) ^ (w & 7)) << 3) | (k & 7));
+}
+// Spectral weights: element (mode, n = (o,ri), k = (c,ri')), same layout.
+__host__ __device__ constexpr size_t r_off(int md, int n, int k) {
+  return (size_t)md * 4096 + (size_t)n * 64 + ((((k >> 3) ^ (n & 7)) << 3) | (k & 7));
+}
+
 struct NnoWork {
   int cap = 0;              // windows per batch
   bf16* X = nullptr;        // [cap][80 y][x/8][c/8][x%8][c%8]  activations, tiled (in place)
   bf16* T1 = nullptr;       // [cap][160 (ri,y)][512 (kx,c)]
-  bf16* Xh = nullptr;       // [512 mode][cap][64 (c,ri)]
+  bf16* Xh = nullptr;       // [512 mode][xh_rows(cap) w][64 (c,ri)], chunks swizzled: xh_off
   bf16* Yh = nullptr;       // [cap][512 (o,kx)][64 (q,ri)]
   bf16* T3 = nullptr;       // [cap][80 y][o/8][k/8][o%8][k%8]  k = (kx,ri), tiled
   float* rho = nullptr;     // [cap]
   int* err = nullptr;       // bounded-wait failure flag
-  int g3_modes = 4;         // spectral mixing: modes per CTA (4 or 2), or 1 = one mode per
-                            // tile + transpose through the Xh buffer; set by nno_autotune
   int g2_split = 2;         // K split of the DFT-y GEMM (1 or 2), set by nno_autotune
 };
 
@@ -85,9 +101,9 @@ struct GridGeom {
 int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t* bytes);
 void nno_free_weights(NnoWeights* W);
 int nno_alloc_work(NnoWork* w, int cap, size_t* bytes);
-// Autotuner: time the variants of the shape-dependent stages (modes per
-// spectral-mixing CTA, K split of the DFT-y GEMM) on n windows of the work
-// buffers with CUDA events and keep the fastest in `work`.
+// Autotuner: time the variants of the shape-dependent stage (K split of the
+// DFT-y GEMM) on n windows of the work buffers with CUDA events and keep the
+// fastest in `work`.
 int nno_autotune(const NnoWeights* W, NnoWork* work, int n, cudaStream_t s);
 void nno_free_work(NnoWork* w);
 struct fdfd_ctx;

@@ -22,7 +22,7 @@ namespace {
 constexpr size_t NW = NOALLOC_MAX_WINDOWS;
 constexpr size_t B_X = NW * 6400 * 32 * 2;
 constexpr size_t B_T1 = NW * 160 * 512 * 2;
-constexpr size_t B_XH = 512 * NW * 64 * 2;
+constexpr size_t B_XH = 512 * (size_t)xh_rows(NW) * 64 * 2;
 constexpr size_t B_YH = NW * 512 * 64 * 2;
 constexpr size_t B_T3 = NW * 80 * 32 * 32 * 2;
 constexpr size_t B_RHO = 256;

@@ -177,7 +177,6 @@ int schwarz_export(fdfd_ctx* h, double* Q, double* Nd) {
 int schwarz_info(fdfd_ctx* h, fdfd_info* info) {
   info->k_coarse = h->sw->k;
   info->n_coarse = h->sw->k * h->sw->n_win;
-  info->tuned_mix_modes = h->sw->work.g3_modes;
   info->tuned_dfty_split = h->sw->work.g2_split;
   return FDFD_OK;
 }

@@ -31,6 +31,20 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
   return d;               // base offset 0, absolute LBO mode, SWIZZLE_NONE
 }
 
+// Descriptor of a K-major tile in the 128-byte swizzled layout: rows of 128
+// bytes (64 BF16 along K), 8-row groups `sbo` bytes apart, the 16-byte chunk
+// c of row r stored at chunk c ^ (r % 8).  The tile must start on a 1024-byte
+// boundary; a K step inside the row advances `saddr` by 32 bytes.
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;  // leading byte offset: unused for swizzled K-major tiles
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;  // SWIZZLE_128B
+  return d;
+}
+
 // Instruction descriptor for kind::f16: BF16 A/B, FP32 accumulator, M = 128.
 __host__ __device__ constexpr uint32_t idesc_bf16(int n, bool a_mn_major, bool b_mn_major) {
   return (1u << 4)                        // D format: F32

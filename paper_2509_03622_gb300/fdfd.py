@@ -54,7 +54,7 @@ class SolveStats(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n_win", C.c_int), ("nwx", C.c_int), ("nwy", C.c_int), ("k_coarse", C.c_int),
                 ("n_coarse", C.c_int), ("workspace_bytes", C.c_size_t), ("graphs_cached", C.c_int),
-                ("graphs_ok", C.c_int), ("tuned_mix_modes", C.c_int), ("tuned_dfty_split", C.c_int)]
+                ("graphs_ok", C.c_int), ("tuned_dfty_split", C.c_int)]
 
 
 class Profile(C.Structure):
