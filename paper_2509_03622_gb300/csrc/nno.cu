@@ -478,9 +478,12 @@ g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int rows, int nwin, int wtile
 // Roles: warp 0 lane 0 = producer (one bulk copy of the 4 X rows, 20 KB, and
 // one of the 4 T3 rows, 8 KB, per unit into a G5_STAGES-deep ring, completion
 // by transaction count), warp 1 lane 0 = MMA issuer, warps 4..11 = epilogue
-// (warp w reads TMEM lanes 32(w%4)..).  Two accumulator sets in TMEM (G5:
-// 4 x 32 columns, G1: 32 columns) let the epilogue of unit i overlap the
-// MMAs of unit i+1.  The G5 MMA has M = 128 rows of which x < 80 are real:
+// (warp w reads TMEM lanes 32(w%4)..).  Three accumulator sets in TMEM (G5:
+// 4 x 32 columns, G1: 32 columns, 160 columns a set) let the epilogue of unit
+// i overlap the MMAs of units i+1 and i+2, and the epilogue is software
+// pipelined: it writes unit i's activations (and G1's A operand), then reads
+// unit i-1's G1 result, issued a whole unit earlier, so it never waits on a
+// just-issued MMA.  The G5 MMA has M = 128 rows of which x < 80 are real:
 // rows 80..127 of one X tile read the next tile (or, for the last row of a
 // stage, the following buffer); those accumulator rows are never read.
 // X and T3 are stored tiled (core-matrix order), so one row is one
@@ -499,7 +502,9 @@ constexpr uint32_t G5_OFF_GX = G5_OFF_A1 + 2 * G5_A1;
 constexpr uint32_t G5_OFF_W = G5_OFF_GX + 128 * 32 * 2;
 constexpr uint32_t G5_OFF_FX = G5_OFF_W + 32 * 32 * 2;
 constexpr uint32_t G5_OFF_BAR = G5_OFF_FX + 32 * 80 * 2;
-constexpr uint32_t G5_NBAR = 3 * G5_STAGES + 8;
+constexpr int G5_NACC = 3;                                        // TMEM accumulator sets
+constexpr uint32_t G5_ACC = 160;                                  // TMEM columns per set
+constexpr uint32_t G5_NBAR = 3 * G5_STAGES + 3 * G5_NACC + 2;
 constexpr uint32_t G5_SMEM = G5_OFF_BAR + G5_NBAR * 8 + 16;
 static_assert(G5_SMEM <= 227 * 1024, "g5 shared memory");
 
@@ -602,14 +607,14 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   extern __shared__ __align__(1024) uint8_t smem[];
   const uint32_t sbase = tc::smem_u32(smem);
   const uint32_t bar = sbase + G5_OFF_BAR;
-  // barriers: full[s], empty[s], g5_full[2], g1_full[2], a1_full[2], acc_empty[2]
+  // barriers: full[s], empty[s], g5_full[3], g1_full[3], acc_empty[3], a1_full[2], conv_full[s]
   auto full = [&](int s) { return bar + 8u * s; };
   auto empty = [&](int s) { return bar + 8u * (G5_STAGES + s); };
   auto g5_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + a); };
-  auto g1_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + 2 + a); };
-  auto a1_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + 4 + a); };
-  auto acc_empty = [&](int a) { return bar + 8u * (2 * G5_STAGES + 6 + a); };
-  auto conv_full = [&](int s) { return bar + 8u * (2 * G5_STAGES + 8 + s); };  // FP8 rows converted
+  auto g1_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + G5_NACC + a); };
+  auto acc_empty = [&](int a) { return bar + 8u * (2 * G5_STAGES + 2 * G5_NACC + a); };
+  auto a1_full = [&](int b) { return bar + 8u * (2 * G5_STAGES + 3 * G5_NACC + b); };
+  auto conv_full = [&](int s) { return bar + 8u * (2 * G5_STAGES + 3 * G5_NACC + 2 + s); };  // FP8 rows converted
   constexpr bool CONV = FP8 && !LIFT;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G5_OFF_BAR + G5_NBAR * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + G5_OFF_BAR + G5_NBAR * 8 + 4);
@@ -635,10 +640,10 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   tc::cp_async_wait_all();
   if (tid == 0) {
     for (int s = 0; s < G5_STAGES; ++s) { tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); }
-    for (int a = 0; a < 2; ++a) {
-      tc::mbar_init(g5_full(a), 1); tc::mbar_init(g1_full(a), 1);
-      tc::mbar_init(a1_full(a), 8); tc::mbar_init(acc_empty(a), 8);
+    for (int a = 0; a < G5_NACC; ++a) {
+      tc::mbar_init(g5_full(a), 1); tc::mbar_init(g1_full(a), 1); tc::mbar_init(acc_empty(a), 8);
     }
+    for (int b = 0; b < 2; ++b) tc::mbar_init(a1_full(b), 8);
     for (int s = 0; s < G5_STAGES; ++s) tc::mbar_init(conv_full(s), 2);
     *abort_flag = 0;
     tc::fence_mbar_init();
@@ -712,12 +717,12 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       constexpr uint32_t id1 = tc::idesc_bf16(32, true, false);
       const uint32_t ag = sbase + G5_OFF_GX, bw = sbase + G5_OFF_W, bfx = sbase + G5_OFF_FX;
       auto issue_g1 = [&](int j) -> bool {  // next block's DFT along x for unit j
-        const int a = j & 1;
-        if (!tc::mbar_wait(a1_full(a), (j >> 1) & 1, WAIT_LIMIT)) return false;
+        const int b = j & 1, a = j % G5_NACC;
+        if (!tc::mbar_wait(a1_full(b), (j >> 1) & 1, WAIT_LIMIT)) return false;
         tc::fence_after();
-        const uint32_t a1 = sbase + G5_OFF_A1 + a * G5_A1;
+        const uint32_t a1 = sbase + G5_OFF_A1 + b * G5_A1;
         for (int s = 0; s < 5; ++s)
-          tc::mma_bf16(tmem + a * 256 + 128, tc::make_desc(a1 + s * 256, 128, 1280),
+          tc::mma_bf16(tmem + a * G5_ACC + 128, tc::make_desc(a1 + s * 256, 128, 1280),
                        tc::make_desc(bfx + s * 256, 128, 1280), id1, s > 0);
         tc::mma_commit(g1_full(a));
         return true;
@@ -725,13 +730,16 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       int it = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
-        const int s = it % G5_STAGES, a = it & 1;
+        const int s = it % G5_STAGES, a = it % G5_NACC;
         if (!tc::mbar_wait(CONV ? conv_full(s) : full(s), (it / G5_STAGES) & 1, WAIT_LIMIT)) { ok = false; break; }
-        if (it >= 2 && !tc::mbar_wait(acc_empty(a), ((it >> 1) - 1) & 1, WAIT_LIMIT)) { ok = false; break; }
+        if (it >= G5_NACC && !tc::mbar_wait(acc_empty(a), ((it / G5_NACC) - 1) & 1, WAIT_LIMIT)) {
+          ok = false;
+          break;
+        }
         tc::fence_after();
         const uint32_t ax = sbase + s * G5_STAGE, bt = ax + G5_XB;
         for (int yy = 0; yy < G5_ROWS; ++yy) {
-          const uint32_t d = tmem + a * 256 + yy * 32;
+          const uint32_t d = tmem + a * G5_ACC + yy * 32;
           if (LIFT) {  // lift: [x][16 inputs] . [32][16]^T
             tc::mma_bf16(d, tc::make_desc(ax + yy * 2560, 128, 256), tc::make_desc(bw, 128, 256), id5, 0);
             continue;
@@ -780,19 +788,41 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
     float bs[32];
 #pragma unroll
     for (int o = 0; o < 32; ++o) bs[o] = bias[o];
+    // phase 2 of unit j (window rows from wy0): its G1 result -> T1, then free its set
+    auto phase2 = [&](int j, size_t wy0) -> bool {
+      const int a = j % G5_NACC;
+      if (!tc::mbar_wait(g1_full(a), (j / G5_NACC) & 1, WAIT_LIMIT)) return false;
+      tc::fence_after();
+      // lanes (yy = q, c = lane), columns (kx,ri) hf*16 .. hf*16+15
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + 128 + hf * 16, v);
+      const int y = (int)(wy0 % 80) + q;
+      bf16* base = T1 + (wy0 / 80) * (size_t)(160 * 512);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int col = hf * 16 + i, kx = col >> 1, ri = col & 1;
+        base[(ri * 80 + y) * 512 + kx * 32 + lane] = __float2bfloat16_rn(v[i]);
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty(a));
+      return true;
+    };
     int it = 0;
+    bool ok = true;
+    size_t prev_wy0 = 0;
     for (int u = blockIdx.x; u < total; u += gridDim.x, ++it) {
-      const int a = it & 1;
-      if (*abort_flag || !tc::mbar_wait(g5_full(a), (it >> 1) & 1, WAIT_LIMIT)) { fail(); break; }
+      const int a = it % G5_NACC;
+      if (*abort_flag || !tc::mbar_wait(g5_full(a), (it / G5_NACC) & 1, WAIT_LIMIT)) { ok = false; break; }
       tc::fence_after();
       const size_t wy0 = (size_t)(u / UPW) * 80 + (u % UPW) * G5_ROWS;
-      uint8_t* a1 = smem + G5_OFF_A1 + a * G5_A1;
+      uint8_t* a1 = smem + G5_OFF_A1 + (it & 1) * G5_A1;
       if (q < 3) {
         const int x = q * 32 + lane;
         for (int yy = hf * 2; yy < hf * 2 + 2; ++yy) {
           float v[32];
-          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * 256 + yy * 32, v);
-          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * 256 + yy * 32 + 16, v + 16);
+          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + yy * 32, v);
+          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + yy * 32 + 16, v + 16);
           if (x < 80) {
             uint32_t p[16];
 #pragma unroll
@@ -833,27 +863,20 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
           }
         }
       }
-      if (!last) {
-        tc::fence_async_smem();  // A1 written by this warp -> visible to the tensor core
+      if (last) {
+        tc::fence_before();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(a1_full(a));
-        if (!tc::mbar_wait(g1_full(a), (it >> 1) & 1, WAIT_LIMIT)) { fail(); break; }
-        tc::fence_after();
-        // lanes (yy = q, c = lane), columns (kx,ri) hf*16 .. hf*16+15
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * 256 + 128 + hf * 16, v);
-        const int y = (int)(wy0 % 80) + q;
-        bf16* base = T1 + (wy0 / 80) * (size_t)(160 * 512);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int col = hf * 16 + i, kx = col >> 1, ri = col & 1;
-          base[(ri * 80 + y) * 512 + kx * 32 + lane] = __float2bfloat16_rn(v[i]);
-        }
+        if (lane == 0) tc::mbar_arrive(acc_empty(a));
+        continue;
       }
-      tc::fence_before();
+      tc::fence_async_smem();  // A1 written by this warp -> visible to the tensor core
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(acc_empty(a));
+      if (lane == 0) tc::mbar_arrive(a1_full(it & 1));
+      if (it >= 1 && !phase2(it - 1, prev_wy0)) { ok = false; break; }
+      prev_wy0 = wy0;
     }
+    if (ok && !last && it >= 1 && !phase2(it - 1, prev_wy0)) ok = false;
+    if (!ok) fail();
   }
   tc::fence_before();
   __syncthreads();
