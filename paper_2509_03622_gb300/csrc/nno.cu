@@ -501,7 +501,9 @@ constexpr uint32_t G5_OFF_A1 = G5_STAGES * G5_STAGE;             // after the ri
 constexpr uint32_t G5_OFF_GX = G5_OFF_A1 + 2 * G5_A1;
 constexpr uint32_t G5_OFF_W = G5_OFF_GX + 128 * 32 * 2;
 constexpr uint32_t G5_OFF_FX = G5_OFF_W + 32 * 32 * 2;
-constexpr uint32_t G5_OFF_BAR = G5_OFF_FX + 32 * 80 * 2;
+constexpr uint32_t G5_OFF_ONE = G5_OFF_FX + 32 * 80 * 2;         // [128][16] K-major: 1, 1, 0 ...
+constexpr uint32_t G5_OFF_BIAS = G5_OFF_ONE + 128 * 16 * 2;      // [32][16] K-major: bias hi, lo, 0 ...
+constexpr uint32_t G5_OFF_BAR = G5_OFF_BIAS + 32 * 16 * 2;
 constexpr int G5_NACC = 3;                                        // TMEM accumulator sets
 constexpr uint32_t G5_ACC = 160;                                  // TMEM columns per set
 constexpr uint32_t G5_NBAR = 3 * G5_STAGES + 3 * G5_NACC + 2;
@@ -637,6 +639,18 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       const int t8 = c & 7, rest = c >> 3, kc = rest % 10, rg = rest / 10;
       tc::cp_async16(smem + G5_OFF_FX + (rg * 10 + kc) * 128 + t8 * 16, Fx + (rg * 8 + t8) * 80 + kc * 8, true);
     }
+  // the bias enters the accumulator through one more MMA: a ones column pair
+  // times the bias split into two BF16 parts (hi + lo carry it to ~2^-16)
+  for (int c = tid; c < 128 * 16; c += G5_THREADS) {
+    const int r = c >> 4, k = c & 15;
+    *reinterpret_cast<bf16*>(smem + G5_OFF_ONE + tc::kmaj_off(r, k, 16)) = __float2bfloat16_rn(k < 2 ? 1.f : 0.f);
+  }
+  for (int c = tid; c < 32 * 16; c += G5_THREADS) {
+    const int o = c >> 4, k = c & 15;
+    const bf16 hi = __float2bfloat16_rn(bias[o]);
+    const float v = k == 0 ? bias[o] : k == 1 ? bias[o] - __bfloat162float(hi) : 0.f;
+    *reinterpret_cast<bf16*>(smem + G5_OFF_BIAS + tc::kmaj_off(o, k, 16)) = __float2bfloat16_rn(v);
+  }
   tc::cp_async_wait_all();
   if (tid == 0) {
     for (int s = 0; s < G5_STAGES; ++s) { tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); }
@@ -740,13 +754,15 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
         const uint32_t ax = sbase + s * G5_STAGE, bt = ax + G5_XB;
         for (int yy = 0; yy < G5_ROWS; ++yy) {
           const uint32_t d = tmem + a * G5_ACC + yy * 32;
+          tc::mma_bf16(d, tc::make_desc(sbase + G5_OFF_ONE, 128, 256), tc::make_desc(sbase + G5_OFF_BIAS, 128, 256),
+                       id5, 0);  // bias
           if (LIFT) {  // lift: [x][16 inputs] . [32][16]^T
-            tc::mma_bf16(d, tc::make_desc(ax + yy * 2560, 128, 256), tc::make_desc(bw, 128, 256), id5, 0);
+            tc::mma_bf16(d, tc::make_desc(ax + yy * 2560, 128, 256), tc::make_desc(bw, 128, 256), id5, 1);
             continue;
           }
           for (int k = 0; k < 2; ++k)
             tc::mma_bf16(d, tc::make_desc(ag + k * 256, 128, 512), tc::make_desc(bt + yy * 2048 + k * 256, 128, 512),
-                         id5, k > 0);
+                         id5, 1);
           for (int k = 0; k < 2; ++k)
             tc::mma_bf16(d, tc::make_desc(ax + yy * G5_XT + k * 256, 128, 512), tc::make_desc(bw + k * 256, 128, 512),
                          id5, 1);
@@ -785,9 +801,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
     float qi[32];
 #pragma unroll
     for (int o = 0; o < 32; ++o) qi[o] = FP8 ? qinv[o] : 1.f;
-    float bs[32];
-#pragma unroll
-    for (int o = 0; o < 32; ++o) bs[o] = bias[o];
+    const __nv_bfloat162 slope = __floats2bfloat162_rn(LEAK, LEAK);
     // phase 2 of unit j (window rows from wy0): its G1 result -> T1, then free its set
     auto phase2 = [&](int j, size_t wy0) -> bool {
       const int a = j % G5_NACC;
@@ -826,10 +840,10 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
           if (x < 80) {
             uint32_t p[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              float e0 = v[2 * i] + bs[2 * i], e1 = v[2 * i + 1] + bs[2 * i + 1];
-              if (!LIFT && !last) { e0 = leaky(e0); e1 = leaky(e1); }
-              p[i] = pack2(e0, e1);
+            for (int i = 0; i < 16; ++i) {  // bias already in the accumulator; leaky-ReLU on BF16 pairs
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+              if (!LIFT && !last) h2 = __hmax2(h2, __hmul2(h2, slope));
+              p[i] = *reinterpret_cast<uint32_t*>(&h2);
             }
             if (FP8) {  // E4M3 activations, 2 x 16 channels
               uint32_t q8[8];
@@ -839,7 +853,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                   const int c = 4 * i + t;
-                  float ev = v[c] + bs[c];
+                  float ev = v[c];
                   if (!LIFT && !last) ev = leaky(ev);
                   e[t] = ev * qi[c];
                 }
