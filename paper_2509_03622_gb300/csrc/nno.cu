@@ -23,6 +23,8 @@
 // mapped to the contiguous output dimension (coalesced stores).
 #include <math.h>
 #include <string.h>
+#include <algorithm>
+#include <cstring>
 #include <vector>
 #include <cuda_fp8.h>
 #include "nno.cuh"
@@ -904,90 +906,77 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
 // Projection, warp-specialised and persistent over units (window, 128
 // consecutive pixels; the tiled activation makes that one contiguous 8 KB
 // operand tile):
-//   H[p][h]  = X[p][:] P1[h][:]^T + p1b[h]     (MMA 1; the bias enters as a
-//              K-column of ones in A against p1b in B)
-//   O[p][.]  = leaky(H[p][:]) P2[.][:]^T       (MMA 2, N = 16 of which 2 used)
+//   G[p][h]  = X[p][:] P1[h][:]^T                (tensor cores), H = G + p1b
+//   O[p][j]  = sum_h P2[j][h] leaky(H[p][h])
+//            = 0.01 sum_h P2[j][h] G[p][h] + 0.99 sum_h P2[j][h] max(G[p][h], -p1b[h])
+//              + c_j,   c_j = sum_h P2[j][h] p1b[h]
 //   z        = (O + p2b) * rho * scale, written to the window's core in the
 //              global field (restricted prolongation) or to a per-window array.
-// Roles: warp 0 producer (bulk copies into a PJ_STAGES ring), warp 1 issues
-// the first MMA and warp 2 the second (separate threads, so neither waits
-// for the other's operands), warps 4..11 epilogue (leaky-ReLU of H in packed BF16
-// into the second MMA's A tile, then the output).  Four TMEM accumulators of
-// 128 columns (MMA 2 reuses the first 16 columns of its unit's accumulator
-// once H has been read).  The epilogue is two groups of four warps taking
-// alternate units, each software-pipelined: it prepares its next unit's
-// second operand while the previous unit's second MMA runs.
-constexpr int PJ_STAGES = 6;
+// The linear part of the leaky-ReLU is folded into the MMA as two more output
+// columns (rows 0.01 P2 P1 of B, N = 144); the rectified part is an FP32
+// dot product in the epilogue with 0.99 P2 and -p1b passed as kernel
+// parameters (constant-bank operands), and the constants c_j join p2b.  A second tensor-core
+// layer with N = 16 spent most of its time moving its 32 KB operand tile
+// through shared memory per 128 pixels.
+// Roles: warp 0 producer (bulk copies into a PJ_STAGES ring), warp 1 MMA
+// issuer, warp 3 FP8 -> BF16 converter (FP8 activations only), warps 4..15
+// epilogue in PJ_GROUPS groups of four taking units in turn.  PJ_ACC TMEM
+// accumulators of 144 columns (160 apart); an accumulator is released as soon
+// as its unit's columns have been read.
+constexpr int PJ_STAGES = 8;
 constexpr uint32_t PJ_A8 = 128 * 32;                      // the X tile in FP8 (staging)
-constexpr int PJ_THREADS = 384;
+constexpr int PJ_GROUPS = 3;
+constexpr int PJ_THREADS = 128 + 128 * PJ_GROUPS;
+constexpr int PJ_N = 144;                                 // hidden units + 2 linear outputs, padded
 constexpr uint32_t PJ_AT = 128 * 32 * 2;                  // X tile (BF16)
 constexpr uint32_t PJ_ST = PJ_AT + PJ_A8;                 // stage: BF16 tile + FP8 staging
-constexpr uint32_t PJ_A2 = 128 * 128 * 2;                 // leaky(H) tile, K-major
-constexpr int PJ_NA2 = 4;                                 // leaky(H) buffers (2 per epilogue group)
-constexpr uint32_t PJ_OFF_A2 = PJ_STAGES * PJ_ST;
-constexpr uint32_t PJ_OFF_B1 = PJ_OFF_A2 + PJ_NA2 * PJ_A2;  // [128 h][48 k]: P1 | p1b | 0
-constexpr uint32_t PJ_OFF_ONE = PJ_OFF_B1 + 128 * 48 * 2; // [128 p][16 k]: 1 | 0
-constexpr uint32_t PJ_OFF_B2 = PJ_OFF_ONE + 128 * 16 * 2; // [16 n][128 h]: P2 rows 0, 1
-constexpr uint32_t PJ_OFF_BAR = PJ_OFF_B2 + 16 * 128 * 2;
-constexpr int PJ_ACC = 4;
-constexpr uint32_t PJ_NBAR = 3 * PJ_STAGES + 4 * PJ_ACC;
+constexpr uint32_t PJ_OFF_B1 = PJ_STAGES * PJ_ST;         // [144 n][32 k]: P1x
+constexpr uint32_t PJ_OFF_BAR = PJ_OFF_B1 + PJ_N * 32 * 2;
+constexpr int PJ_ACC = 3;
+constexpr uint32_t PJ_ACC_COLS = 160;
+constexpr uint32_t PJ_NBAR = 3 * PJ_STAGES + 2 * PJ_ACC;
 constexpr uint32_t PJ_SMEM = PJ_OFF_BAR + PJ_NBAR * 8 + 16;
 static_assert(PJ_SMEM <= 227 * 1024, "proj shared memory");
+static_assert(PJ_ACC * PJ_ACC_COLS <= 512, "proj TMEM columns");
 
 struct ProjArgs {
-  const bf16* X; const bf16* P1; const float* p1b; const float* P2; float p2b0, p2b1;
+  const bf16* X; const bf16* P1x;
+  float p2w[2][128];  // 0.99 P2
+  float nb[128];      // -p1b
+  float p2b0, p2b1;   // p2b + sum_h P2[j][h] p1b[h]
   const float* rho; const double* scale; const int* win_id; const double* scale_win;
   float2* z_global; float2* e_win; int nx, ny, nwx;
   const int2* wtab; const ProbGeom* ptab;
 };
 
 // FP8: X holds E4M3 activations; the tile is bulk-copied as FP8, converted to
-// BF16 by warp 3 and multiplied by P1 diag(s) (P.P1 then points at it).
+// BF16 by warp 3 and multiplied by P1x diag(s) (P.P1x then points at it).
 template <bool FP8>
-__global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int total, int* err) {
+__global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(const __grid_constant__ ProjArgs P, int total, int* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const uint32_t sbase = tc::smem_u32(smem);
   const uint32_t bar = sbase + PJ_OFF_BAR;
   auto full = [&](int s) { return bar + 8u * s; };
   auto empty = [&](int s) { return bar + 8u * (PJ_STAGES + s); };
-  auto m1_full = [&](int a) { return bar + 8u * (2 * PJ_STAGES + a); };
-  auto m2_full = [&](int a) { return bar + 8u * (2 * PJ_STAGES + PJ_ACC + a); };
-  auto a2_full = [&](int a) { return bar + 8u * (2 * PJ_STAGES + 2 * PJ_ACC + a); };
-  auto acc_empty = [&](int a) { return bar + 8u * (2 * PJ_STAGES + 3 * PJ_ACC + a); };
-  auto conv_full = [&](int s) { return bar + 8u * (2 * PJ_STAGES + 4 * PJ_ACC + s); };
+  auto conv_full = [&](int s) { return bar + 8u * (2 * PJ_STAGES + s); };
+  auto m1_full = [&](int a) { return bar + 8u * (3 * PJ_STAGES + a); };
+  auto acc_empty = [&](int a) { return bar + 8u * (3 * PJ_STAGES + PJ_ACC + a); };
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + PJ_OFF_BAR + PJ_NBAR * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + PJ_OFF_BAR + PJ_NBAR * 8 + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int UPW = NPIX / 128;  // 50 units per window
   if ((int)blockIdx.x >= total) return;
   // constant operands
-  for (int c = tid; c < 128 * 4; c += PJ_THREADS) {  // P1 -> B1 k-groups 0..3
+  for (int c = tid; c < PJ_N * 4; c += PJ_THREADS) {  // P1x -> B1, K-major tiles
     const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-    tc::cp_async16(smem + PJ_OFF_B1 + (rg * 6 + kc) * 128 + t8 * 16, P.P1 + (rg * 8 + t8) * 32 + kc * 8, true);
-  }
-  for (int c = tid; c < 128 * 16; c += PJ_THREADS) {  // B1 k = 32..47: p1b then zeros
-    const int n = c >> 4, k = 32 + (c & 15);
-    *reinterpret_cast<bf16*>(smem + PJ_OFF_B1 + tc::kmaj_off(n, k, 48)) =
-        __float2bfloat16_rn(k == 32 ? P.p1b[n] : 0.f);
-  }
-  for (int c = tid; c < 128 * 16; c += PJ_THREADS) {  // ones column of A
-    const int r = c >> 4, k = c & 15;
-    *reinterpret_cast<bf16*>(smem + PJ_OFF_ONE + tc::kmaj_off(r, k, 16)) = __float2bfloat16_rn(k == 0 ? 1.f : 0.f);
-  }
-  for (int c = tid; c < 16 * 128; c += PJ_THREADS) {  // B2: rows 0, 1 = P2
-    const int n = c >> 7, k = c & 127;
-    *reinterpret_cast<bf16*>(smem + PJ_OFF_B2 + tc::kmaj_off(n, k, 128)) =
-        __float2bfloat16_rn(n < 2 ? P.P2[n * 128 + k] : 0.f);
+    tc::cp_async16(smem + PJ_OFF_B1 + (rg * 4 + kc) * 128 + t8 * 16, P.P1x + (rg * 8 + t8) * 32 + kc * 8, true);
   }
   tc::cp_async_wait_all();
   if (tid == 0) {
     for (int s = 0; s < PJ_STAGES; ++s) {
       tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); tc::mbar_init(conv_full(s), 1);
     }
-    for (int a = 0; a < PJ_ACC; ++a) {
-      tc::mbar_init(m1_full(a), 1); tc::mbar_init(m2_full(a), 1);
-      tc::mbar_init(a2_full(a), 4); tc::mbar_init(acc_empty(a), 4);
-    }
+    for (int a = 0; a < PJ_ACC; ++a) { tc::mbar_init(m1_full(a), 1); tc::mbar_init(acc_empty(a), 4); }
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -1020,37 +1009,20 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int tot
         if (!tc::mbar_wait(full(j % PJ_STAGES), (j / PJ_STAGES) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
     }
   } else if (warp == 1) {
-    if (lane == 0) {  // MMA 1 issuer: H = X P1^T + p1b, runs ahead by PJ_ACC units
-      constexpr uint32_t id1 = tc::idesc_bf16(128, false, false);
-      const uint32_t b1 = sbase + PJ_OFF_B1, one = sbase + PJ_OFF_ONE;
+    if (lane == 0) {  // MMA issuer: [G | linear part] = X P1x^T
+      constexpr uint32_t id1 = tc::idesc_bf16(PJ_N, false, false);
+      const uint32_t b1 = sbase + PJ_OFF_B1;
       int it = 0;
       for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
         const int s = it % PJ_STAGES, a = it % PJ_ACC;
         if (!tc::mbar_wait(FP8 ? conv_full(s) : full(s), (it / PJ_STAGES) & 1, WAIT_LIMIT)) { fail(); break; }
         if (it >= PJ_ACC && !tc::mbar_wait(acc_empty(a), ((it / PJ_ACC) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
         tc::fence_after();
-        const uint32_t ax = sbase + s * PJ_ST, d = tmem + a * 128;
-        tc::mma_bf16(d, tc::make_desc(ax, 128, 512), tc::make_desc(b1, 128, 768), id1, 0);
-        tc::mma_bf16(d, tc::make_desc(ax + 256, 128, 512), tc::make_desc(b1 + 256, 128, 768), id1, 1);
-        tc::mma_bf16(d, tc::make_desc(one, 128, 256), tc::make_desc(b1 + 512, 128, 768), id1, 1);
+        const uint32_t ax = sbase + s * PJ_ST, d = tmem + a * PJ_ACC_COLS;
+        tc::mma_bf16(d, tc::make_desc(ax, 128, 512), tc::make_desc(b1, 128, 512), id1, 0);
+        tc::mma_bf16(d, tc::make_desc(ax + 256, 128, 512), tc::make_desc(b1 + 256, 128, 512), id1, 1);
         tc::mma_commit(empty(s));
         tc::mma_commit(m1_full(a));
-      }
-    }
-  } else if (warp == 2) {
-    if (lane == 0) {  // MMA 2 issuer: O = leaky(H) P2^T, as soon as a unit's A2 tile is ready
-      constexpr uint32_t id2 = tc::idesc_bf16(16, false, false);
-      const uint32_t b2 = sbase + PJ_OFF_B2;
-      int j = 0;
-      for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++j) {
-        const int a = j % PJ_ACC;
-        if (!tc::mbar_wait(a2_full(a), (j / PJ_ACC) & 1, WAIT_LIMIT)) { fail(); break; }
-        tc::fence_after();
-        const uint32_t a2 = sbase + PJ_OFF_A2 + (j % PJ_NA2) * PJ_A2;
-        for (int k = 0; k < 8; ++k)
-          tc::mma_bf16(tmem + a * 128, tc::make_desc(a2 + k * 256, 128, 2048), tc::make_desc(b2 + k * 256, 128, 2048),
-                       id2, k > 0);
-        tc::mma_commit(m2_full(a));
       }
     }
   } else if (warp == 3) {
@@ -1074,98 +1046,64 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(ProjArgs P, int tot
         if (lane == 0) tc::mbar_arrive(conv_full(s));
       }
     }
-  } else if (warp >= 4) {  // epilogue: group grp takes units it = grp, grp + 2, ...
+  } else if (warp >= 4) {  // epilogue: group grp takes units it = grp, grp + PJ_GROUPS, ...
     const int q = warp & 3, grp = (warp - 4) >> 2;
     const int px = q * 32 + lane;
-    const __nv_bfloat162 slope = __floats2bfloat162_rn(LEAK, LEAK);
-    // leaky(H) of unit j into its A2 buffer
-    auto stage1 = [&](int j) -> bool {
-      const int a = j % PJ_ACC;
-      if (*abort_flag || !tc::mbar_wait(m1_full(a), (j / PJ_ACC) & 1, WAIT_LIMIT)) return false;
-      tc::fence_after();
-      uint8_t* a2 = smem + PJ_OFF_A2 + (j % PJ_NA2) * PJ_A2;
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {  // 32 hidden units per round
-        float v[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * 128 + g * 32, v);
-        uint32_t p[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-          h2 = __hmax2(h2, __hmul2(h2, slope));
-          p[i] = *reinterpret_cast<uint32_t*>(&h2);
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          *reinterpret_cast<uint4*>(a2 + ((px >> 3) * 16 + g * 4 + t) * 128 + (px & 7) * 16) =
-              make_uint4(p[4 * t], p[4 * t + 1], p[4 * t + 2], p[4 * t + 3]);
-      }
-      tc::fence_before();
-      tc::fence_async_smem();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(a2_full(a));
-      return true;
-    };
-    // per-unit output parameters, loaded one unit ahead of their use
-    struct OutP { float2* dst; float rho; double sc, sw; int ld, x0, y0, cx0, cy0; };
-    auto prep = [&](int u) -> OutP {
-      OutP o;
+    int it = grp;
+    for (int u = blockIdx.x + grp * gridDim.x; u < total; u += PJ_GROUPS * gridDim.x, it += PJ_GROUPS) {
+      // this unit's output parameters (loads in flight while the MMA runs)
       const int b = u / UPW;
       int w = P.win_id ? P.win_id[b] : b;
       int gnx = P.nx, gny = P.ny, gnwx = P.nwx;
-      const double* sc = P.scale;
-      o.dst = P.z_global;
+      const double* scp = P.scale;
+      float2* dst = P.z_global;
       if (P.ptab) {
         const int2 e = P.wtab[b];
         const ProbGeom& G = P.ptab[e.x];
-        w = e.y; gnx = G.nx; gny = G.ny; gnwx = G.nwx; sc = G.scale; o.dst = G.z;
+        w = e.y; gnx = G.nx; gny = G.ny; gnwx = G.nwx; scp = G.scale; dst = G.z;
       }
-      o.rho = P.rho[b];  // raw loads; combined at first use in stage2
-      o.sc = sc ? *sc : 1.0;
-      o.sw = P.scale_win ? P.scale_win[b] : 1.0;
-      if (P.e_win) {  // per-window output: x0 = -1 marks it
-        o.dst = P.e_win + (size_t)b * NPIX;
-        o.x0 = -1; o.ld = 80; o.y0 = o.cx0 = o.cy0 = 0;
-      } else {
-        const int wa = w % gnwx, wb = w / gnwx;
-        o.ld = gnx;
-        o.x0 = min(max(FDFD_CORE * wa - FDFD_OVL, 0), gnx - FDFD_WIN);
-        o.y0 = min(max(FDFD_CORE * wb - FDFD_OVL, 0), gny - FDFD_WIN);
-        o.cx0 = FDFD_CORE * wa; o.cy0 = FDFD_CORE * wb;
-      }
-      return o;
-    };
-    // output of unit j (its 128 pixels of window entry u / UPW)
-    auto stage2 = [&](int j, int u, const OutP& o) -> bool {
-      const int a = j % PJ_ACC;
-      if (!tc::mbar_wait(m2_full(a), (j / PJ_ACC) & 1, WAIT_LIMIT)) return false;
+      const float rho = P.rho[b];
+      const double sc = scp ? *scp : 1.0;
+      const double sw = P.scale_win ? P.scale_win[b] : 1.0;
+      const int a = it % PJ_ACC;
+      if (*abort_flag || !tc::mbar_wait(m1_full(a), (it / PJ_ACC) & 1, WAIT_LIMIT)) { fail(); break; }
       tc::fence_after();
-      float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * 128, v);
-      const int m = (u % UPW) * 128 + px;
-      const float f = o.rho * (float)o.sc * (float)o.sw;
-      const float2 val = make_float2((v[0] + P.p2b0) * f, (v[1] + P.p2b1) * f);
-      if (o.x0 < 0) {
-        o.dst[m] = val;
-      } else {  // restricted prolongation: only the window's 64 x 64 core
-        const int gx = o.x0 + m % 80, gy = o.y0 + m / 80;
-        if (gx >= o.cx0 && gx < o.cx0 + FDFD_CORE && gy >= o.cy0 && gy < o.cy0 + FDFD_CORE)
-          o.dst[(size_t)gy * o.ld + gx] = val;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + a * PJ_ACC_COLS;
+      float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
+      float lin[16];
+      tc::tmem_ld16(trow + 128, lin);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {  // 32 hidden units per TMEM load
+        float v[32];
+        tc::tmem_ld32(trow + g * 32, v);
+        if (g == 3) {  // columns read: the MMA may reuse them
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(acc_empty(a));
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float r = fmaxf(v[i], P.nb[g * 32 + i]);
+          s0[i & 3] = fmaf(P.p2w[0][g * 32 + i], r, s0[i & 3]);
+          s1[i & 3] = fmaf(P.p2w[1][g * 32 + i], r, s1[i & 3]);
+        }
       }
-      tc::fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(acc_empty(a));
-      return true;
-    };
-    int it = grp, prev = -1, prev_u = -1;
-    OutP prev_o{};
-    for (int u = blockIdx.x + grp * gridDim.x; u < total; u += 2 * gridDim.x, it += 2) {
-      const OutP cur = prep(u);
-      if (!stage1(it)) { fail(); prev = -1; break; }
-      if (prev >= 0 && !stage2(prev, prev_u, prev_o)) { fail(); prev = -1; break; }
-      prev = it; prev_u = u; prev_o = cur;
+      const float f = rho * (float)sc * (float)sw;
+      const float2 val = make_float2(((s0[0] + s0[1]) + (s0[2] + s0[3]) + lin[0] + P.p2b0) * f,
+                                     ((s1[0] + s1[1]) + (s1[2] + s1[3]) + lin[1] + P.p2b1) * f);
+      const int m = (u % UPW) * 128 + px;
+      if (P.e_win) {
+        P.e_win[(size_t)b * NPIX + m] = val;
+      } else {  // restricted prolongation: only the window's 64 x 64 core
+        const int wa = w % gnwx, wb = w / gnwx;
+        const int x0 = min(max(FDFD_CORE * wa - FDFD_OVL, 0), gnx - FDFD_WIN);
+        const int y0 = min(max(FDFD_CORE * wb - FDFD_OVL, 0), gny - FDFD_WIN);
+        const int gx = x0 + m % 80, gy = y0 + m / 80;
+        if (gx >= FDFD_CORE * wa && gx < FDFD_CORE * wa + FDFD_CORE && gy >= FDFD_CORE * wb &&
+            gy < FDFD_CORE * wb + FDFD_CORE)
+          dst[(size_t)gy * gnx + gx] = val;
+      }
     }
-    if (prev >= 0 && !*abort_flag && !stage2(prev, prev_u, prev_o)) fail();
   }
   tc::fence_before();
   __syncthreads();
@@ -1294,19 +1232,33 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
     if ((rc = up(&W->bias[bl], std::vector<float>(p, p + 32), bytes))) return rc;
     p += 32;
   }
-  if ((rc = up(&W->P1, to_bf16(std::vector<float>(p, p + 128 * 32)), bytes))) return rc;
-  p += 128 * 32;
-  if ((rc = up(&W->p1b, std::vector<float>(p, p + 128), bytes))) return rc;
-  p += 128;
-  if ((rc = up(&W->P2, std::vector<float>(p, p + 256), bytes))) return rc;
-  p += 256;
-  W->p2b[0] = p[0];
-  W->p2b[1] = p[1];
+  {  // projection: P1 extended by the leaky-ReLU's linear part 0.01 P2 P1; the bias is taken in the epilogue
+    const float* p1 = p;
+    const float* pb = p + 128 * 32;
+    const float* p2 = pb + 128;
+    std::vector<float> P1x(144 * 32, 0.f);
+    std::copy(p1, p1 + 128 * 32, P1x.begin());
+    double cb[2] = {0.0, 0.0};
+    for (int j = 0; j < 2; ++j) {
+      for (int c = 0; c < 32; ++c) {
+        double acc = 0.0;
+        for (int hh = 0; hh < 128; ++hh) acc += (double)p2[j * 128 + hh] * p1[hh * 32 + c];
+        P1x[(128 + j) * 32 + c] = (float)(0.01 * acc);
+      }
+      for (int hh = 0; hh < 128; ++hh) cb[j] += (double)p2[j * 128 + hh] * pb[hh];
+    }
+    for (int i = 0; i < 256; ++i) W->p2w[i] = 0.99f * p2[i];
+    for (int hh = 0; hh < 128; ++hh) W->nb[hh] = -pb[hh];
+    if ((rc = up(&W->P1, to_bf16(P1x), bytes))) return rc;
+    p += 128 * 32 + 128 + 256;
+    W->p2b[0] = (float)(p[0] + cb[0]);
+    W->p2b[1] = (float)(p[1] + cb[1]);
+  }
   return FDFD_OK;
 }
 
 void nno_free_weights(NnoWeights* W) {
-  void* ptrs[] = {W->lift_w, W->lift_b, W->Fx, W->Fy, W->Gy, W->Gx, W->P1, W->p1b, W->P2, W->qinv, W->P18};
+  void* ptrs[] = {W->lift_w, W->lift_b, W->Fx, W->Fy, W->Gy, W->Gx, W->P1, W->qinv, W->P18};
   for (void* q : ptrs) if (q) cudaFree(q);
   for (int b = 0; b < 4; ++b) {
     if (W->R[b]) cudaFree(W->R[b]);
@@ -1482,8 +1434,14 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
       CK(cudaFuncSetAttribute(proj_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PJ_SMEM));
       pj_cap = persistent_grid((const void*)proj_kernel<false>, PJ_THREADS, PJ_SMEM, 512);
     }
-    ProjArgs pa{k->X, W->fp8 ? W->P18 : W->P1, W->p1b, W->P2, W->p2b[0], W->p2b[1], k->rho, out.scale, in.win_id, out.scale_win,
-                out.z_global, out.e_win, g.nx, g.ny, g.nwx, in.wtab, in.ptab};
+    ProjArgs pa;
+    pa.X = k->X; pa.P1x = W->fp8 ? W->P18 : W->P1;
+    memcpy(pa.p2w, W->p2w, sizeof(pa.p2w));
+    memcpy(pa.nb, W->nb, sizeof(pa.nb));
+    pa.p2b0 = W->p2b[0]; pa.p2b1 = W->p2b[1];
+    pa.rho = k->rho; pa.scale = out.scale; pa.win_id = in.win_id; pa.scale_win = out.scale_win;
+    pa.z_global = out.z_global; pa.e_win = out.e_win; pa.nx = g.nx; pa.ny = g.ny; pa.nwx = g.nwx;
+    pa.wtab = in.wtab; pa.ptab = in.ptab;
     const int pj_total = n * (NPIX / 128);
     ProfScope ps(h, 14, 1);
     const int pj_grid = pj_total < pj_cap ? pj_total : pj_cap;
@@ -1535,9 +1493,16 @@ int nno_enable_fp8(NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInp
   }
   {
     const float* p1 = blob + 32 * 15 + 32 + 4 * blk;
-    std::vector<float> ps(128 * 32);
+    const float* p2 = p1 + 128 * 32 + 128;
+    std::vector<float> ps(144 * 32, 0.f);  // the extended P1 (as at upload) times diag(s[4])
     for (int hh = 0; hh < 128; ++hh)
       for (int c = 0; c < 32; ++c) ps[hh * 32 + c] = p1[hh * 32 + c] * sc[4][c];
+    for (int j = 0; j < 2; ++j)
+      for (int c = 0; c < 32; ++c) {
+        double acc = 0.0;
+        for (int hh = 0; hh < 128; ++hh) acc += (double)p2[j * 128 + hh] * p1[hh * 32 + c];
+        ps[(128 + j) * 32 + c] = (float)(0.01 * acc) * sc[4][c];
+      }
     if ((rc = up(&W->P18, to_bf16(ps), bytes))) return rc;
   }
   if ((rc = up(&W->qinv, std::vector<float>(&qi[0][0], &qi[0][0] + 5 * 32), bytes))) return rc;

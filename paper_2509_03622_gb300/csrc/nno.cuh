@@ -15,10 +15,10 @@ struct NnoWeights {
   bf16* Gx = nullptr;       // [128 x][32 (kx,ri)]          inverse real DFT along x (1/80), rows >= 80 zero
   bf16* W[4] = {};          // [32 o][32 c]
   float* bias[4] = {};      // [32]
-  bf16* P1 = nullptr;       // [128][32]
-  float* p1b = nullptr;     // [128]
-  float* P2 = nullptr;      // [2][128]
-  float p2b[2] = {0.f, 0.f};
+  bf16* P1 = nullptr;       // [144][32]: P1, then 0.01 P2 P1 (the leaky-ReLU's linear part), 0
+  float p2w[256] = {};      // 0.99 P2 [2][128]  (host copies: kernel parameters)
+  float nb[128] = {};       // -p1b
+  float p2b[2] = {0.f, 0.f};  // p2b + P2 p1b
   // FP8 activations (precision pattern): the activation entering block b
   // (b = 0..3) and the projection (b = 4) is stored as E4M3 q with
   // x = q * s[b][c] (power-of-two per-channel scales from a calibration pass);
@@ -26,7 +26,7 @@ struct NnoWeights {
   bool fp8 = false;
   float* qinv = nullptr;    // [5][32]  1 / s[b][c], used by the writers
   bf16* W8[4] = {};         // [32 o][32 c]  W[b] diag(s[b])
-  bf16* P18 = nullptr;      // [128][32]     P1 diag(s[4])
+  bf16* P18 = nullptr;      // [144][32]     P1 (extended as above) diag(s[4])
 };
 
 // Rows of the spectrum per mode: the windows rounded up to a whole 8-row
