@@ -92,7 +92,7 @@ class Clocks:
 # channels = 64 B per pixel, complex64 fields = 8 B per cell).
 WIN_BYTES = {
     "nno_pack": 6400 * 8,                     # residual in (window RMS)
-    "nno_lift": 6400 * (8 + 4 + 64) + 160 * 512 * 2,  # residual + eps in, activation and block 0's T1 out
+    "nno_lift": 6400 * (8 + 4) + 160 * 512 * 2,  # residual + eps in, block 0's T1 out (X is not stored)
     "nno_dft_x": 6400 * 64 + 160 * 512 * 2,   # activation in, half-spectrum along x out
     "nno_dft_y": 160 * 512 * 2 + 512 * 64 * 2,
     "nno_mix": 512 * 64 * 2 * 2,              # spectrum in and out (weights amortised)
@@ -137,7 +137,9 @@ def algorithmic_bytes(cls, launches, N, steps):
         return 16.0 * N * launches
     if cls in WIN_BYTES:
         per = WIN_BYTES[cls] * nwin + (512 * 64 * 64 * 2 if cls == "nno_mix" else 0)
-        extra = G5_T1_BYTES * nwin * (launches * 3 // 4) if cls == "nno_idft_x_mix_act" else 0
+        extra = 0
+        if cls == "nno_idft_x_mix_act":  # blocks 0..2 write T1; block 0 reads the inputs, not X
+            extra = (G5_T1_BYTES * 3 - 6400 * (64 - 12)) * nwin * (launches // 4)
         return float(per) * launches + extra
     return None
 

@@ -595,16 +595,24 @@ __device__ __forceinline__ void win_channels(const WinSrc& ws, int y, int x, flo
   hi = make_uint4(pack2(c[8], c[9]), pack2(c[10], c[11]), pack2(c[12], c[13]), pack2(c[14], c[15]));
 }
 
-struct LiftSrc { NnoInput in; GridGeom g; const float* rho; };
+struct LiftSrc {
+  NnoInput in; GridGeom g; const float* rho;
+  int store_x;  // lift: write the lifted activation X (0: only the next block's DFT along x)
+};
 
-template <bool LIFT, bool FP8>
+template <bool LIFT, bool FP8, bool IN0 = false>
 __global__ void __launch_bounds__(G5_THREADS, 1)
 g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* bias, const bf16* Fx, bf16* T1,
           const float* qinv, int last, int total, int* err, LiftSrc lsrc) {
   // LIFT: warps 0, 2, 3 build each unit's 4 rows of the 16 input channels
   // (restriction, RMS normalisation by the window's rho) directly in the
   // stage as the lift's K-major A tile; Wb is the lift weights [32][16]; the
-  // unit's MMA is the lift (K = 16), no activation, then block 0's DFT along x.
+  // unit's MMA is the lift (K = 16), no activation, then block 0's DFT along x
+  // (the lifted X itself is stored only if lsrc.store_x).
+  // IN0 (block 0 without a stored lifted activation): warps 2, 3 build the
+  // input channels as in LIFT and warp 0 copies the T3 rows; the residual
+  // path W0 X = (W0 L) I + W0 l_b takes Wb = W0 L [32][16] against the
+  // inputs I (K = 16), W0 l_b being part of `bias`.
   // FP8: X holds E4M3 activations (x8_off layout).  The unit's input rows
   // are bulk-copied as FP8 and converted to BF16 by warps 2-3 (the scale is
   // folded into Wb); the output rows are written as E4M3 times qinv[c].
@@ -626,12 +634,13 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   constexpr int UPW = 80 / G5_ROWS;
   if ((int)blockIdx.x >= total) return;
   // constant operands: Gx [128][32], W [32][32] (lift: [32][16]), Fx [32][80] (K-major tiles)
+  static_assert(!(IN0 && (LIFT || FP8)), "IN0 is a BF16 block-0 mode");
   if (!LIFT)
     for (int c = tid; c < 128 * 4; c += G5_THREADS) {
       const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
       tc::cp_async16(smem + G5_OFF_GX + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
     }
-  constexpr int WK = LIFT ? 2 : 4;  // k-groups of the mixer / lift weights
+  constexpr int WK = (LIFT || IN0) ? 2 : 4;  // k-groups of the mixer / lift weights
   for (int c = tid; c < 32 * WK; c += G5_THREADS) {
     const int t8 = c & 7, rest = c >> 3, kc = rest % WK, rg = rest / WK;
     tc::cp_async16(smem + G5_OFF_W + (rg * WK + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * (8 * WK) + kc * 8, true);
@@ -655,7 +664,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   }
   tc::cp_async_wait_all();
   if (tid == 0) {
-    for (int s = 0; s < G5_STAGES; ++s) { tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); }
+    for (int s = 0; s < G5_STAGES; ++s) { tc::mbar_init(full(s), IN0 ? 2 : 1); tc::mbar_init(empty(s), 1); }
     for (int a = 0; a < G5_NACC; ++a) {
       tc::mbar_init(g5_full(a), 1); tc::mbar_init(g1_full(a), 1); tc::mbar_init(acc_empty(a), 8);
     }
@@ -672,12 +681,14 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   const uint32_t tmem = *tslot;
   auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
 
-  if (LIFT && (warp == 0 || warp == 2 || warp == 3)) {  // ---------------- input builders ----------------
-    // Builder bw (0..2) fills the stages of units it = bw, bw + 3, ...: three
-    // units are built at once, each warp issuing all loads of a half unit
+  if ((LIFT && (warp == 0 || warp == 2 || warp == 3)) || (IN0 && (warp == 2 || warp == 3))) {
+    // ---------------- input builders ----------------
+    // Builder bw (0..NB-1) fills the stages of units it = bw, bw + NB, ...:
+    // NB units are built at once, each warp issuing all loads of a half unit
     // before its shared-memory stores.
-    const int bw = warp == 0 ? 0 : warp - 1;
-    for (int u = blockIdx.x + bw * gridDim.x, it = bw; u < total && !*abort_flag; u += 3 * gridDim.x, it += 3) {
+    constexpr int NB = LIFT ? 3 : 2;
+    const int bw = LIFT ? (warp == 0 ? 0 : warp - 1) : warp - 2;
+    for (int u = blockIdx.x + bw * gridDim.x, it = bw; u < total && !*abort_flag; u += NB * gridDim.x, it += NB) {
       const int s = it % G5_STAGES;
       if (it >= G5_STAGES && !tc::mbar_wait(empty(s), ((it / G5_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
       const int b = u / UPW, y0r = (u % UPW) * G5_ROWS;
@@ -712,7 +723,10 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
         const int s = it % G5_STAGES;
         if (it >= G5_STAGES && !tc::mbar_wait(empty(s), ((it / G5_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
         const size_t wy = (size_t)(u / UPW) * 80 + (u % UPW) * G5_ROWS;
-        if (FP8) {  // FP8 rows into the staging area, the inverse-y spectrum as usual
+        if (IN0) {  // the input channels come from the builders: only the inverse-y spectrum
+          tc::mbar_arrive_tx(full(s), G5_TB);
+          tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
+        } else if (FP8) {  // FP8 rows into the staging area, the inverse-y spectrum as usual
           tc::mbar_arrive_tx(full(s), G5_X8B + G5_TB);
           tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB + G5_TB, reinterpret_cast<const uint8_t*>(X) + wy * 2560, G5_X8B,
                        full(s));
@@ -765,6 +779,10 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
           for (int k = 0; k < 2; ++k)
             tc::mma_bf16(d, tc::make_desc(ag + k * 256, 128, 512), tc::make_desc(bt + yy * 2048 + k * 256, 128, 512),
                          id5, 1);
+          if (IN0) {  // (W0 L) I: the built input channels, K = 16
+            tc::mma_bf16(d, tc::make_desc(ax + yy * 2560, 128, 256), tc::make_desc(bw, 128, 256), id5, 1);
+            continue;
+          }
           for (int k = 0; k < 2; ++k)
             tc::mma_bf16(d, tc::make_desc(ax + yy * G5_XT + k * 256, 128, 512), tc::make_desc(bw + k * 256, 128, 512),
                          id5, 1);
@@ -864,7 +882,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
               uint8_t* d8 = reinterpret_cast<uint8_t*>(X) + x8_off(wy0 + yy, x, 0);
               *reinterpret_cast<uint4*>(d8) = make_uint4(q8[0], q8[1], q8[2], q8[3]);
               *reinterpret_cast<uint4*>(d8 + 128) = make_uint4(q8[4], q8[5], q8[6], q8[7]);
-            } else {
+            } else if (!LIFT || lsrc.store_x) {
               bf16* dst = X + xt_off(wy0 + yy, x, 0);
 #pragma unroll
               for (int cg = 0; cg < 4; ++cg)
@@ -1232,6 +1250,25 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
     if ((rc = up(&W->bias[bl], std::vector<float>(p, p + 32), bytes))) return rc;
     p += 32;
   }
+  {  // block 0's residual path from the inputs: W0 L [32][16] and W0 l_b + b_0
+    const float* lw = blob;
+    const float* lb = blob + 32 * 15;
+    const float* w0 = blob + 32 * 15 + 32 + 2 * 32 * 32 * 512;
+    const float* b0 = w0 + 32 * 32;
+    std::vector<float> wl(32 * 16, 0.f), bl0(32);
+    for (int o = 0; o < 32; ++o) {
+      double accb = b0[o];
+      for (int c = 0; c < 32; ++c) accb += (double)w0[o * 32 + c] * lb[c];
+      bl0[o] = (float)accb;
+      for (int i = 0; i < 15; ++i) {
+        double acc = 0.0;
+        for (int c = 0; c < 32; ++c) acc += (double)w0[o * 32 + c] * lw[c * 15 + i];
+        wl[o * 16 + i] = (float)acc;
+      }
+    }
+    if ((rc = up(&W->W0L, to_bf16(wl), bytes))) return rc;
+    if ((rc = up(&W->bias0L, bl0, bytes))) return rc;
+  }
   {  // projection: P1 extended by the leaky-ReLU's linear part 0.01 P2 P1; the bias is taken in the epilogue
     const float* p1 = p;
     const float* pb = p + 128 * 32;
@@ -1258,7 +1295,7 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
 }
 
 void nno_free_weights(NnoWeights* W) {
-  void* ptrs[] = {W->lift_w, W->lift_b, W->Fx, W->Fy, W->Gy, W->Gx, W->P1, W->qinv, W->P18};
+  void* ptrs[] = {W->lift_w, W->lift_b, W->Fx, W->Fy, W->Gy, W->Gx, W->P1, W->qinv, W->P18, W->W0L, W->bias0L};
   for (void* q : ptrs) if (q) cudaFree(q);
   for (int b = 0; b < 4; ++b) {
     if (W->R[b]) cudaFree(W->R[b]);
@@ -1383,11 +1420,16 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     CK(cudaFuncSetAttribute(g5_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
     CK(cudaFuncSetAttribute(g5_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
     CK(cudaFuncSetAttribute(g5_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
+    CK(cudaFuncSetAttribute(g5_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)G5_SMEM));
     g5_cap = persistent_grid((const void*)g5_kernel<false, false>, G5_THREADS, G5_SMEM, 512);
   }
   const int g5_total = n * (80 / G5_ROWS);
   const int g5_grid = g5_total < g5_cap ? g5_total : g5_cap;
-  const LiftSrc lsrc{in, g, k->rho};
+  // BF16 without calibration: the lifted activation is never stored; block 0
+  // rebuilds the input channels and applies W0 L to them (IN0)
+  const bool in0 = !W->fp8 && !calib;
+  const LiftSrc lsrc{in, g, k->rho, in0 ? 0 : 1};
   {  // lift 15 -> 32 and block 0's DFT along x, in the G5 pipeline; blocks 1..3
      // get their DFT along x from the previous block's G5 kernel
     ProfScope ps(h, 8, 1);
@@ -1419,6 +1461,10 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
         g5_kernel<false, true><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W8[bl], W->bias[bl], W->Fx,
                                                                      k->T1, W->qinv + 32 * (bl + 1), bl == 3,
                                                                      g5_total, k->err, LiftSrc{});
+      else if (bl == 0 && in0)
+        g5_kernel<false, false, true><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W0L, W->bias0L,
+                                                                            W->Fx, k->T1, nullptr, 0, g5_total, k->err,
+                                                                            lsrc);
       else
         g5_kernel<false, false><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], W->Fx,
                                                                       k->T1, nullptr, bl == 3, g5_total, k->err,

@@ -15,6 +15,8 @@ struct NnoWeights {
   bf16* Gx = nullptr;       // [128 x][32 (kx,ri)]          inverse real DFT along x (1/80), rows >= 80 zero
   bf16* W[4] = {};          // [32 o][32 c]
   float* bias[4] = {};      // [32]
+  bf16* W0L = nullptr;      // [32][16]  W[0] lift_w: block 0's residual path applied to the inputs
+  float* bias0L = nullptr;  // [32]      W[0] lift_b + bias[0]
   bf16* P1 = nullptr;       // [144][32]: P1, then 0.01 P2 P1 (the leaky-ReLU's linear part), 0
   float p2w[256] = {};      // 0.99 P2 [2][128]  (host copies: kernel parameters)
   float nb[128] = {};       // -p1b
