@@ -504,8 +504,8 @@ constexpr uint32_t G5_OFF_GX = G5_OFF_A1 + 2 * G5_A1;
 constexpr uint32_t G5_OFF_W = G5_OFF_GX + 128 * 32 * 2;
 constexpr uint32_t G5_OFF_FX = G5_OFF_W + 32 * 32 * 2;
 constexpr uint32_t G5_OFF_ONE = G5_OFF_FX + 32 * 80 * 2;         // [128][16] K-major: 1, 1, 0 ...
-constexpr uint32_t G5_OFF_BIAS = G5_OFF_ONE + 128 * 16 * 2;      // [32][16] K-major: bias hi, lo, 0 ...
-constexpr uint32_t G5_OFF_BAR = G5_OFF_BIAS + 32 * 16 * 2;
+constexpr uint32_t G5_OFF_BIAS = G5_OFF_ONE + 128 * 16 * 2;      // [128 (yy,o)][16] K-major: bias hi, lo, 0 ...
+constexpr uint32_t G5_OFF_BAR = G5_OFF_BIAS + 128 * 16 * 2;
 constexpr int G5_NACC = 3;                                        // TMEM accumulator sets
 constexpr uint32_t G5_ACC = 160;                                  // TMEM columns per set
 constexpr uint32_t G5_NBAR = 3 * G5_STAGES + 3 * G5_NACC + 2;
@@ -656,11 +656,11 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
     const int r = c >> 4, k = c & 15;
     *reinterpret_cast<bf16*>(smem + G5_OFF_ONE + tc::kmaj_off(r, k, 16)) = __float2bfloat16_rn(k < 2 ? 1.f : 0.f);
   }
-  for (int c = tid; c < 32 * 16; c += G5_THREADS) {
-    const int o = c >> 4, k = c & 15;
+  for (int c = tid; c < 128 * 16; c += G5_THREADS) {  // one row of bias per (yy, o): the unit's 4 rows at once
+    const int n = c >> 4, k = c & 15, o = n & 31;
     const bf16 hi = __float2bfloat16_rn(bias[o]);
     const float v = k == 0 ? bias[o] : k == 1 ? bias[o] - __bfloat162float(hi) : 0.f;
-    *reinterpret_cast<bf16*>(smem + G5_OFF_BIAS + tc::kmaj_off(o, k, 16)) = __float2bfloat16_rn(v);
+    *reinterpret_cast<bf16*>(smem + G5_OFF_BIAS + tc::kmaj_off(n, k, 16)) = __float2bfloat16_rn(v);
   }
   tc::cp_async_wait_all();
   if (tid == 0) {
@@ -744,6 +744,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------- MMA issuer ----------------
       constexpr uint32_t id5 = tc::idesc_bf16(32, false, false);
+      constexpr uint32_t id128 = tc::idesc_bf16(128, false, false);
       constexpr uint32_t id1 = tc::idesc_bf16(32, true, false);
       const uint32_t ag = sbase + G5_OFF_GX, bw = sbase + G5_OFF_W, bfx = sbase + G5_OFF_FX;
       auto issue_g1 = [&](int j) -> bool {  // next block's DFT along x for unit j
@@ -768,17 +769,21 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
         }
         tc::fence_after();
         const uint32_t ax = sbase + s * G5_STAGE, bt = ax + G5_XB;
-        for (int yy = 0; yy < G5_ROWS; ++yy) {
+        // the unit's 4 rows side by side (N = 128 columns (yy, o)) where A is shared:
+        // the inverse DFT along x (A = Gx, B = the 4 rows of T3) and the bias
+        const uint32_t d4 = tmem + a * G5_ACC;
+        if (!LIFT)
+          for (int k = 0; k < 2; ++k)
+            tc::mma_bf16(d4, tc::make_desc(ag + k * 256, 128, 512), tc::make_desc(bt + k * 256, 128, 512), id128,
+                         k > 0);
+        tc::mma_bf16(d4, tc::make_desc(sbase + G5_OFF_ONE, 128, 256), tc::make_desc(sbase + G5_OFF_BIAS, 128, 256),
+                     id128, LIFT ? 0 : 1);
+        for (int yy = 0; yy < G5_ROWS; ++yy) {  // per row: the mixer (or lift) on the row's own A tile
           const uint32_t d = tmem + a * G5_ACC + yy * 32;
-          tc::mma_bf16(d, tc::make_desc(sbase + G5_OFF_ONE, 128, 256), tc::make_desc(sbase + G5_OFF_BIAS, 128, 256),
-                       id5, 0);  // bias
           if (LIFT) {  // lift: [x][16 inputs] . [32][16]^T
             tc::mma_bf16(d, tc::make_desc(ax + yy * 2560, 128, 256), tc::make_desc(bw, 128, 256), id5, 1);
             continue;
           }
-          for (int k = 0; k < 2; ++k)
-            tc::mma_bf16(d, tc::make_desc(ag + k * 256, 128, 512), tc::make_desc(bt + yy * 2048 + k * 256, 128, 512),
-                         id5, 1);
           if (IN0) {  // (W0 L) I: the built input channels, K = 16
             tc::mma_bf16(d, tc::make_desc(ax + yy * 2560, 128, 256), tc::make_desc(bw, 128, 256), id5, 1);
             continue;
