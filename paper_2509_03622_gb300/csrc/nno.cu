@@ -124,7 +124,7 @@ __device__ __forceinline__ void gemm_load(const Op& op, uint8_t* sA, uint8_t* sB
 
 template <int BN, int K, bool AMN, class Op, int KS>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_per_batch, int total, int* err) {
-  static_assert(K % 16 == 0 && BN % 16 == 0 && BN <= 256, "shape");
+  static_assert(K % 16 == 0 && BN % 32 == 0 && BN <= 256, "shape");
   typedef GemmCfg<BN, K, AMN, Op, KS> Cfg;
   extern __shared__ __align__(1024) uint8_t smem[];
   const uint32_t sbase = tc::smem_u32(smem);
@@ -214,10 +214,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_
       typename Op::State sst;
       op.epi_begin(sst);
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * Cfg::TCOLS + (uint32_t)c0, v);
-        if (valid) op.epi(b, m, c0, v, sst);
+      for (int c0 = 0; c0 < BN; c0 += 32) {  // 32 columns per TMEM load (BN is a multiple of 32)
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * Cfg::TCOLS + (uint32_t)c0, v);
+        if (valid) {
+          op.epi(b, m, c0, v, sst);
+          op.epi(b, m, c0 + 16, v + 16, sst);
+        }
       }
       if (valid) op.epi_end(b, m, sst);
       tc::fence_before();
