@@ -46,7 +46,9 @@ extern "C" {
 #define FDFD_EINVAL        -1   /* bad argument (checked on the host)        */
 #define FDFD_ECUDA         -2   /* a CUDA call failed                        */
 #define FDFD_ENUMERIC      -3   /* NaN / Inf met in the iteration            */
-#define FDFD_ETIMEOUT      -4   /* a bounded device wait ran out             */
+#define FDFD_ETIMEOUT      -4   /* a bounded device wait ran out; the handle's
+                                   neural operator then skips its work in
+                                   every later call (recreate the handle)    */
 #define FDFD_ENOSETUP      -5   /* schwarz_setup required first              */
 #define FDFD_ENOMEM        -6   /* workspace allocation failed               */
 

@@ -310,6 +310,7 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
     int nonfinite = 0, breakdown = 0;
     if ((rc = read_flags(h, &relres, &nonfinite, &breakdown))) return rc;
     if (nonfinite) { status = FDFD_ENUMERIC; break; }
+    if (o->precond == FDFD_PRECOND_SCHWARZ && (rc = schwarz_error(h))) { status = rc; break; }
     est = relres;
     if (relres <= o->tol) { status = FDFD_OK; break; }
     if (iters >= o->max_iters) { status = FDFD_NOT_CONVERGED; break; }
@@ -332,6 +333,7 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
       if (est <= o->tol || breakdown || iters >= o->max_iters) break;
     }
     if (status == FDFD_ENUMERIC) break;
+    if (o->precond == FDFD_PRECOND_SCHWARZ && (rc = schwarz_error(h))) { status = rc; break; }
     ProfScope ps(h, 4, 2);
     if ((rc = launch_solve_y(h->st, k, m, s))) return rc;
     if (o->precond == FDFD_PRECOND_JACOBI)
@@ -341,7 +343,7 @@ int solve_impl(fdfd_ctx* h, const float2* rhs, int rhs_is_source, int transpose,
     if (rc) return rc;
     ++cycles;
   }
-  if (status != FDFD_ENUMERIC) {
+  if (status != FDFD_ENUMERIC && status != FDFD_ETIMEOUT) {
     ProfScope ps(h, 4, 1);
     if ((rc = launch_store_field(h->x64, E, n, 1.0 / rs, s))) return rc;
   }

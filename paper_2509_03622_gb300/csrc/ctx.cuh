@@ -77,6 +77,9 @@ int schwarz_apply(fdfd_ctx* h, const float2* v, const double* scale_dev, float2*
 int schwarz_nno_solve(fdfd_ctx* h, const float2* r_win, const float2* g_win, const int* win_id,
                       int n, float2* e_win);
 int schwarz_traces(fdfd_ctx* h, const float2* u, float2* g);
+// FDFD_ETIMEOUT once a bounded wait inside a neural-operator kernel ran out
+// (the flag stays set: later neural passes of the handle skip their work).
+int schwarz_error(fdfd_ctx* h);
 int schwarz_export(fdfd_ctx* h, double* Q, double* Nd);
 struct NnoWeights;
 const NnoWeights* schwarz_weights(fdfd_ctx* h);  // nullptr before schwarz_setup

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_
   if (tid == 0) {
     for (int s = 0; s < Cfg::S; ++s) { tc::mbar_init(full(s), 128); tc::mbar_init(empty(s), 1); }
     for (int a = 0; a < 2; ++a) { tc::mbar_init(acc_full(a), 1); tc::mbar_init(acc_empty(a), 4); }
-    *abort_flag = 0;
+    *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
     tc::fence_mbar_init();
   }
   if (warp == 4) tc::tmem_alloc(tc::smem_u32(tslot), 2 * Cfg::TCOLS);
@@ -376,7 +376,7 @@ g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int rows, int nwin, int wtile
   if (tid == 0) {
     for (int s = 0; s < G3_STAGES; ++s) { tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); }
     for (int a = 0; a < NACC; ++a) { tc::mbar_init(acc_full(a), 1); tc::mbar_init(acc_empty(a), 4); }
-    *abort_flag = 0;
+    *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
     tc::fence_mbar_init();
   }
   if (warp == 1) tc::tmem_alloc(tc::smem_u32(tslot), 512);
@@ -482,7 +482,8 @@ g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int rows, int nwin, int wtile
 // read again for it.
 // Roles: warp 0 lane 0 = producer (one bulk copy of the 4 X rows, 20 KB, and
 // one of the 4 T3 rows, 8 KB, per unit into a G5_STAGES-deep ring, completion
-// by transaction count), warp 1 lane 0 = MMA issuer, warps 4..11 = epilogue
+// by transaction count), warp 1 lane 0 = MMA issuer, warps 4..11 = epilogue;
+// in the lift and IN0, warps 2, 3, 12, 13 build the input channels
 // (warp w reads TMEM lanes 32(w%4)..).  Three accumulator sets in TMEM (G5:
 // 4 x 32 columns, G1: 32 columns, 160 columns a set) let the epilogue of unit
 // i overlap the MMAs of units i+1 and i+2, and the epilogue is software
@@ -495,7 +496,7 @@ g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int rows, int nwin, int wtile
 // contiguous K-major operand tile.
 constexpr int G5_ROWS = 4;
 constexpr int G5_STAGES = 4;
-constexpr int G5_THREADS = 384;
+constexpr int G5_THREADS = 448;  // warps 12, 13: extra input builders (lift, IN0)
 constexpr uint32_t G5_XT = 80 * 32 * 2;                          // one tiled [80][32] X row
 constexpr uint32_t G5_XB = G5_ROWS * G5_XT;                      // 20480
 constexpr uint32_t G5_TB = G5_ROWS * 2048;                       // 8192
@@ -673,7 +674,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
     }
     for (int b = 0; b < 2; ++b) tc::mbar_init(a1_full(b), 8);
     for (int s = 0; s < G5_STAGES; ++s) tc::mbar_init(conv_full(s), 2);
-    *abort_flag = 0;
+    *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 512);
@@ -684,13 +685,16 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   const uint32_t tmem = *tslot;
   auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
 
-  if ((LIFT && (warp == 0 || warp == 2 || warp == 3)) || (IN0 && (warp == 2 || warp == 3))) {
+  if ((LIFT || IN0) && (warp == 2 || warp == 3 || warp >= 12)) {
     // ---------------- input builders ----------------
     // Builder bw (0..NB-1) fills the stages of units it = bw, bw + NB, ...:
     // NB units are built at once, each warp issuing all loads of a half unit
-    // before its shared-memory stores.
-    constexpr int NB = LIFT ? 3 : 2;
-    const int bw = LIFT ? (warp == 0 ? 0 : warp - 1) : warp - 2;
+    // before its shared-memory stores.  NB must not exceed the ring depth:
+    // a builder then never waits on a stage's empty barrier more than one
+    // phase ahead of it (a parity wait cannot tell phases two apart).
+    constexpr int NB = 4;
+    static_assert(NB <= G5_STAGES, "builders ahead of the ring");
+    const int bw = warp >= 12 ? warp - 10 : warp - 2;
     for (int u = blockIdx.x + bw * gridDim.x, it = bw; u < total && !*abort_flag; u += NB * gridDim.x, it += NB) {
       const int s = it % G5_STAGES;
       if (it >= G5_STAGES && !tc::mbar_wait(empty(s), ((it / G5_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
@@ -720,7 +724,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       if (lane == 0) tc::mbar_arrive(full(s));
     }
   } else if (warp == 0) {
-    if (lane == 0) {  // ---------------- producer ----------------
+    if (lane == 0 && !LIFT) {  // ---------------- producer (the lift has none) ----------------
       int it = 0;
       for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
         const int s = it % G5_STAGES;
@@ -824,7 +828,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
         if ((tid & 31) == 0) tc::mbar_arrive(conv_full(s));
       }
     }
-  } else if (warp >= 4) {  // ---------------- epilogue ----------------
+  } else if (warp >= 4 && warp < 12) {  // ---------------- epilogue ----------------
     const int ew = warp - 4, q = ew & 3, hf = ew >> 2;
     float qi[32];
 #pragma unroll
@@ -1003,7 +1007,7 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(const __grid_consta
       tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); tc::mbar_init(conv_full(s), 1);
     }
     for (int a = 0; a < PJ_ACC; ++a) { tc::mbar_init(m1_full(a), 1); tc::mbar_init(acc_empty(a), 4); }
-    *abort_flag = 0;
+    *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 512);

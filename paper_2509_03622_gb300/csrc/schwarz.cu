@@ -81,6 +81,8 @@ static int check_err(fdfd_ctx* h) {
   return e ? FDFD_ETIMEOUT : FDFD_OK;
 }
 
+int schwarz_error(fdfd_ctx* h) { return (h && h->sw) ? check_err(h) : FDFD_OK; }
+
 int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd) {
   if (sd->k_coarse < 0 || sd->k_coarse > 256) return FDFD_EINVAL;
   if (sd->precision != FDFD_PREC_BF16 && sd->precision != FDFD_PREC_FP8) return FDFD_EINVAL;

@@ -74,10 +74,23 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar_saddr, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_saddr), "r"(count) : "memory");
 }
 
-// Wait for phase `parity` of the barrier; gives up after `limit` polls and
-// returns false (the caller records the error).
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of the barrier; gives up after `limit` polls or
+// about one second, whichever comes first, and returns false (the caller
+// records the error).
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar_saddr, uint32_t parity, long long limit) {
+  uint64_t t0 = 0;
   for (long long i = 0; i < limit; ++i) {
+    if ((i & 1023) == 1023) {  // a try_wait may itself block for a while: bound the total time too
+      const uint64_t t = globaltimer_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > 1000000000ull) return false;
+    }
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred P;\n\t"
