@@ -101,12 +101,18 @@ WIN_BYTES = {
     "nno_proj": 6400 * 64 + 4096 * 8,         # activation in, core field out
 }
 G5_T1_BYTES = 160 * 512 * 2                   # next block's half-spectrum, written by blocks 0..2
-# DRAM bytes (read + write) per window of one launch, from ncu captures of the
-# same kernels on freeform1536 (576 windows, above L2), scaled by the windows
-# of the benched launch; kernel -> (bytes per window, summary under profiles/).
+# DRAM bytes (read + write) per window of one launch of each neural stage,
+# from one single-pass ncu capture of the 4096^2 bench workload (averaged
+# over the class's launches; scaled by the window count for other sizes).
+TRAFFIC_SRC = "profiles/dram_traffic_freeform4096.md"
 MEASURED_TRAFFIC = {
-    "nno_idft_x_mix_act": (601.5e6 / 576, "profiles/g5_kernel_freeform1536.md"),  # a block-0..2 launch
-    "nno_proj": (250.7e6 / 576, "profiles/proj_kernel_freeform1536.md"),
+    "nno_idft_x_mix_act": 1001377,  # G5 block 0 (inputs rebuilt) and blocks 1..3, class average
+    "nno_proj": 440615,
+    "nno_mix": 119420,
+    "nno_lift": 198972,
+    "nno_dft_y": 221897,
+    "nno_idft_y": 215025,
+    "nno_pack": 32807,
 }
 # Useful FLOPs per window of each stage (padding excluded).
 NNO_FLOP_PER_WIN = {
@@ -353,15 +359,10 @@ def main():
         if fl:
             r["tflops"] = fl * (N / 4096.0) * nl / (ms_c / 1e3) / 1e12
         roofs[cls] = r
-    for cls, (per_win, src_file) in MEASURED_TRAFFIC.items():
-        if cls in roofs and precond == F.PRECOND_SCHWARZ and prec_nno == "bf16":
-            nl = roofs[cls]["launches"]
-            tr = per_win * (N / 4096.0)
-            if cls == "nno_idft_x_mix_act":  # the last block writes no next-block spectrum
-                last = (WIN_BYTES[cls]) / (WIN_BYTES[cls] + G5_T1_BYTES)
-                tr *= ((nl - nl // 4) + (nl // 4) * last) / nl
-            roofs[cls]["traffic"] = tr
-            roofs[cls]["traffic_source"] = src_file + " (scaled by windows)"
+    for cls, per_win in MEASURED_TRAFFIC.items():
+        if cls in roofs and precond == F.PRECOND_SCHWARZ and prec_nno == "bf16" and kc == 0:
+            roofs[cls]["traffic"] = per_win * (N / 4096.0)  # bytes per launch: per window x windows
+            roofs[cls]["traffic_source"] = TRAFFIC_SRC + (" (scaled by windows)" if N != 4096 * 4096 else "")
     dom = max(roofs, key=lambda c: roofs[c]["ms"]) if roofs else None
     roof = dict(roofs[dom]) if dom else None
     line = {"metric": METRIC, "value": value, "unit": "Mcell-it/s", "n_gpus": world, "steps": steps,
