@@ -298,6 +298,21 @@ int  fdfd_coarse_export(fdfd_handle h, double* Q_host, double* Ndiag_host);
  * FDFD_ETIMEOUT if the tensor-core completion wait ran out. */
 int  fdfd_selftest_gemm(const void* A, const void* B, float* C, int M, int N, int K, int a_mn_major);
 
+/* Diagnostic of failure detection (no counterpart in the paper): one kernel
+ * waits, with the same bound as every pipeline wait (2^22 polls or about one
+ * second of device time), on a barrier nothing arrives on.  Returns
+ * FDFD_ETIMEOUT when the wait gave up as it must (the expected result; the
+ * CUDA context stays usable), FDFD_OK if it completed, FDFD_ECUDA on a CUDA
+ * error.  Synchronous on the legacy stream. */
+int  fdfd_selftest_wait(void);
+
+/* Failure injection from the host (no counterpart in the paper): mark the
+ * handle's neural operator as failed, exactly as a bounded device wait that
+ * ran out does.  Every later neural pass of the handle then skips its work
+ * and fdfd_solve with FDFD_PRECOND_SCHWARZ returns FDFD_ETIMEOUT at its next
+ * restart.  FDFD_ENOSETUP before schwarz_setup. */
+int  fdfd_nno_mark_failed(fdfd_handle h);
+
 #ifdef __cplusplus
 }
 #endif

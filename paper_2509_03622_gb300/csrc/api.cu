@@ -602,6 +602,15 @@ int fdfd_profile_stop(fdfd_handle h, fdfd_profile* out) {
   return FDFD_OK;
 }
 
+int fdfd_selftest_wait(void) {
+  int r = 0;
+  const int rc = nno_wait_selftest(&r, 0);
+  if (rc) return rc;
+  return r == 2 ? FDFD_ETIMEOUT : FDFD_OK;
+}
+
+int fdfd_nno_mark_failed(fdfd_handle h) { return schwarz_mark_failed(h); }
+
 int fdfd_selftest_gemm(const void* A, const void* B, float* C, int M, int N, int K, int a_mn) {
   if (!A || !B || !C || M <= 0) return FDFD_EINVAL;
   int* err = nullptr;

@@ -80,6 +80,8 @@ int schwarz_traces(fdfd_ctx* h, const float2* u, float2* g);
 // FDFD_ETIMEOUT once a bounded wait inside a neural-operator kernel ran out
 // (the flag stays set: later neural passes of the handle skip their work).
 int schwarz_error(fdfd_ctx* h);
+// Set that flag from the host (failure injection for tests).
+int schwarz_mark_failed(fdfd_ctx* h);
 int schwarz_export(fdfd_ctx* h, double* Q, double* Nd);
 struct NnoWeights;
 const NnoWeights* schwarz_weights(fdfd_ctx* h);  // nullptr before schwarz_setup

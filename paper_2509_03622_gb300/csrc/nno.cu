@@ -1568,6 +1568,36 @@ int nno_enable_fp8(NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInp
   return FDFD_OK;
 }
 
+// A bounded wait on a barrier that nothing ever arrives on: it must give up
+// (limit polls or about a second) and report so, leaving the context usable.
+__global__ void wait_selftest_kernel(int* out, long long limit) {
+  __shared__ uint64_t bar;
+  const uint32_t b = tc::smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(b, 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  const bool done = tc::mbar_wait(b, 0, limit);
+  if (threadIdx.x == 0) out[0] = done ? 1 : 2;
+}
+
+int nno_wait_selftest(int* result, cudaStream_t s) {
+  int* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(int)));
+  int rc = FDFD_OK;
+  if (cudaMemsetAsync(d, 0, sizeof(int), s) != cudaSuccess) rc = FDFD_ECUDA;
+  if (!rc) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(d, WAIT_LIMIT);
+    if (cudaGetLastError() != cudaSuccess) rc = FDFD_ECUDA;
+  }
+  if (!rc && (cudaMemcpyAsync(result, d, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess))
+    rc = FDFD_ECUDA;
+  cudaFree(d);
+  return rc;
+}
+
 int nno_gemm_selftest(const bf16* A, const bf16* B, float* C, int M, int N, int K, int a_mn, int* err,
                       cudaStream_t s) {
   TestOp op{A, B, C, M, N, K, a_mn};

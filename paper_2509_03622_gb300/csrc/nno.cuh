@@ -124,5 +124,8 @@ int nno_enable_fp8(NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInp
 // A[M][K] . B[N][K]^T with A K-major (a_mn = 0, row stride K) or MN-major
 // (a_mn = 1, stored [K][M]); supported (N, K): (32,80) (64,160) (64,64)
 // (160,64) (32,16) (128,32).
+// Diagnostic of the bounded waits: *result = 2 if a wait that can never
+// complete gave up as it must, 1 if it (wrongly) completed.
+int nno_wait_selftest(int* result, cudaStream_t s);
 int nno_gemm_selftest(const bf16* A, const bf16* B, float* C, int M, int N, int K, int a_mn, int* err,
                       cudaStream_t s);

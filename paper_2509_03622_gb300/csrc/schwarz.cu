@@ -83,6 +83,14 @@ static int check_err(fdfd_ctx* h) {
 
 int schwarz_error(fdfd_ctx* h) { return (h && h->sw) ? check_err(h) : FDFD_OK; }
 
+int schwarz_mark_failed(fdfd_ctx* h) {
+  if (!h || !h->sw) return FDFD_ENOSETUP;
+  const int one = 1;
+  CK(cudaMemcpyAsync(h->sw->work.err, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return FDFD_OK;
+}
+
 int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd) {
   if (sd->k_coarse < 0 || sd->k_coarse > 256) return FDFD_EINVAL;
   if (sd->precision != FDFD_PREC_BF16 && sd->precision != FDFD_PREC_FP8) return FDFD_EINVAL;

@@ -89,6 +89,8 @@ _SIGS = {
     "fdfd_coarse_export": ([_P, _P, _P], C.c_int),
     "fdfd_profile_start": ([_P], C.c_int),
     "fdfd_selftest_gemm": ([_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
+    "fdfd_selftest_wait": ([], C.c_int),
+    "fdfd_nno_mark_failed": ([_P], C.c_int),
     "fdfd_profile_stop": ([_P, C.POINTER(Profile)], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -120,6 +122,11 @@ def _ptr(t):
 
 def status_string(code: int) -> str:
     return lib.fdfd_status_string(code).decode()
+
+
+def selftest_wait() -> int:
+    """Bounded-wait diagnostic: the raw status (FDFD_ETIMEOUT expected)."""
+    return lib.fdfd_selftest_wait()
 
 
 def selftest_gemm(A, B, C_out, a_mn_major=False):
@@ -240,6 +247,10 @@ class Solver:
 
     def trace_extract(self, u, g):
         _check(lib.fdfd_trace_extract(self.h, _ptr(u), _ptr(g)), "fdfd_trace_extract")
+
+    def nno_mark_failed(self):
+        """Failure injection: mark the neural operator failed (as a timed-out device wait does)."""
+        _check(lib.fdfd_nno_mark_failed(self.h), "fdfd_nno_mark_failed")
 
     def profile_start(self):
         _check(lib.fdfd_profile_start(self.h), "fdfd_profile_start")
