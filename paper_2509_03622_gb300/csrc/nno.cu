@@ -942,17 +942,19 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
 //              + c_j,   c_j = sum_h P2[j][h] p1b[h]
 //   z        = (O + p2b) * rho * scale, written to the window's core in the
 //              global field (restricted prolongation) or to a per-window array.
-// The linear part of the leaky-ReLU is folded into the MMA as two more output
-// columns (rows 0.01 P2 P1 of B, N = 144); the rectified part is an FP32
-// dot product in the epilogue with 0.99 P2 and -p1b passed as kernel
-// parameters (constant-bank operands), and the constants c_j join p2b.  A second tensor-core
-// layer with N = 16 spent most of its time moving its 32 KB operand tile
-// through shared memory per 128 pixels.
-// Roles: warp 0 producer (bulk copies into a PJ_STAGES ring), warp 1 MMA
-// issuer, warp 3 FP8 -> BF16 converter (FP8 activations only), warps 4..15
-// epilogue in PJ_GROUPS groups of four taking units in turn.  PJ_ACC TMEM
-// accumulators of 144 columns (160 apart); an accumulator is released as soon
-// as its unit's columns have been read.
+// The linear part of the leaky-ReLU is folded into the first MMA as two more
+// output columns (rows 0.01 P2 P1 of B, N = 144).  The epilogue writes
+// max(G, -p1b) as packed BF16 back into the accumulator's own columns
+// (tcgen05.st, in place: 128 FP32 columns -> 64 BF16-pair columns), and the
+// second MMA (N = 16, rows 0.99 P2 of B) reads its A operand from tensor
+// memory, so neither layer's intermediate passes through shared memory; the
+// constants c_j join p2b.
+// Roles: warp 0 producer (bulk copies into a PJ_STAGES ring), warp 1 first
+// MMA, warp 2 second MMA, warp 3 FP8 -> BF16 converter (FP8 activations
+// only), warps 4..15 epilogue in PJ_GROUPS groups of four taking units in
+// turn.  PJ_ACC TMEM accumulators of 144 columns (160 apart): G and the
+// linear part, then the rectified BF16 operand in columns 0..63 and the
+// second layer's output in columns 64..79.
 constexpr int PJ_STAGES = 8;
 constexpr uint32_t PJ_A8 = 128 * 32;                      // the X tile in FP8 (staging)
 constexpr int PJ_GROUPS = 3;
@@ -961,10 +963,11 @@ constexpr int PJ_N = 144;                                 // hidden units + 2 li
 constexpr uint32_t PJ_AT = 128 * 32 * 2;                  // X tile (BF16)
 constexpr uint32_t PJ_ST = PJ_AT + PJ_A8;                 // stage: BF16 tile + FP8 staging
 constexpr uint32_t PJ_OFF_B1 = PJ_STAGES * PJ_ST;         // [144 n][32 k]: P1x
-constexpr uint32_t PJ_OFF_BAR = PJ_OFF_B1 + PJ_N * 32 * 2;
+constexpr uint32_t PJ_OFF_B2 = PJ_OFF_B1 + PJ_N * 32 * 2;   // [16 n][128 k]: 0.99 P2 rows 0, 1, then 0
+constexpr uint32_t PJ_OFF_BAR = PJ_OFF_B2 + 16 * 128 * 2;
 constexpr int PJ_ACC = 3;
 constexpr uint32_t PJ_ACC_COLS = 160;
-constexpr uint32_t PJ_NBAR = 3 * PJ_STAGES + 2 * PJ_ACC;
+constexpr uint32_t PJ_NBAR = 3 * PJ_STAGES + 4 * PJ_ACC;
 constexpr uint32_t PJ_SMEM = PJ_OFF_BAR + PJ_NBAR * 8 + 16;
 static_assert(PJ_SMEM <= 227 * 1024, "proj shared memory");
 static_assert(PJ_ACC * PJ_ACC_COLS <= 512, "proj TMEM columns");
@@ -991,6 +994,8 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(const __grid_consta
   auto conv_full = [&](int s) { return bar + 8u * (2 * PJ_STAGES + s); };
   auto m1_full = [&](int a) { return bar + 8u * (3 * PJ_STAGES + a); };
   auto acc_empty = [&](int a) { return bar + 8u * (3 * PJ_STAGES + PJ_ACC + a); };
+  auto a2_full = [&](int a) { return bar + 8u * (3 * PJ_STAGES + 2 * PJ_ACC + a); };
+  auto m2_full = [&](int a) { return bar + 8u * (3 * PJ_STAGES + 3 * PJ_ACC + a); };
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + PJ_OFF_BAR + PJ_NBAR * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + PJ_OFF_BAR + PJ_NBAR * 8 + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1001,12 +1006,20 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(const __grid_consta
     const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
     tc::cp_async16(smem + PJ_OFF_B1 + (rg * 4 + kc) * 128 + t8 * 16, P.P1x + (rg * 8 + t8) * 32 + kc * 8, true);
   }
+  for (int c = tid; c < 16 * 128; c += PJ_THREADS) {  // B2: rows 0, 1 = 0.99 P2
+    const int n = c >> 7, k = c & 127;
+    *reinterpret_cast<bf16*>(smem + PJ_OFF_B2 + tc::kmaj_off(n, k, 128)) =
+        __float2bfloat16_rn(n < 2 ? P.p2w[n][k] : 0.f);
+  }
   tc::cp_async_wait_all();
   if (tid == 0) {
     for (int s = 0; s < PJ_STAGES; ++s) {
       tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); tc::mbar_init(conv_full(s), 1);
     }
-    for (int a = 0; a < PJ_ACC; ++a) { tc::mbar_init(m1_full(a), 1); tc::mbar_init(acc_empty(a), 4); }
+    for (int a = 0; a < PJ_ACC; ++a) {
+      tc::mbar_init(m1_full(a), 1); tc::mbar_init(acc_empty(a), 4);
+      tc::mbar_init(a2_full(a), 4); tc::mbar_init(m2_full(a), 1);
+    }
     *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
     tc::fence_mbar_init();
   }
@@ -1055,6 +1068,21 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(const __grid_consta
         tc::mma_commit(m1_full(a));
       }
     }
+  } else if (warp == 2) {
+    if (lane == 0) {  // second MMA: O = max(G, -p1b) (BF16, in TMEM) x (0.99 P2)^T
+      constexpr uint32_t id2 = tc::idesc_bf16(16, false, false);
+      const uint32_t b2 = sbase + PJ_OFF_B2;
+      int j = 0;
+      for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++j) {
+        const int a = j % PJ_ACC;
+        if (!tc::mbar_wait(a2_full(a), (j / PJ_ACC) & 1, WAIT_LIMIT)) { fail(); break; }
+        tc::fence_after();
+        const uint32_t acc = tmem + a * PJ_ACC_COLS;
+        for (int k = 0; k < 8; ++k)
+          tc::mma_bf16_ts(acc + 64, acc + k * 8, tc::make_desc(b2 + k * 256, 128, 2048), id2, k > 0);
+        tc::mma_commit(m2_full(a));
+      }
+    }
   } else if (warp == 3) {
     if (FP8) {  // FP8 -> BF16 converter
       int it = 0;
@@ -1099,28 +1127,31 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(const __grid_consta
       if (*abort_flag || !tc::mbar_wait(m1_full(a), (it / PJ_ACC) & 1, WAIT_LIMIT)) { fail(); break; }
       tc::fence_after();
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + a * PJ_ACC_COLS;
-      float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
       float lin[16];
       tc::tmem_ld16(trow + 128, lin);
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {  // 32 hidden units per TMEM load
+      for (int g = 0; g < 4; ++g) {  // 32 hidden units per TMEM load -> 16 BF16 pairs, in place
         float v[32];
         tc::tmem_ld32(trow + g * 32, v);
-        if (g == 3) {  // columns read: the MMA may reuse them
-          tc::fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(acc_empty(a));
-        }
+        uint32_t pk[16];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float r = fmaxf(v[i], P.nb[g * 32 + i]);
-          s0[i & 3] = fmaf(P.p2w[0][g * 32 + i], r, s0[i & 3]);
-          s1[i & 3] = fmaf(P.p2w[1][g * 32 + i], r, s1[i & 3]);
-        }
+        for (int i = 0; i < 16; ++i)
+          pk[i] = pack2(fmaxf(v[2 * i], P.nb[g * 32 + 2 * i]), fmaxf(v[2 * i + 1], P.nb[g * 32 + 2 * i + 1]));
+        tc::tmem_st16(trow + g * 16, pk);  // columns 16g.. were read by this or an earlier load
       }
+      tc::tmem_st_wait();
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(a2_full(a));
+      if (!tc::mbar_wait(m2_full(a), (it / PJ_ACC) & 1, WAIT_LIMIT)) { fail(); break; }
+      tc::fence_after();
+      float o2[16];
+      tc::tmem_ld16(trow + 64, o2);
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty(a));  // columns read: the first MMA may reuse them
       const float f = rho * (float)sc * (float)sw;
-      const float2 val = make_float2(((s0[0] + s0[1]) + (s0[2] + s0[3]) + lin[0] + P.p2b0) * f,
-                                     ((s1[0] + s1[1]) + (s1[2] + s1[3]) + lin[1] + P.p2b1) * f);
+      const float2 val = make_float2((o2[0] + lin[0] + P.p2b0) * f, (o2[1] + lin[1] + P.p2b1) * f);
       const int m = (u % UPW) * 128 + px;
       if (P.e_win) {
         P.e_win[(size_t)b * NPIX + m] = val;
