@@ -122,8 +122,24 @@ __device__ __forceinline__ void gemm_load(const Op& op, uint8_t* sA, uint8_t* sB
     }
 }
 
+// Ops whose A tiles are stored as 128-byte swizzled K-major rows (kBulkA,
+// K = 64, no K split) are moved by one bulk copy per stage and read through
+// swizzled descriptors instead of the gather.
+template <class Op, class = void>
+struct HasBulkA { static constexpr bool value = false; };
+template <class Op>
+struct HasBulkA<Op, decltype((void)Op::kBulkA)> { static constexpr bool value = Op::kBulkA; };
+template <class Op>
+__host__ __device__ constexpr bool bulk_a() { return HasBulkA<Op>::value; }
+template <class Op>
+__device__ __forceinline__ const void* bulk_a_src(const Op& op, int b, int m0) {
+  if constexpr (bulk_a<Op>()) return op.a_tile(b, m0, 0);
+  else return nullptr;
+}
+
 template <int BN, int K, bool AMN, class Op, int KS>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_per_batch, int total, int* err) {
+  static_assert(!bulk_a<Op>() || (!AMN && K == 64 && KS == 1), "bulk A: swizzled 128-byte K-major rows");
   static_assert(K % 16 == 0 && BN % 32 == 0 && BN <= 256, "shape");
   typedef GemmCfg<BN, K, AMN, Op, KS> Cfg;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -146,7 +162,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_
     tc::cp_async_wait_all();
   }
   if (tid == 0) {
-    for (int s = 0; s < Cfg::S; ++s) { tc::mbar_init(full(s), 128); tc::mbar_init(empty(s), 1); }
+    for (int s = 0; s < Cfg::S; ++s) { tc::mbar_init(full(s), bulk_a<Op>() ? 1 : 128); tc::mbar_init(empty(s), 1); }
     for (int a = 0; a < 2; ++a) { tc::mbar_init(acc_full(a), 1); tc::mbar_init(acc_empty(a), 4); }
     *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
     tc::fence_mbar_init();
@@ -159,7 +175,25 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_
   const uint32_t tmem = *tslot;
   auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
 
-  if (warp < 4) {  // ---------------- producers ----------------
+  if (bulk_a<Op>() && (sbase & 1023)) {  // swizzled tiles need 1024-byte alignment
+    if (tid == 0) atomicExch(err, 1);
+    *abort_flag = 1;
+  }
+  if (warp < 4 && bulk_a<Op>()) {  // ---------------- producer: one bulk copy per stage ----------------
+    if (warp == 0 && lane == 0) {
+      int it = 0;
+      for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x, ++it) {
+        const int b = tile / tiles_per_batch, m0 = (tile % tiles_per_batch) * 128;
+        const int s = it % Cfg::S;
+        if (it >= Cfg::S && !tc::mbar_wait(empty(s), ((it / Cfg::S) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+        tc::mbar_arrive_tx(full(s), Cfg::A_BYTES);
+        tc::bulk_g2s(sbase + s * Cfg::STAGE, bulk_a_src(op, b, m0), Cfg::A_BYTES, full(s));
+      }
+      // every copy issued must have landed before the CTA may exit
+      for (int j = (it > Cfg::S ? it - Cfg::S : 0); j < it; ++j)
+        if (!tc::mbar_wait(full(j % Cfg::S), (j / Cfg::S) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
+    }
+  } else if (warp < 4) {  // ---------------- producers ----------------
     int it = 0;  // stage fills: KS per tile
     for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x) {
       const int b = tile / tiles_per_batch, m0 = (tile % tiles_per_batch) * 128;
@@ -191,9 +225,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_
                                           : a0 + Cfg::A_BYTES;
           const uint32_t bsbo = Op::kConstB ? K * 16 : Cfg::KH * 16;
 #pragma unroll
-          for (int k = 0; k < Cfg::KH / 16; ++k)
-            tc::mma_bf16(tmem + a * Cfg::TCOLS, tc::make_desc(a0 + k * 256, 128, Cfg::KH * 16),
-                         tc::make_desc(b0 + k * 256, 128, bsbo), idesc, (part > 0) || (k > 0));
+          for (int k = 0; k < Cfg::KH / 16; ++k) {
+            const uint64_t ad = bulk_a<Op>() ? tc::make_desc_sw128(a0 + k * 32, 1024)
+                                             : tc::make_desc(a0 + k * 256, 128, Cfg::KH * 16);
+            tc::mma_bf16(tmem + a * Cfg::TCOLS, ad, tc::make_desc(b0 + k * 256, 128, bsbo), idesc,
+                         (part > 0) || (k > 0));
+          }
           tc::mma_commit(empty(s));
         }
         if (!ok) break;
@@ -306,12 +343,12 @@ struct G2Op {  // DFT along y: rows (kx,c), K = (ri,y) (A MN-major from T1), N =
 
 struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
   static constexpr bool kConstB = true;
+  static constexpr bool kBulkA = true;  // Yh rows are the swizzled A tiles (yh_off)
   const bf16* Yh; const bf16* Gy; bf16* T3;
   typedef NoState State;
   __device__ int rows(int) const { return 512; }
-  __device__ const uint4* a_src(int b, int m, int k) const {
-    return reinterpret_cast<const uint4*>(Yh + ((size_t)b * 512 + m) * 64 + k);
-  }
+  __device__ const uint4* a_src(int b, int m, int k) const { return reinterpret_cast<const uint4*>(Yh + yh_off(b, m, k)); }
+  __device__ const bf16* a_tile(int b, int m0, int) const { return Yh + (size_t)(b * 512 + m0) * 64; }
   __device__ const uint4* b_src(int, int n, int k) const { return reinterpret_cast<const uint4*>(Gy + n * 64 + k); }
   __device__ void epi_begin(State&) const {}
   __device__ void epi(int b, int m, int c0, const float* v, State&) const {
@@ -457,7 +494,12 @@ g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int rows, int nwin, int wtile
                                  pack2(v[4 * h + 1][2 * oo], v[4 * h + 1][2 * oo + 1]),
                                  pack2(v[4 * h + 2][2 * oo], v[4 * h + 2][2 * oo + 1]),
                                  pack2(v[4 * h + 3][2 * oo], v[4 * h + 3][2 * oo + 1]));
-            st_global_v8(Yh + (((size_t)w * 512) + (oc * 8 + oo) * 16 + kx) * 64 + qg * Q * 2, q4[0], q4[1]);
+            // logical chunks 2 qg, 2 qg + 1 of row (w, o, kx) sit at (2 qg) ^ r, (2 qg + 1) ^ r with
+            // r = kx % 8: the same 32-byte sector, halves swapped when r is odd (yh_off)
+            const int r = kx & 7, c0 = (2 * qg) ^ r;
+            bf16* row = Yh + (((size_t)w * 512) + (oc * 8 + oo) * 16 + kx) * 64;
+            if (c0 & 1) st_global_v8(row + (c0 & ~1) * 8, q4[1], q4[0]);
+            else st_global_v8(row + c0 * 8, q4[0], q4[1]);
           }
         }
       }

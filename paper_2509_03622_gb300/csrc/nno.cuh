@@ -48,12 +48,20 @@ __host__ __device__ constexpr size_t r_off(int md, int n, int k) {
   return (size_t)md * 4096 + (size_t)n * 64 + ((((k >> 3) ^ (n & 7)) << 3) | (k & 7));
 }
 
+// Mixed spectrum: element (window w, m = (o,kx), k = (q,ri)); each 128-byte
+// row (w, m) keeps its 16-byte chunk k/8 at chunk (k/8) ^ (m % 8), the
+// 128-byte swizzled K-major operand layout, so a tile of 128 rows of one
+// window is one contiguous bulk copy for the inverse DFT along y.
+__host__ __device__ constexpr size_t yh_off(int w, int m, int k) {
+  return ((size_t)w * 512 + m) * 64 + ((((k >> 3) ^ (m & 7)) << 3) | (k & 7));
+}
+
 struct NnoWork {
   int cap = 0;              // windows per batch
   bf16* X = nullptr;        // [cap][80 y][x/8][c/8][x%8][c%8]  activations, tiled (in place)
   bf16* T1 = nullptr;       // [cap][160 (ri,y)][512 (kx,c)]
   bf16* Xh = nullptr;       // [512 mode][xh_rows(cap) w][64 (c,ri)], chunks swizzled: xh_off
-  bf16* Yh = nullptr;       // [cap][512 (o,kx)][64 (q,ri)]
+  bf16* Yh = nullptr;       // [cap][512 (o,kx)][64 (q,ri)], chunks swizzled: yh_off
   bf16* T3 = nullptr;       // [cap][80 y][o/8][k/8][o%8][k%8]  k = (kx,ri), tiled
   float* rho = nullptr;     // [cap]
   int* err = nullptr;       // bounded-wait failure flag
