@@ -5,20 +5,22 @@
 //   rho    : window RMS (residual and Robin data)                 (SIMT)
 //   lift   : restriction + the 15 input channels over rho, built in shared
 //            memory by the kernel's own warps, [6400 px][16] x [32][16]^T,
-//            then block 0's G1, in the G5 pipeline
+//            then block 0's G1, in the G5 pipeline (only G1's result is
+//            stored: block 0 rebuilds the inputs and applies W0 L to them)
 //   block b (the truncated 2D DFT is done as two 1D DFT GEMMs each way):
 //     G1  DFT along x   : rows (y,c)   K = x 80        N = (kx,ri) 32   A MN-major
 //         (inside the kernel that produced the block's input rows)
 //     G2  DFT along y   : rows (kx,c)  K = (ri,y) 160  N = (q,ri) 64    A MN-major
-//     G3  spectral mix  : rows = windows, K = (c,ri) 64, N = (o,ri) 64, 4 or 2 modes per CTA
-//         writing window-major, or one mode per tile + a transpose (autotuned)
-//     G4  inverse DFT y : rows (o,kx)  K = (q,ri) 64   N = (y,ri) 160
+//     G3  spectral mix  : rows = windows, K = (c,ri) 64, N = (o,ri) 64 per mode,
+//         8 modes per work item, writing window-major (persistent, bulk copies)
+//     G4  inverse DFT y : rows (o,kx)  K = (q,ri) 64   N = (y,ri) 160  (A bulk-copied)
 //     G5  fused: inverse real DFT along x + W x + bias + leaky-ReLU, per y row:
 //         D_y[x][o] = Gx[x][:] . T3_y[o][:] + X_y[x][:] . W[o][:]
 //         then the next block's G1 on the new rows (warp-specialised, bulk copies)
-//   proj   : [6400 px][32] x [128][32]^T, leaky, 128 -> 2, times rho,
-//            written to the window's core in the global field (restricted
-//            prolongation) or to a per-window array.
+//   proj   : [6400 px][32] x [128 (+2)][32]^T, leaky, 128 -> 2 (second MMA
+//            with its operand in tensor memory), times rho, written to the
+//            window's core in the global field (restricted prolongation) or
+//            to a per-window array.
 // Each GEMM epilogue writes the layout the next stage reads, with lanes
 // mapped to the contiguous output dimension (coalesced stores).
 #include <math.h>
@@ -48,10 +50,6 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
 // tiled activation layout: [window*80 + y][x/8][c/8][x%8][c%8] (bf16 elements)
 __device__ __forceinline__ size_t xt_off(size_t wy, int x, int c) {
   return wy * 2560 + (size_t)((x >> 3) * 256 + (c >> 3) * 64 + (x & 7) * 8 + (c & 7));
-}
-// tiled packed inputs: [window*80 + y][x/8][k/8][x%8][k%8] (16 input channels)
-__device__ __forceinline__ size_t in_off(size_t wy, int x, int k) {
-  return wy * 1280 + (size_t)((x >> 3) * 128 + (k >> 3) * 64 + (x & 7) * 8 + (k & 7));
 }
 // tiled inverse-y spectrum: [window*80 + y][o/8][k/8][o%8][k%8], k = (kx,ri)
 __device__ __forceinline__ size_t t3_off(size_t wy, int o, int k) {
