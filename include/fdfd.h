@@ -135,8 +135,9 @@ typedef struct {
   size_t workspace_bytes;/* device memory held by the handle              */
   int graphs_cached;     /* Arnoldi-step graph sets currently captured     */
   int graphs_ok;         /* 0 once a capture failed (eager launches only)  */
-  int tuned_dfty_split;  /* autotuned at set-up: K split of the DFT-y GEMM
-                            (1 or 2)                                      */
+  int tuned_dfty_split;  /* autotuned at set-up: DFT-y GEMM variant, 0 =
+                            operand tiles by TMA, 1 or 2 = gather with that
+                            K split                                       */
 } fdfd_info;
 
 /* ---- handle life cycle ----------------------------------------------- */

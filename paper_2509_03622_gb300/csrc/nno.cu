@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cstring>
 #include <vector>
+#include <cuda.h>
 #include <cuda_fp8.h>
 #include "nno.cuh"
 #include "ctx.cuh"
@@ -134,10 +135,23 @@ __device__ __forceinline__ const void* bulk_a_src(const Op& op, int b, int m0) {
   if constexpr (bulk_a<Op>()) return op.a_tile(b, m0, 0);
   else return nullptr;
 }
+template <class Op, class = void>
+struct HasTmaA { static constexpr bool value = false; };
+template <class Op>
+struct HasTmaA<Op, decltype((void)Op::kTmaA)> { static constexpr bool value = Op::kTmaA; };
+template <class Op>
+__host__ __device__ constexpr bool tma_a() { return HasTmaA<Op>::value; }
+template <class Op>
+__device__ __forceinline__ const void* tma_map(const Op& op) {
+  if constexpr (tma_a<Op>()) return &op.tmap;
+  else return nullptr;
+}
 
 template <int BN, int K, bool AMN, class Op, int KS>
-__global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_per_batch, int total, int* err) {
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+gemm_kernel(const __grid_constant__ Op op, int tiles_per_batch, int total, int* err) {
   static_assert(!bulk_a<Op>() || (!AMN && K == 64 && KS == 1), "bulk A: swizzled 128-byte K-major rows");
+  static_assert(!tma_a<Op>() || (AMN && K == 160 && KS == 2), "TMA A: two 64 x 80 boxes per stage");
   static_assert(K % 16 == 0 && BN % 32 == 0 && BN <= 256, "shape");
   typedef GemmCfg<BN, K, AMN, Op, KS> Cfg;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -160,7 +174,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_
     tc::cp_async_wait_all();
   }
   if (tid == 0) {
-    for (int s = 0; s < Cfg::S; ++s) { tc::mbar_init(full(s), bulk_a<Op>() ? 1 : 128); tc::mbar_init(empty(s), 1); }
+    for (int s = 0; s < Cfg::S; ++s) {
+      tc::mbar_init(full(s), (bulk_a<Op>() || tma_a<Op>()) ? 1 : 128);
+      tc::mbar_init(empty(s), 1);
+    }
     for (int a = 0; a < 2; ++a) { tc::mbar_init(acc_full(a), 1); tc::mbar_init(acc_empty(a), 4); }
     *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
     tc::fence_mbar_init();
@@ -173,7 +190,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_
   const uint32_t tmem = *tslot;
   auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
 
-  if (bulk_a<Op>() && (sbase & 1023)) {  // swizzled tiles need 1024-byte alignment
+  if ((bulk_a<Op>() || tma_a<Op>()) && (sbase & 1023)) {  // swizzled tiles need 1024-byte alignment
     if (tid == 0) atomicExch(err, 1);
     *abort_flag = 1;
   }
@@ -188,6 +205,23 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_
         tc::bulk_g2s(sbase + s * Cfg::STAGE, bulk_a_src(op, b, m0), Cfg::A_BYTES, full(s));
       }
       // every copy issued must have landed before the CTA may exit
+      for (int j = (it > Cfg::S ? it - Cfg::S : 0); j < it; ++j)
+        if (!tc::mbar_wait(full(j % Cfg::S), (j / Cfg::S) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
+    }
+  } else if (warp < 4 && tma_a<Op>()) {  // ---------------- producer: two TMA boxes per stage ----------------
+    if (warp == 0 && lane == 0) {
+      int it = 0;
+      for (int tile = blockIdx.x; tile < total && !*abort_flag; tile += gridDim.x) {
+        const int b = tile / tiles_per_batch, m0 = (tile % tiles_per_batch) * 128;
+        for (int part = 0; part < KS; ++part, ++it) {
+          const int s = it % Cfg::S;
+          if (it >= Cfg::S && !tc::mbar_wait(empty(s), ((it / Cfg::S) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+          tc::mbar_arrive_tx(full(s), Cfg::A_BYTES);
+          for (int h = 0; h < 2; ++h)
+            tc::tma_load_2d(sbase + s * Cfg::STAGE + h * (Cfg::A_BYTES / 2), tma_map(op), m0 + 64 * h,
+                            b * K + part * Cfg::KH, full(s));
+        }
+      }
       for (int j = (it > Cfg::S ? it - Cfg::S : 0); j < it; ++j)
         if (!tc::mbar_wait(full(j % Cfg::S), (j / Cfg::S) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
     }
@@ -224,8 +258,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(Op op, int tiles_
           const uint32_t bsbo = Op::kConstB ? K * 16 : Cfg::KH * 16;
 #pragma unroll
           for (int k = 0; k < Cfg::KH / 16; ++k) {
-            const uint64_t ad = bulk_a<Op>() ? tc::make_desc_sw128(a0 + k * 32, 1024)
-                                             : tc::make_desc(a0 + k * 256, 128, Cfg::KH * 16);
+            const uint64_t ad = tma_a<Op>()    ? tc::make_desc_sw128_mn(a0 + k * 2048, Cfg::A_BYTES / 2, 1024)
+                                : bulk_a<Op>() ? tc::make_desc_sw128(a0 + k * 32, 1024)
+                                               : tc::make_desc(a0 + k * 256, 128, Cfg::KH * 16);
             tc::mma_bf16(tmem + a * Cfg::TCOLS, ad, tc::make_desc(b0 + k * 256, 128, bsbo), idesc,
                          (part > 0) || (k > 0));
           }
@@ -338,6 +373,14 @@ struct G2Op {  // DFT along y: rows (kx,c), K = (ri,y) (A MN-major from T1), N =
   __device__ void epi_end(int, int, State&) const {}
 };
 
+
+// The same GEMM with its A tiles loaded by TMA from T1 viewed as a 2D
+// tensor [rows (w, ri, y)][512 (kx,c)]: per stage (80 rows of K) two boxes of
+// 64 x 80 with 128-byte swizzle, read through MN-major swizzled descriptors.
+struct G2TmaOp : G2Op {
+  static constexpr bool kTmaA = true;
+  CUtensorMap tmap;
+};
 
 struct G4Op {  // inverse DFT along y: rows (o,kx), K = (q,ri), N = (y,ri)
   static constexpr bool kConstB = true;
@@ -1442,8 +1485,43 @@ int launch_g3(NnoWork* k, const bf16* R, int n, cudaStream_t s) {
   return FDFD_OK;
 }
 
-int launch_g2(NnoWork* k, const NnoWeights* W, int n, int split, cudaStream_t s) {
-  if (split == 2) return launch_gemm<64, 160, true, G2Op, 2>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s);
+// The driver's tensor-map encoder, looked up through the runtime so that the
+// library has no load-time dependency on the driver library.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// DFT-y GEMM variants: 0 = A tiles by TMA (tensor map over T1), 1 or 2 =
+// the cp.async gather with that K split.
+int launch_g2(NnoWork* k, const NnoWeights* W, int n, int variant, cudaStream_t s) {
+  if (variant == 0) {
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return FDFD_ECUDA;
+    G2TmaOp op;
+    static_cast<G2Op&>(op) = G2Op{k->T1, W->Fy, k->Xh, k->cap};
+    const cuuint64_t dims[2] = {512, (cuuint64_t)k->cap * 160};
+    const cuuint64_t strides[1] = {512 * sizeof(bf16)};
+    const cuuint32_t box[2] = {64, 80}, estr[2] = {1, 1};
+    if (enc(&op.tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)k->T1, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return FDFD_ECUDA;
+    return launch_gemm<64, 160, true, G2TmaOp, 2>(op, 512 / 128, n, k->err, s);
+  }
+  if (variant == 2) return launch_gemm<64, 160, true, G2Op, 2>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s);
   return launch_gemm<64, 160, true, G2Op, 1>(G2Op{k->T1, W->Fy, k->Xh, k->cap}, 512 / 128, n, k->err, s);
 }
 
@@ -1471,8 +1549,8 @@ int nno_autotune(const NnoWeights* W, NnoWork* k, int n, cudaStream_t s) {
     }
     return best;
   };
-  const int g2opts[2] = {2, 1};
-  const int g2 = best_of([&](int sp) { return launch_g2(k, W, n, sp, s); }, g2opts, 2);
+  const int g2opts[3] = {0, 2, 1};
+  const int g2 = best_of([&](int v) { return launch_g2(k, W, n, v, s); }, g2opts, 3);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (g2 < 0) return FDFD_ECUDA;

@@ -65,7 +65,8 @@ struct NnoWork {
   bf16* T3 = nullptr;       // [cap][80 y][o/8][k/8][o%8][k%8]  k = (kx,ri), tiled
   float* rho = nullptr;     // [cap]
   int* err = nullptr;       // bounded-wait failure flag
-  int g2_split = 2;         // K split of the DFT-y GEMM (1 or 2), set by nno_autotune
+  int g2_split = 0;         // DFT-y GEMM variant, set by nno_autotune: 0 = A tiles by TMA,
+                            // 1 or 2 = cp.async gather with that K split
 };
 
 // One problem of a multi-problem window batch (batching pattern).
@@ -111,9 +112,9 @@ struct GridGeom {
 int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t* bytes);
 void nno_free_weights(NnoWeights* W);
 int nno_alloc_work(NnoWork* w, int cap, size_t* bytes);
-// Autotuner: time the variants of the shape-dependent stage (K split of the
-// DFT-y GEMM) on n windows of the work buffers with CUDA events and keep the
-// fastest in `work`.
+// Autotuner: time the variants of the shape-dependent stage (the DFT-y
+// GEMM: TMA-loaded operand tiles, or the gather with K split 1 or 2) on n
+// windows of the work buffers with CUDA events and keep the fastest in `work`.
 int nno_autotune(const NnoWeights* W, NnoWork* work, int n, cudaStream_t s);
 void nno_free_work(NnoWork* w);
 struct fdfd_ctx;

@@ -45,6 +45,21 @@ __device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr, uint32_t sbo
   return d;
 }
 
+// Descriptor of an MN-major tile in the 128-byte swizzled layout (as a TMA
+// load with 128-byte swizzle writes it): 8-row K groups of 128-byte rows
+// (64 M/N elements each), `sbo` bytes between K groups, `lbo` bytes between
+// 64-element M/N blocks; 1024-byte aligned; a K step of 16 advances `saddr`
+// by two K groups.
+__device__ __forceinline__ uint64_t make_desc_sw128_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;  // SWIZZLE_128B
+  return d;
+}
+
 // Instruction descriptor for kind::f16: BF16 A/B, FP32 accumulator, M = 128.
 __host__ __device__ constexpr uint32_t idesc_bf16(int n, bool a_mn_major, bool b_mn_major) {
   return (1u << 4)                        // D format: F32
@@ -192,6 +207,17 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst_saddr, const void* src, ui
       "l"(src), "r"(bytes), "r"(mbar_saddr)
       : "memory");
 }
+// One 2D tile of a tensor map (in parameter or global memory) into shared
+// memory, counted against the transaction count of the mbarrier; (x, y) is
+// the tile's origin, x along the contiguous dimension.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst_saddr, const void* tmap, int x, int y, uint32_t mbar_saddr) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst_saddr),
+      "l"(tmap), "r"(x), "r"(y), "r"(mbar_saddr)
+      : "memory");
+}
+
 // Arrive on the barrier and add `bytes` to the transactions its phase awaits.
 __device__ __forceinline__ void mbar_arrive_tx(uint32_t mbar_saddr, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_saddr), "r"(bytes) : "memory");
