@@ -110,7 +110,7 @@ MEASURED_TRAFFIC = {
     "nno_proj": 440609,
     "nno_mix": 119429,
     "nno_lift": 198995,
-    "nno_dft_y": 222071,
+    "nno_dft_y": 221240,
     "nno_idft_y": 215262,
     "nno_pack": 32796,
 }
@@ -123,8 +123,8 @@ NNO_FLOP_PER_WIN = {
 KERNEL_NAMES = {"stencil": "stencil_c64", "cgs_dots": "cgs_dots_kernel", "cgs_update": "cgs_update_kernel",
                 "residual64": "residual64", "nno_pack": "rho_kernel (window RMS)",
                 "nno_lift": "g5_kernel<lift> (input channels + lift + block-0 DFT-x)",
-                "nno_dft_x": "gemm_kernel<32,80,MN> (G1Op)", "nno_dft_y": "gemm_kernel<64,160,MN> (G2Op)",
-                "nno_mix": "g3_kernel (spectral mixing)", "nno_idft_y": "gemm_kernel<160,64> (G4Op)",
+                "nno_dft_x": "gemm_kernel<32,80,MN> (G1Op)", "nno_dft_y": "gemm_kernel<64,160,MN> (G2Op; operand tiles by TMA or gather, autotuned)",
+                "nno_mix": "g3_kernel (spectral mixing)", "nno_idft_y": "gemm_kernel<160,64> (G4Op, bulk-copied swizzled operand)",
                 "nno_idft_x_mix_act": "g5_kernel", "nno_proj": "proj_kernel", "rhs_norm": "residual64 (x = 0)"}
 
 

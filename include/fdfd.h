@@ -137,7 +137,8 @@ typedef struct {
   int graphs_ok;         /* 0 once a capture failed (eager launches only)  */
   int tuned_dfty_split;  /* autotuned at set-up: DFT-y GEMM variant, 0 =
                             operand tiles by TMA, 1 or 2 = gather with that
-                            K split                                       */
+                            K split; the environment variable
+                            FDFD_DFTY_VARIANT=0|1|2 fixes it instead      */
 } fdfd_info;
 
 /* ---- handle life cycle ----------------------------------------------- */

@@ -24,6 +24,7 @@
 // Each GEMM epilogue writes the layout the next stage reads, with lanes
 // mapped to the contiguous output dimension (coalesced stores).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 #include <algorithm>
 #include <cstring>
@@ -1550,7 +1551,12 @@ int nno_autotune(const NnoWeights* W, NnoWork* k, int n, cudaStream_t s) {
     return best;
   };
   const int g2opts[3] = {0, 2, 1};
-  const int g2 = best_of([&](int v) { return launch_g2(k, W, n, v, s); }, g2opts, 3);
+  // FDFD_DFTY_VARIANT=0|1|2 fixes the choice (e.g. under a profiler, whose
+  // serialised replay distorts the timings)
+  const char* fix = getenv("FDFD_DFTY_VARIANT");
+  const int g2 = (fix && fix[0] >= '0' && fix[0] <= '2' && fix[1] == 0)
+                     ? fix[0] - '0'
+                     : best_of([&](int v) { return launch_g2(k, W, n, v, s); }, g2opts, 3);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (g2 < 0) return FDFD_ECUDA;
