@@ -565,7 +565,7 @@ g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int rows, int nwin, int wtile
 // (G1: T1[(ri,y)][(kx,c)] = sum_x Fx[(kx,ri)][x] X_y[x][c]), so X is not
 // read again for it.
 // Roles: warp 0 lane 0 = producer (one bulk copy of the 4 X rows, 20 KB, and
-// one of the 4 T3 rows, 8 KB, per unit into a G5_STAGES-deep ring, completion
+// one of the 4 T3 rows, 8 KB, per unit into a ring of 5 stages (4 with FP8 staging), completion
 // by transaction count), warp 1 lane 0 = MMA issuer, warps 4..11 = epilogue;
 // in the lift and IN0, warps 2, 3, 12, 13 build the input channels
 // (warp w reads TMEM lanes 32(w%4)..).  Three accumulator sets in TMEM (G5:
@@ -579,26 +579,32 @@ g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int rows, int nwin, int wtile
 // X and T3 are stored tiled (core-matrix order), so one row is one
 // contiguous K-major operand tile.
 constexpr int G5_ROWS = 4;
-constexpr int G5_STAGES = 4;
 constexpr int G5_THREADS = 448;  // warps 12, 13: extra input builders (lift, IN0)
 constexpr uint32_t G5_XT = 80 * 32 * 2;                          // one tiled [80][32] X row
 constexpr uint32_t G5_XB = G5_ROWS * G5_XT;                      // 20480
 constexpr uint32_t G5_TB = G5_ROWS * 2048;                       // 8192
 constexpr uint32_t G5_X8B = G5_ROWS * 2560;                      // 10240: the rows in FP8 (staging)
-constexpr uint32_t G5_STAGE = G5_XB + G5_TB + G5_X8B;            // 38912
 constexpr uint32_t G5_A1 = 128 * 80 * 2;                         // G1 A tile, MN-major (yy,c) x x
-constexpr uint32_t G5_OFF_A1 = G5_STAGES * G5_STAGE;             // after the ring (absorbs the over-read)
-constexpr uint32_t G5_OFF_GX = G5_OFF_A1 + 2 * G5_A1;
-constexpr uint32_t G5_OFF_W = G5_OFF_GX + 128 * 32 * 2;
-constexpr uint32_t G5_OFF_FX = G5_OFF_W + 32 * 32 * 2;
-constexpr uint32_t G5_OFF_ONE = G5_OFF_FX + 32 * 80 * 2;         // [128][16] K-major: 1, 1, 0 ...
-constexpr uint32_t G5_OFF_BIAS = G5_OFF_ONE + 128 * 16 * 2;      // [128 (yy,o)][16] K-major: bias hi, lo, 0 ...
-constexpr uint32_t G5_OFF_BAR = G5_OFF_BIAS + 128 * 16 * 2;
 constexpr int G5_NACC = 3;                                        // TMEM accumulator sets
 constexpr uint32_t G5_ACC = 160;                                  // TMEM columns per set
-constexpr uint32_t G5_NBAR = 3 * G5_STAGES + 3 * G5_NACC + 2;
-constexpr uint32_t G5_SMEM = G5_OFF_BAR + G5_NBAR * 8 + 16;
-static_assert(G5_SMEM <= 227 * 1024, "g5 shared memory");
+// Shared-memory layout: the ring of stages (the FP8 variant also stages the
+// rows in FP8, so its stages are larger and fewer), then the G1 A tiles, the
+// constant operands and the barriers.
+template <bool FP8>
+struct G5L {
+  static constexpr int STAGES = FP8 ? 4 : 5;
+  static constexpr uint32_t STAGE = G5_XB + G5_TB + (FP8 ? G5_X8B : 0);  // 38912 or 28672
+  static constexpr uint32_t OFF_A1 = STAGES * STAGE;                     // after the ring (absorbs the over-read)
+  static constexpr uint32_t OFF_GX = OFF_A1 + 2 * G5_A1;
+  static constexpr uint32_t OFF_W = OFF_GX + 128 * 32 * 2;
+  static constexpr uint32_t OFF_FX = OFF_W + 32 * 32 * 2;
+  static constexpr uint32_t OFF_ONE = OFF_FX + 32 * 80 * 2;               // [128][16] K-major: 1, 1, 0 ...
+  static constexpr uint32_t OFF_BIAS = OFF_ONE + 128 * 16 * 2;            // [128 (yy,o)][16]: bias hi, lo, 0 ...
+  static constexpr uint32_t OFF_BAR = OFF_BIAS + 128 * 16 * 2;
+  static constexpr uint32_t NBAR = 3 * STAGES + 3 * G5_NACC + 2;
+  static constexpr uint32_t SMEM = OFF_BAR + NBAR * 8 + 16;
+  static_assert(SMEM <= 227 * 1024, "g5 shared memory");
+};
 
 // FP8 tiled activation layout: [window*80 + y][x/8][c/16][x%8][c%16] (bytes)
 __device__ __forceinline__ size_t x8_off(size_t wy, int x, int c) {
@@ -704,20 +710,21 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   // FP8: X holds E4M3 activations (x8_off layout).  The unit's input rows
   // are bulk-copied as FP8 and converted to BF16 by warps 2-3 (the scale is
   // folded into Wb); the output rows are written as E4M3 times qinv[c].
+  typedef G5L<FP8> L;
   extern __shared__ __align__(1024) uint8_t smem[];
   const uint32_t sbase = tc::smem_u32(smem);
-  const uint32_t bar = sbase + G5_OFF_BAR;
+  const uint32_t bar = sbase + L::OFF_BAR;
   // barriers: full[s], empty[s], g5_full[3], g1_full[3], acc_empty[3], a1_full[2], conv_full[s]
   auto full = [&](int s) { return bar + 8u * s; };
-  auto empty = [&](int s) { return bar + 8u * (G5_STAGES + s); };
-  auto g5_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + a); };
-  auto g1_full = [&](int a) { return bar + 8u * (2 * G5_STAGES + G5_NACC + a); };
-  auto acc_empty = [&](int a) { return bar + 8u * (2 * G5_STAGES + 2 * G5_NACC + a); };
-  auto a1_full = [&](int b) { return bar + 8u * (2 * G5_STAGES + 3 * G5_NACC + b); };
-  auto conv_full = [&](int s) { return bar + 8u * (2 * G5_STAGES + 3 * G5_NACC + 2 + s); };  // FP8 rows converted
+  auto empty = [&](int s) { return bar + 8u * (L::STAGES + s); };
+  auto g5_full = [&](int a) { return bar + 8u * (2 * L::STAGES + a); };
+  auto g1_full = [&](int a) { return bar + 8u * (2 * L::STAGES + G5_NACC + a); };
+  auto acc_empty = [&](int a) { return bar + 8u * (2 * L::STAGES + 2 * G5_NACC + a); };
+  auto a1_full = [&](int b) { return bar + 8u * (2 * L::STAGES + 3 * G5_NACC + b); };
+  auto conv_full = [&](int s) { return bar + 8u * (2 * L::STAGES + 3 * G5_NACC + 2 + s); };  // FP8 rows converted
   constexpr bool CONV = FP8 && !LIFT;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G5_OFF_BAR + G5_NBAR * 8);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + G5_OFF_BAR + G5_NBAR * 8 + 4);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::OFF_BAR + L::NBAR * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::OFF_BAR + L::NBAR * 8 + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int UPW = 80 / G5_ROWS;
   if ((int)blockIdx.x >= total) return;
@@ -726,38 +733,38 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   if (!LIFT)
     for (int c = tid; c < 128 * 4; c += G5_THREADS) {
       const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
-      tc::cp_async16(smem + G5_OFF_GX + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
+      tc::cp_async16(smem + L::OFF_GX + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
     }
   constexpr int WK = (LIFT || IN0) ? 2 : 4;  // k-groups of the mixer / lift weights
   for (int c = tid; c < 32 * WK; c += G5_THREADS) {
     const int t8 = c & 7, rest = c >> 3, kc = rest % WK, rg = rest / WK;
-    tc::cp_async16(smem + G5_OFF_W + (rg * WK + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * (8 * WK) + kc * 8, true);
+    tc::cp_async16(smem + L::OFF_W + (rg * WK + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * (8 * WK) + kc * 8, true);
   }
   if (!last)
     for (int c = tid; c < 32 * 10; c += G5_THREADS) {
       const int t8 = c & 7, rest = c >> 3, kc = rest % 10, rg = rest / 10;
-      tc::cp_async16(smem + G5_OFF_FX + (rg * 10 + kc) * 128 + t8 * 16, Fx + (rg * 8 + t8) * 80 + kc * 8, true);
+      tc::cp_async16(smem + L::OFF_FX + (rg * 10 + kc) * 128 + t8 * 16, Fx + (rg * 8 + t8) * 80 + kc * 8, true);
     }
   // the bias enters the accumulator through one more MMA: a ones column pair
   // times the bias split into two BF16 parts (hi + lo carry it to ~2^-16)
   for (int c = tid; c < 128 * 16; c += G5_THREADS) {
     const int r = c >> 4, k = c & 15;
-    *reinterpret_cast<bf16*>(smem + G5_OFF_ONE + tc::kmaj_off(r, k, 16)) = __float2bfloat16_rn(k < 2 ? 1.f : 0.f);
+    *reinterpret_cast<bf16*>(smem + L::OFF_ONE + tc::kmaj_off(r, k, 16)) = __float2bfloat16_rn(k < 2 ? 1.f : 0.f);
   }
   for (int c = tid; c < 128 * 16; c += G5_THREADS) {  // one row of bias per (yy, o): the unit's 4 rows at once
     const int n = c >> 4, k = c & 15, o = n & 31;
     const bf16 hi = __float2bfloat16_rn(bias[o]);
     const float v = k == 0 ? bias[o] : k == 1 ? bias[o] - __bfloat162float(hi) : 0.f;
-    *reinterpret_cast<bf16*>(smem + G5_OFF_BIAS + tc::kmaj_off(n, k, 16)) = __float2bfloat16_rn(v);
+    *reinterpret_cast<bf16*>(smem + L::OFF_BIAS + tc::kmaj_off(n, k, 16)) = __float2bfloat16_rn(v);
   }
   tc::cp_async_wait_all();
   if (tid == 0) {
-    for (int s = 0; s < G5_STAGES; ++s) { tc::mbar_init(full(s), IN0 ? 2 : 1); tc::mbar_init(empty(s), 1); }
+    for (int s = 0; s < L::STAGES; ++s) { tc::mbar_init(full(s), IN0 ? 2 : 1); tc::mbar_init(empty(s), 1); }
     for (int a = 0; a < G5_NACC; ++a) {
       tc::mbar_init(g5_full(a), 1); tc::mbar_init(g1_full(a), 1); tc::mbar_init(acc_empty(a), 8);
     }
     for (int b = 0; b < 2; ++b) tc::mbar_init(a1_full(b), 8);
-    for (int s = 0; s < G5_STAGES; ++s) tc::mbar_init(conv_full(s), 2);
+    for (int s = 0; s < L::STAGES; ++s) tc::mbar_init(conv_full(s), 2);
     *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
     tc::fence_mbar_init();
   }
@@ -777,16 +784,16 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
     // a builder then never waits on a stage's empty barrier more than one
     // phase ahead of it (a parity wait cannot tell phases two apart).
     constexpr int NB = 4;
-    static_assert(NB <= G5_STAGES, "builders ahead of the ring");
+    static_assert(NB <= L::STAGES, "builders ahead of the ring");
     const int bw = warp >= 12 ? warp - 10 : warp - 2;
     for (int u = blockIdx.x + bw * gridDim.x, it = bw; u < total && !*abort_flag; u += NB * gridDim.x, it += NB) {
-      const int s = it % G5_STAGES;
-      if (it >= G5_STAGES && !tc::mbar_wait(empty(s), ((it / G5_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+      const int s = it % L::STAGES;
+      if (it >= L::STAGES && !tc::mbar_wait(empty(s), ((it / L::STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
       const int b = u / UPW, y0r = (u % UPW) * G5_ROWS;
       const WinSrc ws = win_src(lsrc.in, lsrc.g, b);
       const float rho = lsrc.rho[b];
       const float inv = rho > 0.f ? 1.f / rho : 0.f;
-      uint8_t* st = smem + s * G5_STAGE;
+      uint8_t* st = smem + s * L::STAGE;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         uint4 lo[5], hi[5];
@@ -811,38 +818,38 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
     if (lane == 0 && !LIFT) {  // ---------------- producer (the lift has none) ----------------
       int it = 0;
       for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
-        const int s = it % G5_STAGES;
-        if (it >= G5_STAGES && !tc::mbar_wait(empty(s), ((it / G5_STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
+        const int s = it % L::STAGES;
+        if (it >= L::STAGES && !tc::mbar_wait(empty(s), ((it / L::STAGES) - 1) & 1, WAIT_LIMIT)) { fail(); break; }
         const size_t wy = (size_t)(u / UPW) * 80 + (u % UPW) * G5_ROWS;
         if (IN0) {  // the input channels come from the builders: only the inverse-y spectrum
           tc::mbar_arrive_tx(full(s), G5_TB);
-          tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
+          tc::bulk_g2s(sbase + s * L::STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
         } else if (FP8) {  // FP8 rows into the staging area, the inverse-y spectrum as usual
           tc::mbar_arrive_tx(full(s), G5_X8B + G5_TB);
-          tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB + G5_TB, reinterpret_cast<const uint8_t*>(X) + wy * 2560, G5_X8B,
+          tc::bulk_g2s(sbase + s * L::STAGE + G5_XB + G5_TB, reinterpret_cast<const uint8_t*>(X) + wy * 2560, G5_X8B,
                        full(s));
-          tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
+          tc::bulk_g2s(sbase + s * L::STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
         } else {
           tc::mbar_arrive_tx(full(s), G5_XB + G5_TB);
-          tc::bulk_g2s(sbase + s * G5_STAGE, X + wy * 2560, G5_XB, full(s));
-          tc::bulk_g2s(sbase + s * G5_STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
+          tc::bulk_g2s(sbase + s * L::STAGE, X + wy * 2560, G5_XB, full(s));
+          tc::bulk_g2s(sbase + s * L::STAGE + G5_XB, T3 + wy * 1024, G5_TB, full(s));
         }
       }
       // every copy issued must have landed before the CTA may exit
-      for (int j = (it > G5_STAGES ? it - G5_STAGES : 0); j < it; ++j)
-        if (!tc::mbar_wait(full(j % G5_STAGES), (j / G5_STAGES) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
+      for (int j = (it > L::STAGES ? it - L::STAGES : 0); j < it; ++j)
+        if (!tc::mbar_wait(full(j % L::STAGES), (j / L::STAGES) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---------------- MMA issuer ----------------
       constexpr uint32_t id5 = tc::idesc_bf16(32, false, false);
       constexpr uint32_t id128 = tc::idesc_bf16(128, false, false);
       constexpr uint32_t id1 = tc::idesc_bf16(32, true, false);
-      const uint32_t ag = sbase + G5_OFF_GX, bw = sbase + G5_OFF_W, bfx = sbase + G5_OFF_FX;
+      const uint32_t ag = sbase + L::OFF_GX, bw = sbase + L::OFF_W, bfx = sbase + L::OFF_FX;
       auto issue_g1 = [&](int j) -> bool {  // next block's DFT along x for unit j
         const int b = j & 1, a = j % G5_NACC;
         if (!tc::mbar_wait(a1_full(b), (j >> 1) & 1, WAIT_LIMIT)) return false;
         tc::fence_after();
-        const uint32_t a1 = sbase + G5_OFF_A1 + b * G5_A1;
+        const uint32_t a1 = sbase + L::OFF_A1 + b * G5_A1;
         for (int s = 0; s < 5; ++s)
           tc::mma_bf16(tmem + a * G5_ACC + 128, tc::make_desc(a1 + s * 256, 128, 1280),
                        tc::make_desc(bfx + s * 256, 128, 1280), id1, s > 0);
@@ -852,14 +859,14 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       int it = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < total && !*abort_flag; u += gridDim.x, ++it) {
-        const int s = it % G5_STAGES, a = it % G5_NACC;
-        if (!tc::mbar_wait(CONV ? conv_full(s) : full(s), (it / G5_STAGES) & 1, WAIT_LIMIT)) { ok = false; break; }
+        const int s = it % L::STAGES, a = it % G5_NACC;
+        if (!tc::mbar_wait(CONV ? conv_full(s) : full(s), (it / L::STAGES) & 1, WAIT_LIMIT)) { ok = false; break; }
         if (it >= G5_NACC && !tc::mbar_wait(acc_empty(a), ((it / G5_NACC) - 1) & 1, WAIT_LIMIT)) {
           ok = false;
           break;
         }
         tc::fence_after();
-        const uint32_t ax = sbase + s * G5_STAGE, bt = ax + G5_XB;
+        const uint32_t ax = sbase + s * L::STAGE, bt = ax + G5_XB;
         // the unit's 4 rows side by side (N = 128 columns (yy, o)) where A is shared:
         // the inverse DFT along x (A = Gx, B = the 4 rows of T3) and the bias
         const uint32_t d4 = tmem + a * G5_ACC;
@@ -867,7 +874,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
           for (int k = 0; k < 2; ++k)
             tc::mma_bf16(d4, tc::make_desc(ag + k * 256, 128, 512), tc::make_desc(bt + k * 256, 128, 512), id128,
                          k > 0);
-        tc::mma_bf16(d4, tc::make_desc(sbase + G5_OFF_ONE, 128, 256), tc::make_desc(sbase + G5_OFF_BIAS, 128, 256),
+        tc::mma_bf16(d4, tc::make_desc(sbase + L::OFF_ONE, 128, 256), tc::make_desc(sbase + L::OFF_BIAS, 128, 256),
                      id128, LIFT ? 0 : 1);
         for (int yy = 0; yy < G5_ROWS; ++yy) {  // per row: the mixer (or lift) on the row's own A tile
           const uint32_t d = tmem + a * G5_ACC + yy * 32;
@@ -895,10 +902,10 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       const int ct = tid - 64;  // 0..63
       int it = 0;
       for (int u = blockIdx.x; u < total; u += gridDim.x, ++it) {
-        const int s = it % G5_STAGES;
-        if (*abort_flag || !tc::mbar_wait(full(s), (it / G5_STAGES) & 1, WAIT_LIMIT)) { fail(); break; }
-        const uint8_t* src = smem + s * G5_STAGE + G5_XB + G5_TB;
-        uint8_t* dst = smem + s * G5_STAGE;
+        const int s = it % L::STAGES;
+        if (*abort_flag || !tc::mbar_wait(full(s), (it / L::STAGES) & 1, WAIT_LIMIT)) { fail(); break; }
+        const uint8_t* src = smem + s * L::STAGE + G5_XB + G5_TB;
+        uint8_t* dst = smem + s * L::STAGE;
         for (int c = ct; c < G5_ROWS * 160; c += 64) {  // 16-byte FP8 chunks, row by row
           const int yy = c / 160, r = c % 160, x8 = r >> 4, c16 = (r >> 3) & 1, xr = r & 7;
           uint4 lo, hi;
@@ -946,7 +953,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       if (*abort_flag || !tc::mbar_wait(g5_full(a), (it / G5_NACC) & 1, WAIT_LIMIT)) { ok = false; break; }
       tc::fence_after();
       const size_t wy0 = (size_t)(u / UPW) * 80 + (u % UPW) * G5_ROWS;
-      uint8_t* a1 = smem + G5_OFF_A1 + (it & 1) * G5_A1;
+      uint8_t* a1 = smem + L::OFF_A1 + (it & 1) * G5_A1;
       if (q < 3) {
         const int x = q * 32 + lane;
         for (int yy = hf * 2; yy < hf * 2 + 2; ++yy) {
@@ -1583,13 +1590,17 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
   }
   static int g5_cap = 0;
   if (!g5_cap) {
-    CK(cudaFuncSetAttribute(g5_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
-    CK(cudaFuncSetAttribute(g5_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
-    CK(cudaFuncSetAttribute(g5_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
-    CK(cudaFuncSetAttribute(g5_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5_SMEM));
+    CK(cudaFuncSetAttribute(g5_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)G5L<false>::SMEM));
+    CK(cudaFuncSetAttribute(g5_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)G5L<false>::SMEM));
+    CK(cudaFuncSetAttribute(g5_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)G5L<true>::SMEM));
+    CK(cudaFuncSetAttribute(g5_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)G5L<true>::SMEM));
     CK(cudaFuncSetAttribute(g5_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)G5_SMEM));
-    g5_cap = persistent_grid((const void*)g5_kernel<false, false>, G5_THREADS, G5_SMEM, 512);
+                            (int)G5L<false>::SMEM));
+    g5_cap = persistent_grid((const void*)g5_kernel<false, true>, G5_THREADS, G5L<true>::SMEM, 512);
   }
   const int g5_total = n * (80 / G5_ROWS);
   const int g5_grid = g5_total < g5_cap ? g5_total : g5_cap;
@@ -1601,10 +1612,10 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
      // get their DFT along x from the previous block's G5 kernel
     ProfScope ps(h, 8, 1);
     if (W->fp8)
-      g5_kernel<true, true><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, nullptr, nullptr, W->lift_w, W->lift_b, W->Fx,
+      g5_kernel<true, true><<<g5_grid, G5_THREADS, G5L<true>::SMEM, s>>>(k->X, nullptr, nullptr, W->lift_w, W->lift_b, W->Fx,
                                                                   k->T1, W->qinv, 0, g5_total, k->err, lsrc);
     else
-      g5_kernel<true, false><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, nullptr, nullptr, W->lift_w, W->lift_b, W->Fx,
+      g5_kernel<true, false><<<g5_grid, G5_THREADS, G5L<false>::SMEM, s>>>(k->X, nullptr, nullptr, W->lift_w, W->lift_b, W->Fx,
                                                                    k->T1, nullptr, 0, g5_total, k->err, lsrc);
     CKL();
   }
@@ -1625,15 +1636,15 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     {
       ProfScope ps(h, 13, 1);
       if (W->fp8)
-        g5_kernel<false, true><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W8[bl], W->bias[bl], W->Fx,
+        g5_kernel<false, true><<<g5_grid, G5_THREADS, G5L<true>::SMEM, s>>>(k->X, k->T3, W->Gx, W->W8[bl], W->bias[bl], W->Fx,
                                                                      k->T1, W->qinv + 32 * (bl + 1), bl == 3,
                                                                      g5_total, k->err, LiftSrc{});
       else if (bl == 0 && in0)
-        g5_kernel<false, false, true><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W0L, W->bias0L,
+        g5_kernel<false, false, true><<<g5_grid, G5_THREADS, G5L<false>::SMEM, s>>>(k->X, k->T3, W->Gx, W->W0L, W->bias0L,
                                                                             W->Fx, k->T1, nullptr, 0, g5_total, k->err,
                                                                             lsrc);
       else
-        g5_kernel<false, false><<<g5_grid, G5_THREADS, G5_SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], W->Fx,
+        g5_kernel<false, false><<<g5_grid, G5_THREADS, G5L<false>::SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], W->Fx,
                                                                       k->T1, nullptr, bl == 3, g5_total, k->err,
                                                                       LiftSrc{});
       CKL();
