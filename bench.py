@@ -125,7 +125,7 @@ KERNEL_NAMES = {"stencil": "stencil_c64", "cgs_dots": "cgs_dots_kernel", "cgs_up
                 "nno_lift": "g5_kernel<lift> (input channels + lift + block-0 DFT-x)",
                 "nno_dft_x": "gemm_kernel<32,80,MN> (G1Op)", "nno_dft_y": "gemm_kernel<64,160,MN> (G2Op; operand tiles by TMA or gather, autotuned)",
                 "nno_mix": "g3_kernel (spectral mixing)", "nno_idft_y": "gemm_kernel<160,64> (G4Op, bulk-copied swizzled operand)",
-                "nno_idft_x_mix_act": "g5_kernel", "nno_proj": "proj_kernel", "rhs_norm": "residual64 (x = 0)"}
+                "nno_idft_x_mix_act": "g5_kernel (block 0) + g5f_kernel (blocks 1-3, inverse DFT-y fused)", "nno_proj": "proj_kernel", "rhs_norm": "residual64 (x = 0)"}
 
 
 def algorithmic_bytes(cls, launches, N, steps):
@@ -144,8 +144,9 @@ def algorithmic_bytes(cls, launches, N, steps):
     if cls in WIN_BYTES:
         per = WIN_BYTES[cls] * nwin + (512 * 64 * 64 * 2 if cls == "nno_mix" else 0)
         extra = 0
-        if cls == "nno_idft_x_mix_act":  # blocks 0..2 write T1; block 0 reads the inputs, not X
-            extra = (G5_T1_BYTES * 3 - 6400 * (64 - 12)) * nwin * (launches // 4)
+        if cls == "nno_idft_x_mix_act":  # blocks 0..2 write T1; block 0 reads the inputs, not X;
+            # blocks 1..3 compute T3 themselves from the mixed spectrum (65,536 B / window)
+            extra = (G5_T1_BYTES * 3 - 6400 * (64 - 12) - 3 * (80 * 32 * 32 * 2 - 512 * 64 * 2)) * nwin * (launches // 4)
         return float(per) * launches + extra
     return None
 

@@ -1024,6 +1024,338 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   }
 }
 
+// G5 with the inverse DFT along y fused in (blocks 1..3, BF16): each CTA
+// takes whole windows.  Per window the producer bulk-copies the window's
+// mixed spectrum (512 rows of 128 bytes, swizzled: 64 KB) into shared memory
+// once; the MMA warp computes T3 for two units (8 rows y) at a time as
+// 4 tiles x 4 K steps of N = 16 MMAs (A = the spectrum rows (o,kx), B = the
+// 16 rows (y,ri) of Gy) into a 64-column TMEM accumulator; the epilogue
+// warps convert it to BF16 into the G5 B operand tiles in shared memory
+// (one 8 KB tile per unit), which replaces the T3 rows read from HBM.  Four
+// converter warps (2, 3, 12, 13: one per TMEM lane quarter) do that
+// conversion off the epilogue's path.  The
+// rest is the G5 pipeline: X rows by bulk copy (2-stage ring), stacked
+// Gx T3 + bias MMAs, the mixer per row, the software-pipelined epilogue and
+// the next block's DFT along x.  TMEM: two G5 sets (2 x 160 columns) and two
+// 64-column T3 accumulators.
+constexpr int G5F_STAGES = 2;
+constexpr int G5F_NACC = 2;
+constexpr uint32_t G5F_OFF_YH = 0;                                  // [512][64] swizzled rows (1024-aligned)
+constexpr uint32_t G5F_OFF_X = G5F_OFF_YH + 512 * 64 * 2;           // ring of 4-row X tiles
+constexpr uint32_t G5F_OFF_T3 = G5F_OFF_X + G5F_STAGES * G5_XB;     // 4 unit tiles [(yy,o) 128][32]
+constexpr uint32_t G5F_OFF_A1 = G5F_OFF_T3 + 4 * G5_TB;             // absorbs the X tiles' over-read
+constexpr uint32_t G5F_OFF_GY = G5F_OFF_A1 + 2 * G5_A1;             // [160 (y,ri)][64 (q,ri)] K-major
+constexpr uint32_t G5F_OFF_GX = G5F_OFF_GY + 160 * 64 * 2;
+constexpr uint32_t G5F_OFF_W = G5F_OFF_GX + 128 * 32 * 2;
+constexpr uint32_t G5F_OFF_FX = G5F_OFF_W + 32 * 32 * 2;
+constexpr uint32_t G5F_OFF_ONE = G5F_OFF_FX + 32 * 80 * 2;
+constexpr uint32_t G5F_OFF_BIAS = G5F_OFF_ONE + 128 * 16 * 2;
+constexpr uint32_t G5F_OFF_BAR = G5F_OFF_BIAS + 128 * 16 * 2;
+// full[2], empty[2], yh_full, yh_empty, g5_full[2], g1_full[2], acc_empty[2], a1_full[2],
+// d4_full[2], d4_empty[2], t3_full[4], t3_empty[4]
+constexpr uint32_t G5F_NBAR = 2 * G5F_STAGES + 2 + 3 * G5F_NACC + 2 + 4 + 8;
+constexpr uint32_t G5F_SMEM = G5F_OFF_BAR + G5F_NBAR * 8 + 16;
+static_assert(G5F_SMEM <= 227 * 1024, "fused G5 shared memory");
+constexpr uint32_t G5F_D4 = G5F_NACC * G5_ACC;                      // TMEM column of the T3 accumulators
+
+constexpr int G5F_THREADS = 448;
+__global__ void __launch_bounds__(G5F_THREADS, 1)
+g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* Wb, const float* bias,
+           const bf16* Fx, bf16* T1, int last, int nwin, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const uint32_t sbase = tc::smem_u32(smem);
+  const uint32_t bar = sbase + G5F_OFF_BAR;
+  auto full = [&](int s) { return bar + 8u * s; };
+  auto empty = [&](int s) { return bar + 8u * (G5F_STAGES + s); };
+  const uint32_t yh_full = bar + 8u * (2 * G5F_STAGES), yh_empty = yh_full + 8u;
+  auto g5_full = [&](int a) { return bar + 8u * (2 * G5F_STAGES + 2 + a); };
+  auto g1_full = [&](int a) { return bar + 8u * (2 * G5F_STAGES + 2 + G5F_NACC + a); };
+  auto acc_empty = [&](int a) { return bar + 8u * (2 * G5F_STAGES + 2 + 2 * G5F_NACC + a); };
+  auto a1_full = [&](int b) { return bar + 8u * (2 * G5F_STAGES + 2 + 3 * G5F_NACC + b); };
+  auto d4_full = [&](int d) { return bar + 8u * (2 * G5F_STAGES + 4 + 3 * G5F_NACC + d); };
+  auto d4_empty = [&](int d) { return bar + 8u * (2 * G5F_STAGES + 6 + 3 * G5F_NACC + d); };
+  auto t3_full = [&](int b) { return bar + 8u * (2 * G5F_STAGES + 8 + 3 * G5F_NACC + b); };
+  auto t3_empty = [&](int b) { return bar + 8u * (2 * G5F_STAGES + 12 + 3 * G5F_NACC + b); };
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G5F_OFF_BAR + G5F_NBAR * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + G5F_OFF_BAR + G5F_NBAR * 8 + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int UPW = 80 / G5_ROWS;  // 20 units per window
+  if ((int)blockIdx.x >= nwin) return;
+  if (sbase & 1023) {  // the swizzled spectrum needs 1024-byte alignment
+    if (tid == 0) atomicExch(err, 1);
+    return;
+  }
+  // constant operands: Gy [160][64], Gx [128][32], W [32][32], Fx [32][80] (K-major tiles), ones, bias
+  for (int c = tid; c < 160 * 8; c += G5F_THREADS) {
+    const int t8 = c & 7, rest = c >> 3, kc = rest & 7, rg = rest >> 3;
+    tc::cp_async16(smem + G5F_OFF_GY + (rg * 8 + kc) * 128 + t8 * 16, Gy + (rg * 8 + t8) * 64 + kc * 8, true);
+  }
+  for (int c = tid; c < 128 * 4; c += G5F_THREADS) {
+    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
+    tc::cp_async16(smem + G5F_OFF_GX + (rg * 4 + kc) * 128 + t8 * 16, Gx + (rg * 8 + t8) * 32 + kc * 8, true);
+  }
+  for (int c = tid; c < 32 * 4; c += G5F_THREADS) {
+    const int t8 = c & 7, rest = c >> 3, kc = rest & 3, rg = rest >> 2;
+    tc::cp_async16(smem + G5F_OFF_W + (rg * 4 + kc) * 128 + t8 * 16, Wb + (rg * 8 + t8) * 32 + kc * 8, true);
+  }
+  if (!last)
+    for (int c = tid; c < 32 * 10; c += G5F_THREADS) {
+      const int t8 = c & 7, rest = c >> 3, kc = rest % 10, rg = rest / 10;
+      tc::cp_async16(smem + G5F_OFF_FX + (rg * 10 + kc) * 128 + t8 * 16, Fx + (rg * 8 + t8) * 80 + kc * 8, true);
+    }
+  for (int c = tid; c < 128 * 16; c += G5F_THREADS) {
+    const int r = c >> 4, k = c & 15;
+    *reinterpret_cast<bf16*>(smem + G5F_OFF_ONE + tc::kmaj_off(r, k, 16)) = __float2bfloat16_rn(k < 2 ? 1.f : 0.f);
+  }
+  for (int c = tid; c < 128 * 16; c += G5F_THREADS) {
+    const int n = c >> 4, k = c & 15, o = n & 31;
+    const bf16 hi = __float2bfloat16_rn(bias[o]);
+    const float v = k == 0 ? bias[o] : k == 1 ? bias[o] - __bfloat162float(hi) : 0.f;
+    *reinterpret_cast<bf16*>(smem + G5F_OFF_BIAS + tc::kmaj_off(n, k, 16)) = __float2bfloat16_rn(v);
+  }
+  tc::cp_async_wait_all();
+  if (tid == 0) {
+    for (int s = 0; s < G5F_STAGES; ++s) { tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); }
+    tc::mbar_init(yh_full, 1); tc::mbar_init(yh_empty, 1);
+    for (int a = 0; a < G5F_NACC; ++a) {
+      tc::mbar_init(g5_full(a), 1); tc::mbar_init(g1_full(a), 1); tc::mbar_init(acc_empty(a), 8);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(a1_full(b), 8); tc::mbar_init(d4_full(b), 1); tc::mbar_init(d4_empty(b), 4);
+    }
+    for (int b = 0; b < 4; ++b) { tc::mbar_init(t3_full(b), 4); tc::mbar_init(t3_empty(b), 1); }
+    *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(tslot), 512);
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  auto fail = [&]() { atomicExch(err, 1); *abort_flag = 1; };
+  // windows of this CTA: w = blockIdx.x + i * gridDim.x; unit it = 20 i + u; pair P = 10 i + p
+  const int nmine = (nwin - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- producer ----------------
+      int it = 0, nyh = 0;
+      bool ok = true;
+      for (int i = 0; i < nmine && ok && !*abort_flag; ++i) {
+        const int w = blockIdx.x + i * gridDim.x;
+        // the window's spectrum, once the previous window's T3 MMAs are done with the buffer
+        if (i >= 1 && !tc::mbar_wait(yh_empty, (i - 1) & 1, WAIT_LIMIT)) { ok = false; break; }
+        tc::mbar_arrive_tx(yh_full, 512 * 128);
+        tc::bulk_g2s(sbase + G5F_OFF_YH, Yh + (size_t)w * 512 * 64, 512 * 128, yh_full);
+        ++nyh;
+        for (int u = 0; u < UPW; ++u, ++it) {
+          const int s = it % G5F_STAGES;
+          if (it >= G5F_STAGES && !tc::mbar_wait(empty(s), ((it / G5F_STAGES) - 1) & 1, WAIT_LIMIT)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_tx(full(s), G5_XB);
+          tc::bulk_g2s(sbase + G5F_OFF_X + s * G5_XB, X + ((size_t)w * 80 + u * G5_ROWS) * 2560, G5_XB, full(s));
+        }
+      }
+      if (!ok) fail();
+      // every copy issued must have landed before the CTA may exit
+      for (int j = (it > G5F_STAGES ? it - G5F_STAGES : 0); j < it; ++j)
+        if (!tc::mbar_wait(full(j % G5F_STAGES), (j / G5F_STAGES) & 1, WAIT_LIMIT)) { atomicExch(err, 1); break; }
+      if (nyh >= 1 && !tc::mbar_wait(yh_full, (nyh - 1) & 1, WAIT_LIMIT)) atomicExch(err, 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer ----------------
+      constexpr uint32_t id5 = tc::idesc_bf16(32, false, false);
+      constexpr uint32_t id128 = tc::idesc_bf16(128, false, false);
+      constexpr uint32_t id1 = tc::idesc_bf16(32, true, false);
+      constexpr uint32_t id4 = tc::idesc_bf16(16, false, false);
+      const uint32_t ag = sbase + G5F_OFF_GX, bw = sbase + G5F_OFF_W, bfx = sbase + G5F_OFF_FX;
+      const uint32_t yh = sbase + G5F_OFF_YH, gy = sbase + G5F_OFF_GY;
+      auto issue_g1 = [&](int j) -> bool {  // next block's DFT along x for unit j
+        const int b = j & 1, a = j % G5F_NACC;
+        if (!tc::mbar_wait(a1_full(b), (j >> 1) & 1, WAIT_LIMIT)) return false;
+        tc::fence_after();
+        const uint32_t a1 = sbase + G5F_OFF_A1 + b * G5_A1;
+        for (int s = 0; s < 5; ++s)
+          tc::mma_bf16(tmem + a * G5_ACC + 128, tc::make_desc(a1 + s * 256, 128, 1280),
+                       tc::make_desc(bfx + s * 256, 128, 1280), id1, s > 0);
+        tc::mma_commit(g1_full(a));
+        return true;
+      };
+      // T3 of pair P (rows 8p .. 8p+7 of its window, p = P % 10) into accumulator P % 2:
+      // D[(o,kx)][(y,ri)] = Yh[(o,kx)][(q,ri')] Gy[(y,ri)][(q,ri')]^T, 4 tiles of 128 rows
+      auto issue_g4 = [&](int P) -> bool {
+        const int d = P & 1, p = P % 10;
+        if (P >= 2 && !tc::mbar_wait(d4_empty(d), ((P >> 1) - 1) & 1, WAIT_LIMIT)) return false;
+        tc::fence_after();
+        const uint32_t acc = tmem + G5F_D4 + d * 64;
+        for (int t = 0; t < 4; ++t)
+          for (int k = 0; k < 4; ++k)
+            tc::mma_bf16(acc + t * 16, tc::make_desc_sw128(yh + t * 16384 + k * 32, 1024),
+                         tc::make_desc(gy + 2 * p * 1024 + k * 256, 128, 1024), id4, k > 0);
+        tc::mma_commit(d4_full(d));
+        return true;
+      };
+      int it = 0;
+      bool ok = true;
+      for (int i = 0; i < nmine && ok && !*abort_flag; ++i) {
+        if (!tc::mbar_wait(yh_full, i & 1, WAIT_LIMIT)) { ok = false; break; }
+        tc::fence_after();
+        if (!issue_g4(10 * i) || !issue_g4(10 * i + 1)) { ok = false; break; }
+        for (int u = 0; u < UPW; ++u, ++it) {
+          const int s = it % G5F_STAGES, a = it % G5F_NACC, P = 10 * i + u / 2, tb = (P & 1) * 2 + (u & 1);
+          if (!tc::mbar_wait(full(s), (it / G5F_STAGES) & 1, WAIT_LIMIT) ||
+              !tc::mbar_wait(t3_full(tb), (P >> 1) & 1, WAIT_LIMIT) ||
+              (it >= G5F_NACC && !tc::mbar_wait(acc_empty(a), ((it / G5F_NACC) - 1) & 1, WAIT_LIMIT))) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const uint32_t ax = sbase + G5F_OFF_X + s * G5_XB, bt = sbase + G5F_OFF_T3 + tb * G5_TB;
+          const uint32_t d5 = tmem + a * G5_ACC;
+          for (int k = 0; k < 2; ++k)  // inverse DFT along x, the unit's 4 rows side by side
+            tc::mma_bf16(d5, tc::make_desc(ag + k * 256, 128, 512), tc::make_desc(bt + k * 256, 128, 512), id128,
+                         k > 0);
+          tc::mma_bf16(d5, tc::make_desc(sbase + G5F_OFF_ONE, 128, 256),
+                       tc::make_desc(sbase + G5F_OFF_BIAS, 128, 256), id128, 1);  // bias
+          for (int yy = 0; yy < G5_ROWS; ++yy)  // the mixer per row
+            for (int k = 0; k < 2; ++k)
+              tc::mma_bf16(d5 + yy * 32, tc::make_desc(ax + yy * G5_XT + k * 256, 128, 512),
+                           tc::make_desc(bw + k * 256, 128, 512), id5, 1);
+          tc::mma_commit(empty(s));
+          tc::mma_commit(t3_empty(tb));
+          tc::mma_commit(g5_full(a));
+          if (!last && it >= 1 && !issue_g1(it - 1)) { ok = false; break; }
+          if ((u & 1) && u / 2 + 2 <= 9) {  // the pair two ahead, once its accumulator is free
+            if (!issue_g4(P + 2)) { ok = false; break; }
+            if (u / 2 + 2 == 9) tc::mma_commit(yh_empty);  // the window's spectrum is no longer read
+          }
+        }
+      }
+      if (ok && !last && it >= 1 && !*abort_flag && !issue_g1(it - 1)) ok = false;
+      if (!ok) fail();
+    }
+  } else if (warp == 2 || warp == 3 || warp >= 12) {  // ---------------- T3 converters ----------------
+    const int q = warp & 3;  // TMEM lane quarter: warps 12, 13, 2, 3 -> 0, 1, 2, 3
+    // T3 of pair P: accumulator rows (o,kx) = tile t, lanes 32 q .. -> the pair's two unit tiles
+    bool ok = true;
+    for (int P = 0; P < 10 * nmine && ok && !*abort_flag; ++P) {
+      const int d = P & 1;
+      if (!tc::mbar_wait(d4_full(d), (P >> 1) & 1, WAIT_LIMIT)) { ok = false; break; }
+      tc::fence_after();
+      float v[4][16];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + G5F_D4 + d * 64 + t * 16, v[t]);
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(d4_empty(d));
+      for (int j = 0; j < 2; ++j)  // the tiles are free once the G5 MMAs of pair P - 2 are done
+        if (P >= 2 && !tc::mbar_wait(t3_empty((P & 1) * 2 + j), ((P >> 1) - 1) & 1, WAIT_LIMIT)) ok = false;
+      if (!ok) break;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int m = t * 128 + q * 32 + lane, o = m >> 4, kx = m & 15;
+#pragma unroll
+        for (int yl = 0; yl < 8; ++yl) {
+          uint8_t* tile = smem + G5F_OFF_T3 + ((P & 1) * 2 + (yl >> 2)) * G5_TB;
+          *reinterpret_cast<uint32_t*>(tile + tc::kmaj_off((yl & 3) * 32 + o, kx * 2, 32)) =
+              pack2(v[t][2 * yl], v[t][2 * yl + 1]);
+        }
+      }
+      tc::fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tc::mbar_arrive(t3_full((P & 1) * 2));
+        tc::mbar_arrive(t3_full((P & 1) * 2 + 1));
+      }
+    }
+    if (!ok) fail();
+  } else if (warp >= 4) {  // ---------------- epilogue (warps 4..11) ----------------
+    const int ew = warp - 4, q = ew & 3, hf = ew >> 2;
+    const __nv_bfloat162 slope = __floats2bfloat162_rn(LEAK, LEAK);
+    // phase 2 of unit j: its G1 result -> T1, then free its set
+    auto phase2 = [&](int j, size_t wy0) -> bool {
+      const int a = j % G5F_NACC;
+      if (!tc::mbar_wait(g1_full(a), (j / G5F_NACC) & 1, WAIT_LIMIT)) return false;
+      tc::fence_after();
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + 128 + hf * 16, v);
+      const int y = (int)(wy0 % 80) + q;
+      bf16* base = T1 + (wy0 / 80) * (size_t)(160 * 512);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int col = hf * 16 + i, kx = col >> 1, ri = col & 1;
+        base[(ri * 80 + y) * 512 + kx * 32 + lane] = __float2bfloat16_rn(v[i]);
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(acc_empty(a));
+      return true;
+    };
+    int it = 0;
+    bool ok = true;
+    size_t prev_wy0 = 0;
+    for (int i = 0; i < nmine && ok; ++i) {
+      const int w = blockIdx.x + i * gridDim.x;
+      for (int u = 0; u < UPW; ++u, ++it) {
+        const int a = it % G5F_NACC;
+        if (*abort_flag || !tc::mbar_wait(g5_full(a), (it / G5F_NACC) & 1, WAIT_LIMIT)) { ok = false; break; }
+        tc::fence_after();
+        const size_t wy0 = (size_t)w * 80 + u * G5_ROWS;
+        uint8_t* a1 = smem + G5F_OFF_A1 + (it & 1) * G5_A1;
+        if (q < 3) {
+          const int x = q * 32 + lane;
+          for (int yy = hf * 2; yy < hf * 2 + 2; ++yy) {
+            float v[32];
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + yy * 32, v);
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + yy * 32 + 16, v + 16);
+            if (x < 80) {
+              uint32_t p[16];
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {  // bias already in the accumulator; leaky-ReLU on BF16 pairs
+                __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+                if (!last) h2 = __hmax2(h2, __hmul2(h2, slope));
+                p[c] = *reinterpret_cast<uint32_t*>(&h2);
+              }
+              bf16* dst = X + xt_off(wy0 + yy, x, 0);
+#pragma unroll
+              for (int cg = 0; cg < 4; ++cg)
+                *reinterpret_cast<uint4*>(dst + cg * 64) =
+                    make_uint4(p[4 * cg], p[4 * cg + 1], p[4 * cg + 2], p[4 * cg + 3]);
+              if (!last)
+#pragma unroll
+                for (int cg = 0; cg < 4; ++cg)
+                  *reinterpret_cast<uint4*>(a1 + ((yy * 4 + cg) * 10 + (x >> 3)) * 128 + (x & 7) * 16) =
+                      make_uint4(p[4 * cg], p[4 * cg + 1], p[4 * cg + 2], p[4 * cg + 3]);
+            }
+          }
+        }
+        if (last) {
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(acc_empty(a));
+        } else {
+          tc::fence_async_smem();  // A1 written by this warp -> visible to the tensor core
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(a1_full(it & 1));
+          if (it >= 1 && !phase2(it - 1, prev_wy0)) { ok = false; break; }
+          prev_wy0 = wy0;
+        }
+      }
+    }
+    if (ok && !last && it >= 1 && !*abort_flag && !phase2(it - 1, prev_wy0)) ok = false;
+    if (!ok) fail();
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc::fence_after();
+    tc::tmem_free(tmem, 512);
+  }
+}
+
 // Projection, warp-specialised and persistent over units (window, 128
 // consecutive pixels; the tiled activation makes that one contiguous 8 KB
 // operand tile):
@@ -1588,7 +1920,7 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     rho_kernel<<<n, 256, 0, s>>>(in, g, k->rho);
     CKL();
   }
-  static int g5_cap = 0;
+  static int g5_cap = 0, g5f_cap = 0;
   if (!g5_cap) {
     CK(cudaFuncSetAttribute(g5_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)G5L<false>::SMEM));
@@ -1601,6 +1933,8 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     CK(cudaFuncSetAttribute(g5_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)G5L<false>::SMEM));
     g5_cap = persistent_grid((const void*)g5_kernel<false, true>, G5_THREADS, G5L<true>::SMEM, 512);
+    CK(cudaFuncSetAttribute(g5f_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G5F_SMEM));
+    g5f_cap = persistent_grid((const void*)g5f_kernel, G5F_THREADS, G5F_SMEM, 512);
   }
   const int g5_total = n * (80 / G5_ROWS);
   const int g5_grid = g5_total < g5_cap ? g5_total : g5_cap;
@@ -1630,8 +1964,10 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
       if ((rc = launch_g3(k, W->R[bl], n, s))) return rc;
     }
     {
-      ProfScope ps(h, 12, 1);
-      if ((rc = launch_gemm<160, 64, false>(G4Op{k->Yh, W->Gy, k->T3}, 512 / 128, n, k->err, s))) return rc;
+      const bool fused = in0 && bl >= 1;  // blocks 1..3 compute T3 inside the G5 kernel
+      ProfScope ps(h, 12, fused ? 0 : 1);
+      if (!fused && (rc = launch_gemm<160, 64, false>(G4Op{k->Yh, W->Gy, k->T3}, 512 / 128, n, k->err, s)))
+        return rc;
     }
     {
       ProfScope ps(h, 13, 1);
@@ -1643,6 +1979,9 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
         g5_kernel<false, false, true><<<g5_grid, G5_THREADS, G5L<false>::SMEM, s>>>(k->X, k->T3, W->Gx, W->W0L, W->bias0L,
                                                                             W->Fx, k->T1, nullptr, 0, g5_total, k->err,
                                                                             lsrc);
+      else if (in0)  // blocks 1..3: the inverse DFT along y fused in, whole windows per CTA
+        g5f_kernel<<<n < g5f_cap ? n : g5f_cap, G5F_THREADS, G5F_SMEM, s>>>(k->X, k->Yh, W->Gy, W->Gx, W->W[bl], W->bias[bl],
+                                                                  W->Fx, k->T1, bl == 3, n, k->err);
       else
         g5_kernel<false, false><<<g5_grid, G5_THREADS, G5L<false>::SMEM, s>>>(k->X, k->T3, W->Gx, W->W[bl], W->bias[bl], W->Fx,
                                                                       k->T1, nullptr, bl == 3, g5_total, k->err,
