@@ -106,13 +106,13 @@ G5_T1_BYTES = 160 * 512 * 2                   # next block's half-spectrum, writ
 # over the class's launches; scaled by the window count for other sizes).
 TRAFFIC_SRC = "profiles/dram_traffic_freeform4096.md"
 MEASURED_TRAFFIC = {
-    "nno_idft_x_mix_act": 1001333,  # G5 block 0 (inputs rebuilt) and blocks 1..3, class average
-    "nno_proj": 440557,
-    "nno_mix": 119425,
-    "nno_lift": 198972,
-    "nno_dft_y": 221307,
-    "nno_idft_y": 215221,
-    "nno_pack": 32807,
+    "nno_idft_x_mix_act": 927039,  # G5 block 0 (inputs rebuilt) and fused blocks 1..3, class average
+    "nno_proj": 440581,
+    "nno_mix": 119328,
+    "nno_lift": 198956,
+    "nno_dft_y": 221283,
+    "nno_idft_y": 215120,
+    "nno_pack": 32797,
 }
 # Useful FLOPs per window of each stage (padding excluded).
 NNO_FLOP_PER_WIN = {
