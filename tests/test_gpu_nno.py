@@ -198,3 +198,32 @@ def test_fp8_precond_matches_oracle(F, weights):
     # BF16 3.9e-2, FP8 0.135 against the FP64 oracle on this input)
     bf16_tol = BF16_TOL if weights == "seeded" else 2 * BF16_TOL
     assert e8 < FP8_TOL and e16 < bf16_tol, (e8, e16)
+
+
+def test_dfty_variants_agree(F, monkeypatch):
+    """The three DFT-y GEMM variants the set-up autotuner chooses from (operand
+    tiles by TMA, or the cp.async gather with K split 1 or 2), each forced
+    through FDFD_DFTY_VARIANT, give the oracle's one-level sweep and agree
+    with one another to BF16 rounding of the accumulation order."""
+    import torch
+    n = 256
+    dx = LAM / 25
+    eps = wl.rectangles_eps(n, n, seed=1000)
+    w = wl.nno_weights(0)
+    v = wl.random_field(n, n, 17)
+    ref = OS.Schwarz(eps, dx, LAM, 20, weights=w, k_coarse=0).apply(v.astype(np.complex128))
+    outs = {}
+    for var in ("0", "1", "2"):
+        monkeypatch.setenv("FDFD_DFTY_VARIANT", var)
+        S = F.Solver(_t(eps), dx, LAM, npml=20)
+        S.schwarz_setup(wl.pack_weights(w), k_coarse=0)
+        assert S.info()["tuned_dfty_split"] == int(var)
+        z = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+        S.precond_apply(_t(v), z)
+        outs[var] = z.cpu().numpy()
+        S.close()
+        err = np.linalg.norm(outs[var] - ref) / np.linalg.norm(ref)
+        assert err < BF16_TOL, (var, err)
+    for var in ("1", "2"):
+        d = np.linalg.norm(outs[var] - outs["0"]) / np.linalg.norm(outs["0"])
+        assert d < 5e-3, (var, d)
