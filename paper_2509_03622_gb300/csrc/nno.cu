@@ -1039,7 +1039,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
 // the next block's DFT along x.  TMEM: two G5 sets (2 x 160 columns) and two
 // 64-column T3 accumulators.
 constexpr int G5F_STAGES = 2;
-constexpr int G5F_NACC = 2;
+constexpr int G5F_NACC = 3;                                         // G5 accumulator sets (128 columns)
 constexpr uint32_t G5F_OFF_YH = 0;                                  // [512][64] swizzled rows (1024-aligned)
 constexpr uint32_t G5F_OFF_X = G5F_OFF_YH + 512 * 64 * 2;           // ring of 4-row X tiles
 constexpr uint32_t G5F_OFF_T3 = G5F_OFF_X + G5F_STAGES * G5_XB;     // 4 unit tiles [(yy,o) 128][32]
@@ -1051,12 +1051,16 @@ constexpr uint32_t G5F_OFF_FX = G5F_OFF_W + 32 * 32 * 2;
 constexpr uint32_t G5F_OFF_ONE = G5F_OFF_FX + 32 * 80 * 2;
 constexpr uint32_t G5F_OFF_BIAS = G5F_OFF_ONE + 128 * 16 * 2;
 constexpr uint32_t G5F_OFF_BAR = G5F_OFF_BIAS + 128 * 16 * 2;
-// full[2], empty[2], yh_full, yh_empty, g5_full[2], g1_full[2], acc_empty[2], a1_full[2],
-// d4_full[2], d4_empty[2], t3_full[4], t3_empty[4]
-constexpr uint32_t G5F_NBAR = 2 * G5F_STAGES + 2 + 3 * G5F_NACC + 2 + 4 + 8;
+// full[S], empty[S], yh_full, yh_empty, g5_full[3], acc_empty[3], g1_full[2], g1_empty[2], a1_full[2],
+// d4_full, d4_empty, t3_full[4], t3_empty[4]
+constexpr uint32_t G5F_NBAR = 2 * G5F_STAGES + 24;
 constexpr uint32_t G5F_SMEM = G5F_OFF_BAR + G5F_NBAR * 8 + 16;
 static_assert(G5F_SMEM <= 227 * 1024, "fused G5 shared memory");
-constexpr uint32_t G5F_D4 = G5F_NACC * G5_ACC;                      // TMEM column of the T3 accumulators
+// TMEM: three G5 sets (4 rows x 32 columns each), the next block's DFT-x
+// result in two 32-column slots of its own (so a G5 set is free as soon as
+// its activations are read), and one 64-column T3 accumulator
+constexpr uint32_t G5F_SET = 128, G5F_G1 = 3 * G5F_SET, G5F_D4 = G5F_G1 + 2 * 32;
+static_assert(G5F_D4 + 64 <= 512, "fused G5 TMEM columns");
 
 constexpr int G5F_THREADS = 448;
 __global__ void __launch_bounds__(G5F_THREADS, 1)
@@ -1069,13 +1073,13 @@ g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* 
   auto empty = [&](int s) { return bar + 8u * (G5F_STAGES + s); };
   const uint32_t yh_full = bar + 8u * (2 * G5F_STAGES), yh_empty = yh_full + 8u;
   auto g5_full = [&](int a) { return bar + 8u * (2 * G5F_STAGES + 2 + a); };
-  auto g1_full = [&](int a) { return bar + 8u * (2 * G5F_STAGES + 2 + G5F_NACC + a); };
-  auto acc_empty = [&](int a) { return bar + 8u * (2 * G5F_STAGES + 2 + 2 * G5F_NACC + a); };
-  auto a1_full = [&](int b) { return bar + 8u * (2 * G5F_STAGES + 2 + 3 * G5F_NACC + b); };
-  auto d4_full = [&](int d) { return bar + 8u * (2 * G5F_STAGES + 4 + 3 * G5F_NACC + d); };
-  auto d4_empty = [&](int d) { return bar + 8u * (2 * G5F_STAGES + 6 + 3 * G5F_NACC + d); };
-  auto t3_full = [&](int b) { return bar + 8u * (2 * G5F_STAGES + 8 + 3 * G5F_NACC + b); };
-  auto t3_empty = [&](int b) { return bar + 8u * (2 * G5F_STAGES + 12 + 3 * G5F_NACC + b); };
+  auto acc_empty = [&](int a) { return bar + 8u * (2 * G5F_STAGES + 5 + a); };
+  auto g1_full = [&](int g) { return bar + 8u * (2 * G5F_STAGES + 8 + g); };
+  auto g1_empty = [&](int g) { return bar + 8u * (2 * G5F_STAGES + 10 + g); };
+  auto a1_full = [&](int b) { return bar + 8u * (2 * G5F_STAGES + 12 + b); };
+  const uint32_t d4_full = bar + 8u * (2 * G5F_STAGES + 14), d4_empty = d4_full + 8u;
+  auto t3_full = [&](int b) { return bar + 8u * (2 * G5F_STAGES + 16 + b); };
+  auto t3_empty = [&](int b) { return bar + 8u * (2 * G5F_STAGES + 20 + b); };
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + G5F_OFF_BAR + G5F_NBAR * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + G5F_OFF_BAR + G5F_NBAR * 8 + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1117,12 +1121,11 @@ g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* 
   if (tid == 0) {
     for (int s = 0; s < G5F_STAGES; ++s) { tc::mbar_init(full(s), 1); tc::mbar_init(empty(s), 1); }
     tc::mbar_init(yh_full, 1); tc::mbar_init(yh_empty, 1);
-    for (int a = 0; a < G5F_NACC; ++a) {
-      tc::mbar_init(g5_full(a), 1); tc::mbar_init(g1_full(a), 1); tc::mbar_init(acc_empty(a), 8);
-    }
+    for (int a = 0; a < G5F_NACC; ++a) { tc::mbar_init(g5_full(a), 1); tc::mbar_init(acc_empty(a), 8); }
     for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(a1_full(b), 8); tc::mbar_init(d4_full(b), 1); tc::mbar_init(d4_empty(b), 4);
+      tc::mbar_init(g1_full(b), 1); tc::mbar_init(g1_empty(b), 8); tc::mbar_init(a1_full(b), 8);
     }
+    tc::mbar_init(d4_full, 1); tc::mbar_init(d4_empty, 4);
     for (int b = 0; b < 4; ++b) { tc::mbar_init(t3_full(b), 4); tc::mbar_init(t3_empty(b), 1); }
     *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
     tc::fence_mbar_init();
@@ -1173,28 +1176,29 @@ g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* 
       const uint32_t ag = sbase + G5F_OFF_GX, bw = sbase + G5F_OFF_W, bfx = sbase + G5F_OFF_FX;
       const uint32_t yh = sbase + G5F_OFF_YH, gy = sbase + G5F_OFF_GY;
       auto issue_g1 = [&](int j) -> bool {  // next block's DFT along x for unit j
-        const int b = j & 1, a = j % G5F_NACC;
+        const int b = j & 1;  // A1 buffer and G1 slot
         if (!tc::mbar_wait(a1_full(b), (j >> 1) & 1, WAIT_LIMIT)) return false;
+        if (j >= 2 && !tc::mbar_wait(g1_empty(b), ((j >> 1) - 1) & 1, WAIT_LIMIT)) return false;
         tc::fence_after();
         const uint32_t a1 = sbase + G5F_OFF_A1 + b * G5_A1;
         for (int s = 0; s < 5; ++s)
-          tc::mma_bf16(tmem + a * G5_ACC + 128, tc::make_desc(a1 + s * 256, 128, 1280),
+          tc::mma_bf16(tmem + G5F_G1 + b * 32, tc::make_desc(a1 + s * 256, 128, 1280),
                        tc::make_desc(bfx + s * 256, 128, 1280), id1, s > 0);
-        tc::mma_commit(g1_full(a));
+        tc::mma_commit(g1_full(b));
         return true;
       };
       // T3 of pair P (rows 8p .. 8p+7 of its window, p = P % 10) into accumulator P % 2:
       // D[(o,kx)][(y,ri)] = Yh[(o,kx)][(q,ri')] Gy[(y,ri)][(q,ri')]^T, 4 tiles of 128 rows
-      auto issue_g4 = [&](int P) -> bool {
-        const int d = P & 1, p = P % 10;
-        if (P >= 2 && !tc::mbar_wait(d4_empty(d), ((P >> 1) - 1) & 1, WAIT_LIMIT)) return false;
+      auto issue_g4 = [&](int P) -> bool {  // one T3 accumulator: pair P - 1 must have been read
+        const int p = P % 10;
+        if (P >= 1 && !tc::mbar_wait(d4_empty, (P - 1) & 1, WAIT_LIMIT)) return false;
         tc::fence_after();
-        const uint32_t acc = tmem + G5F_D4 + d * 64;
+        const uint32_t acc = tmem + G5F_D4;
         for (int t = 0; t < 4; ++t)
           for (int k = 0; k < 4; ++k)
             tc::mma_bf16(acc + t * 16, tc::make_desc_sw128(yh + t * 16384 + k * 32, 1024),
                          tc::make_desc(gy + 2 * p * 1024 + k * 256, 128, 1024), id4, k > 0);
-        tc::mma_commit(d4_full(d));
+        tc::mma_commit(d4_full);
         return true;
       };
       int it = 0;
@@ -1213,7 +1217,7 @@ g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* 
           }
           tc::fence_after();
           const uint32_t ax = sbase + G5F_OFF_X + s * G5_XB, bt = sbase + G5F_OFF_T3 + tb * G5_TB;
-          const uint32_t d5 = tmem + a * G5_ACC;
+          const uint32_t d5 = tmem + a * G5F_SET;
           for (int k = 0; k < 2; ++k)  // inverse DFT along x, the unit's 4 rows side by side
             tc::mma_bf16(d5, tc::make_desc(ag + k * 256, 128, 512), tc::make_desc(bt + k * 256, 128, 512), id128,
                          k > 0);
@@ -1241,15 +1245,14 @@ g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* 
     // T3 of pair P: accumulator rows (o,kx) = tile t, lanes 32 q .. -> the pair's two unit tiles
     bool ok = true;
     for (int P = 0; P < 10 * nmine && ok && !*abort_flag; ++P) {
-      const int d = P & 1;
-      if (!tc::mbar_wait(d4_full(d), (P >> 1) & 1, WAIT_LIMIT)) { ok = false; break; }
+      if (!tc::mbar_wait(d4_full, P & 1, WAIT_LIMIT)) { ok = false; break; }
       tc::fence_after();
       float v[4][16];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + G5F_D4 + d * 64 + t * 16, v[t]);
+      for (int t = 0; t < 4; ++t) tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + G5F_D4 + t * 16, v[t]);
       tc::fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(d4_empty(d));
+      if (lane == 0) tc::mbar_arrive(d4_empty);
       for (int j = 0; j < 2; ++j)  // the tiles are free once the G5 MMAs of pair P - 2 are done
         if (P >= 2 && !tc::mbar_wait(t3_empty((P & 1) * 2 + j), ((P >> 1) - 1) & 1, WAIT_LIMIT)) ok = false;
       if (!ok) break;
@@ -1276,11 +1279,11 @@ g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* 
     const __nv_bfloat162 slope = __floats2bfloat162_rn(LEAK, LEAK);
     // phase 2 of unit j: its G1 result -> T1, then free its set
     auto phase2 = [&](int j, size_t wy0) -> bool {
-      const int a = j % G5F_NACC;
-      if (!tc::mbar_wait(g1_full(a), (j / G5F_NACC) & 1, WAIT_LIMIT)) return false;
+      const int g = j & 1;
+      if (!tc::mbar_wait(g1_full(g), (j >> 1) & 1, WAIT_LIMIT)) return false;
       tc::fence_after();
       float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + 128 + hf * 16, v);
+      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + G5F_G1 + g * 32 + hf * 16, v);
       const int y = (int)(wy0 % 80) + q;
       bf16* base = T1 + (wy0 / 80) * (size_t)(160 * 512);
 #pragma unroll
@@ -1290,7 +1293,7 @@ g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* 
       }
       tc::fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(acc_empty(a));
+      if (lane == 0) tc::mbar_arrive(g1_empty(g));
       return true;
     };
     int it = 0;
@@ -1308,8 +1311,8 @@ g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* 
           const int x = q * 32 + lane;
           for (int yy = hf * 2; yy < hf * 2 + 2; ++yy) {
             float v[32];
-            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + yy * 32, v);
-            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + yy * 32 + 16, v + 16);
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5F_SET + yy * 32, v);
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5F_SET + yy * 32 + 16, v + 16);
             if (x < 80) {
               uint32_t p[16];
 #pragma unroll
@@ -1331,14 +1334,15 @@ g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* 
             }
           }
         }
-        if (last) {
-          tc::fence_before();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(acc_empty(a));
-        } else {
-          tc::fence_async_smem();  // A1 written by this warp -> visible to the tensor core
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(a1_full(it & 1));
+        // the set's columns are read: the next MMAs may reuse it (the DFT-x result has its own slot)
+        if (!last) tc::fence_async_smem();  // A1 written by this warp -> visible to the tensor core
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          tc::mbar_arrive(acc_empty(a));
+          if (!last) tc::mbar_arrive(a1_full(it & 1));
+        }
+        if (!last) {
           if (it >= 1 && !phase2(it - 1, prev_wy0)) { ok = false; break; }
           prev_wy0 = wy0;
         }
