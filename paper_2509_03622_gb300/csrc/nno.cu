@@ -586,7 +586,8 @@ constexpr uint32_t G5_TB = G5_ROWS * 2048;                       // 8192
 constexpr uint32_t G5_X8B = G5_ROWS * 2560;                      // 10240: the rows in FP8 (staging)
 constexpr uint32_t G5_A1 = 128 * 80 * 2;                         // G1 A tile, MN-major (yy,c) x x
 constexpr int G5_NACC = 3;                                        // TMEM accumulator sets
-constexpr uint32_t G5_ACC = 160;                                  // TMEM columns per set
+constexpr uint32_t G5_SET = 128;                                  // TMEM columns per set (4 rows x 32)
+constexpr uint32_t G5_G1 = G5_NACC * G5_SET;                      // two 32-column slots: next block's DFT-x
 // Shared-memory layout: the ring of stages (the FP8 variant also stages the
 // rows in FP8, so its stages are larger and fewer), then the G1 A tiles, the
 // constant operands and the barriers.
@@ -601,7 +602,7 @@ struct G5L {
   static constexpr uint32_t OFF_ONE = OFF_FX + 32 * 80 * 2;               // [128][16] K-major: 1, 1, 0 ...
   static constexpr uint32_t OFF_BIAS = OFF_ONE + 128 * 16 * 2;            // [128 (yy,o)][16]: bias hi, lo, 0 ...
   static constexpr uint32_t OFF_BAR = OFF_BIAS + 128 * 16 * 2;
-  static constexpr uint32_t NBAR = 3 * STAGES + 3 * G5_NACC + 2;
+  static constexpr uint32_t NBAR = 3 * STAGES + 2 * G5_NACC + 6;
   static constexpr uint32_t SMEM = OFF_BAR + NBAR * 8 + 16;
   static_assert(SMEM <= 227 * 1024, "g5 shared memory");
 };
@@ -714,14 +715,15 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   extern __shared__ __align__(1024) uint8_t smem[];
   const uint32_t sbase = tc::smem_u32(smem);
   const uint32_t bar = sbase + L::OFF_BAR;
-  // barriers: full[s], empty[s], g5_full[3], g1_full[3], acc_empty[3], a1_full[2], conv_full[s]
+  // barriers: full[s], empty[s], g5_full[3], acc_empty[3], g1_full[2], g1_empty[2], a1_full[2], conv_full[s]
   auto full = [&](int s) { return bar + 8u * s; };
   auto empty = [&](int s) { return bar + 8u * (L::STAGES + s); };
   auto g5_full = [&](int a) { return bar + 8u * (2 * L::STAGES + a); };
-  auto g1_full = [&](int a) { return bar + 8u * (2 * L::STAGES + G5_NACC + a); };
-  auto acc_empty = [&](int a) { return bar + 8u * (2 * L::STAGES + 2 * G5_NACC + a); };
-  auto a1_full = [&](int b) { return bar + 8u * (2 * L::STAGES + 3 * G5_NACC + b); };
-  auto conv_full = [&](int s) { return bar + 8u * (2 * L::STAGES + 3 * G5_NACC + 2 + s); };  // FP8 rows converted
+  auto acc_empty = [&](int a) { return bar + 8u * (2 * L::STAGES + G5_NACC + a); };
+  auto g1_full = [&](int g) { return bar + 8u * (2 * L::STAGES + 2 * G5_NACC + g); };
+  auto g1_empty = [&](int g) { return bar + 8u * (2 * L::STAGES + 2 * G5_NACC + 2 + g); };
+  auto a1_full = [&](int b) { return bar + 8u * (2 * L::STAGES + 2 * G5_NACC + 4 + b); };
+  auto conv_full = [&](int s) { return bar + 8u * (2 * L::STAGES + 2 * G5_NACC + 6 + s); };  // FP8 rows converted
   constexpr bool CONV = FP8 && !LIFT;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::OFF_BAR + L::NBAR * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L::OFF_BAR + L::NBAR * 8 + 4);
@@ -760,10 +762,10 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
   tc::cp_async_wait_all();
   if (tid == 0) {
     for (int s = 0; s < L::STAGES; ++s) { tc::mbar_init(full(s), IN0 ? 2 : 1); tc::mbar_init(empty(s), 1); }
-    for (int a = 0; a < G5_NACC; ++a) {
-      tc::mbar_init(g5_full(a), 1); tc::mbar_init(g1_full(a), 1); tc::mbar_init(acc_empty(a), 8);
+    for (int a = 0; a < G5_NACC; ++a) { tc::mbar_init(g5_full(a), 1); tc::mbar_init(acc_empty(a), 8); }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(g1_full(b), 1); tc::mbar_init(g1_empty(b), 8); tc::mbar_init(a1_full(b), 8);
     }
-    for (int b = 0; b < 2; ++b) tc::mbar_init(a1_full(b), 8);
     for (int s = 0; s < L::STAGES; ++s) tc::mbar_init(conv_full(s), 2);
     *abort_flag = *reinterpret_cast<volatile int*>(err);  // an earlier failure: skip all work
     tc::fence_mbar_init();
@@ -846,14 +848,15 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       constexpr uint32_t id1 = tc::idesc_bf16(32, true, false);
       const uint32_t ag = sbase + L::OFF_GX, bw = sbase + L::OFF_W, bfx = sbase + L::OFF_FX;
       auto issue_g1 = [&](int j) -> bool {  // next block's DFT along x for unit j
-        const int b = j & 1, a = j % G5_NACC;
+        const int b = j & 1;  // A1 buffer and G1 slot
         if (!tc::mbar_wait(a1_full(b), (j >> 1) & 1, WAIT_LIMIT)) return false;
+        if (j >= 2 && !tc::mbar_wait(g1_empty(b), ((j >> 1) - 1) & 1, WAIT_LIMIT)) return false;
         tc::fence_after();
         const uint32_t a1 = sbase + L::OFF_A1 + b * G5_A1;
         for (int s = 0; s < 5; ++s)
-          tc::mma_bf16(tmem + a * G5_ACC + 128, tc::make_desc(a1 + s * 256, 128, 1280),
+          tc::mma_bf16(tmem + G5_G1 + b * 32, tc::make_desc(a1 + s * 256, 128, 1280),
                        tc::make_desc(bfx + s * 256, 128, 1280), id1, s > 0);
-        tc::mma_commit(g1_full(a));
+        tc::mma_commit(g1_full(b));
         return true;
       };
       int it = 0;
@@ -869,7 +872,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
         const uint32_t ax = sbase + s * L::STAGE, bt = ax + G5_XB;
         // the unit's 4 rows side by side (N = 128 columns (yy, o)) where A is shared:
         // the inverse DFT along x (A = Gx, B = the 4 rows of T3) and the bias
-        const uint32_t d4 = tmem + a * G5_ACC;
+        const uint32_t d4 = tmem + a * G5_SET;
         if (!LIFT)
           for (int k = 0; k < 2; ++k)
             tc::mma_bf16(d4, tc::make_desc(ag + k * 256, 128, 512), tc::make_desc(bt + k * 256, 128, 512), id128,
@@ -877,7 +880,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
         tc::mma_bf16(d4, tc::make_desc(sbase + L::OFF_ONE, 128, 256), tc::make_desc(sbase + L::OFF_BIAS, 128, 256),
                      id128, LIFT ? 0 : 1);
         for (int yy = 0; yy < G5_ROWS; ++yy) {  // per row: the mixer (or lift) on the row's own A tile
-          const uint32_t d = tmem + a * G5_ACC + yy * 32;
+          const uint32_t d = tmem + a * G5_SET + yy * 32;
           if (LIFT) {  // lift: [x][16 inputs] . [32][16]^T
             tc::mma_bf16(d, tc::make_desc(ax + yy * 2560, 128, 256), tc::make_desc(bw, 128, 256), id5, 1);
             continue;
@@ -927,12 +930,12 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
     const __nv_bfloat162 slope = __floats2bfloat162_rn(LEAK, LEAK);
     // phase 2 of unit j (window rows from wy0): its G1 result -> T1, then free its set
     auto phase2 = [&](int j, size_t wy0) -> bool {
-      const int a = j % G5_NACC;
-      if (!tc::mbar_wait(g1_full(a), (j / G5_NACC) & 1, WAIT_LIMIT)) return false;
+      const int g = j & 1;
+      if (!tc::mbar_wait(g1_full(g), (j >> 1) & 1, WAIT_LIMIT)) return false;
       tc::fence_after();
       // lanes (yy = q, c = lane), columns (kx,ri) hf*16 .. hf*16+15
       float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + 128 + hf * 16, v);
+      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + G5_G1 + g * 32 + hf * 16, v);
       const int y = (int)(wy0 % 80) + q;
       bf16* base = T1 + (wy0 / 80) * (size_t)(160 * 512);
 #pragma unroll
@@ -942,7 +945,7 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       }
       tc::fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(acc_empty(a));
+      if (lane == 0) tc::mbar_arrive(g1_empty(g));
       return true;
     };
     int it = 0;
@@ -958,8 +961,8 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
         const int x = q * 32 + lane;
         for (int yy = hf * 2; yy < hf * 2 + 2; ++yy) {
           float v[32];
-          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + yy * 32, v);
-          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_ACC + yy * 32 + 16, v + 16);
+          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_SET + yy * 32, v);
+          tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + a * G5_SET + yy * 32 + 16, v + 16);
           if (x < 80) {
             uint32_t p[16];
 #pragma unroll
@@ -1000,15 +1003,15 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
           }
         }
       }
-      if (last) {
-        tc::fence_before();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(acc_empty(a));
-        continue;
-      }
-      tc::fence_async_smem();  // A1 written by this warp -> visible to the tensor core
+      // the set's columns are read: the next MMAs may reuse it (the DFT-x result has its own slot)
+      if (!last) tc::fence_async_smem();  // A1 written by this warp -> visible to the tensor core
+      tc::fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(a1_full(it & 1));
+      if (lane == 0) {
+        tc::mbar_arrive(acc_empty(a));
+        if (!last) tc::mbar_arrive(a1_full(it & 1));
+      }
+      if (last) continue;
       if (it >= 1 && !phase2(it - 1, prev_wy0)) { ok = false; break; }
       prev_wy0 = wy0;
     }
