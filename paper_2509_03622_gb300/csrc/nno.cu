@@ -568,9 +568,10 @@ g3_kernel(const bf16* Xh, const bf16* R, bf16* Yh, int rows, int nwin, int wtile
 // one of the 4 T3 rows, 8 KB, per unit into a ring of 5 stages (4 with FP8 staging), completion
 // by transaction count), warp 1 lane 0 = MMA issuer, warps 4..11 = epilogue;
 // in the lift and IN0, warps 2, 3, 12, 13 build the input channels
-// (warp w reads TMEM lanes 32(w%4)..).  Three accumulator sets in TMEM (G5:
-// 4 x 32 columns, G1: 32 columns, 160 columns a set) let the epilogue of unit
-// i overlap the MMAs of units i+1 and i+2, and the epilogue is software
+// (warp w reads TMEM lanes 32(w%4)..).  Three G5 accumulator sets in TMEM
+// (4 x 32 columns each, released once the epilogue has read them) and two
+// 32-column G1 slots let the epilogue of unit i overlap the MMAs of units
+// i+1 and i+2, and the epilogue is software
 // pipelined: it writes unit i's activations (and G1's A operand), then reads
 // unit i-1's G1 result, issued a whole unit earlier, so it never waits on a
 // just-issued MMA.  The G5 MMA has M = 128 rows of which x < 80 are real:
@@ -1039,8 +1040,8 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
 // conversion off the epilogue's path.  The
 // rest is the G5 pipeline: X rows by bulk copy (2-stage ring), stacked
 // Gx T3 + bias MMAs, the mixer per row, the software-pipelined epilogue and
-// the next block's DFT along x.  TMEM: two G5 sets (2 x 160 columns) and two
-// 64-column T3 accumulators.
+// the next block's DFT along x.  TMEM: three G5 sets (3 x 128 columns), two
+// 32-column G1 slots and one 64-column T3 accumulator.
 constexpr int G5F_STAGES = 2;
 constexpr int G5F_NACC = 3;                                         // G5 accumulator sets (128 columns)
 constexpr uint32_t G5F_OFF_YH = 0;                                  // [512][64] swizzled rows (1024-aligned)
