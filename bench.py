@@ -269,6 +269,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tts", action="store_true", help="also time a full solve to 1e-6")
+    ap.add_argument("--stationary", type=int, default=0,
+                    help="also time this many iterations of the stationary Schwarz loop (Algorithm 3)")
     ap.add_argument("--nno-precision", default="bf16", choices=["bf16", "fp8"],
                     help="neural-operator activations: BF16, or E4M3 with per-channel scales")
     args = ap.parse_args()
@@ -393,6 +395,20 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": "Mcell-it/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{ns}x{ns} grid, same recipe and preconditioner configuration, "
                                           f"{it} FGMRES steps ({args.precond}), {t:.1f} s"}
+    if args.stationary > 0 and precond == F.PRECOND_SCHWARZ:
+        # Algorithm 3 on the same workload; the loop is linear in b, so the
+        # source field itself serves as the right-hand side
+        U = torch.empty_like(E)
+        S.schwarz_stationary(Jd, U, max_iters=2, tol=0.0, momentum=0.5)  # warm-up
+        torch.cuda.synchronize()
+        ev0.record(S.stream)
+        it_s, rr_s = S.schwarz_stationary(Jd, U, max_iters=args.stationary, tol=0.0, momentum=0.5)
+        ev1.record(S.stream)
+        torch.cuda.synchronize()
+        ms_s = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+        line["stationary"] = {"iters": it_s, "ms_per_iter": ms_s / max(it_s, 1), "momentum": 0.5,
+                              "value": job_rate(world, n * n, it_s, ms_s / 1e3), "unit": "Mcell-it/s",
+                              "relres": rr_s, "note": "each iteration includes its FP64 true residual"}
     if args.tts and rank == 0:
         E.zero_()
         rc, st2 = S.solve(Jd, E, restart=30, max_iters=3000, tol=1e-6, precond=precond)

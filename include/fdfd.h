@@ -248,6 +248,25 @@ int  fdfd_apply_A(fdfd_handle h, const fdfd_c64* x, fdfd_c64* y, int transpose);
  * solve and correction (Algorithm 3; Sec. 2.2).  Requires schwarz_setup. */
 int  fdfd_precond_apply(fdfd_handle h, const fdfd_c64* v, fdfd_c64* z);
 
+/* Algorithm 3 as a solver: the stationary (two-level) Schwarz iteration for
+ * A~ u = b (b the right-hand side of the dx^2-scaled system of Eq. 1, device
+ * complex64 [ny][nx]; u device complex64 [ny][nx], output only).  Each
+ * iteration solves every window's local Robin problem with the restricted
+ * source and the current Robin data g (the neural operator, or k inner
+ * NN-FGMRES steps when schwarz_setup asked for them), assembles u by
+ * restricted prolongation, takes the traces of u (Eq. 2), with a coarse space
+ * corrects u for the mismatch between those traces and g (Eq. 8) and takes
+ * them again, and blends g = momentum g + (1 - momentum) traces.  It stops
+ * after max_iters iterations or once the FP64 relative residual
+ * ||b - A~ u|| / ||b|| is <= tol.  g starts at zero, so the first iterate is
+ * fdfd_precond_apply(b).  Writes the iterations done and the last relative
+ * residual (may be NULL).  FDFD_EINVAL for max_iters < 1, tol < 0 or momentum
+ * outside [0, 1); FDFD_ENOSETUP without schwarz_setup; FDFD_ENUMERIC if the
+ * residual is not finite (u then holds the last iterate); FDFD_ETIMEOUT as
+ * for the solve.  Uses the handle's Krylov workspace; synchronous. */
+int  fdfd_schwarz_stationary(fdfd_handle h, const fdfd_c64* b_dev, fdfd_c64* u_dev, int max_iters,
+                             double tol, double momentum, int* iters, double* relres);
+
 /* Batched neural local solves (Fig. 2) on n windows: r_win [n][80][80]
  * window residuals, g_win [n][4][80] Robin data (sides x-, x+, y-, y+;
  * Eq. 2), win_id [n] (device int) the window whose eps / PML the solve

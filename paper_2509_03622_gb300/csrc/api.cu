@@ -152,6 +152,11 @@ int read_double(fdfd_ctx* h, const double* dev, double* out) {
   return FDFD_OK;
 }
 
+__global__ void to_f64_kernel(const float2* __restrict__ u, double2* __restrict__ x, size_t n) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    x[c] = make_double2((double)u[c].x, (double)u[c].y);
+}
+
 __global__ void set_bnorm_kernel(KrylovState* st) {
   st->bnorm = sqrt(st->resid);
   st->nonfinite = 0;
@@ -571,6 +576,51 @@ int fdfd_trace_extract(fdfd_handle h, const fdfd_c64* u, fdfd_c64* g) {
   if (rc) return rc;
   CK(cudaStreamSynchronize(h->stream));
   return FDFD_OK;
+}
+
+int fdfd_schwarz_stationary(fdfd_handle h, const fdfd_c64* b_dev, fdfd_c64* u_dev, int max_iters, double tol,
+                            double momentum, int* iters, double* relres) {
+  if (!h || !b_dev || !u_dev || max_iters < 1 || !(tol >= 0.0) || !(momentum >= 0.0 && momentum < 1.0))
+    return FDFD_EINVAL;
+  if (!h->sw) return FDFD_ENOSETUP;
+  const float2* b = reinterpret_cast<const float2*>(b_dev);
+  float2* u = reinterpret_cast<float2*>(u_dev);
+  cudaStream_t s = h->stream;
+  const size_t n_win = (size_t)(h->nx / FDFD_CORE) * (h->ny / FDFD_CORE), nt = n_win * 4 * FDFD_WIN;
+  // Robin data, new traces and the inner solver's window right-hand sides
+  // live in the FGMRES search-direction space Z (rmax x n >= 1.8 n)
+  float2 *g = h->Z, *g_new = h->Z + nt, *rhs = h->Z + 2 * nt;
+  int rc;
+  if ((rc = schwarz_error(h))) return rc;
+  CK(cudaMemsetAsync(g, 0, nt * sizeof(float2), s));
+  double b2 = 0.0, r2 = 0.0;
+  if ((rc = launch_residual64(nullptr, b, h->sb, 0, 1.0, h->eps, h->cx64, h->cy64, h->k2, h->nx, h->ny, h->w,
+                              h->partials, h->counter, &h->st->resid, s)) ||
+      (rc = read_double(h, &h->st->resid, &b2)))
+    return rc;
+  int it = 0;
+  double rr = 0.0;
+  if (b2 == 0.0) {  // u = 0 solves it exactly
+    CK(cudaMemsetAsync(u, 0, h->n * sizeof(float2), s));
+  } else {
+    for (it = 1; it <= max_iters; ++it) {
+      if ((rc = schwarz_sweep_data(h, b, g, u, rhs)) || (rc = schwarz_stationary_update(h, u, g, g_new, momentum)))
+        return rc;
+      to_f64_kernel<<<krylov_grid(h->n), 256, 0, s>>>(u, h->x64, h->n);
+      CKL();
+      if ((rc = launch_residual64(h->x64, b, h->sb, 0, 1.0, h->eps, h->cx64, h->cy64, h->k2, h->nx, h->ny, h->w,
+                                  h->partials, h->counter, &h->st->resid, s)) ||
+          (rc = read_double(h, &h->st->resid, &r2)) || (rc = schwarz_error(h)))
+        return rc;
+      rr = sqrt(r2 / b2);
+      if (!isfinite(rr) || rr <= tol) break;
+    }
+    if (it > max_iters) it = max_iters;
+  }
+  CK(cudaStreamSynchronize(s));
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return isfinite(rr) ? FDFD_OK : FDFD_ENUMERIC;
 }
 
 int fdfd_profile_start(fdfd_handle h) {

@@ -288,6 +288,11 @@ __global__ void gemv32_kernel(float2* z, const float2* A, const float2* x, const
   if (lane == 0) z[row] = dropped[row] ? make_float2(0.f, 0.f) : make_float2(sr, si);
 }
 
+__global__ void sub_kernel(float2* a, const float2* b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = make_float2(a[i].x - b[i].x, a[i].y - b[i].y);
+}
+
 __global__ void to_f32_kernel(float2* dst, const double2* src, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = make_float2((float)src[i].x, (float)src[i].y);
@@ -391,13 +396,18 @@ int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, 
   return FDFD_OK;
 }
 
-int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u) {
+int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u, const float2* g_ref) {
   const int nwx = h->nx / FDFD_CORE, nwy = h->ny / FDFD_CORE, n_win = nwx * nwy;
   cudaStream_t s = h->stream;
   int rc;
   {
-    ProfScope ps(h, 6, 1);
+    ProfScope ps(h, 6, g_ref ? 2 : 1);
     if ((rc = schwarz_traces(h, u, c->ebc))) return rc;
+    if (g_ref) {  // boundary mismatch against the Robin data the local solves used
+      const int tot = n_win * 320;
+      sub_kernel<<<(tot + 255) / 256, 256, 0, s>>>(c->ebc, g_ref, tot);
+      CKL();
+    }
   }
   ProfScope ps(h, 7, 3);
   coarse_rhs32_kernel<<<n_win, 256, 0, s>>>(c->rcf, c->Cf, c->ebc, c->k, nwx, nwy);

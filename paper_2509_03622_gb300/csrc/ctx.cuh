@@ -77,6 +77,13 @@ int schwarz_apply(fdfd_ctx* h, const float2* v, const double* scale_dev, float2*
 int schwarz_nno_solve(fdfd_ctx* h, const float2* r_win, const float2* g_win, const int* win_id,
                       int n, float2* e_win);
 int schwarz_traces(fdfd_ctx* h, const float2* u, float2* g);
+// Algorithm 3 pieces: local solves with source b and Robin data g_win,
+// assembled into u (rhs_scratch: n_win x 6400 complex64, used with inner
+// FGMRES local solves) ...
+int schwarz_sweep_data(fdfd_ctx* h, const float2* b, const float2* g_win, float2* u, float2* rhs_scratch);
+// ... then new traces, the coarse correction of their mismatch with g, and
+// the momentum blend of g (g_new: scratch, n_win x 320 complex64).
+int schwarz_stationary_update(fdfd_ctx* h, float2* u, float2* g, float2* g_new, double momentum);
 // FDFD_ETIMEOUT once a bounded wait inside a neural-operator kernel ran out
 // (the flag stays set: later neural passes of the handle skip their work).
 int schwarz_error(fdfd_ctx* h);

@@ -8,7 +8,7 @@ struct CoarseData;
 void coarse_free(CoarseData* c);
 int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, int k, CoarseData** out,
                  size_t* bytes);
-int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u);
+int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u, const float2* g_ref = nullptr);
 int coarse_export(fdfd_ctx* h, CoarseData* c, double* Qh, double* Ndh);
 
 struct SchwarzData {
@@ -45,6 +45,28 @@ __global__ void traces_kernel(const float2* __restrict__ u, const float* __restr
     r = make_float2(uo.x - ub.x - kd * ub.y, uo.y - ub.y + kd * ub.x);
   }
   g[idx] = r;
+}
+
+// rhs_w += R_w b: the restricted source joins the Robin data's right-hand side.
+__global__ void add_restricted_kernel(float2* __restrict__ rhs, const float2* __restrict__ b, int nx, int ny,
+                                      int nwx) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x, w = blockIdx.y;
+  if (p >= FDFD_WIN * FDFD_WIN) return;
+  const int a = w % nwx, bb = w / nwx;
+  const int x0 = min(max(FDFD_CORE * a - FDFD_OVL, 0), nx - FDFD_WIN);
+  const int y0 = min(max(FDFD_CORE * bb - FDFD_OVL, 0), ny - FDFD_WIN);
+  const float2 v = b[(size_t)(y0 + p / FDFD_WIN) * nx + x0 + p % FDFD_WIN];
+  float2& r = rhs[(size_t)w * FDFD_WIN * FDFD_WIN + p];
+  r = make_float2(r.x + v.x, r.y + v.y);
+}
+
+// Momentum blend of the Robin data: g = m g + (1 - m) g_new.
+__global__ void blend_kernel(float2* __restrict__ g, const float2* __restrict__ g_new, float m, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float2 a = g[i], c = g_new[i];
+    g[i] = make_float2(m * a.x + (1.f - m) * c.x, m * a.y + (1.f - m) * c.y);
+  }
 }
 
 }  // namespace
@@ -167,6 +189,47 @@ int schwarz_nno_solve(fdfd_ctx* h, const float2* r_win, const float2* g_win, con
   int rc = nno_forward(&S->W, &S->work, geom(h), in, out, n, h->stream);
   if (rc) return rc;
   return check_err(h);
+}
+
+// Local solves of Algorithm 3 with data: every window's problem has the
+// restricted source R_w b and the Robin data g_win [n_win][4][80] on its
+// interface sides; the solutions are assembled into u by restricted
+// prolongation (each cell from its owning window's core).
+int schwarz_sweep_data(fdfd_ctx* h, const float2* b, const float2* g_win, float2* u, float2* rhs_scratch) {
+  SchwarzData* S = h->sw;
+  if (S->inner > 0) {  // k steps of NN-preconditioned FGMRES on R_w b - sum_sides c_bo g
+    int rc = local_robin_rhs(h, g_win, rhs_scratch, S->n_win);
+    if (rc) return rc;
+    add_restricted_kernel<<<dim3((FDFD_WIN * FDFD_WIN + 255) / 256, S->n_win), 256, 0, h->stream>>>(
+        rhs_scratch, b, h->nx, h->ny, S->nwx);
+    CKL();
+    return local_fgmres(h, &S->local, &S->W, &S->work, nullptr, rhs_scratch, u, nullptr, h->d_one, 0);
+  }
+  NnoInput in;  // one neural application to (source, Robin data)
+  in.v_global = b;
+  in.g_win = g_win;
+  NnoOutput out;
+  out.z_global = u;
+  out.scale = h->d_one;
+  return nno_forward(&S->W, &S->work, geom(h), in, out, S->n_win, h->stream, h);
+}
+
+// The rest of one iteration of Algorithm 3 after the local solves: new Robin
+// data from the assembled field u (traces, Eq. 2); with a coarse space, u is
+// first corrected for the boundary mismatch between those traces and the
+// data g the local solves used (Eq. 8) and the traces are taken again; then
+// g = m g + (1 - m) g_new.  g_new is scratch of the same size as g.
+int schwarz_stationary_update(fdfd_ctx* h, float2* u, float2* g, float2* g_new, double momentum) {
+  SchwarzData* S = h->sw;
+  int rc = schwarz_traces(h, u, g_new);
+  if (!rc && S->coarse) {
+    if (!(rc = coarse_apply(h, S->coarse, u, g))) rc = schwarz_traces(h, u, g_new);
+  }
+  if (rc) return rc;
+  const int tot = S->n_win * 4 * FDFD_WIN;
+  blend_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(g, g_new, (float)momentum, tot);
+  CKL();
+  return FDFD_OK;
 }
 
 const NnoWeights* schwarz_weights(fdfd_ctx* h) { return (h && h->sw) ? &h->sw->W : nullptr; }

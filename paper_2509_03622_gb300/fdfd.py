@@ -79,6 +79,8 @@ _SIGS = {
     "fdfd_grad_eps": ([_P, _P, _P, _P, C.c_int], C.c_int),
     "fdfd_apply_A": ([_P, _P, _P, C.c_int], C.c_int),
     "fdfd_precond_apply": ([_P, _P, _P], C.c_int),
+    "fdfd_schwarz_stationary": ([_P, _P, _P, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_int),
+                                 C.POINTER(C.c_double)], C.c_int),
     "fdfd_nno_solve": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "fdfd_trace_extract": ([_P, _P, _P], C.c_int),
     "fdfd_local_apply": ([_P, _P, _P, _P, C.c_int], C.c_int),
@@ -229,6 +231,14 @@ class Solver:
 
     def precond_apply(self, v, z):
         _check(lib.fdfd_precond_apply(self.h, _ptr(v), _ptr(z)), "fdfd_precond_apply")
+
+    def schwarz_stationary(self, b, u, max_iters=200, tol=1e-6, momentum=0.0):
+        """Algorithm 3: the stationary Schwarz iteration for A~ u = b.
+        Returns (iterations, relative residual)."""
+        it, rr = C.c_int(0), C.c_double(0.0)
+        _check(lib.fdfd_schwarz_stationary(self.h, _ptr(b), _ptr(u), int(max_iters), float(tol), float(momentum),
+                                           C.byref(it), C.byref(rr)), "fdfd_schwarz_stationary")
+        return it.value, rr.value
 
     def nno_solve(self, r_win, g_win, win_id, e_win):
         n = r_win.shape[0]
