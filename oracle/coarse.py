@@ -15,9 +15,19 @@ Set-up, in the order of Algorithm 3:
 4. traces of the restricted basis fields on the neighbours' boundaries
    (extract_neighboring_bc) -> the columns of B Q;
 5. assemble the normal matrix of Eq. 8.
-The Rayleigh-Ritz step (eig of (x, y)) keeps all k Ritz vectors in this
-build, which leaves span(Q) and hence the correction unchanged; it is
-omitted (reading).
+The Rayleigh-Ritz step (eig of (x, y)) keeping all k Ritz vectors leaves
+span(Q) and hence the correction unchanged, so by default it is omitted
+(reading).  With ritz_tol > 0 the basis is truncated instead:
+6. H_w = (x, y) over the trials of window w, where y = B x is the Robin
+   data the window's basis field hands to each neighbour, read on that
+   neighbour's side facing w and identified with w's own side
+   (robin_to_robin).  With orthonormal trials H_w = Q_w^H B Q_w is the
+   Rayleigh-Ritz matrix; its eigenpairs H_w u = eta u give the Ritz vectors
+   Q_w u.  Q_w, Phi_w and the window's columns of C are combined by the
+   eigenvectors with |eta| >= ritz_tol (the fields are combined linearly,
+   not solved again) and the other directions are dropped (Sec. 2.2: the
+   slowly decaying modes, those with the largest eta, above a threshold span
+   the coarse space).
 
 Coarse equation (reading of Eq. 7): after adding sum_m z_{w,m} Phi_{w,m} to
 window w the boundary mismatch becomes e_bc + (BQ - Q) z, so the coarse
@@ -31,7 +41,10 @@ diagonal in the normal matrix.
 Parity: pinned in tests/test_oracle_coarse.py (normal-equation solve equals
 numpy.linalg.lstsq; the correction removes a mismatch that lies in the
 range of C; Gram-Schmidt orthonormality; exact plane-wave phase on a
-homogeneous window).
+homogeneous window; the Ritz step: keeping every direction leaves the
+correction unchanged, truncation equals least squares over the kept
+columns, |eta| <= 1 with a strongly transmitting interior window in a
+lossless medium, and the truncated two-level loop still converges).
 """
 from __future__ import annotations
 
@@ -96,9 +109,11 @@ def gram_schmidt(X: np.ndarray, drop_tol: float = 1e-10) -> np.ndarray:
 class CoarseSpace:
     """Q, Phi, C = BQ - Q and the factored normal matrix C^H C."""
 
-    def __init__(self, win: Windows, eps, dx, wavelength, k: int, local_solve):
+    def __init__(self, win: Windows, eps, dx, wavelength, k: int, local_solve, ritz_tol: float = 0.0):
         """local_solve(g [n_win][4][80]) -> fields [n_win][80][80]: the
-        homogeneous (zero-source) local Robin solver of every window."""
+        homogeneous (zero-source) local Robin solver of every window.
+        ritz_tol > 0: keep per window the Ritz vectors of the Robin-to-Robin
+        map whose eigenvalue has modulus >= ritz_tol (step 6 above)."""
         self.win, self.k = win, k
         self.eps, self.dx, self.wavelength = eps, dx, wavelength
         X = plane_wave_trials(win, eps, dx, wavelength, k)
@@ -107,6 +122,9 @@ class CoarseSpace:
         for m in range(k):
             self.Phi[:, m] = local_solve(self.Q[:, m])
         self.C = self.assemble_C()
+        self.eta = None
+        if ritz_tol > 0.0:
+            self.truncate(ritz_tol)
         self.N = self.C.conj().T @ self.C
         # Trial vectors removed by Gram-Schmidt (exactly dependent trials,
         # e.g. symmetric direction sets on a corner window's two sides) give
@@ -114,6 +132,45 @@ class CoarseSpace:
         self.dropped = ~np.any(self.Q.reshape(win.n * k, -1), axis=1)
         self.N[self.dropped, self.dropped] = 1.0
         self.L = np.linalg.cholesky(self.N)
+
+    def robin_to_robin(self, w: int) -> np.ndarray:
+        """Y_w [k][4][80]: for each interface side s of window w, the trace
+        that each basis field of w leaves on the neighbour across s, on that
+        neighbour's side facing w (read from C, whose rows off window w hold
+        the traces alone)."""
+        win, k = self.win, self.k
+        a, b = w % win.nwx, w // win.nwx
+        across = {0: (a - 1, b, 1), 1: (a + 1, b, 0), 2: (a, b - 1, 3), 3: (a, b + 1, 2)}
+        Y = np.zeros((k, SIDES, WIN), dtype=np.complex128)
+        for s, (ai, bi, facing) in across.items():
+            if not win.interface[w, s]:
+                continue
+            i = bi * win.nwx + ai
+            r0 = (i * SIDES + facing) * WIN
+            Y[:, s, :] = self.C[r0:r0 + WIN, w * k:(w + 1) * k].T
+        return Y
+
+    def ritz_matrix(self, w: int) -> np.ndarray:
+        """H_w[p, q] = (q_p, y_q) = sum conj(Q_w[p]) Y_w[q] (k x k)."""
+        k = self.k
+        return self.Q[w].reshape(k, -1).conj() @ self.robin_to_robin(w).reshape(k, -1).T
+
+    def truncate(self, ritz_tol: float) -> None:
+        """Step 6: per window, the eigenpairs H u = eta u of the Ritz matrix;
+        Q, Phi and the window's columns of C are combined by the eigenvectors
+        with |eta| >= ritz_tol, the other directions become zero columns
+        (their unknowns are then pinned like dropped trials)."""
+        win, k = self.win, self.k
+        H = [self.ritz_matrix(w) for w in range(win.n)]  # all from the untruncated C
+        self.eta = np.zeros((win.n, k), dtype=np.complex128)
+        for w in range(win.n):
+            eta, U = np.linalg.eig(H[w])
+            U = U * (np.abs(eta) >= ritz_tol)[None, :]
+            self.eta[w] = eta
+            self.Q[w] = np.einsum("mq,msl->qsl", U, self.Q[w])
+            self.Phi[w] = np.einsum("mq,myx->qyx", U, self.Phi[w])
+            cols = slice(w * k, (w + 1) * k)
+            self.C[:, cols] = self.C[:, cols] @ U
 
     def restricted_field(self, w: int, f_loc: np.ndarray) -> np.ndarray:
         """R~_w^T f: window field placed on w's core only."""

@@ -29,7 +29,7 @@ from .coarse import CoarseSpace
 
 class Schwarz:
     def __init__(self, eps, dx, wavelength, npml, weights=None, k_coarse: int = 0,
-                 local: str = "nno", inner: int = 0):
+                 local: str = "nno", inner: int = 0, ritz_tol: float = 0.0):
         """local = "nno": neural local solves -- one application of the
         network to (residual, Robin data) when inner = 0, else `inner` steps
         of NN-preconditioned FGMRES (Algorithm 1) on the window's Robin
@@ -56,7 +56,7 @@ class Schwarz:
         if k_coarse > 0:
             zero = np.zeros((self.win.n, WIN, WIN), dtype=np.complex128)
             self.coarse = CoarseSpace(self.win, self.eps, dx, wavelength, k_coarse,
-                                      lambda g: self.local_solve(zero, g))
+                                      lambda g: self.local_solve(zero, g), ritz_tol=ritz_tol)
 
     def aux(self, w: int):
         x0, y0 = int(self.win.x0[w]), int(self.win.y0[w])

@@ -103,3 +103,67 @@ def test_exact_oras_beats_jacobi_in_fgmres():
     assert not ij["converged"]
     xs = fdfd.DirectSolver(A).solve(b)
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-4
+
+
+@pytest.fixture(scope="module")
+def ritz_pair():
+    """The same layout and local solver without and with the Ritz step."""
+    n, dx = 192, LAM / 25
+    eps = wl.rectangles_eps(n, n, npml=20, n_rect=10, seed=31)
+    S0 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact")
+    S1 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact", ritz_tol=1e-12)
+    S3 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact", ritz_tol=0.3)
+    return S0, S1, S3
+
+
+def test_ritz_all_directions_keep_the_correction(ritz_pair):
+    """Keeping every Ritz vector with a nonzero eigenvalue spans the same
+    space as the trials, so the coarse correction of any mismatch is
+    unchanged (Q, Phi and C are combined consistently)."""
+    S0, S1, _ = ritz_pair
+    c0, c1 = S0.coarse, S1.coarse
+    assert np.array_equal(c0.dropped, c1.dropped)
+    e = wl.rng(4).standard_normal(c0.C.shape[0]) + 1j * wl.rng(5).standard_normal(c0.C.shape[0])
+    u0, u1 = c0.correction(c0.solve(e)), c1.correction(c1.solve(e))
+    assert np.linalg.norm(u1 - u0) / np.linalg.norm(u0) < 1e-8
+
+
+def test_ritz_truncation_is_least_squares_on_the_kept_span(ritz_pair):
+    """With a threshold the kept directions are the Ritz vectors with
+    |eta| >= tol; the correction is the least-squares fit of the mismatch
+    over their columns of C alone (the others pinned to zero)."""
+    _, S1, S3 = ritz_pair
+    c1, c3 = S1.coarse, S3.coarse
+    kept = ~c3.dropped
+    assert kept.sum() == (np.abs(c3.eta) >= 0.3).sum() < (~c1.dropped).sum()
+    e = wl.rng(6).standard_normal(c3.C.shape[0]) + 0j
+    z = c3.solve(e)
+    z_ls, *_ = np.linalg.lstsq(c3.C[:, kept], -e, rcond=None)
+    assert np.all(z[~kept] == 0)
+    assert np.linalg.norm(z[kept] - z_ls) / np.linalg.norm(z_ls) < 1e-8
+
+
+def test_ritz_eigenvalues_of_a_lossless_layout():
+    """Homogeneous lossless medium, exact local solves: no Robin-to-Robin
+    mode grows (|eta| <= 1), the interior window hands most of a plane wave
+    on (its largest |eta| is well above the corner windows'; reading the
+    wrong side of a neighbour would leave it near zero)."""
+    n, dx = 192, LAM / 24
+    S = schwarz.Schwarz(np.ones((n, n), np.float32), dx, LAM, 20, k_coarse=8, local="exact", ritz_tol=1e-12)
+    a = np.abs(S.coarse.eta)
+    assert a.max() <= 1.0
+    assert a[4].max() >= 0.5 and a[4].max() > 2 * a[0].max()
+
+
+@pytest.mark.slow
+def test_ritz_truncated_two_level_still_converges():
+    """Algorithm 3 with the coarse space truncated at |eta| >= 0.05 (homogeneous
+    256^2, k = 36, exact local solves) still converges to 1e-6 within 80
+    iterations while keeping fewer than two thirds of the modes."""
+    n, dx = 256, LAM / 24
+    eps = np.ones((n, n), np.float32)
+    b = fdfd.source_rhs(wl.point_source(n, n), dx, LAM)
+    S = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=36, local="exact", ritz_tol=0.05)
+    kept = (~S.coarse.dropped).sum()
+    _, it, r = schwarz.stationary_solve(S, b, tol=1e-6, max_iters=80)
+    assert r <= 1e-6 and kept < 2 * S.coarse.dropped.size / 3
