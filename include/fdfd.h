@@ -103,6 +103,16 @@ typedef struct {
                             with the residual and Robin data as inputs;
                             m in 1..16 = m steps of NN-preconditioned FGMRES
                             (Algorithm 1) on the window's Robin problem     */
+  double ritz_tol;       /* Rayleigh-Ritz truncation of the coarse space
+                            (Algorithm 3 set-up, eta, u = eig(H); Sec. 2.2):
+                            0 = keep the k orthonormalised trials (span
+                            unchanged by the eig step); > 0 = per window,
+                            the eigenpairs of H = Q^H Y, Y the Robin data
+                            each basis field hands to the neighbours (read
+                            on their sides facing the window), and only the
+                            Ritz vectors with |eta| >= ritz_tol kept; the
+                            basis fields are combined, not solved again.
+                            Needs k_coarse <= 64.                           */
 } schwarz_desc;
 
 typedef struct {
@@ -139,6 +149,8 @@ typedef struct {
                             operand tiles by TMA, 1 or 2 = gather with that
                             K split; the environment variable
                             FDFD_DFTY_VARIANT=0|1|2 fixes it instead      */
+  int n_coarse_kept;     /* coarse unknowns kept (trials not dropped as
+                            dependent, Ritz vectors above ritz_tol)        */
 } fdfd_info;
 
 /* ---- handle life cycle ----------------------------------------------- */
@@ -310,6 +322,13 @@ int  fdfd_trace_extract(fdfd_handle h, const fdfd_c64* u, fdfd_c64* g);
  * Q [n_win][k][4][80] complex128 (interleaved doubles) orthonormalised trials;
  * normal matrix diagonal blocks N_ww [n_win][k][k] complex128. */
 int  fdfd_coarse_export(fdfd_handle h, double* Q_host, double* Ndiag_host);
+
+/* Rayleigh-Ritz data of the coarse set-up (schwarz_desc.ritz_tol > 0), host
+ * pointers, each may be NULL: eta_host [n_win][k] Ritz values and H_host
+ * [n_win][k][k] row-major Ritz matrices H[p][q] = (q_p, y_q), complex128
+ * (interleaved doubles); the values per window in the order the eigen
+ * solver returns them.  FDFD_ENOSETUP without a Ritz step. */
+int  fdfd_coarse_ritz(fdfd_handle h, double* eta_host, double* H_host);
 
 /* Diagnostic: one tile GEMM on the tcgen05 path used by the neural operator
  * (no counterpart in the paper; validates the tensor-core operand encoding).

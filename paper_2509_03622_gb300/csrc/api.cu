@@ -677,6 +677,12 @@ int fdfd_selftest_gemm(const void* A, const void* B, float* C, int M, int N, int
   return rc;
 }
 
+int fdfd_coarse_ritz(fdfd_handle h, double* eta_host, double* H_host) {
+  if (!h) return FDFD_EINVAL;
+  if (!h->sw) return FDFD_ENOSETUP;
+  return schwarz_ritz_export(h, eta_host, H_host);
+}
+
 int fdfd_coarse_export(fdfd_handle h, double* Q, double* Nd) {
   if (!h) return FDFD_EINVAL;
   if (!h->sw) return FDFD_ENOSETUP;

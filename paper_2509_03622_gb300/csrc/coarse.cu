@@ -7,13 +7,22 @@
 // neighbours' boundaries minus the window's own data (C = BQ - Q, stored as
 // 9 neighbour blocks per window), the normal matrix C^H C (Eq. 8) and its
 // inverse (FP64 Gauss-Jordan; the matrix is Hermitian positive definite).
+// Optional Rayleigh-Ritz truncation (Algorithm 3 set-up: eta, u = eig(H);
+// Sec. 2.2: the slowly decaying modes above a threshold): per window the
+// Ritz matrix H = Q^H Y of the Robin-to-Robin map (Y: the data each basis
+// field hands to the neighbours, read on their sides facing the window),
+// its eigenpairs (one thread per window, eig.cuh), and Q, Phi and the
+// window's columns of C combined by the eigenvectors with |eta| >= ritz_tol;
+// the other directions become zero columns, pinned like dependent trials.
 // Apply: e_bc = traces of the one-level field, r_c = -C^H e_bc, z = N^-1 r_c,
 // u += sum_w R~_w^T sum_m z_{w,m} Phi_{w,m}.
 #include <math.h>
+#include <vector>
 #include "ctx.cuh"
 #include "nno.cuh"
 #include "local.cuh"
 #include "reduce.cuh"
+#include "eig.cuh"
 
 struct CoarseData {
   int k = 0, nc = 0;
@@ -28,6 +37,9 @@ struct CoarseData {
   float2* ebc = nullptr;     // [n_win][320]
   float2* tmp = nullptr;     // [n_win][6400] window fields during set-up
   int* dropped = nullptr;    // [nc]
+  double2* eta = nullptr;    // [n_win][k] Ritz values (Ritz step only)
+  double2* H = nullptr;      // [n_win][k][k] Ritz matrices (Ritz step only)
+  int n_kept = 0;            // unknowns not dropped
   // FP32 copies used by the per-iteration apply (the correction is part of a
   // flexible preconditioner, and FP64 arithmetic is scarce on this GPU)
   float2* Cf = nullptr;      // [n_win][9][320][k]
@@ -288,6 +300,93 @@ __global__ void gemv32_kernel(float2* z, const float2* A, const float2* x, const
   if (lane == 0) z[row] = dropped[row] ? make_float2(0.f, 0.f) : make_float2(sr, si);
 }
 
+// H[w][p][q] = sum over w's interface sides s of conj(Q_w[p][s]) . Y_w[q][s],
+// Y_w[q][s] = the trace basis field (w, q) leaves on the neighbour across s,
+// on its side facing w: C block (neighbour i, j = w's offset from i).
+__global__ void ritz_H_kernel(const double2* __restrict__ Q, const double2* __restrict__ C, double2* __restrict__ H,
+                              int k, int nx, int ny, int nwx) {
+  const int w = blockIdx.x;
+  const Win W = win_of(w, nx, ny, nwx);
+  // side s: neighbour offset (di), block index of w seen from it (j), its facing side (f)
+  const int di[4] = {-1, 1, -nwx, nwx}, jb[4] = {5, 3, 7, 1}, fs[4] = {1, 0, 3, 2};
+  for (int pq = threadIdx.x; pq < k * k; pq += blockDim.x) {
+    const int p = pq / k, q = pq % k;
+    double sr = 0.0, si = 0.0;
+    for (int sd = 0; sd < 4; ++sd) {
+      if (!W.iface[sd]) continue;
+      const int i = w + di[sd];
+      const double2* qp = Q + ((size_t)w * k + p) * 320 + sd * 80;
+      const double2* cy = C + (((size_t)i * 9 + jb[sd]) * 320 + fs[sd] * 80) * k + q;
+      for (int t = 0; t < 80; ++t) {  // conj(q) . y
+        const double2 a = qp[t], b = cy[(size_t)t * k];
+        sr += a.x * b.x + a.y * b.y;
+        si += a.x * b.y - a.y * b.x;
+      }
+    }
+    H[((size_t)w * k + p) * k + q] = make_double2(sr, si);
+  }
+}
+
+// Eigenpairs of each window's Ritz matrix (one thread per window); the
+// eigenvectors with |eta| < tol become zero columns of U.
+__global__ void ritz_eig_kernel(double2* H, double2* Z, double2* U, double2* eta, int k, int n_win, double tol,
+                                int* fail) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n_win) return;
+  const size_t o = (size_t)w * k * k;
+  ecd* e = reinterpret_cast<ecd*>(eta + (size_t)w * k);
+  ecd* u = reinterpret_cast<ecd*>(U + o);
+  if (!eig_small(reinterpret_cast<ecd*>(H + o), reinterpret_cast<ecd*>(Z + o), e, u, k)) atomicExch(fail, 1);
+  for (int q = 0; q < k; ++q)
+    if (e_abs(e[q]) < tol)
+      for (int m = 0; m < k; ++m) u[m * k + q] = {0.0, 0.0};
+}
+
+// out[w][q][e] = sum_m in[w][m][e] U[w][m][q]  (Q: L = 320, Phi: L = 4096)
+template <typename T>
+__global__ void ritz_rotate_kernel(const T* __restrict__ in, T* __restrict__ out, const double2* __restrict__ U,
+                                   int k, int L) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x, w = blockIdx.y;
+  if (e >= L) return;
+  const double2* Uw = U + (size_t)w * k * k;
+  for (int q = 0; q < k; ++q) {
+    double sr = 0.0, si = 0.0;
+    for (int m = 0; m < k; ++m) {
+      const T x = in[((size_t)w * k + m) * L + e];
+      const double2 c = Uw[m * k + q];
+      sr += (double)x.x * c.x - (double)x.y * c.y;
+      si += (double)x.x * c.y + (double)x.y * c.x;
+    }
+    T r;
+    r.x = sr; r.y = si;
+    out[((size_t)w * k + q) * L + e] = r;
+  }
+}
+
+// C rows of window i, block j (columns of window J = i + offset j): the
+// k-vector of each slot times U_J.
+__global__ void ritz_rotate_C_kernel(const double2* __restrict__ C, double2* __restrict__ out,
+                                     const double2* __restrict__ U, int k, int nwx, int nwy) {
+  const int ij = blockIdx.x, i = ij / 9, j = ij % 9;
+  const int aJ = i % nwx + j % 3 - 1, bJ = i / nwx + j / 3 - 1;
+  const bool hasJ = aJ >= 0 && aJ < nwx && bJ >= 0 && bJ < nwy;
+  const double2* UJ = U + (size_t)(hasJ ? bJ * nwx + aJ : 0) * k * k;
+  for (int slot = threadIdx.x; slot < 320; slot += blockDim.x) {
+    const double2* x = C + ((size_t)ij * 320 + slot) * k;
+    double2* y = out + ((size_t)ij * 320 + slot) * k;
+    for (int q = 0; q < k; ++q) {
+      double sr = 0.0, si = 0.0;
+      if (hasJ)
+        for (int m = 0; m < k; ++m) {
+          const double2 a = x[m], c = UJ[m * k + q];
+          sr += a.x * c.x - a.y * c.y;
+          si += a.x * c.y + a.y * c.x;
+        }
+      y[q] = make_double2(sr, si);
+    }
+  }
+}
+
 __global__ void sub_kernel(float2* a, const float2* b, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = make_float2(a[i].x - b[i].x, a[i].y - b[i].y);
@@ -326,16 +425,59 @@ int ca(T** p, size_t n, size_t* bytes) {
 void coarse_free(CoarseData* c) {
   if (!c) return;
   void* ptrs[] = {c->Q, c->Qf, c->Phi, c->C, c->N, c->Nd, c->rc, c->zc, c->ebc, c->tmp, c->dropped,
-                  c->Cf, c->Nf, c->rcf, c->zcf};
+                  c->Cf, c->Nf, c->rcf, c->zcf, c->eta, c->H};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete c;
 }
 
-int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, int k, CoarseData** out,
-                 size_t* bytes) {
+// The Rayleigh-Ritz truncation of a set-up whose C is assembled: Q, Phi
+// and C are replaced by their combinations with the kept eigenvectors.
+static int ritz_truncate(fdfd_ctx* h, CoarseData* c, double tol, size_t* bytes) {
+  const int nwx = h->nx / FDFD_CORE, nwy = h->ny / FDFD_CORE, n_win = nwx * nwy, k = c->k, nc = c->nc;
+  cudaStream_t s = h->stream;
+  double2 *H = nullptr, *Z = nullptr, *U = nullptr, *Q2 = nullptr, *C2 = nullptr;
+  float2* P2 = nullptr;
+  int* fail = nullptr;
+  size_t tb = 0;  // temporaries, released before returning
+  int rc = FDFD_OK, f = 0;
+  if ((rc = ca(&c->eta, (size_t)n_win * k, bytes)) || (rc = ca(&c->H, (size_t)n_win * k * k, bytes)) ||
+      (rc = ca(&H, (size_t)n_win * k * k, &tb)) ||
+      (rc = ca(&Z, (size_t)n_win * k * k, &tb)) || (rc = ca(&U, (size_t)n_win * k * k, &tb)) ||
+      (rc = ca(&Q2, (size_t)nc * 320, &tb)) || (rc = ca(&P2, (size_t)nc * 4096, &tb)) ||
+      (rc = ca(&C2, (size_t)n_win * 9 * 320 * k, &tb)) || (rc = ca(&fail, 1, &tb)))
+    goto done;
+  ritz_H_kernel<<<n_win, 256, 0, s>>>(c->Q, c->C, H, k, h->nx, h->ny, nwx);
+  if (cudaMemcpyAsync(c->H, H, (size_t)n_win * k * k * sizeof(double2), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+    rc = FDFD_ECUDA;
+    goto done;
+  }
+  ritz_eig_kernel<<<(n_win + 31) / 32, 32, 0, s>>>(H, Z, U, c->eta, k, n_win, tol, fail);
+  ritz_rotate_kernel<double2><<<dim3((320 + 255) / 256, n_win), 256, 0, s>>>(c->Q, Q2, U, k, 320);
+  ritz_rotate_kernel<float2><<<dim3(4096 / 256, n_win), 256, 0, s>>>(c->Phi, P2, U, k, 4096);
+  ritz_rotate_C_kernel<<<n_win * 9, 256, 0, s>>>(c->C, C2, U, k, nwx, nwy);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&f, fail, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    rc = FDFD_ECUDA;
+    goto done;
+  }
+  if (f) { rc = FDFD_ENUMERIC; goto done; }  // a QR iteration did not converge
+  { double2* t = c->Q; c->Q = Q2; Q2 = t; }
+  { float2* t = c->Phi; c->Phi = P2; P2 = t; }
+  { double2* t = c->C; c->C = C2; C2 = t; }
+done:
+  cudaStreamSynchronize(s);
+  void* tmp[] = {H, Z, U, Q2, P2, C2, fail};
+  for (void* p : tmp) if (p) cudaFree(p);
+  return rc;
+}
+
+int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, int k, double ritz_tol,
+                 CoarseData** out, size_t* bytes) {
   const int nwx = h->nx / FDFD_CORE, nwy = h->ny / FDFD_CORE, n_win = nwx * nwy;
   const int nc = n_win * k;
   if (k < 1 || k > 256 || (size_t)nc * nc * 16 > ((size_t)16 << 30)) return FDFD_EINVAL;
+  if (!(ritz_tol >= 0.0) || (ritz_tol > 0.0 && k > EIG_KMAX)) return FDFD_EINVAL;
   CoarseData* c = new CoarseData();
   c->k = k; c->nc = nc;
   int rc;
@@ -376,6 +518,7 @@ int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, 
   if (rhs) { cudaStreamSynchronize(s); cudaFree(rhs); *bytes -= (size_t)n_win * 6400 * sizeof(float2); }
   assemble_C_kernel<<<dim3(n_win, 9), 256, 0, s>>>(c->C, c->Q, c->Phi, k, h->eps, h->k0dx, h->nx, h->ny, nwx, nwy);
   CKL();
+  if (ritz_tol > 0.0 && (rc = ritz_truncate(h, c, ritz_tol, bytes))) { coarse_free(c); return rc; }
   if (cudaMemsetAsync(c->N, 0, (size_t)nc * nc * sizeof(double2), s) != cudaSuccess) { coarse_free(c); return FDFD_ECUDA; }
   assemble_N_kernel<<<dim3(n_win, 25), 256, 0, s>>>(c->N, c->Nd, c->C, k, nwx, nwy);
   CKL();
@@ -391,8 +534,27 @@ int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, 
   to_f32_kernel<<<1024, 256, 0, s>>>(c->Cf, c->C, (size_t)n_win * 9 * 320 * k);
   to_f32_kernel<<<1024, 256, 0, s>>>(c->Nf, c->N, (size_t)nc * nc);
   CKL();
-  CK(cudaStreamSynchronize(s));
+  {
+    std::vector<int> dr(nc);
+    if (cudaMemcpyAsync(dr.data(), c->dropped, (size_t)nc * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      coarse_free(c);
+      return FDFD_ECUDA;
+    }
+    c->n_kept = 0;
+    for (int d : dr) c->n_kept += d ? 0 : 1;
+  }
   *out = c;
+  return FDFD_OK;
+}
+
+int coarse_kept(CoarseData* c) { return c ? c->n_kept : 0; }
+
+int coarse_ritz_export(fdfd_ctx* h, CoarseData* c, double* eta_host, double* H_host) {
+  if (!c->eta) return FDFD_ENOSETUP;
+  const size_t n = (size_t)(h->nx / FDFD_CORE) * (h->ny / FDFD_CORE) * c->k;
+  if (eta_host) CK(cudaMemcpy(eta_host, c->eta, n * sizeof(double2), cudaMemcpyDeviceToHost));
+  if (H_host) CK(cudaMemcpy(H_host, c->H, n * c->k * sizeof(double2), cudaMemcpyDeviceToHost));
   return FDFD_OK;
 }
 

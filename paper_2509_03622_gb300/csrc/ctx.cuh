@@ -90,6 +90,7 @@ int schwarz_error(fdfd_ctx* h);
 // Set that flag from the host (failure injection for tests).
 int schwarz_mark_failed(fdfd_ctx* h);
 int schwarz_export(fdfd_ctx* h, double* Q, double* Nd);
+int schwarz_ritz_export(fdfd_ctx* h, double* eta, double* H);
 struct NnoWeights;
 const NnoWeights* schwarz_weights(fdfd_ctx* h);  // nullptr before schwarz_setup
 int schwarz_info(fdfd_ctx* h, fdfd_info* info);

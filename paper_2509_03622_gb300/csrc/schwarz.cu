@@ -6,8 +6,10 @@
 
 struct CoarseData;
 void coarse_free(CoarseData* c);
-int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, int k, CoarseData** out,
-                 size_t* bytes);
+int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, int k, double ritz_tol,
+                 CoarseData** out, size_t* bytes);
+int coarse_kept(CoarseData* c);
+int coarse_ritz_export(fdfd_ctx* h, CoarseData* c, double* eta_host, double* H_host);
 int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u, const float2* g_ref = nullptr);
 int coarse_export(fdfd_ctx* h, CoarseData* c, double* Qh, double* Ndh);
 
@@ -135,8 +137,8 @@ int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd) {
   h->sw = S;
   if (!rc && sd->k_coarse > 0) {
     S->k = sd->k_coarse;
-    rc = coarse_setup(h, &S->W, &S->work, S->inner > 0 ? &S->local : nullptr, sd->k_coarse, &S->coarse,
-                      &S->bytes);
+    rc = coarse_setup(h, &S->W, &S->work, S->inner > 0 ? &S->local : nullptr, sd->k_coarse, sd->ritz_tol,
+                      &S->coarse, &S->bytes);
     if (!rc) rc = check_err(h);
   }
   if (rc) { schwarz_destroy(h); return rc; }
@@ -242,6 +244,11 @@ int schwarz_coarse(fdfd_ctx* h, float2* z) {
   return coarse_apply(h, h->sw->coarse, z);
 }
 
+int schwarz_ritz_export(fdfd_ctx* h, double* eta, double* H) {
+  if (!h->sw->coarse) return FDFD_ENOSETUP;
+  return coarse_ritz_export(h, h->sw->coarse, eta, H);
+}
+
 int schwarz_export(fdfd_ctx* h, double* Q, double* Nd) {
   if (!h->sw->coarse) return FDFD_ENOSETUP;
   return coarse_export(h, h->sw->coarse, Q, Nd);
@@ -250,6 +257,7 @@ int schwarz_export(fdfd_ctx* h, double* Q, double* Nd) {
 int schwarz_info(fdfd_ctx* h, fdfd_info* info) {
   info->k_coarse = h->sw->k;
   info->n_coarse = h->sw->k * h->sw->n_win;
+  info->n_coarse_kept = coarse_kept(h->sw->coarse);
   info->tuned_dfty_split = h->sw->work.g2_split;
   return FDFD_OK;
 }

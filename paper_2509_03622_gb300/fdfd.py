@@ -35,7 +35,7 @@ class Desc(C.Structure):
 
 class SchwarzDesc(C.Structure):
     _fields_ = [("k_coarse", C.c_int), ("precision", C.c_int), ("weights", C.c_void_p),
-                ("n_weights", C.c_size_t), ("inner_iters", C.c_int)]
+                ("n_weights", C.c_size_t), ("inner_iters", C.c_int), ("ritz_tol", C.c_double)]
 
 
 class SolveOpts(C.Structure):
@@ -54,7 +54,7 @@ class SolveStats(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n_win", C.c_int), ("nwx", C.c_int), ("nwy", C.c_int), ("k_coarse", C.c_int),
                 ("n_coarse", C.c_int), ("workspace_bytes", C.c_size_t), ("graphs_cached", C.c_int),
-                ("graphs_ok", C.c_int), ("tuned_dfty_split", C.c_int)]
+                ("graphs_ok", C.c_int), ("tuned_dfty_split", C.c_int), ("n_coarse_kept", C.c_int)]
 
 
 class Profile(C.Structure):
@@ -89,6 +89,7 @@ _SIGS = {
     "fdfd_batch_destroy": ([_P], None),
     "fdfd_nno_solve_noalloc": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "fdfd_coarse_export": ([_P, _P, _P], C.c_int),
+    "fdfd_coarse_ritz": ([_P, _P, _P], C.c_int),
     "fdfd_profile_start": ([_P], C.c_int),
     "fdfd_selftest_gemm": ([_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "fdfd_selftest_wait": ([], C.c_int),
@@ -183,10 +184,10 @@ class Solver:
         _check(lib.fdfd_set_eps(self.h, _ptr(eps)), "fdfd_set_eps")
 
     def schwarz_setup(self, weights_blob: np.ndarray, k_coarse: int = 0, precision: int = PREC_BF16,
-                      inner_iters: int = 0):
+                      inner_iters: int = 0, ritz_tol: float = 0.0):
         blob = np.ascontiguousarray(weights_blob, dtype=np.float32)
         sd = SchwarzDesc()
-        sd.k_coarse, sd.precision, sd.inner_iters = k_coarse, precision, inner_iters
+        sd.k_coarse, sd.precision, sd.inner_iters, sd.ritz_tol = k_coarse, precision, inner_iters, float(ritz_tol)
         sd.weights = blob.ctypes.data
         sd.n_weights = blob.size
         _check(lib.schwarz_setup(self.h, C.byref(sd)), "schwarz_setup")
@@ -279,6 +280,17 @@ class Solver:
         Nd = np.zeros((nw, k, k, 2), dtype=np.float64)
         _check(lib.fdfd_coarse_export(self.h, Q.ctypes.data, Nd.ctypes.data), "fdfd_coarse_export")
         return Q[..., 0] + 1j * Q[..., 1], Nd[..., 0] + 1j * Nd[..., 1]
+
+
+    def coarse_ritz(self):
+        """(Ritz values [n_win][k], Ritz matrices [n_win][k][k]) of a set-up
+        with ritz_tol > 0."""
+        inf = self.info()
+        nw, k = inf["n_win"], inf["k_coarse"]
+        eta = np.zeros((nw, k, 2), dtype=np.float64)
+        H = np.zeros((nw, k, k, 2), dtype=np.float64)
+        _check(lib.fdfd_coarse_ritz(self.h, eta.ctypes.data, H.ctypes.data), "fdfd_coarse_ritz")
+        return eta[..., 0] + 1j * eta[..., 1], H[..., 0] + 1j * H[..., 1]
 
 
 class Batch:
