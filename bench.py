@@ -189,7 +189,7 @@ def make_problem(n, seed_off=0):
     return eps, J, dx, lam
 
 
-def cpu_oracle_rate(n_sample, iters, precond, weights=None, k_coarse=0, inner=0, budget_s=None):
+def cpu_oracle_rate(n_sample, iters, precond, weights=None, k_coarse=0, inner=0, budget_s=None, ritz_tol=0.0):
     """Mcell-it/s of the FP64 oracle FGMRES (as it stands) on an n_sample^2
     grid of the same recipe, `iters` Arnoldi steps (or, with budget_s, as
     many as fit in about that many seconds after a 2-step probe)."""
@@ -203,7 +203,8 @@ def cpu_oracle_rate(n_sample, iters, precond, weights=None, k_coarse=0, inner=0,
         M = lambda v: v / d
     else:
         from oracle import schwarz as OS
-        M = OS.Schwarz(eps, dx, lam, 20, weights=weights, k_coarse=k_coarse, inner=inner)
+        M = OS.Schwarz(eps, dx, lam, 20, weights=weights, k_coarse=k_coarse, inner=inner,
+                       ritz_tol=ritz_tol if k_coarse > 0 else 0.0)
     t1 = time.perf_counter()
     if budget_s:
         OK.fgmres(lambda v: A @ v, b, precond=M, restart=30, tol=1e-14, max_iters=2)
@@ -237,7 +238,7 @@ def run_reference(args):
     for _ in range(args.warmup):
         pass  # the oracle has no device state to warm
     for _ in range(args.steps):
-        rate, t, _ = cpu_oracle_rate(n_s, 1, args.precond, w, k, inner)
+        rate, t, _ = cpu_oracle_rate(n_s, 1, args.precond, w, k, inner, ritz_tol=args.ritz_tol)
         tot_t += t
         tot_cells += n_s * n_s
     v = tot_cells / tot_t / 1e6
@@ -265,6 +266,8 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--k-coarse", type=int, default=-1)
     ap.add_argument("--inner", type=int, default=0, help="NN-FGMRES steps per local solve (0 = one application)")
+    ap.add_argument("--ritz-tol", type=float, default=0.0,
+                    help="Rayleigh-Ritz truncation of the coarse space: keep |eta| >= this (0 = off)")
     ap.add_argument("--weights", default=None, help="weight blob (.npy); default the trained blob if present")
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
@@ -300,7 +303,7 @@ def main():
         blob, wsrc = load_weights(args.weights)
         t0 = time.perf_counter()
         S.schwarz_setup(blob, k_coarse=kc, precision=F.PREC_FP8 if prec_nno == "fp8" else F.PREC_BF16,
-                        inner_iters=args.inner)
+                        inner_iters=args.inner, ritz_tol=args.ritz_tol if kc > 0 else 0.0)
         t_setup = time.perf_counter() - t0
     Jd = torch.from_numpy(J).to(dev)
     E = torch.zeros((n, n), dtype=torch.complex64, device=dev)
@@ -377,6 +380,8 @@ def main():
                        "inner_iters": args.inner if precond == F.PRECOND_SCHWARZ else None,
                        "weights": wsrc if precond == F.PRECOND_SCHWARZ else None,
                        "setup_s": t_setup if precond == F.PRECOND_SCHWARZ else None,
+                       "ritz_tol": args.ritz_tol if precond == F.PRECOND_SCHWARZ and kc > 0 else None,
+                       "n_coarse_kept": S.info()["n_coarse_kept"] if precond == F.PRECOND_SCHWARZ else None,
                        "nno_precision": prec_nno if precond == F.PRECOND_SCHWARZ else None,
                        "l2": "inputs larger than L2 (each Krylov vector 134 MB; V, Z 8 GB)",
                        "parallelism": f"replicas x{world}"},
@@ -391,7 +396,7 @@ def main():
     if rank == 0 and not args.no_cpu:
         w, kc_o, inner_o = oracle_preconditioner(args)
         ns = args.cpu_sample if precond == F.PRECOND_SCHWARZ else 1024
-        rate, t, it = cpu_oracle_rate(ns, 0, args.precond, w, kc_o, inner_o, budget_s=10.0)
+        rate, t, it = cpu_oracle_rate(ns, 0, args.precond, w, kc_o, inner_o, budget_s=10.0, ritz_tol=args.ritz_tol)
         line["cpu_baseline"] = {"value": rate, "unit": "Mcell-it/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{ns}x{ns} grid, same recipe and preconditioner configuration, "
                                           f"{it} FGMRES steps ({args.precond}), {t:.1f} s"}
