@@ -221,6 +221,62 @@ def workload_name(n, precond):
             f"{'Schwarz-NNO FGMRES(30)' if precond == 'schwarz' else 'Jacobi-GMRES(30)'}")
 
 
+def design_bench(iters, blob, dev):
+    """Inverse-design iterations on the three-port demultiplexer (512^2,
+    200 x 200 design square, wavelengths 1.50 / 1.55 / 1.60 um routed to the
+    three output guides): density -> filter/projection -> forward solve per
+    wavelength -> mode overlaps -> adjoint solves -> dF/drho -> Adam step.
+    The figure of merit is the sum of |overlap|^2 with a Gaussian profile
+    of each output guide; each solve runs at most 200 FGMRES steps."""
+    import numpy as np
+    import torch
+    from paper_2509_03622_gb300 import fdfd as F
+    from paper_2509_03622_gb300 import workloads as wl
+    from paper_2509_03622_gb300.autograd import fdfd_field, mode_overlap, last_stats
+    from paper_2509_03622_gb300.design import Adam, Design, density_to_eps
+    n, dx = 512, 1.55e-6 / 30
+    base, mask, src_x, yin, port_x, port_rows = wl.demux_layout(n)
+    ys, xs = np.nonzero(mask)
+    x0, y0, w, h = int(xs.min()), int(ys.min()), int(xs.max() - xs.min() + 1), int(ys.max() - ys.min() + 1)
+    J = np.zeros((n, n), np.complex64)
+    J[yin[0] - 4:yin[1] + 4, src_x] = 1.0
+    lams = [1.50e-6, 1.55e-6, 1.60e-6]
+    solvers = [F.Solver(torch.from_numpy(base).to(dev), dx, lam, npml=20) for lam in lams]
+    D = Design(solvers[0], x0, y0, w, h, radius=3.0, beta=8.0)
+    rho = torch.full((h, w), 0.5, dtype=torch.float32, device=dev)
+    opt = Adam(solvers[0], (h, w), lr=0.02)
+    Jd, bd = torch.from_numpy(J).to(dev), torch.from_numpy(base).to(dev)
+    modes = []
+    for (r0, r1) in port_rows:
+        yy = np.arange(r0 - 8, r1 + 8)
+        modes.append((int(r0 - 8), torch.from_numpy(np.exp(-((yy - (r0 + r1 - 1) / 2) / 4.0) ** 2)
+                                                    .astype(np.complex64)).to(dev)))
+    foms, relres, f0 = [], [], None
+    for it in range(iters + 1):  # the first iteration is the warm-up (set-up, graph capture)
+        if it == 1:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        r = rho.clone().requires_grad_(True)
+        eps = density_to_eps(D, r, bd)
+        fom = 0.0
+        for S, (my0, m) in zip(solvers, modes):
+            E = fdfd_field(S, eps, Jd, blob, restart=30, max_iters=200, tol=1e-6, precond=F.PRECOND_SCHWARZ)
+            c = mode_overlap(E, port_x, m, my0, dx)
+            fom = fom + c.abs() ** 2
+            relres.append(last_stats["forward"]["relres_true"])
+        fom.backward()
+        fv = float(fom.detach())
+        f0 = f0 or fv
+        foms.append(fv / f0)
+        opt.step(rho, r.grad, scale=1.0 / f0)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / max(iters, 1)
+    return {"grid": n, "design": [h, w], "wavelengths": len(lams), "iters": iters, "ms_per_iter": ms,
+            "fom_rel": foms, "max_forward_relres": max(relres),
+            "note": "per iteration: 3 forward + 3 adjoint Schwarz-NO FGMRES solves (<= 200 steps each), "
+                    "filter/projection, chain rule and Adam on the GPU; FoM relative to the first"}
+
+
 def oracle_preconditioner(args):
     """The oracle counterpart of the arm's preconditioner configuration."""
     from paper_2509_03622_gb300 import workloads as wl
@@ -266,6 +322,8 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--k-coarse", type=int, default=-1)
     ap.add_argument("--inner", type=int, default=0, help="NN-FGMRES steps per local solve (0 = one application)")
+    ap.add_argument("--design", type=int, default=0,
+                    help="also time this many inverse-design iterations (512^2 demultiplexer, 3 wavelengths)")
     ap.add_argument("--ritz-tol", type=float, default=0.0,
                     help="Rayleigh-Ritz truncation of the coarse space: keep |eta| >= this (0 = off)")
     ap.add_argument("--weights", default=None, help="weight blob (.npy); default the trained blob if present")
@@ -414,6 +472,8 @@ def main():
         line["stationary"] = {"iters": it_s, "ms_per_iter": ms_s / max(it_s, 1), "momentum": 0.5,
                               "value": job_rate(world, n * n, it_s, ms_s / 1e3), "unit": "Mcell-it/s",
                               "relres": rr_s, "note": "each iteration includes its FP64 true residual"}
+    if args.design > 0 and rank == 0 and precond == F.PRECOND_SCHWARZ:
+        line["design"] = design_bench(args.design, blob, dev)
     if args.tts and rank == 0:
         E.zero_()
         rc, st2 = S.solve(Jd, E, restart=30, max_iters=3000, tol=1e-6, precond=precond)

@@ -330,6 +330,46 @@ int  fdfd_coarse_export(fdfd_handle h, double* Q_host, double* Ndiag_host);
  * solver returns them.  FDFD_ENOSETUP without a Ritz step. */
 int  fdfd_coarse_ritz(fdfd_handle h, double* eta_host, double* H_host);
 
+/* ---- inverse design (Sec. 2.2: density-based optimisation with filtering,
+ * projection and Adam, gradients from fdfd_solve_adjoint + fdfd_grad_eps) -- */
+
+/* Design rectangle and its parameterisation: rho in [0, 1] on h x w cells at
+ * (x0, y0) of the grid; rho_f = cone filter of rho (weights max(0, R - |d|)
+ * over the offsets inside the rectangle, each output divided by its own
+ * weight sum); eps = eps_lo + P(rho_f) (eps_hi - eps_lo) with
+ * P(x) = (tanh(beta eta) + tanh(beta (x - eta))) /
+ *        (tanh(beta eta) + tanh(beta (1 - eta))). */
+typedef struct {
+  int   x0, y0, w, h;    /* rectangle in cells, inside the grid            */
+  float radius;          /* filter radius in cells, 0 < radius <= 16       */
+  float beta, eta;       /* projection sharpness (> 0), threshold (0, 1)   */
+  float eps_lo, eps_hi;  /* permittivity at rho = 0 and rho = 1            */
+} fdfd_design;
+
+/* Adam (Kingma and Ba) with bias correction, as an ascent. */
+typedef struct {
+  float lr, beta1, beta2, eps;  /* step, moment decays in [0, 1), eps > 0   */
+} fdfd_adam;
+
+/* rho [h][w] -> rho_f [h][w] (kept for fdfd_design_grad) and the design
+ * rectangle of eps [ny][nx] (the rest of eps untouched); device float32
+ * pointers; h supplies the grid and the stream.  Synchronous; FDFD_EINVAL
+ * for a rectangle outside the grid or parameters out of range. */
+int  fdfd_design_eps(fdfd_handle h, const fdfd_design* d, const float* rho, float* rho_f, float* eps);
+
+/* Chain rule from dF/deps (g_eps [ny][nx], e.g. from fdfd_grad_eps, summed
+ * over wavelengths) to dF/drho: g_rho = W^T (P'(rho_f) (eps_hi - eps_lo)
+ * g_eps) on the rectangle; work [h][w] is scratch.  Device float32. */
+int  fdfd_design_grad(fdfd_handle h, const fdfd_design* d, const float* rho_f, const float* g_eps, float* work,
+                      float* g_rho);
+
+/* One Adam ascent step (t = 1, 2, ... counts the steps) on theta [n] with the
+ * gradient g [n] times g_scale (e.g. 1 / F at the start, so that the
+ * gradient is well above eps), moments m, v [n] (zero before the first
+ * step); theta is clipped to [0, 1].  Device float32; synchronous. */
+int  fdfd_adam_step(fdfd_handle h, const fdfd_adam* a, int t, float g_scale, float* theta, const float* g,
+                    float* m, float* v, int n);
+
 /* Diagnostic: one tile GEMM on the tcgen05 path used by the neural operator
  * (no counterpart in the paper; validates the tensor-core operand encoding).
  * C[M][N] (float32, device) = A . B^T with A bf16 [M][K] (a_mn_major = 0)

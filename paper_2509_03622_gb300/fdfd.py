@@ -57,6 +57,15 @@ class Info(C.Structure):
                 ("graphs_ok", C.c_int), ("tuned_dfty_split", C.c_int), ("n_coarse_kept", C.c_int)]
 
 
+class DesignDesc(C.Structure):
+    _fields_ = [("x0", C.c_int), ("y0", C.c_int), ("w", C.c_int), ("h", C.c_int), ("radius", C.c_float),
+                ("beta", C.c_float), ("eta", C.c_float), ("eps_lo", C.c_float), ("eps_hi", C.c_float)]
+
+
+class AdamDesc(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * 18), ("launches", C.c_longlong * 18), ("total_launches", C.c_longlong)]
 
@@ -90,6 +99,9 @@ _SIGS = {
     "fdfd_nno_solve_noalloc": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "fdfd_coarse_export": ([_P, _P, _P], C.c_int),
     "fdfd_coarse_ritz": ([_P, _P, _P], C.c_int),
+    "fdfd_design_eps": ([_P, C.POINTER(DesignDesc), _P, _P, _P], C.c_int),
+    "fdfd_design_grad": ([_P, C.POINTER(DesignDesc), _P, _P, _P, _P], C.c_int),
+    "fdfd_adam_step": ([_P, C.POINTER(AdamDesc), C.c_int, C.c_float, _P, _P, _P, _P, C.c_int], C.c_int),
     "fdfd_profile_start": ([_P], C.c_int),
     "fdfd_selftest_gemm": ([_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "fdfd_selftest_wait": ([], C.c_int),

@@ -124,7 +124,7 @@ def demux_layout(n: int = 512, npml: int = NPML_DEFAULT, design: int = 200,
         eps[r[0]:r[1], d1:] = 12.25
     mask = np.zeros((n, n), dtype=bool)
     mask[d0:d1, d0:d1] = True
-    eps[mask] = g.uniform(2.1, 12.25, size=(design, design)).astype(np.float32)
+    eps[mask] = g.uniform(2.1, 12.25, size=design * design).astype(np.float32)
     src_x = npml + 20
     port_x = n - npml - 20
     return eps, mask, src_x, yin, port_x, port_rows
