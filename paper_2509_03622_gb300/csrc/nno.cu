@@ -700,13 +700,13 @@ template <bool LIFT, bool FP8, bool IN0 = false>
 __global__ void __launch_bounds__(G5_THREADS, 1)
 g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* bias, const bf16* Fx, bf16* T1,
           const float* qinv, int last, int total, int* err, LiftSrc lsrc) {
-  // LIFT: warps 0, 2, 3 build each unit's 4 rows of the 16 input channels
+  // LIFT: warps 2, 3, 12, 13 build each unit's 4 rows of the 16 input channels
   // (restriction, RMS normalisation by the window's rho) directly in the
   // stage as the lift's K-major A tile; Wb is the lift weights [32][16]; the
   // unit's MMA is the lift (K = 16), no activation, then block 0's DFT along x
   // (the lifted X itself is stored only if lsrc.store_x).
-  // IN0 (block 0 without a stored lifted activation): warps 2, 3 build the
-  // input channels as in LIFT and warp 0 copies the T3 rows; the residual
+  // IN0 (block 0 without a stored lifted activation): the same four warps
+  // build the input channels as in LIFT and warp 0 copies the T3 rows; the residual
   // path W0 X = (W0 L) I + W0 l_b takes Wb = W0 L [32][16] against the
   // inputs I (K = 16), W0 l_b being part of `bias`.
   // FP8: X holds E4M3 activations (x8_off layout).  The unit's input rows
