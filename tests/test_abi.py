@@ -68,3 +68,17 @@ def test_no_oracle_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_host_side_validation_of_the_extensions(lib):
+    """Algorithm 3's stationary solver, the Ritz export and the inverse-design
+    entry points refuse a missing handle or out-of-range arguments before any
+    device work."""
+    L = lib.lib
+    assert L.fdfd_schwarz_stationary(None, None, None, 5, 1e-6, 0.5, None, None) == lib.EINVAL
+    assert L.fdfd_coarse_ritz(None, None, None) == lib.EINVAL
+    d = lib.DesignDesc(0, 0, 8, 8, 2.0, 8.0, 0.5, 2.1, 12.25)
+    assert L.fdfd_design_eps(None, C.byref(d), None, None, None) == lib.EINVAL
+    assert L.fdfd_design_grad(None, C.byref(d), None, None, None, None) == lib.EINVAL
+    a = lib.AdamDesc(0.01, 0.9, 0.999, 1e-8)
+    assert L.fdfd_adam_step(None, C.byref(a), 1, 1.0, None, None, None, None, 4) == lib.EINVAL
