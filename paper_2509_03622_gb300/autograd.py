@@ -29,7 +29,8 @@ class _FieldSolve(torch.autograd.Function):
     def forward(ctx, eps, J, solver, weights, opts):
         solver.set_eps(eps.detach().contiguous())
         if opts.get("precond", F.PRECOND_SCHWARZ) == F.PRECOND_SCHWARZ:
-            solver.schwarz_setup(weights, k_coarse=opts.get("k_coarse", 0), inner_iters=opts.get("inner", 0))
+            solver.schwarz_setup(weights, k_coarse=opts.get("k_coarse", 0), inner_iters=opts.get("inner", 0),
+                                 ritz_tol=opts.get("ritz_tol", 0.0))
         E = torch.zeros(J.shape, dtype=torch.complex64, device=J.device)
         kw = {k: v for k, v in opts.items() if k in ("restart", "max_iters", "tol", "precond")}
         rc, st = solver.solve(J, E, **kw)
@@ -57,7 +58,7 @@ class _FieldSolve(torch.autograd.Function):
 def fdfd_field(solver: "F.Solver", eps: torch.Tensor, J: torch.Tensor, weights=None, **opts) -> torch.Tensor:
     """Field of the current density J in the permittivity eps (float32 CUDA
     tensor, may require grad).  opts: restart, max_iters, tol, precond,
-    k_coarse, inner (Schwarz set-up is redone for every new eps)."""
+    k_coarse, inner, ritz_tol (Schwarz set-up is redone for every new eps)."""
     return _FieldSolve.apply(eps, J, solver, weights, opts)
 
 
