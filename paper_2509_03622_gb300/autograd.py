@@ -65,3 +65,24 @@ def fdfd_field(solver: "F.Solver", eps: torch.Tensor, J: torch.Tensor, weights=N
 def mode_overlap(E: torch.Tensor, port_x: int, mode: torch.Tensor, y0: int, dx: float) -> torch.Tensor:
     """c = sum_port conj(m) E dx along the vertical line x = port_x."""
     return torch.sum(torch.conj(mode) * E[y0:y0 + mode.numel(), port_x]) * dx
+
+
+class FDFDSolve:
+    """Fields of one current density at several wavelengths, differentiable
+    in eps: one library handle per wavelength (created on the first call, on
+    eps's device), each solved by fdfd_field with the same options.
+
+        solve = FDFDSolve(dx, [1.50e-6, 1.55e-6, 1.60e-6], weights, tol=1e-6)
+        E1, E2, E3 = solve(eps, J)
+    """
+
+    def __init__(self, dx: float, wavelengths, weights=None, npml=20, **opts):
+        self.dx, self.wavelengths = dx, list(wavelengths)
+        self.weights, self.npml, self.opts = weights, npml, opts
+        self.solvers = None
+
+    def __call__(self, eps: torch.Tensor, J: torch.Tensor):
+        if self.solvers is None:
+            self.solvers = [F.Solver(eps.detach().contiguous(), self.dx, lam, npml=self.npml)
+                            for lam in self.wavelengths]
+        return [fdfd_field(S, eps, J, self.weights, **self.opts) for S in self.solvers]
