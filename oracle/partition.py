@@ -109,14 +109,23 @@ def traces(win: Windows, u: np.ndarray, eps: np.ndarray, dx: float, wavelength: 
     interface side of every window: [n_win][4][80] (zero on grid-edge sides)."""
     kd = kd_map(eps, dx, wavelength)
     g = np.zeros((win.n, SIDES, WIN), dtype=np.complex128)
-    for w in range(win.n):
-        for s in range(SIDES):
-            if not win.interface[w, s]:
-                continue
-            bx, by, ox, oy = win.side_cells(w, s)
-            ub = u[by, bx]
-            g[w, s] = u[oy, ox] - ub + 1j * kd[by, bx] * ub
+    bx, by, ox, oy, iface = _side_tables(win)
+    ub = u[by[iface], bx[iface]]
+    g[iface] = u[oy[iface], ox[iface]] - ub + 1j * kd[by[iface], bx[iface]] * ub
     return g
+
+
+def _side_tables(win: Windows):
+    """Boundary and ghost cells of every side of every window, [n_win][4][80]
+    each, and the interface mask (side_cells stacked; cached on the table)."""
+    if getattr(win, "_tables", None) is None:
+        cells = np.zeros((4, win.n, SIDES, WIN), dtype=np.int64)
+        for w in range(win.n):
+            for s in range(SIDES):
+                cells[:, w, s] = win.side_cells(w, s)
+        iface = np.broadcast_to(win.interface[:, :, None], (win.n, SIDES, WIN))
+        win._tables = (*cells, iface)
+    return win._tables
 
 
 def local_operator(win: Windows, w: int, A: sp.csr_matrix, eps: np.ndarray, dx: float,

@@ -9,7 +9,8 @@ equation A~ e = v from e = 0 (so every window starts with zero Robin data):
     e_w = M.solve(r_w, g = 0)                   (local solves)
     u   = sum_w R~_w^T e_w                      (assemble, restricted)
     e_bc = traces of u on every window's interface sides (minus g = 0)
-    z   = coarse solve of e_bc (Eq. 8),  u += sum_w R~_w^T sum_m z Phi
+    z   = coarse solve of e_bc (Galerkin form, or Eq. 8),
+    u  += sum_w R~_w^T sum_m z Phi
 Local solves are the neural operator (product semantics) or exact SuperLU
 solves of the local Robin problem (the ideal-preconditioner diagnostic).
 
@@ -29,7 +30,8 @@ from .coarse import CoarseSpace
 
 class Schwarz:
     def __init__(self, eps, dx, wavelength, npml, weights=None, k_coarse: int = 0,
-                 local: str = "nno", inner: int = 0, ritz_tol: float = 0.0):
+                 local: str = "nno", inner: int = 0, ritz_tol: float = 0.0,
+                 coarse_form: str = "galerkin"):
         """local = "nno": neural local solves -- one application of the
         network to (residual, Robin data) when inner = 0, else `inner` steps
         of NN-preconditioned FGMRES (Algorithm 1) on the window's Robin
@@ -56,7 +58,8 @@ class Schwarz:
         if k_coarse > 0:
             zero = np.zeros((self.win.n, WIN, WIN), dtype=np.complex128)
             self.coarse = CoarseSpace(self.win, self.eps, dx, wavelength, k_coarse,
-                                      lambda g: self.local_solve(zero, g), ritz_tol=ritz_tol)
+                                      lambda g: self.local_solve(zero, g), ritz_tol=ritz_tol,
+                                      form=coarse_form)
 
     def aux(self, w: int):
         x0, y0 = int(self.win.x0[w]), int(self.win.y0[w])

@@ -41,8 +41,66 @@ def test_gram_schmidt_orthonormal():
 def small_exact():
     n, dx = 192, LAM / 25
     eps = wl.rectangles_eps(n, n, npml=20, n_rect=10, seed=31)
-    S = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact")
+    S = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact", coarse_form="normal")
     return S
+
+
+@pytest.fixture(scope="module")
+def small_galerkin():
+    n, dx = 192, LAM / 25
+    eps = wl.rectangles_eps(n, n, npml=20, n_rect=10, seed=31)
+    return schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact")
+
+
+def test_galerkin_mismatch_orthogonal_to_trials(small_galerkin):
+    """The Galerkin correction of a random mismatch e leaves, on every
+    window's own slots, a mismatch with no component along any of that
+    window's trial vectors.  The new mismatch is measured through the fields:
+    the traces of the added basis fields minus the data Q z they were solved
+    with (a transposed, conjugated or mis-signed coarse matrix fails)."""
+    S = small_galerkin
+    cs = S.coarse
+    g = wl.rng(7)
+    e = g.standard_normal((S.win.n, 4, 80)) + 1j * g.standard_normal((S.win.n, 4, 80))
+    e[~S.win.interface] = 0.0
+    z = cs.solve(e)
+    tr = P.traces(S.win, cs.correction(z), S.eps, S.dx, S.wavelength)
+    Qz = np.einsum("wm,wmst->wst", z.reshape(S.win.n, cs.k), cs.Q)
+    left = (e + tr - Qz).reshape(S.win.n, -1)
+    proj = np.einsum("wmt,wt->wm", cs.Q.reshape(S.win.n, cs.k, -1).conj(), left)
+    assert np.max(np.abs(proj)) < 1e-9 * np.max(np.abs(e))
+    assert np.max(np.abs(left)) > 1e-3 * np.max(np.abs(e))  # not trivially zero
+
+
+def test_galerkin_recovers_a_mismatch_in_its_range(small_galerkin):
+    """A mismatch produced by coefficients z0 (e = -C z0) is removed exactly."""
+    cs = small_galerkin.coarse
+    g = wl.rng(8)
+    z0 = g.standard_normal(cs.C.shape[1]) + 1j * g.standard_normal(cs.C.shape[1])
+    z0[cs.dropped] = 0.0
+    assert np.allclose(cs.solve(-(cs.C @ z0)), z0, rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.slow
+def test_galerkin_two_level_fgmres_trend_table1():
+    """Trend of Table 1 for FGMRES(30) with the two-level sweep, exact local
+    solves, homogeneous medium at 24 cells per wavelength: from 4 x 4 to
+    8 x 8 windows the one-level count grows more than twofold while the
+    two-level count (Galerkin coarse equation, k = 36) stays nearly flat and
+    several times smaller."""
+    dx = LAM / 24
+    its = {}
+    for n in (256, 512):
+        eps = np.ones((n, n), np.float32)
+        b = fdfd.source_rhs(wl.point_source(n, n), dx, LAM)
+        for k in (0, 36):
+            S = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=k, local="exact")
+            _, info = krylov.fgmres(lambda v: S.A @ v, b, precond=S, restart=30, tol=1e-6, max_iters=200)
+            assert info["converged"]
+            its[n, k] = info["iters"]
+    assert its[512, 0] >= 2 * its[256, 0]
+    assert its[512, 36] <= its[256, 36] + 4 <= 14
+    assert 3 * its[512, 36] <= its[512, 0]
 
 
 def test_normal_equations_equal_lstsq(small_exact):
@@ -110,10 +168,23 @@ def ritz_pair():
     """The same layout and local solver without and with the Ritz step."""
     n, dx = 192, LAM / 25
     eps = wl.rectangles_eps(n, n, npml=20, n_rect=10, seed=31)
-    S0 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact")
-    S1 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact", ritz_tol=1e-12)
-    S3 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact", ritz_tol=0.3)
+    f = "normal"
+    S0 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact", coarse_form=f)
+    S1 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact", ritz_tol=1e-12, coarse_form=f)
+    S3 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact", ritz_tol=0.3, coarse_form=f)
     return S0, S1, S3
+
+
+def test_ritz_all_directions_keep_the_galerkin_correction():
+    """Galerkin form: the kept Ritz vectors span the trial space, so both the
+    trial and the test space are unchanged and so is the correction."""
+    n, dx = 192, LAM / 25
+    eps = wl.rectangles_eps(n, n, npml=20, n_rect=10, seed=31)
+    c0 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact").coarse
+    c1 = schwarz.Schwarz(eps, dx, LAM, 20, k_coarse=8, local="exact", ritz_tol=1e-12).coarse
+    e = wl.rng(9).standard_normal(c0.C.shape[0]) + 1j * wl.rng(10).standard_normal(c0.C.shape[0])
+    u0, u1 = c0.correction(c0.solve(e)), c1.correction(c1.solve(e))
+    assert np.linalg.norm(u1 - u0) / np.linalg.norm(u0) < 1e-8
 
 
 def test_ritz_all_directions_keep_the_correction(ritz_pair):
