@@ -169,7 +169,12 @@ int  fdfd_set_eps(fdfd_handle h, const float* eps_dev);
 /* Set up the neural local solver and, if k_coarse > 0, the coarse space of
  * Algorithm 3: pseudo-plane-wave Robin trials, Gram-Schmidt (FP64), the
  * homogeneous neural solves, their traces on the neighbours (B Q), the
- * normal matrix (Eq. 8) and its FP64 Cholesky factor.  Weights are copied. */
+ * Galerkin coarse matrix G = Q^H (BQ - Q) (FP64 blocks; the reading of
+ * Eq. 7-8 as the Rayleigh-Ritz projection of the interface operator), and
+ * its factorisation by block elimination over the window rows (each row's
+ * Schur complement inverted in FP32 by LU with partial pivoting; storage
+ * (ny/64) (nx/64 k)^2 complex64).  Weights are copied.  FDFD_ENUMERIC if a
+ * Schur complement is singular, FDFD_ENOMEM if the factors do not fit. */
 int  schwarz_setup(fdfd_handle h, const schwarz_desc* sd);
 
 void fdfd_destroy(fdfd_handle h);
@@ -288,22 +293,28 @@ int  fdfd_nno_solve(fdfd_handle h, const fdfd_c64* r_win, const fdfd_c64* g_win,
 
 /* fdfd_nno_solve for callers that cannot allocate device memory (the paper
  * has no counterpart: this is an interface convenience).  Such callers are,
- * for example, code that runs while a CUDA graph is being captured (a
- * cudaMalloc cannot be captured), code that must stay within a memory pool
- * it manages itself, or a latency-bound loop that cannot pay for an
- * allocation's implicit device-wide synchronisation.  Same arguments and
- * results as fdfd_nno_solve, but the neural operator's intermediates live in
- * one fixed device array inside the library (about 3.5 MB, held by every
- * GPU that loads the library until the process exits) instead of the
- * handle's workspace, and the call allocates nothing.
+ * for example, code that must stay within a device-memory budget that its
+ * own pool allocator hands out (a cudaMalloc would take memory promised to
+ * others), or a latency-bound loop that cannot pay for the device-wide
+ * synchronisation an allocation or free may cause.  Same arguments and
+ * results as fdfd_nno_solve (the same kernels, bit for bit), but the neural
+ * operator's intermediates live in one fixed device array inside the
+ * library (about 3.5 MB, held by every GPU that loads the library until the
+ * process exits) instead of the handle's workspace, and the call allocates
+ * nothing.
  *   - n must be <= 4 windows; larger n returns FDFD_EINVAL (with a message on
  *     stderr) and does nothing.
- *   - The first call on a device looks the array's device address up once;
- *     make that first call before any stream capture.
- *   - All calls share the one array: calls that overlap on the GPU (from
- *     several streams, threads or handles) race and corrupt each other's
- *     results.  Serialise them.
- *   - Requires schwarz_setup on h (FDFD_ENOSETUP otherwise); synchronous. */
+ *   - The first call on a device (and the first after that device's context
+ *     was replaced, e.g. by cudaDeviceReset) looks the array's device address
+ *     up; later calls reuse it.
+ *   - All calls share the one array, which keeps the last call's contents:
+ *     calls that overlap on the GPU (from several streams, threads or
+ *     handles) race and corrupt each other's results.  Serialise them.
+ *   - Requires schwarz_setup on h (FDFD_ENOSETUP otherwise).  Returns
+ *     FDFD_ETIMEOUT without launching anything once a neural pass of h has
+ *     given up on a bounded wait (as fdfd_nno_solve does).
+ *   - Synchronous: it reads the kernels' error flag back and waits for the
+ *     handle's stream. */
 int  fdfd_nno_solve_noalloc(fdfd_handle h, const fdfd_c64* r_win, const fdfd_c64* g_win,
                             const int* win_id, int n, fdfd_c64* e_win);
 
@@ -319,9 +330,22 @@ int  fdfd_local_apply(fdfd_handle h, const fdfd_c64* x_win, fdfd_c64* y_win, con
 int  fdfd_trace_extract(fdfd_handle h, const fdfd_c64* u, fdfd_c64* g);
 
 /* Copy the coarse set-up out for inspection (host pointers, may be NULL):
- * Q [n_win][k][4][80] complex128 (interleaved doubles) orthonormalised trials;
- * normal matrix diagonal blocks N_ww [n_win][k][k] complex128. */
-int  fdfd_coarse_export(fdfd_handle h, double* Q_host, double* Ndiag_host);
+ * Q [n_win][k][4][80] complex128 (interleaved doubles) orthonormalised trials
+ * (rotated by the kept Ritz vectors after a Ritz step); the Galerkin blocks
+ * G [n_win][9][k][k] complex128, G[i][j][p][q] = sum over window i's slots of
+ * conj(Q_i[p]) times the mismatch that basis vector q of window
+ * J = i + (j % 3 - 1, j / 3 - 1) leaves there (its field's traces minus, for
+ * J = i, its own data), zero where J lies outside the grid; a dropped unknown
+ * (zero trial vector) has a unit diagonal. */
+int  fdfd_coarse_export(fdfd_handle h, double* Q_host, double* G_host);
+
+/* The coarse solve alone (reading of Eq. 7 with the Rayleigh-Ritz step of
+ * Algorithm 3): for a boundary mismatch e_bc (device [n_win][4][80]
+ * complex64) returns z (device [n_win][k] complex64) with
+ * G z = -Q^H e_bc, by the block elimination over window rows that the
+ * preconditioner uses (FP32).  Synchronous.  FDFD_ENOSETUP without a coarse
+ * space. */
+int  fdfd_coarse_solve(fdfd_handle h, const fdfd_c64* ebc_dev, fdfd_c64* z_dev);
 
 /* Rayleigh-Ritz data of the coarse set-up (schwarz_desc.ritz_tol > 0), host
  * pointers, each may be NULL: eta_host [n_win][k] Ritz values and H_host

@@ -683,10 +683,16 @@ int fdfd_coarse_ritz(fdfd_handle h, double* eta_host, double* H_host) {
   return schwarz_ritz_export(h, eta_host, H_host);
 }
 
-int fdfd_coarse_export(fdfd_handle h, double* Q, double* Nd) {
+int fdfd_coarse_export(fdfd_handle h, double* Q, double* G) {
   if (!h) return FDFD_EINVAL;
   if (!h->sw) return FDFD_ENOSETUP;
-  return schwarz_export(h, Q, Nd);
+  return schwarz_export(h, Q, G);
+}
+
+int fdfd_coarse_solve(fdfd_handle h, const fdfd_c64* ebc, fdfd_c64* z) {
+  if (!h || !ebc || !z) return FDFD_EINVAL;
+  if (!h->sw) return FDFD_ENOSETUP;
+  return schwarz_coarse_solve(h, reinterpret_cast<const float2*>(ebc), reinterpret_cast<float2*>(z));
 }
 
 }  // extern "C"

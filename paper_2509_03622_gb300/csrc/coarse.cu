@@ -5,19 +5,33 @@
 // the local wavenumber, modified Gram-Schmidt in FP64, homogeneous neural
 // solves for each trial, the traces of the restricted basis fields on the
 // neighbours' boundaries minus the window's own data (C = BQ - Q, stored as
-// 9 neighbour blocks per window), the normal matrix C^H C (Eq. 8) and its
-// inverse (FP64 Gauss-Jordan; the matrix is Hermitian positive definite).
-// Optional Rayleigh-Ritz truncation (Algorithm 3 set-up: eta, u = eig(H);
-// Sec. 2.2: the slowly decaying modes above a threshold): per window the
-// Ritz matrix H = Q^H Y of the Robin-to-Robin map (Y: the data each basis
-// field hands to the neighbours, read on their sides facing the window),
-// its eigenpairs (one thread per window, eig.cuh), and Q, Phi and the
-// window's columns of C combined by the eigenvectors with |eta| >= ritz_tol;
-// the other directions become zero columns, pinned like dependent trials.
-// Apply: e_bc = traces of the one-level field, r_c = -C^H e_bc, z = N^-1 r_c,
-// u += sum_w R~_w^T sum_m z_{w,m} Phi_{w,m}.
+// 9 neighbour blocks per window).  Optional Rayleigh-Ritz truncation
+// (Algorithm 3 set-up: eta, u = eig(H); Sec. 2.2: the slowly decaying modes
+// above a threshold): per window the Ritz matrix H = Q^H Y of the
+// Robin-to-Robin map (Y: the data each basis field hands to the neighbours,
+// read on their sides facing the window), its eigenpairs (one thread per
+// window, eig.cuh), and Q, Phi and the window's columns of C combined by the
+// eigenvectors with |eta| >= ritz_tol; the other directions become zero
+// columns, pinned like dependent trials.
+//
+// Coarse equation (reading of Eq. 7 with the Rayleigh-Ritz step): the
+// Galerkin projection of the interface operator onto the trial space,
+//     G z = -Q^H e_bc,   G = Q^H C   (blocks G[i][j] = Q_i^H C[i][j]),
+// a 9-block stencil over the window grid.  Ordered by window rows it is
+// block tridiagonal, G = tridiag(L_b, D_b, U_b) with blocks of size
+// D = nwx k, and is factored once by block elimination over the rows:
+//     S_0 = D_0,   S_b = D_b - L_b S_{b-1}^-1 U_{b-1},
+// each S_b inverted explicitly (FP32 LU with partial pivoting, cuSOLVER, at
+// set-up; the block-sparse products L_b S^-1 U are this file's kernels).
+// Apply: e_bc = traces of the one-level field, r = -Q^H e_bc, a forward
+// sweep y_b = S_b^-1 (r_b - L_b y_{b-1}) and a backward sweep
+// z_b = y_b - S_b^-1 U_b z_{b+1} (dense GEMVs, HBM-bound), then
+// u += sum_w R~_w^T sum_m z_{w,m} Phi_{w,m}.  Storage grows as
+// nwy D^2 (8.6 GB at 4096^2, k = 64) instead of the (nwx nwy k)^2 of a
+// dense inverse.
 #include <math.h>
 #include <vector>
+#include <cusolverDn.h>
 #include "ctx.cuh"
 #include "nno.cuh"
 #include "local.cuh"
@@ -25,27 +39,24 @@
 #include "eig.cuh"
 
 struct CoarseData {
-  int k = 0, nc = 0;
+  int k = 0, nc = 0, nwx = 0, nwy = 0, D = 0;
   double2* Q = nullptr;      // [n_win][k][320]
   float2* Qf = nullptr;      // [k][n_win][320]
   float2* Phi = nullptr;     // [n_win][k][64*64] core of each basis field
-  double2* C = nullptr;      // [n_win][9][320][k]
-  double2* N = nullptr;      // [nc][nc]  -> inverse after set-up
-  double2* Nd = nullptr;     // [n_win][k][k] diagonal blocks of the normal matrix
-  double2* rc = nullptr;     // [nc]
-  double2* zc = nullptr;     // [nc]
+  double2* C = nullptr;      // [n_win][9][320][k]   (set-up only)
+  double2* G = nullptr;      // [n_win][9][k][k]     Galerkin blocks, FP64
+  float2* Gf = nullptr;      // [n_win][9][k][k]     FP32 copy used by the sweeps
+  float2* Sinv = nullptr;    // [nwy][D][D]          row-major S_b^-1
+  float2* rcf = nullptr;     // [nc] right-hand side -Q^H e_bc
+  float2* ycf = nullptr;     // [nc] forward sweep
+  float2* zcf = nullptr;     // [nc] coarse solution
+  float2* tcf = nullptr;     // [D]  row temporary
   float2* ebc = nullptr;     // [n_win][320]
   float2* tmp = nullptr;     // [n_win][6400] window fields during set-up
   int* dropped = nullptr;    // [nc]
   double2* eta = nullptr;    // [n_win][k] Ritz values (Ritz step only)
   double2* H = nullptr;      // [n_win][k][k] Ritz matrices (Ritz step only)
   int n_kept = 0;            // unknowns not dropped
-  // FP32 copies used by the per-iteration apply (the correction is part of a
-  // flexible preconditioner, and FP64 arithmetic is scarce on this GPU)
-  float2* Cf = nullptr;      // [n_win][9][320][k]
-  float2* Nf = nullptr;      // [nc][nc] inverse normal matrix
-  float2* rcf = nullptr;     // [nc]
-  float2* zcf = nullptr;     // [nc]
 };
 
 namespace {
@@ -188,116 +199,206 @@ __global__ void assemble_C_kernel(double2* C, const double2* Q, const float2* Ph
   }
 }
 
-// Normal-matrix block (w, w' = w + (ex, ey)): sum over windows i adjacent to both.
-__global__ void assemble_N_kernel(double2* N, double2* Nd, const double2* C, int k, int nwx, int nwy) {
-  const int w = blockIdx.x, e = blockIdx.y;
-  const int ex = e % 5 - 2, ey = e / 5 - 2;
-  const int aw = w % nwx, bw = w / nwx, aw2 = aw + ex, bw2 = bw + ey;
-  if (aw2 < 0 || aw2 >= nwx || bw2 < 0 || bw2 >= nwy) return;
-  const int w2 = bw2 * nwx + aw2;
-  const int nc = nwx * nwy * k;
+// Galerkin blocks G[i][j][p][q] = sum_slot conj(Q_i[p][slot]) C[i][j][slot][q]
+// (window i's test functions against the basis of J = i + offset j).
+// Unknowns with a zero trial vector (dropped) get a unit diagonal.
+__global__ void assemble_G_kernel(double2* __restrict__ G, const double2* __restrict__ Q,
+                                  const double2* __restrict__ C, int k) {
+  const int i = blockIdx.x, j = blockIdx.y;
+  const double2* Qi = Q + (size_t)i * k * 320;
+  const double2* Cij = C + ((size_t)i * 9 + j) * 320 * k;
+  double2* Gij = G + ((size_t)i * 9 + j) * k * k;
   for (int pq = threadIdx.x; pq < k * k; pq += blockDim.x) {
     const int p = pq / k, q = pq % k;
-    double sr = 0.0, si = 0.0;
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int ai = aw - dx, bi = bw - dy;            // w = i + (dx, dy)
-        if (ai < 0 || ai >= nwx || bi < 0 || bi >= nwy) continue;
-        const int dx2 = aw2 - ai, dy2 = bw2 - bi;        // w2 = i + (dx2, dy2)
-        if (dx2 < -1 || dx2 > 1 || dy2 < -1 || dy2 > 1) continue;
-        const int i = bi * nwx + ai;
-        const double2* c1 = C + (((size_t)i * 9 + (dy + 1) * 3 + dx + 1) * 320) * k;
-        const double2* c2 = C + (((size_t)i * 9 + (dy2 + 1) * 3 + dx2 + 1) * 320) * k;
-        for (int sl = 0; sl < 320; ++sl) {
-          const double2 a = c1[sl * k + p], b = c2[sl * k + q];  // conj(a) * b
-          sr += a.x * b.x + a.y * b.y;
-          si += a.x * b.y - a.y * b.x;
-        }
-      }
-    N[(size_t)(w * k + p) * nc + w2 * k + q] = make_double2(sr, si);
-    if (w2 == w) Nd[((size_t)w * k + p) * k + q] = make_double2(sr, si);
+    double sr = 0.0, si = 0.0, qn = 0.0;
+    for (int sl = 0; sl < 320; ++sl) {
+      const double2 a = Qi[(size_t)p * 320 + sl], c = Cij[(size_t)sl * k + q];  // conj(a) * c
+      sr += a.x * c.x + a.y * c.y;
+      si += a.x * c.y - a.y * c.x;
+      qn += a.x * a.x + a.y * a.y;
+    }
+    if (j == 4 && p == q && qn == 0.0) { sr = 1.0; si = 0.0; }
+    Gij[pq] = make_double2(sr, si);
   }
 }
 
-__global__ void dropped_kernel(double2* N, int* dropped, const double2* Q, int nc) {
+__global__ void dropped_kernel(int* dropped, const double2* Q, int nc) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const double2* q = Q + (size_t)c * 320;
   bool any = false;
   for (int t = 0; t < 320; ++t) any |= (q[t].x != 0.0 || q[t].y != 0.0);
   dropped[c] = !any;
-  if (!any) N[(size_t)c * nc + c] = make_double2(1.0, 0.0);
 }
 
-// Gauss-Jordan inversion in place (no pivoting; the matrix is HPD).
-__global__ void gj_row_kernel(double2* A, int n, int p, double2* prow) {
-  const double2 piv = A[(size_t)p * n + p];
-  const double den = piv.x * piv.x + piv.y * piv.y;
-  const double2 inv = make_double2(piv.x / den, -piv.y / den);
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const double2 a = (j == p) ? make_double2(1.0, 0.0) : A[(size_t)p * n + j];
-    const double2 r = zmul(a, inv);
-    A[(size_t)p * n + j] = r;
-    prow[j] = r;
+// Q [w][k][320] FP64 -> Qf [k][w][320] FP32 (after the Ritz rotation).
+__global__ void q_to_f32_kernel(float2* Qf, const double2* Q, int k, int n_win) {
+  const int w = blockIdx.x;
+  for (int e = threadIdx.x; e < k * 320; e += blockDim.x) {
+    const int m = e / 320, sl = e % 320;
+    const double2 v = Q[((size_t)w * k + m) * 320 + sl];
+    Qf[((size_t)m * n_win + w) * 320 + sl] = make_float2((float)v.x, (float)v.y);
   }
-}
-__global__ void gj_elim_kernel(double2* A, int n, int p, const double2* prow, double2* pcol) {
-  // pcol holds column p before elimination (copied by gj_col_kernel)
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / n), j = (int)(e % n);
-    if (i == p) continue;
-    const double2 f = pcol[i];
-    const double2 a = (j == p) ? make_double2(0.0, 0.0) : A[e];
-    A[e] = zsub(a, zmul(f, prow[j]));
-  }
-}
-__global__ void gj_col_kernel(const double2* A, int n, int p, double2* pcol) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) pcol[i] = A[(size_t)i * n + p];
 }
 
-// r_c[(w,m)] = -sum_{i adjacent to w} sum_slot conj(C[i][j(w)][slot][m]) e_bc[i][slot]
-// FP32 apply: r_c[w][m] = -sum C[i][d][sl][m]^H e_bc[i][sl] over the window and
-// its 8 neighbours (warp per basis vector m, lanes over the 9 x 320 terms)
-__global__ void __launch_bounds__(256) coarse_rhs32_kernel(float2* rc, const float2* C, const float2* ebc, int k,
-                                                           int nwx, int nwy) {
+// S (row-major D x D) = D_b: the blocks of window row b coupling windows
+// of the same row (offsets j = 3, 4, 5).
+__global__ void build_S_kernel(float2* __restrict__ S, const float2* __restrict__ Gf, int k, int nwx, int b) {
+  const int D = nwx * k;
+  const size_t n = (size_t)D * D;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / D), c = (int)(e % D);
+    const int a = r / k, p = r % k, a2 = c / k, q = c % k;
+    const int d = a2 - a;
+    float2 v = make_float2(0.f, 0.f);
+    if (d >= -1 && d <= 1) v = Gf[(((size_t)(b * nwx + a) * 9 + 4 + d) * k + p) * k + q];
+    S[e] = v;
+  }
+}
+
+// T = Sinv_{b-1} U_{b-1}: U couples window (a, b-1) to (a + d, b), offset
+// j = 7 + d.  T[r][(a2, q)] = sum_{a = a2-1..a2+1} sum_p Sinv[r][(a, p)]
+// U[(a, p)][(a2, q)].  Each thread: RT rows of one column.
+constexpr int RT = 4;
+__global__ void __launch_bounds__(256) schur_T_kernel(float2* __restrict__ T, const float2* __restrict__ Sinv,
+                                                      const float2* __restrict__ Gf, int k, int nwx, int b) {
+  const int D = nwx * k;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = blockIdx.y * RT;
+  if (c >= D) return;
+  const int a2 = c / k, q = c % k;
+  float2 acc[RT];
+#pragma unroll
+  for (int t = 0; t < RT; ++t) acc[t] = make_float2(0.f, 0.f);
+  for (int a = max(a2 - 1, 0); a <= min(a2 + 1, nwx - 1); ++a) {
+    const float2* Ub = Gf + ((size_t)((b - 1) * nwx + a) * 9 + 7 + (a2 - a)) * k * k + q;
+    for (int p = 0; p < k; ++p) {
+      const float2 u = __ldg(Ub + (size_t)p * k);
+#pragma unroll
+      for (int t = 0; t < RT; ++t) {
+        const int r = r0 + t;
+        if (r < D) acc[t] = cadd(acc[t], cmul(__ldg(Sinv + (size_t)r * D + a * k + p), u));
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < RT; ++t)
+    if (r0 + t < D) T[(size_t)(r0 + t) * D + c] = acc[t];
+}
+
+// S -= L_b T: L couples window (a, b) to (a + d, b - 1), offset j = 1 + d.
+// S[(a, p)][c] -= sum_{a3 = a-1..a+1} sum_p3 L[(a, p)][(a3, p3)] T[(a3, p3)][c].
+// Each thread: RT consecutive rows (which may straddle two windows) of one column.
+__global__ void __launch_bounds__(256) schur_update_kernel(float2* __restrict__ S, const float2* __restrict__ T,
+                                                           const float2* __restrict__ Gf, int k, int nwx, int b) {
+  const int D = nwx * k;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r0 = blockIdx.y * RT;
+  if (c >= D || r0 >= D) return;
+  const int alo = r0 / k, ahi = min(r0 + RT - 1, D - 1) / k;
+  float2 acc[RT];
+#pragma unroll
+  for (int t = 0; t < RT; ++t) acc[t] = make_float2(0.f, 0.f);
+  for (int a3 = max(alo - 1, 0); a3 <= min(ahi + 1, nwx - 1); ++a3) {
+    for (int p3 = 0; p3 < k; ++p3) {
+      const float2 tv = __ldg(T + (size_t)(a3 * k + p3) * D + c);
+#pragma unroll
+      for (int t = 0; t < RT; ++t) {
+        const int r = r0 + t;
+        if (r >= D) continue;
+        const int a = r / k, d = a3 - a;
+        if (d < -1 || d > 1) continue;
+        const float2 l = __ldg(Gf + (((size_t)(b * nwx + a) * 9 + 1 + d) * k + r % k) * k + p3);
+        acc[t] = cadd(acc[t], cmul(l, tv));
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < RT; ++t) {
+    if (r0 + t >= D) continue;
+    float2& d = S[(size_t)(r0 + t) * D + c];
+    d = make_float2(d.x - acc[t].x, d.y - acc[t].y);
+  }
+}
+
+__global__ void identity_kernel(float2* X, int D) {
+  const size_t n = (size_t)D * D;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    X[e] = make_float2((e / D == e % D) ? 1.f : 0.f, 0.f);
+}
+
+// r[w][m] = -sum_slot conj(Qf[m][w][slot]) e_bc[w][slot]  (warp per m)
+__global__ void __launch_bounds__(256) galerkin_rhs_kernel(float2* __restrict__ r, const float2* __restrict__ Qf,
+                                                           const float2* __restrict__ ebc, int k, int n_win) {
   const int w = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int aw = w % nwx, bw = w / nwx;
   for (int m = warp; m < k; m += blockDim.x / 32) {
+    const float2* q = Qf + ((size_t)m * n_win + w) * 320;
+    const float2* e = ebc + (size_t)w * 320;
     float sr = 0.f, si = 0.f;
-    for (int t = lane; t < 9 * 320; t += 32) {
-      const int d = t / 320, sl = t % 320, dy = d / 3 - 1, dx = d % 3 - 1;
-      const int ai = aw - dx, bi = bw - dy;
-      if (ai < 0 || ai >= nwx || bi < 0 || bi >= nwy) continue;
-      const int i = bi * nwx + ai;
-      const float2 a = C[(((size_t)i * 9 + d) * 320 + sl) * k + m];
-      const float2 e = ebc[(size_t)i * 320 + sl];
-      sr += a.x * e.x + a.y * e.y;
-      si += a.x * e.y - a.y * e.x;
+    for (int t = lane; t < 320; t += 32) {
+      const float2 a = q[t], b = e[t];
+      sr += a.x * b.x + a.y * b.y;
+      si += a.x * b.y - a.y * b.x;
     }
     for (int o = 16; o > 0; o >>= 1) {
       sr += __shfl_xor_sync(0xffffffffu, sr, o);
       si += __shfl_xor_sync(0xffffffffu, si, o);
     }
-    if (lane == 0) rc[w * k + m] = make_float2(-sr, -si);
+    if (lane == 0) r[(size_t)w * k + m] = make_float2(-sr, -si);
   }
 }
 
-// z = Ninv r_c in FP32 (one warp per row)
-__global__ void gemv32_kernel(float2* z, const float2* A, const float2* x, const int* dropped, int n) {
-  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
-  if (row >= n) return;
+// Row temporary of the sweeps (warp per entry (a, p) of window row b):
+//   forward  (jbase = 0): t = r_b - L_b y_{b-1}   (x = y of row b-1)
+//   backward (jbase = 6): t = U_b z_{b+1}          (x = z of row b+1, r = NULL)
+__global__ void __launch_bounds__(256) sweep_t_kernel(float2* __restrict__ t, const float2* __restrict__ r,
+                                                      const float2* __restrict__ x, const float2* __restrict__ Gf,
+                                                      int k, int nwx, int b, int jbase) {
+  const int D = nwx * k;
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= D) return;
+  const int a = row / k, p = row % k;
   float sr = 0.f, si = 0.f;
-  const float2* a = A + (size_t)row * n;
-  for (int j = lane; j < n; j += 32) {
-    if (dropped[j]) continue;
-    const float2 p = cmul(a[j], x[j]);
-    sr += p.x; si += p.y;
+  for (int a3 = max(a - 1, 0); a3 <= min(a + 1, nwx - 1); ++a3) {
+    const float2* g = Gf + (((size_t)(b * nwx + a) * 9 + jbase + 1 + (a3 - a)) * k + p) * k;
+    const float2* xv = x + (size_t)a3 * k;
+    for (int p3 = lane; p3 < k; p3 += 32) {
+      const float2 v = cmul(g[p3], xv[p3]);
+      sr += v.x; si += v.y;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     sr += __shfl_xor_sync(0xffffffffu, sr, o);
     si += __shfl_xor_sync(0xffffffffu, si, o);
   }
-  if (lane == 0) z[row] = dropped[row] ? make_float2(0.f, 0.f) : make_float2(sr, si);
+  if (lane == 0) t[row] = r ? make_float2(r[row].x - sr, r[row].y - si) : make_float2(sr, si);
+}
+
+// out = base + sgn * A t for a row-major D x D complex matrix A (warp per
+// row, two complex numbers per 16-byte load); base may be NULL.
+__global__ void __launch_bounds__(256) gemv_rows_kernel(float2* __restrict__ out, const float2* __restrict__ base,
+                                                        const float2* __restrict__ A, const float2* __restrict__ t,
+                                                        int D, float sgn) {
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= D) return;
+  const float4* a4 = reinterpret_cast<const float4*>(A + (size_t)row * D);
+  const float4* t4 = reinterpret_cast<const float4*>(t);
+  float sr = 0.f, si = 0.f;
+  const int n4 = D / 2;
+#pragma unroll 8
+  for (int j = lane; j < n4; j += 32) {
+    const float4 m = __ldcs(a4 + j), v = __ldg(t4 + j);
+    sr += m.x * v.x - m.y * v.y + m.z * v.z - m.w * v.w;
+    si += m.x * v.y + m.y * v.x + m.z * v.w + m.w * v.z;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) {
+    const float2 b0 = base ? base[row] : make_float2(0.f, 0.f);
+    out[row] = make_float2(b0.x + sgn * sr, b0.y + sgn * si);
+  }
 }
 
 // H[w][p][q] = sum over w's interface sides s of conj(Q_w[p][s]) . Y_w[q][s],
@@ -424,8 +525,8 @@ int ca(T** p, size_t n, size_t* bytes) {
 
 void coarse_free(CoarseData* c) {
   if (!c) return;
-  void* ptrs[] = {c->Q, c->Qf, c->Phi, c->C, c->N, c->Nd, c->rc, c->zc, c->ebc, c->tmp, c->dropped,
-                  c->Cf, c->Nf, c->rcf, c->zcf, c->eta, c->H};
+  void* ptrs[] = {c->Q, c->Qf, c->Phi, c->C, c->G, c->Gf, c->Sinv, c->rcf, c->ycf, c->zcf, c->tcf, c->ebc,
+                  c->tmp, c->dropped, c->eta, c->H};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete c;
 }
@@ -472,23 +573,82 @@ done:
   return rc;
 }
 
+
+// Block elimination over the window rows of G: S_b^-1 for every row b
+// (row-major, FP32).  cuSOLVER sees each row-major S as its transpose, so
+// getrf/getrs with the identity as right-hand side return inv(S^T) in
+// column-major order, which is inv(S) in row-major order.
+static int factor_rows(fdfd_ctx* h, CoarseData* c) {
+  const int k = c->k, nwx = c->nwx, nwy = c->nwy, D = c->D;
+  cudaStream_t s = h->stream;
+  float2 *S = nullptr, *T = nullptr;
+  int *ipiv = nullptr, *info = nullptr;
+  cuComplex* work = nullptr;
+  cusolverDnHandle_t sh = nullptr;
+  size_t tb = 0;
+  int rc = FDFD_OK, lwork = 0;
+  std::vector<int> hinfo(2 * nwy, 0);
+  const size_t DD = (size_t)D * D;
+  const dim3 tile((D + 255) / 256, (D + RT - 1) / RT);
+  if ((rc = ca(&S, DD, &tb)) || (rc = ca(&T, DD, &tb)) || (rc = ca(&ipiv, (size_t)D, &tb)) ||
+      (rc = ca(&info, (size_t)2 * nwy, &tb)))
+    goto done;
+  if (cusolverDnCreate(&sh) != CUSOLVER_STATUS_SUCCESS || cusolverDnSetStream(sh, s) != CUSOLVER_STATUS_SUCCESS ||
+      cusolverDnCgetrf_bufferSize(sh, D, D, reinterpret_cast<cuComplex*>(S), D, &lwork) != CUSOLVER_STATUS_SUCCESS) {
+    rc = FDFD_ECUDA;
+    goto done;
+  }
+  if ((rc = ca(&work, (size_t)(lwork > 0 ? lwork : 1), &tb))) goto done;
+  for (int b = 0; b < nwy; ++b) {
+    float2* Sinv_b = c->Sinv + (size_t)b * DD;
+    build_S_kernel<<<2048, 256, 0, s>>>(S, c->Gf, k, nwx, b);
+    if (b > 0) {
+      schur_T_kernel<<<tile, 256, 0, s>>>(T, c->Sinv + (size_t)(b - 1) * DD, c->Gf, k, nwx, b);
+      schur_update_kernel<<<tile, 256, 0, s>>>(S, T, c->Gf, k, nwx, b);
+    }
+    identity_kernel<<<2048, 256, 0, s>>>(Sinv_b, D);
+    if (cudaGetLastError() != cudaSuccess ||
+        cusolverDnCgetrf(sh, D, D, reinterpret_cast<cuComplex*>(S), D, work, ipiv, info + 2 * b) !=
+            CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnCgetrs(sh, CUBLAS_OP_N, D, D, reinterpret_cast<const cuComplex*>(S), D, ipiv,
+                         reinterpret_cast<cuComplex*>(Sinv_b), D, info + 2 * b + 1) != CUSOLVER_STATUS_SUCCESS) {
+      rc = FDFD_ECUDA;
+      goto done;
+    }
+  }
+  if (cudaMemcpyAsync(hinfo.data(), info, hinfo.size() * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    rc = FDFD_ECUDA;
+    goto done;
+  }
+  for (int v : hinfo)
+    if (v != 0) rc = FDFD_ENUMERIC;  // a singular Schur complement (or a bad argument)
+done:
+  cudaStreamSynchronize(s);
+  if (sh) cusolverDnDestroy(sh);
+  void* tmp[] = {S, T, ipiv, info, work};
+  for (void* p : tmp) if (p) cudaFree(p);
+  return rc;
+}
+
 int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, int k, double ritz_tol,
                  CoarseData** out, size_t* bytes) {
   const int nwx = h->nx / FDFD_CORE, nwy = h->ny / FDFD_CORE, n_win = nwx * nwy;
   const int nc = n_win * k;
-  if (k < 1 || k > 256 || (size_t)nc * nc * 16 > ((size_t)16 << 30)) return FDFD_EINVAL;
+  if (k < 1 || k > 256) return FDFD_EINVAL;
   if (!(ritz_tol >= 0.0) || (ritz_tol > 0.0 && k > EIG_KMAX)) return FDFD_EINVAL;
   CoarseData* c = new CoarseData();
-  c->k = k; c->nc = nc;
+  c->k = k; c->nc = nc; c->nwx = nwx; c->nwy = nwy; c->D = nwx * k;
+  const size_t DD = (size_t)c->D * c->D;
+  const size_t c_bytes = (size_t)n_win * 9 * 320 * k * sizeof(double2);
   int rc;
   if ((rc = ca(&c->Q, (size_t)nc * 320, bytes)) || (rc = ca(&c->Qf, (size_t)nc * 320, bytes)) ||
       (rc = ca(&c->Phi, (size_t)nc * 4096, bytes)) || (rc = ca(&c->C, (size_t)n_win * 9 * 320 * k, bytes)) ||
-      (rc = ca(&c->N, (size_t)nc * nc, bytes)) || (rc = ca(&c->Nd, (size_t)n_win * k * k, bytes)) ||
-      (rc = ca(&c->rc, (size_t)nc, bytes)) || (rc = ca(&c->zc, (size_t)nc, bytes)) ||
-      (rc = ca(&c->ebc, (size_t)n_win * 320, bytes)) || (rc = ca(&c->tmp, (size_t)n_win * 6400, bytes)) ||
-      (rc = ca(&c->dropped, (size_t)nc, bytes)) || (rc = ca(&c->Cf, (size_t)n_win * 9 * 320 * k, bytes)) ||
-      (rc = ca(&c->Nf, (size_t)nc * nc, bytes)) || (rc = ca(&c->rcf, (size_t)nc, bytes)) ||
-      (rc = ca(&c->zcf, (size_t)nc, bytes))) {
+      (rc = ca(&c->G, (size_t)n_win * 9 * k * k, bytes)) || (rc = ca(&c->Gf, (size_t)n_win * 9 * k * k, bytes)) ||
+      (rc = ca(&c->Sinv, (size_t)nwy * DD, bytes)) || (rc = ca(&c->rcf, (size_t)nc, bytes)) ||
+      (rc = ca(&c->ycf, (size_t)nc, bytes)) || (rc = ca(&c->zcf, (size_t)nc, bytes)) ||
+      (rc = ca(&c->tcf, (size_t)c->D, bytes)) || (rc = ca(&c->ebc, (size_t)n_win * 320, bytes)) ||
+      (rc = ca(&c->tmp, (size_t)n_win * 6400, bytes)) || (rc = ca(&c->dropped, (size_t)nc, bytes))) {
     coarse_free(c);
     return rc;
   }
@@ -518,22 +678,21 @@ int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, 
   if (rhs) { cudaStreamSynchronize(s); cudaFree(rhs); *bytes -= (size_t)n_win * 6400 * sizeof(float2); }
   assemble_C_kernel<<<dim3(n_win, 9), 256, 0, s>>>(c->C, c->Q, c->Phi, k, h->eps, h->k0dx, h->nx, h->ny, nwx, nwy);
   CKL();
-  if (ritz_tol > 0.0 && (rc = ritz_truncate(h, c, ritz_tol, bytes))) { coarse_free(c); return rc; }
-  if (cudaMemsetAsync(c->N, 0, (size_t)nc * nc * sizeof(double2), s) != cudaSuccess) { coarse_free(c); return FDFD_ECUDA; }
-  assemble_N_kernel<<<dim3(n_win, 25), 256, 0, s>>>(c->N, c->Nd, c->C, k, nwx, nwy);
-  CKL();
-  dropped_kernel<<<(nc + 255) / 256, 256, 0, s>>>(c->N, c->dropped, c->Q, nc);
-  CKL();
-  // Gauss-Jordan inverse (rc, zc reused as the pivot row / column buffers)
-  const int gb = 1024;
-  for (int p = 0; p < nc; ++p) {
-    gj_col_kernel<<<(nc + 255) / 256, 256, 0, s>>>(c->N, nc, p, c->zc);
-    gj_row_kernel<<<(nc + 255) / 256, 256, 0, s>>>(c->N, nc, p, c->rc);
-    gj_elim_kernel<<<gb, 256, 0, s>>>(c->N, nc, p, c->rc, c->zc);
+  if (ritz_tol > 0.0) {
+    if ((rc = ritz_truncate(h, c, ritz_tol, bytes))) { coarse_free(c); return rc; }
+    q_to_f32_kernel<<<n_win, 256, 0, s>>>(c->Qf, c->Q, k, n_win);  // rotated test functions
+    CKL();
   }
-  to_f32_kernel<<<1024, 256, 0, s>>>(c->Cf, c->C, (size_t)n_win * 9 * 320 * k);
-  to_f32_kernel<<<1024, 256, 0, s>>>(c->Nf, c->N, (size_t)nc * nc);
+  assemble_G_kernel<<<dim3(n_win, 9), 256, 0, s>>>(c->G, c->Q, c->C, k);
+  to_f32_kernel<<<1024, 256, 0, s>>>(c->Gf, c->G, (size_t)n_win * 9 * k * k);
+  dropped_kernel<<<(nc + 255) / 256, 256, 0, s>>>(c->dropped, c->Q, nc);
   CKL();
+  // C is a set-up temporary: the Galerkin blocks replace it
+  cudaStreamSynchronize(s);
+  cudaFree(c->C);
+  c->C = nullptr;
+  *bytes -= c_bytes;
+  if ((rc = factor_rows(h, c))) { coarse_free(c); return rc; }
   {
     std::vector<int> dr(nc);
     if (cudaMemcpyAsync(dr.data(), c->dropped, (size_t)nc * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -558,8 +717,37 @@ int coarse_ritz_export(fdfd_ctx* h, CoarseData* c, double* eta_host, double* H_h
   return FDFD_OK;
 }
 
+// Kernel launches of one coarse solve (right-hand side, both sweeps).
+static int solve_launches(const CoarseData* c) { return 1 + (2 * c->nwy - 1) + 2 * (c->nwy - 1); }
+
+// z = G^-1 r (rcf -> zcf): forward then backward sweep over the window rows.
+static int solve_rows(fdfd_ctx* h, CoarseData* c) {
+  const int D = c->D, k = c->k, nwx = c->nwx, nwy = c->nwy;
+  const size_t DD = (size_t)D * D;
+  const int grid = (D + 7) / 8;
+  cudaStream_t s = h->stream;
+  for (int b = 0; b < nwy; ++b) {
+    const float2* t = c->rcf + (size_t)b * D;
+    if (b > 0) {
+      sweep_t_kernel<<<grid, 256, 0, s>>>(c->tcf, c->rcf + (size_t)b * D, c->ycf + (size_t)(b - 1) * D, c->Gf, k,
+                                          nwx, b, 0);
+      t = c->tcf;
+    }
+    gemv_rows_kernel<<<grid, 256, 0, s>>>(c->ycf + (size_t)b * D, nullptr, c->Sinv + (size_t)b * DD, t, D, 1.f);
+  }
+  CK(cudaMemcpyAsync(c->zcf + (size_t)(nwy - 1) * D, c->ycf + (size_t)(nwy - 1) * D, (size_t)D * sizeof(float2),
+                     cudaMemcpyDeviceToDevice, s));
+  for (int b = nwy - 2; b >= 0; --b) {
+    sweep_t_kernel<<<grid, 256, 0, s>>>(c->tcf, nullptr, c->zcf + (size_t)(b + 1) * D, c->Gf, k, nwx, b, 6);
+    gemv_rows_kernel<<<grid, 256, 0, s>>>(c->zcf + (size_t)b * D, c->ycf + (size_t)b * D, c->Sinv + (size_t)b * DD,
+                                          c->tcf, D, -1.f);
+  }
+  CKL();
+  return FDFD_OK;
+}
+
 int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u, const float2* g_ref) {
-  const int nwx = h->nx / FDFD_CORE, nwy = h->ny / FDFD_CORE, n_win = nwx * nwy;
+  const int nwx = c->nwx, n_win = c->nwx * c->nwy;
   cudaStream_t s = h->stream;
   int rc;
   {
@@ -571,17 +759,31 @@ int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u, const float2* g_ref) {
       CKL();
     }
   }
-  ProfScope ps(h, 7, 3);
-  coarse_rhs32_kernel<<<n_win, 256, 0, s>>>(c->rcf, c->Cf, c->ebc, c->k, nwx, nwy);
-  gemv32_kernel<<<(c->nc + 7) / 8, 256, 0, s>>>(c->zcf, c->Nf, c->rcf, c->dropped, c->nc);
+  ProfScope ps(h, 7, solve_launches(c) + 1);
+  galerkin_rhs_kernel<<<n_win, 256, 0, s>>>(c->rcf, c->Qf, c->ebc, c->k, n_win);
+  CKL();
+  if ((rc = solve_rows(h, c))) return rc;
   correction_kernel<<<dim3(4096 / 256, n_win), 256, 0, s>>>(u, c->Phi, c->zcf, c->k, h->nx, nwx);
   CKL();
   return FDFD_OK;
 }
 
-int coarse_export(fdfd_ctx* h, CoarseData* c, double* Qh, double* Ndh) {
-  const int n_win = (h->nx / FDFD_CORE) * (h->ny / FDFD_CORE);
+int coarse_solve_mismatch(fdfd_ctx* h, CoarseData* c, const float2* ebc, float2* z) {
+  const int n_win = c->nwx * c->nwy;
+  cudaStream_t s = h->stream;
+  galerkin_rhs_kernel<<<n_win, 256, 0, s>>>(c->rcf, c->Qf, ebc, c->k, n_win);
+  CKL();
+  int rc;
+  if ((rc = solve_rows(h, c))) return rc;
+  CK(cudaMemcpyAsync(z, c->zcf, (size_t)c->nc * sizeof(float2), cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return FDFD_OK;
+}
+
+int coarse_export(fdfd_ctx* h, CoarseData* c, double* Qh, double* Gh) {
+  const int n_win = c->nwx * c->nwy;
+  (void)h;
   if (Qh) CK(cudaMemcpy(Qh, c->Q, (size_t)c->nc * 320 * sizeof(double2), cudaMemcpyDeviceToHost));
-  if (Ndh) CK(cudaMemcpy(Ndh, c->Nd, (size_t)n_win * c->k * c->k * sizeof(double2), cudaMemcpyDeviceToHost));
+  if (Gh) CK(cudaMemcpy(Gh, c->G, (size_t)n_win * 9 * c->k * c->k * sizeof(double2), cudaMemcpyDeviceToHost));
   return FDFD_OK;
 }

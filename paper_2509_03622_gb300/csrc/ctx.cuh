@@ -89,8 +89,10 @@ int schwarz_stationary_update(fdfd_ctx* h, float2* u, float2* g, float2* g_new, 
 int schwarz_error(fdfd_ctx* h);
 // Set that flag from the host (failure injection for tests).
 int schwarz_mark_failed(fdfd_ctx* h);
-int schwarz_export(fdfd_ctx* h, double* Q, double* Nd);
+int schwarz_export(fdfd_ctx* h, double* Q, double* G);
+int schwarz_coarse_solve(fdfd_ctx* h, const float2* ebc, float2* z);
 int schwarz_ritz_export(fdfd_ctx* h, double* eta, double* H);
 struct NnoWeights;
 const NnoWeights* schwarz_weights(fdfd_ctx* h);  // nullptr before schwarz_setup
 int schwarz_info(fdfd_ctx* h, fdfd_info* info);
+int schwarz_dfty_variant(fdfd_ctx* h);  // the DFT-y GEMM variant autotuned at set-up

@@ -11,7 +11,8 @@ int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, 
 int coarse_kept(CoarseData* c);
 int coarse_ritz_export(fdfd_ctx* h, CoarseData* c, double* eta_host, double* H_host);
 int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u, const float2* g_ref = nullptr);
-int coarse_export(fdfd_ctx* h, CoarseData* c, double* Qh, double* Ndh);
+int coarse_export(fdfd_ctx* h, CoarseData* c, double* Qh, double* Gh);
+int coarse_solve_mismatch(fdfd_ctx* h, CoarseData* c, const float2* ebc, float2* z);
 
 struct SchwarzData {
   int k = 0, n_win = 0, nwx = 0, precision = 0, inner = 0;
@@ -238,6 +239,8 @@ const NnoWeights* schwarz_weights(fdfd_ctx* h) { return (h && h->sw) ? &h->sw->W
 
 int schwarz_inner_iters(fdfd_ctx* h) { return (h && h->sw) ? h->sw->inner : 0; }
 
+int schwarz_dfty_variant(fdfd_ctx* h) { return (h && h->sw) ? h->sw->work.g2_split : 0; }
+
 // Coarse correction of a one-level sweep result z (no-op without a coarse space).
 int schwarz_coarse(fdfd_ctx* h, float2* z) {
   if (!h->sw || !h->sw->coarse) return FDFD_OK;
@@ -249,9 +252,14 @@ int schwarz_ritz_export(fdfd_ctx* h, double* eta, double* H) {
   return coarse_ritz_export(h, h->sw->coarse, eta, H);
 }
 
-int schwarz_export(fdfd_ctx* h, double* Q, double* Nd) {
+int schwarz_export(fdfd_ctx* h, double* Q, double* G) {
   if (!h->sw->coarse) return FDFD_ENOSETUP;
-  return coarse_export(h, h->sw->coarse, Q, Nd);
+  return coarse_export(h, h->sw->coarse, Q, G);
+}
+
+int schwarz_coarse_solve(fdfd_ctx* h, const float2* ebc, float2* z) {
+  if (!h->sw->coarse) return FDFD_ENOSETUP;
+  return coarse_solve_mismatch(h, h->sw->coarse, ebc, z);
 }
 
 int schwarz_info(fdfd_ctx* h, fdfd_info* info) {

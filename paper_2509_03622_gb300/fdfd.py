@@ -98,6 +98,7 @@ _SIGS = {
     "fdfd_batch_destroy": ([_P], None),
     "fdfd_nno_solve_noalloc": ([_P, _P, _P, _P, C.c_int, _P], C.c_int),
     "fdfd_coarse_export": ([_P, _P, _P], C.c_int),
+    "fdfd_coarse_solve": ([_P, _P, _P], C.c_int),
     "fdfd_coarse_ritz": ([_P, _P, _P], C.c_int),
     "fdfd_design_eps": ([_P, C.POINTER(DesignDesc), _P, _P, _P], C.c_int),
     "fdfd_design_grad": ([_P, C.POINTER(DesignDesc), _P, _P, _P, _P], C.c_int),
@@ -289,9 +290,14 @@ class Solver:
         inf = self.info()
         nw, k = inf["n_win"], inf["k_coarse"]
         Q = np.zeros((nw, k, 4, 80, 2), dtype=np.float64)
-        Nd = np.zeros((nw, k, k, 2), dtype=np.float64)
-        _check(lib.fdfd_coarse_export(self.h, Q.ctypes.data, Nd.ctypes.data), "fdfd_coarse_export")
-        return Q[..., 0] + 1j * Q[..., 1], Nd[..., 0] + 1j * Nd[..., 1]
+        G = np.zeros((nw, 9, k, k, 2), dtype=np.float64)
+        _check(lib.fdfd_coarse_export(self.h, Q.ctypes.data, G.ctypes.data), "fdfd_coarse_export")
+        return Q[..., 0] + 1j * Q[..., 1], G[..., 0] + 1j * G[..., 1]
+
+    def coarse_solve(self, ebc, z):
+        """z = G^-1 (-Q^H ebc) for device tensors ebc [n_win][4][80] and
+        z [n_win][k] (complex64)."""
+        _check(lib.fdfd_coarse_solve(self.h, _ptr(ebc), _ptr(z)), "fdfd_coarse_solve")
 
 
     def coarse_ritz(self):

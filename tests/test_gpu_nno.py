@@ -96,15 +96,22 @@ def test_precond_apply_matches_oracle(F, k):
     err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
     assert err < BF16_TOL, err
     if k:
-        Q, Nd = S.coarse_export()
+        Q, G = S.coarse_export()
         assert np.max(np.abs(Q - O.coarse.Q)) < 1e-9
-        nd_ref = np.stack([O.coarse.N[i * k:(i + 1) * k, i * k:(i + 1) * k] for i in range(16)])
-        drop = O.coarse.dropped.reshape(16, k)
+        # Galerkin blocks G[i][j] vs the oracle's dense G at (window i, window J = i + offset j)
+        got, ref = [], []
         for i in range(16):
-            for m in range(k):
-                if drop[i, m]:
-                    nd_ref[i, m, m] = 0.0
-        assert np.linalg.norm(Nd - nd_ref) / np.linalg.norm(nd_ref) < 2 * BF16_TOL
+            a, b = i % 4, i // 4
+            for j in range(9):
+                a2, b2 = a + j % 3 - 1, b + j // 3 - 1
+                if 0 <= a2 < 4 and 0 <= b2 < 4:
+                    J = b2 * 4 + a2
+                    got.append(G[i, j])
+                    ref.append(O.coarse.G[i * k:(i + 1) * k, J * k:(J + 1) * k])
+                else:
+                    assert not np.any(G[i, j])
+        got, ref = np.stack(got), np.stack(ref)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2 * BF16_TOL
 
 
 def test_precond_is_positively_homogeneous(F):
