@@ -331,11 +331,21 @@ int persistent_grid(const void* kern, int threads, size_t smem, uint32_t tcols) 
   return nsm * per_sm;
 }
 
+// Index of the current device for per-device one-time set-up: a kernel's
+// dynamic-shared-memory attribute is a property of each device.
+constexpr int MAX_DEV = 64;
+inline int cur_dev() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MAX_DEV) d = 0;
+  return d;
+}
+
 template <int BN, int K, bool AMN, class Op, int KS = 1>
 int launch_gemm(const Op& op, int tiles, int batches, int* err, cudaStream_t s) {
   typedef GemmCfg<BN, K, AMN, Op, KS> Cfg;
   auto kern = gemm_kernel<BN, K, AMN, Op, KS>;
-  static int grid_cap = 0;
+  static int grid_caps[MAX_DEV] = {};
+  int& grid_cap = grid_caps[cur_dev()];
   if (grid_cap == 0) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess)
       return FDFD_ECUDA;
@@ -1821,7 +1831,8 @@ __global__ void absmax_kernel(const bf16* X, size_t n_elem, unsigned* out) {
 
 // Spectral mixing of all n windows into the window-major layout G4 reads.
 int launch_g3(NnoWork* k, const bf16* R, int n, cudaStream_t s) {
-  static int g3_cap = 0;
+  static int g3_caps[MAX_DEV] = {};
+  int& g3_cap = g3_caps[cur_dev()];
   if (!g3_cap) {
     CK(cudaFuncSetAttribute(g3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G3_SMEM));
     g3_cap = persistent_grid((const void*)g3_kernel, G3_THREADS, G3_SMEM, 512);
@@ -1928,7 +1939,9 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     rho_kernel<<<n, 256, 0, s>>>(in, g, k->rho);
     CKL();
   }
-  static int g5_cap = 0, g5f_cap = 0;
+  static int g5_caps[MAX_DEV] = {}, g5f_caps[MAX_DEV] = {};
+  const int dev = cur_dev();
+  int &g5_cap = g5_caps[dev], &g5f_cap = g5f_caps[dev];
   if (!g5_cap) {
     CK(cudaFuncSetAttribute(g5_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)G5L<false>::SMEM));
@@ -1999,7 +2012,8 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     if ((rc = record(bl + 1))) return rc;
   }
   {
-    static int pj_cap = 0;
+    static int pj_caps[MAX_DEV] = {};
+    int& pj_cap = pj_caps[cur_dev()];
     if (!pj_cap) {
       CK(cudaFuncSetAttribute(proj_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PJ_SMEM));
       CK(cudaFuncSetAttribute(proj_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PJ_SMEM));

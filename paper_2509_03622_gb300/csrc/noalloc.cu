@@ -1,16 +1,19 @@
 // fdfd_nno_solve_noalloc: the batched neural local solve of fdfd_nno_solve
-// for callers that must not allocate device memory, e.g. code running while
-// a CUDA graph is being captured (cudaMalloc is not capturable), code that
-// owns a fixed memory budget through its own pool allocator, or a real-time
-// loop that cannot afford an allocation's device-wide synchronisation.
+// for callers that must not allocate device memory: code that runs inside a
+// fixed device-memory budget handed out by its own pool allocator (a
+// cudaMalloc there would take memory the pool has already promised to
+// others), or a latency-bound loop that cannot afford the device-wide
+// synchronisation an allocation or free may cause.  The call is synchronous:
+// it copies the kernels' error flag back and waits for the stream.
 //
 // Instead of the handle's per-call workspace, the intermediates of the
 // neural operator live in one file-scope device array of fixed size
 // (NOALLOC_MAX_WINDOWS windows, about 3.5 MB), which every GPU that loads
 // the library holds until the process exits.  In host code the array's name
-// is only a host-side stand-in, so its device address is looked up once per
-// device with cudaGetSymbolAddress (on the first call made on that device)
-// and then passed to the kernels.
+// is only a host-side stand-in, so its device address is looked up with
+// cudaGetSymbolAddress, with the device current, the first time a call runs
+// on a device (and again if that device's context has been replaced, e.g.
+// after cudaDeviceReset), and then passed to the kernels.
 #include <mutex>
 #include "ctx.cuh"
 #include "nno.cuh"
@@ -34,17 +37,44 @@ static __device__ __align__(256) unsigned char g_nno_scratch[SCRATCH_BYTES];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 unsigned char* g_scratch_dev[MAX_DEVICES] = {};
+void* g_scratch_ctx[MAX_DEVICES] = {};  // context the cached address belongs to
 
-// Device address of the scratch array on the current device (looked up once).
+// The driver's cuCtxGetCurrent, looked up through the runtime (the library
+// keeps no load-time dependency on the driver library).
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  }
+  return fn;
+}
+
+void* current_ctx() {
+  void* ctx = nullptr;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get || get(&ctx) != 0) return nullptr;
+  return ctx;
+}
+
+// Device address of the scratch array on the current device and context.
 int scratch_address(unsigned char** out) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= MAX_DEVICES) return FDFD_EINVAL;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_dev[dev]) {
+  void* ctx = current_ctx();
+  if (!g_scratch_dev[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
-    CK(cudaGetSymbolAddress(&p, g_nno_scratch));
+    CK(cudaGetSymbolAddress(&p, g_nno_scratch));  // also makes the device's context current
     g_scratch_dev[dev] = static_cast<unsigned char*>(p);
+    g_scratch_ctx[dev] = current_ctx();
   }
   *out = g_scratch_dev[dev];
   return FDFD_OK;
@@ -62,12 +92,16 @@ extern "C" int fdfd_nno_solve_noalloc(fdfd_handle h, const fdfd_c64* r_win, cons
   }
   const NnoWeights* W = schwarz_weights(h);
   if (!W) return FDFD_ENOSETUP;
+  // a neural pass of this handle already gave up on a bounded wait: the
+  // same sticky failure fdfd_nno_solve reports
+  int rc = schwarz_error(h);
+  if (rc) return rc;
   if (n == 0) return FDFD_OK;
   unsigned char* base = nullptr;
-  int rc = scratch_address(&base);
-  if (rc) return rc;
+  if ((rc = scratch_address(&base))) return rc;
   NnoWork k;
   k.cap = NOALLOC_MAX_WINDOWS;
+  k.g2_split = schwarz_dfty_variant(h);  // the same kernels as the handle's own passes
   size_t off = 0;
   k.X = reinterpret_cast<bf16*>(base + off); off += B_X;
   k.T1 = reinterpret_cast<bf16*>(base + off); off += B_T1;
