@@ -24,13 +24,23 @@ from . import fdfd as F
 last_stats = {"forward": None, "adjoint": None}
 
 
+def _setup(solver, eps, weights, opts):
+    """Load eps into the handle and redo its Schwarz set-up; every set-up
+    bumps the handle's version so that a pending backward can tell whether
+    the handle still holds the operator and preconditioner of its forward."""
+    solver.set_eps(eps)
+    if opts.get("precond", F.PRECOND_SCHWARZ) == F.PRECOND_SCHWARZ:
+        solver.schwarz_setup(weights, k_coarse=opts.get("k_coarse", 0), inner_iters=opts.get("inner", 0),
+                             ritz_tol=opts.get("ritz_tol", 0.0))
+    solver._setup_version = getattr(solver, "_setup_version", 0) + 1
+    return solver._setup_version
+
+
 class _FieldSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, eps, J, solver, weights, opts):
-        solver.set_eps(eps.detach().contiguous())
-        if opts.get("precond", F.PRECOND_SCHWARZ) == F.PRECOND_SCHWARZ:
-            solver.schwarz_setup(weights, k_coarse=opts.get("k_coarse", 0), inner_iters=opts.get("inner", 0),
-                                 ritz_tol=opts.get("ritz_tol", 0.0))
+        eps_saved = eps.detach().contiguous().clone()
+        version = _setup(solver, eps_saved, weights, opts)
         E = torch.zeros(J.shape, dtype=torch.complex64, device=J.device)
         kw = {k: v for k, v in opts.items() if k in ("restart", "max_iters", "tol", "precond")}
         rc, st = solver.solve(J, E, **kw)
@@ -38,20 +48,26 @@ class _FieldSolve(torch.autograd.Function):
         if rc != F.OK:
             warnings.warn(f"forward solve: {F.status_string(rc)} (relres {st['relres_true']:.2e})")
         ctx.solver, ctx.kw, ctx.stats = solver, kw, st
-        ctx.save_for_backward(E)
+        ctx.weights, ctx.opts, ctx.version = weights, opts, version
+        ctx.save_for_backward(E, eps_saved)
         return E
 
     @staticmethod
     def backward(ctx, grad_E):
-        (E,) = ctx.saved_tensors
+        E, eps_saved = ctx.saved_tensors
+        S = ctx.solver
+        # The adjoint needs A~(eps) of this forward solve: if the handle was
+        # set up again since (another fdfd_field call on it), restore it.
+        if getattr(S, "_setup_version", None) != ctx.version:
+            ctx.version = _setup(S, eps_saved, ctx.weights, ctx.opts)
         g = (grad_E.conj() * 0.5).to(torch.complex64).contiguous()
         lam = torch.zeros_like(E)
-        rc, st = ctx.solver.solve_adjoint(g, lam, **ctx.kw)
+        rc, st = S.solve_adjoint(g, lam, **ctx.kw)
         last_stats["adjoint"] = st
         if rc != F.OK:
             warnings.warn(f"adjoint solve: {F.status_string(rc)} (relres {st['relres_true']:.2e})")
         grad = torch.empty(E.shape, dtype=torch.float32, device=E.device)
-        ctx.solver.grad_eps(E, lam, grad)
+        S.grad_eps(E, lam, grad)
         return grad, None, None, None, None
 
 
@@ -80,9 +96,28 @@ class FDFDSolve:
         self.dx, self.wavelengths = dx, list(wavelengths)
         self.weights, self.npml, self.opts = weights, npml, opts
         self.solvers = None
+        self._key = None
 
     def __call__(self, eps: torch.Tensor, J: torch.Tensor):
+        if eps.dim() != 2 or J.shape != eps.shape:
+            raise ValueError("eps must be 2D and J of the same shape")
+        key = (tuple(eps.shape), eps.device)
+        if self.solvers is not None and key != self._key:
+            self.close()  # another grid or device: new handles
         if self.solvers is None:
             self.solvers = [F.Solver(eps.detach().contiguous(), self.dx, lam, npml=self.npml)
                             for lam in self.wavelengths]
+            self._key = key
         return [fdfd_field(S, eps, J, self.weights, **self.opts) for S in self.solvers]
+
+    def close(self):
+        """Free the per-wavelength handles (they are recreated on the next call)."""
+        for S in self.solvers or []:
+            S.close()
+        self.solvers, self._key = None, None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
