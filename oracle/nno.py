@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-The plain form of the paper's modified FNO (the modulation path and the
-low-rank parameterisation of R are not part of this build):
+The paper's modified FNO; without the optional parts below it is the plain
+form:
     h0 = Lift x                                  (1x1, 15 -> 32)
     h_{b+1} = sigma( F^-1[ R_b . F[h_b] ] + W_b h_b + beta_b ),  b = 0..3
     out = P2 sigma(P1 h4 + p1) + p2              (32 -> 128 -> 2: Re, Im)
@@ -24,9 +24,27 @@ traces" plus the PML maps of Methods):
 rho^2 = (sum |r|^2 + sum |g|^2) / 6400 makes the solve 1-homogeneous:
 e = rho * (out_re + j out_im), and e = 0 when rho = 0.
 
+Modified FNO (Sec. 2.1, Fig. 2), both parts optional (readings: the paper
+leaves the layer sizes to its supplement):
+* modulation path: the five auxiliary channels (0 and 11..14, the
+  permittivity and PML maps) of the window go through a 3 x 3 convolution
+  with stride 2 and no padding (80 -> 39, 5 -> 16 channels), leaky-ReLU,
+  average pooling over 13 x 13 tiles (39 -> 3) and a fully connected layer
+  (144 -> 4 x 32 x 16) giving a real modulation tensor mod[b][ky][kx]; block
+  b uses R*_b = R_b (1 + mod_b) element-wise (broadcast over the channel
+  axes), i.e. it modulates the linearly transformed retained modes.  The
+  residual form 1 + mod reduces to the plain FNO when the fully connected
+  layer outputs zero.  mod depends on the auxiliary inputs only, not on the
+  residual, so the solve stays 1-homogeneous;
+* low-rank R: R_b[o][i][q] = sum_r theta_b[o][i][r] V_b[r][q] (q the 512
+  retained modes): a linear layer V_b expands the rank-r tensor theta_b.
+
 Parity: the FFT convolution is pinned in tests/test_oracle_nno.py by a
 brute-force DFT on the retained modes, by the projector property of the
-mode truncation, and by the reduction to a pointwise map when R = 0.
+mode truncation, and by the reduction to a pointwise map when R = 0; the
+modified FNO by its reduction to the plain one (zero modulation; rank 512
+with V the identity), the closed-form modulation of constant auxiliary
+inputs, and positive homogeneity with the modulation on.
 """
 from __future__ import annotations
 
@@ -62,12 +80,52 @@ def pointwise(Wm: np.ndarray, b: np.ndarray, h: np.ndarray) -> np.ndarray:
     return np.einsum("oi,iyx->oyx", Wm, h) + b[:, None, None]
 
 
+MOD_AUX = (0, 11, 12, 13, 14)   # auxiliary input channels of the modulation path
+MOD_CH = 16                     # convolution channels
+MOD_OUT = 39                    # (80 - 3) / 2 + 1
+MOD_POOL = 3                    # pooled grid (13 x 13 tiles)
+
+
+def modulation(x: np.ndarray, w: dict, blocks: int = 4) -> np.ndarray:
+    """mod[b][ky][kx] of one window from its auxiliary channels: 3 x 3
+    convolution (stride 2, no padding), leaky-ReLU, 13 x 13 average pooling,
+    fully connected layer."""
+    a = np.asarray(x, dtype=np.float64)[list(MOD_AUX)]
+    cw = w["mod_conv_w"].astype(np.float64)      # [16][5][3][3]
+    cb = w["mod_conv_b"].astype(np.float64)      # [16]
+    c = np.zeros((MOD_CH, MOD_OUT, MOD_OUT))
+    for o in range(MOD_CH):
+        acc = np.full((MOD_OUT, MOD_OUT), cb[o])
+        for i in range(len(MOD_AUX)):
+            for dy in range(3):
+                for dx in range(3):
+                    acc = acc + cw[o, i, dy, dx] * a[i, dy:dy + 2 * MOD_OUT - 1:2, dx:dx + 2 * MOD_OUT - 1:2]
+        c[o] = acc
+    t = MOD_OUT // MOD_POOL
+    p = leaky(c).reshape(MOD_CH, MOD_POOL, t, MOD_POOL, t).mean(axis=(2, 4))
+    m = w["mod_fc_w"].astype(np.float64) @ p.ravel() + w["mod_fc_b"].astype(np.float64)
+    return m.reshape(blocks, MY, MX)
+
+
+def spectral_weights(w: dict, b: int) -> np.ndarray:
+    """R_b [32][32][32][16] complex: stored, or expanded from its rank-r
+    factors theta_b [32][32][r] and V_b [r][32][16]."""
+    if f"R{b}_theta_re" in w:
+        th = w[f"R{b}_theta_re"].astype(np.float64) + 1j * w[f"R{b}_theta_im"].astype(np.float64)
+        V = w[f"R{b}_V_re"].astype(np.float64) + 1j * w[f"R{b}_V_im"].astype(np.float64)
+        return np.einsum("oir,ryx->oiyx", th, V)
+    return w[f"R{b}_re"].astype(np.float64) + 1j * w[f"R{b}_im"].astype(np.float64)
+
+
 def forward(x: np.ndarray, w: dict, blocks: int = 4) -> np.ndarray:
     """[15][80][80] -> [2][80][80] (Fig. 2)."""
     x = np.asarray(x, dtype=np.float64)
+    mod = modulation(x, w, blocks) if "mod_fc_w" in w else None
     h = pointwise(w["lift_w"].astype(np.float64), w["lift_b"].astype(np.float64), x)
     for b in range(blocks):
-        R = w[f"R{b}_re"].astype(np.float64) + 1j * w[f"R{b}_im"].astype(np.float64)
+        R = spectral_weights(w, b)
+        if mod is not None:
+            R = R * (1.0 + mod[b])[None, None]
         h = spectral_conv(h, R) + pointwise(w[f"W{b}"].astype(np.float64),
                                             w[f"b{b}"].astype(np.float64), h)
         if b < blocks - 1:

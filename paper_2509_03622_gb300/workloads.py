@@ -130,14 +130,22 @@ def demux_layout(n: int = 512, npml: int = NPML_DEFAULT, design: int = 200,
     return eps, mask, src_x, yin, port_x, port_rows
 
 
+MOD_CH, MOD_AUX, MOD_FEAT = 16, 5, 144   # modulation path: conv channels, aux inputs, pooled features
+
+
 def nno_weights(seed: int = 0, width: int = NNO_WIDTH, cin: int = NNO_CIN,
                 hidden: int = NNO_HIDDEN, blocks: int = NNO_BLOCKS,
-                my: int = NNO_MODES_Y, mx: int = NNO_MODES_X) -> dict:
+                my: int = NNO_MODES_Y, mx: int = NNO_MODES_X, rank: int = 0,
+                modulation: bool = False) -> dict:
     """Seeded initialisation of the Fourier neural operator (Fig. 2).
 
     Spectral weights follow the usual FNO recipe (uniform in [0, 1) times
     1/(in*out), real and imaginary parts drawn independently); 1x1 layers
-    are uniform in +-1/sqrt(fan_in).  Arrays are float32.
+    are uniform in +-1/sqrt(fan_in).  rank > 0: R_b is given by the factors
+    theta_b [width][width][rank] (FNO recipe) and V_b [rank][my][mx]
+    (uniform +-1/sqrt(rank)).  modulation: the modulation path's
+    convolution (uniform +-1/sqrt(45)) and fully connected layer (uniform
+    +-0.1/sqrt(144), so the seeded modulation is small).  Arrays are float32.
     """
     g = rng(seed)
 
@@ -150,42 +158,75 @@ def nno_weights(seed: int = 0, width: int = NNO_WIDTH, cin: int = NNO_CIN,
     w["lift_w"], w["lift_b"] = lin(width, cin)
     scale = 1.0 / (width * width)
     for b in range(blocks):
-        w[f"R{b}_re"] = (scale * g.random((width, width, my, mx))).astype(np.float32)
-        w[f"R{b}_im"] = (scale * g.random((width, width, my, mx))).astype(np.float32)
+        if rank:
+            w[f"R{b}_theta_re"] = (scale * g.random((width, width, rank))).astype(np.float32)
+            w[f"R{b}_theta_im"] = (scale * g.random((width, width, rank))).astype(np.float32)
+            v = 1.0 / np.sqrt(rank)
+            w[f"R{b}_V_re"] = g.uniform(-v, v, size=(rank, my, mx)).astype(np.float32)
+            w[f"R{b}_V_im"] = g.uniform(-v, v, size=(rank, my, mx)).astype(np.float32)
+        else:
+            w[f"R{b}_re"] = (scale * g.random((width, width, my, mx))).astype(np.float32)
+            w[f"R{b}_im"] = (scale * g.random((width, width, my, mx))).astype(np.float32)
         w[f"W{b}"], w[f"b{b}"] = lin(width, width)
     w["p1_w"], w["p1_b"] = lin(hidden, width)
     w["p2_w"], w["p2_b"] = lin(2, hidden)
+    if modulation:
+        c = 1.0 / np.sqrt(MOD_AUX * 9)
+        w["mod_conv_w"] = g.uniform(-c, c, size=(MOD_CH, MOD_AUX, 3, 3)).astype(np.float32)
+        w["mod_conv_b"] = g.uniform(-c, c, size=(MOD_CH,)).astype(np.float32)
+        f = 0.1 / np.sqrt(MOD_FEAT)
+        w["mod_fc_w"] = g.uniform(-f, f, size=(blocks * my * mx, MOD_FEAT)).astype(np.float32)
+        w["mod_fc_b"] = g.uniform(-f, f, size=(blocks * my * mx,)).astype(np.float32)
     return w
 
 
+def weight_rank(w: dict) -> int:
+    """Rank of the spectral weights' factorisation (0 = full R)."""
+    return int(w["R0_theta_re"].shape[2]) if "R0_theta_re" in w else 0
+
+
 # Order of tensors in the flat float32 weight blob handed to the library.
-def weight_order(blocks: int = NNO_BLOCKS):
+def weight_order(blocks: int = NNO_BLOCKS, rank: int = 0, modulation: bool = False):
     names = ["lift_w", "lift_b"]
     for b in range(blocks):
-        names += [f"R{b}_re", f"R{b}_im", f"W{b}", f"b{b}"]
+        if rank:
+            names += [f"R{b}_theta_re", f"R{b}_theta_im", f"R{b}_V_re", f"R{b}_V_im"]
+        else:
+            names += [f"R{b}_re", f"R{b}_im"]
+        names += [f"W{b}", f"b{b}"]
     names += ["p1_w", "p1_b", "p2_w", "p2_b"]
+    if modulation:
+        names += ["mod_conv_w", "mod_conv_b", "mod_fc_w", "mod_fc_b"]
     return names
 
 
 def pack_weights(w: dict) -> np.ndarray:
     """Flatten a weight dict into the blob layout the C-ABI expects."""
-    return np.concatenate([np.ascontiguousarray(w[n], dtype=np.float32).ravel()
-                           for n in weight_order()])
+    order = weight_order(rank=weight_rank(w), modulation="mod_fc_w" in w)
+    return np.concatenate([np.ascontiguousarray(w[n], dtype=np.float32).ravel() for n in order])
 
 
-def unpack_weights(blob: np.ndarray, width: int = NNO_WIDTH, cin: int = NNO_CIN,
-                   hidden: int = NNO_HIDDEN, blocks: int = NNO_BLOCKS,
-                   my: int = NNO_MODES_Y, mx: int = NNO_MODES_X) -> dict:
+def weight_shapes(width: int = NNO_WIDTH, cin: int = NNO_CIN, hidden: int = NNO_HIDDEN,
+                  blocks: int = NNO_BLOCKS, my: int = NNO_MODES_Y, mx: int = NNO_MODES_X, rank: int = 0):
     shapes = {"lift_w": (width, cin), "lift_b": (width,),
               "p1_w": (hidden, width), "p1_b": (hidden,),
-              "p2_w": (2, hidden), "p2_b": (2,)}
+              "p2_w": (2, hidden), "p2_b": (2,),
+              "mod_conv_w": (MOD_CH, MOD_AUX, 3, 3), "mod_conv_b": (MOD_CH,),
+              "mod_fc_w": (blocks * my * mx, MOD_FEAT), "mod_fc_b": (blocks * my * mx,)}
     for b in range(blocks):
         shapes[f"R{b}_re"] = (width, width, my, mx)
         shapes[f"R{b}_im"] = (width, width, my, mx)
+        shapes[f"R{b}_theta_re"] = shapes[f"R{b}_theta_im"] = (width, width, rank)
+        shapes[f"R{b}_V_re"] = shapes[f"R{b}_V_im"] = (rank, my, mx)
         shapes[f"W{b}"] = (width, width)
         shapes[f"b{b}"] = (width,)
+    return shapes
+
+
+def unpack_weights(blob: np.ndarray, rank: int = 0, modulation: bool = False, **kw) -> dict:
+    shapes = weight_shapes(rank=rank, **kw)
     out, off = {}, 0
-    for n in weight_order(blocks):
+    for n in weight_order(rank=rank, modulation=modulation):
         sz = int(np.prod(shapes[n]))
         out[n] = blob[off:off + sz].reshape(shapes[n]).astype(np.float32)
         off += sz
