@@ -38,19 +38,46 @@ def build_model(torch, w0: dict):
             super().__init__()
             P = lambda a: nn.Parameter(torch.tensor(np.asarray(a, dtype=np.float32)))
             self.lift_w, self.lift_b = P(w0["lift_w"]), P(w0["lift_b"])
-            self.Rr = nn.ParameterList([P(w0[f"R{b}_re"]) for b in range(4)])
-            self.Ri = nn.ParameterList([P(w0[f"R{b}_im"]) for b in range(4)])
+            self.rank = int(w0["R0_theta_re"].shape[2]) if "R0_theta_re" in w0 else 0
+            if self.rank:  # modified FNO: R_b = theta_b V_b (Sec. 2.1)
+                self.Tr = nn.ParameterList([P(w0[f"R{b}_theta_re"]) for b in range(4)])
+                self.Ti = nn.ParameterList([P(w0[f"R{b}_theta_im"]) for b in range(4)])
+                self.Vr = nn.ParameterList([P(w0[f"R{b}_V_re"]) for b in range(4)])
+                self.Vi = nn.ParameterList([P(w0[f"R{b}_V_im"]) for b in range(4)])
+            else:
+                self.Rr = nn.ParameterList([P(w0[f"R{b}_re"]) for b in range(4)])
+                self.Ri = nn.ParameterList([P(w0[f"R{b}_im"]) for b in range(4)])
+            self.mod = "mod_fc_w" in w0
+            if self.mod:  # modulation path (Sec. 2.1, Fig. 2)
+                self.mcw, self.mcb = P(w0["mod_conv_w"]), P(w0["mod_conv_b"])
+                self.mfw, self.mfb = P(w0["mod_fc_w"]), P(w0["mod_fc_b"])
             self.W = nn.ParameterList([P(w0[f"W{b}"]) for b in range(4)])
             self.bb = nn.ParameterList([P(w0[f"b{b}"]) for b in range(4)])
             self.p1_w, self.p1_b = P(w0["p1_w"]), P(w0["p1_b"])
             self.p2_w, self.p2_b = P(w0["p2_w"]), P(w0["p2_b"])
 
+        def spectral(self, b):
+            if self.rank:
+                return torch.einsum("oir,ryx->oiyx", torch.complex(self.Tr[b], self.Ti[b]),
+                                    torch.complex(self.Vr[b], self.Vi[b]))
+            return torch.complex(self.Rr[b], self.Ri[b])
+
+        def modulation(self, x):  # [B][4][32][16]
+            F_ = torch.nn.functional
+            a = x[:, [0, 11, 12, 13, 14]]
+            c = F_.leaky_relu(F_.conv2d(a, self.mcw, self.mcb, stride=2), 0.01)
+            f = F_.avg_pool2d(c, 13).flatten(1)
+            return (f @ self.mfw.t() + self.mfb).reshape(-1, 4, 32, 16)
+
         def forward(self, x):  # [B][15][80][80] -> [B][2][80][80]
+            m = self.modulation(x) if self.mod else None
             h = torch.einsum("oi,biyx->boyx", self.lift_w, x) + self.lift_b[None, :, None, None]
             for b in range(4):
                 H = torch.fft.rfft2(h)
                 Hk = torch.cat([H[:, :, :16, :16], H[:, :, -16:, :16]], dim=2)
-                R = torch.complex(self.Rr[b], self.Ri[b])
+                if m is not None:  # R (1 + mod) on every channel pair = scaling the retained modes
+                    Hk = Hk * (1.0 + m[:, b])[:, None]
+                R = self.spectral(b)
                 Y = torch.einsum("biyx,oiyx->boyx", Hk, R)
                 Yf = torch.zeros(h.shape[0], 32, WIN, WIN // 2 + 1, dtype=Y.dtype, device=h.device)
                 Yf[:, :, :16, :16] = Y[:, :, :16]
@@ -67,8 +94,14 @@ def build_model(torch, w0: dict):
             d = {"lift_w": self.lift_w, "lift_b": self.lift_b, "p1_w": self.p1_w, "p1_b": self.p1_b,
                  "p2_w": self.p2_w, "p2_b": self.p2_b}
             for b in range(4):
-                d[f"R{b}_re"], d[f"R{b}_im"] = self.Rr[b], self.Ri[b]
+                if self.rank:
+                    d[f"R{b}_theta_re"], d[f"R{b}_theta_im"] = self.Tr[b], self.Ti[b]
+                    d[f"R{b}_V_re"], d[f"R{b}_V_im"] = self.Vr[b], self.Vi[b]
+                else:
+                    d[f"R{b}_re"], d[f"R{b}_im"] = self.Rr[b], self.Ri[b]
                 d[f"W{b}"], d[f"b{b}"] = self.W[b], self.bb[b]
+            if self.mod:
+                d.update(mod_conv_w=self.mcw, mod_conv_b=self.mcb, mod_fc_w=self.mfw, mod_fc_b=self.mfb)
             return {k: v.detach().float().cpu().numpy() for k, v in d.items()}
 
     return FNO()
@@ -221,24 +254,139 @@ def dense_operator(t, P):
     return A
 
 
+def initial_weights(init, seed, rank=0, modulation=False):
+    """Starting weights: a saved blob (plain, or of the requested layout) or
+    the seeded initialisation.  From a plain blob the modified parts start
+    where they change nothing or little: the modulation's fully connected
+    layer at zero (the network is then the plain one) and each R split into
+    rank-r factors by a truncated SVD along the mode axis."""
+    from paper_2509_03622_gb300 import workloads as wl
+    if not init:
+        return wl.nno_weights(seed, rank=rank, modulation=modulation)
+    blob = np.load(init)
+    plain_n = wl.pack_weights(wl.nno_weights(0)).size
+    if blob.size != plain_n:
+        return wl.unpack_weights(blob, rank=rank, modulation=modulation)
+    w = wl.unpack_weights(blob)
+    if rank:
+        for b in range(4):
+            R = (w.pop(f"R{b}_re") + 1j * w.pop(f"R{b}_im")).astype(np.complex128).reshape(32 * 32, 512)
+            U, sv, Vh = np.linalg.svd(R, full_matrices=False)
+            th = (U[:, :rank] * sv[:rank]).reshape(32, 32, rank)
+            V = Vh[:rank].reshape(rank, 32, 16)
+            w[f"R{b}_theta_re"], w[f"R{b}_theta_im"] = th.real.astype(np.float32), th.imag.astype(np.float32)
+            w[f"R{b}_V_re"], w[f"R{b}_V_im"] = V.real.astype(np.float32), V.imag.astype(np.float32)
+    if modulation:
+        m = wl.nno_weights(seed, modulation=True)
+        for k in ("mod_conv_w", "mod_conv_b"):
+            w[k] = m[k]
+        w["mod_fc_w"] = np.zeros_like(m["mod_fc_w"])
+        w["mod_fc_b"] = np.zeros_like(m["mod_fc_b"])
+    return w
+
+
+def row_blocks(t, P):
+    """The local Robin operator A_w ordered by window rows: diagonal blocks
+    D_y [B][80][80] (tridiagonal in x, Robin eliminations on interface
+    sides) and the scalar couplings ylo[y], yhi[y] to the rows below and
+    above (the same stencil as local_apply)."""
+    B = P["eps"].shape[0]
+    dev = P["eps"].device
+    xlo, xhi, ylo, yhi = P["xlo"], P["xhi"], P["ylo"], P["yhi"]
+    k2 = (P["k0dx"] ** 2)[:, None, None]
+    kd = P["k0dx"][:, None, None] * t.sqrt(P["eps"])
+    f = 1 - 1j * kd                                        # [B][y][x]
+    rb = P["robin"]
+    dg = -(xlo + xhi)[:, None, :] - (ylo + yhi)[:, :, None] + k2 * P["eps"]
+    dg = dg.to(t.complex64)
+    dg[:, :, 0] += rb[:, 0, None] * xlo[:, None, 0] * f[:, :, 0]
+    dg[:, :, -1] += rb[:, 1, None] * xhi[:, None, -1] * f[:, :, -1]
+    dg[:, 0, :] += rb[:, 2, None] * ylo[:, 0, None] * f[:, 0, :]
+    dg[:, -1, :] += rb[:, 3, None] * yhi[:, -1, None] * f[:, -1, :]
+    D = t.zeros(B, WIN, WIN, WIN, dtype=t.complex64, device=dev)  # [B][y][x][x']
+    i = t.arange(WIN, device=dev)
+    D[:, :, i, i] = dg
+    D[:, :, i[1:], i[1:] - 1] = xlo[:, None, 1:].expand(B, WIN, WIN - 1)
+    D[:, :, i[:-1], i[:-1] + 1] = xhi[:, None, :-1].expand(B, WIN, WIN - 1)
+    return D, ylo, yhi
+
+
+def exact_local_solve(t, P, rhs):
+    """Exact solutions of the local Robin problems A_w x = rhs ([B][80][80],
+    several right-hand sides per window allowed as rhs [B][R][80][80]) by
+    block elimination over the 80 window rows: S_0 = D_0,
+    S_y = D_y - ylo_y yhi_{y-1} S_{y-1}^-1 (the row couplings are scalar),
+    then the forward and backward sweeps.  About 80 batched 80 x 80 inverses
+    per window instead of a dense 6400 x 6400 factorisation."""
+    D, ylo, yhi = row_blocks(t, P)
+    # FP64 throughout: the row recursion amplifies rounding (and on GPUs
+    # with TF32 matmuls enabled a complex64 einsum would lose bits)
+    D, ylo, yhi = D.to(t.complex128), ylo.to(t.complex128), yhi.to(t.complex128)
+    multi = rhs.dim() == 4
+    b = (rhs if multi else rhs[:, None]).to(t.complex128)  # [B][R][y][x]
+    Sinv = []
+    prev = None
+    for y in range(WIN):
+        S = D[:, y]
+        if prev is not None:
+            S = S - (ylo[:, y] * yhi[:, y - 1])[:, None, None] * prev
+        prev = t.linalg.inv(S)
+        Sinv.append(prev)
+    z = []
+    zy = None
+    for y in range(WIN):
+        r = b[:, :, y, :]
+        if zy is not None:
+            r = r - ylo[:, y, None, None] * zy
+        zy = t.einsum("bij,brj->bri", Sinv[y], r)
+        z.append(zy)
+    x = [None] * WIN
+    x[WIN - 1] = z[WIN - 1]
+    for y in range(WIN - 2, -1, -1):
+        x[y] = z[y] - t.einsum("bij,brj->bri", Sinv[y], yhi[:, y, None, None] * x[y + 1])
+    out = t.stack(x, 2).to(t.complex64)
+    return out if multi else out[:, 0]
+
+
+def plane_wave_data(t, P):
+    """Robin data of a plane wave of random direction on every side,
+    exp(-j kd (d . r)) at the side cells, kd from the mean permittivity of
+    the window's boundary (the kind of data the coarse space's trials are)."""
+    B = P["eps"].shape[0]
+    dev = P["eps"].device
+    th = 2 * math.pi * t.rand(B, device=dev)
+    e = P["eps"]
+    eb = t.cat([e[:, :, 0], e[:, :, -1], e[:, 0, :], e[:, -1, :]], 1).mean(1)
+    kd = P["k0dx"] * t.sqrt(eb)
+    s = t.arange(WIN, device=dev, dtype=t.float32)
+    z, h = t.zeros_like(s), t.full_like(s, WIN - 1.0)
+    xs = t.stack([z, h, s, s])                       # side cell coordinates [4][80]
+    ys = t.stack([s, s, z, h])
+    ph = kd[:, None, None] * (t.cos(th)[:, None, None] * xs + t.sin(th)[:, None, None] * ys)
+    return t.polar(t.ones_like(ph), -ph)
+
+
 def expand(P, reps):
     """Repeat each window's parameters `reps` times (several right-hand sides per window)."""
     return {k: v.repeat_interleave(reps, 0) for k, v in P.items()}
 
 
-def train_data(minutes, windows, rhs_per_win, lr, seed, out, log_every, device, init, c_res=0.3):
-    """Supervised training on exact local solutions (LU of the dense local
-    operator, several right-hand sides per factorisation) plus the residual
+def train_data(minutes, windows, rhs_per_win, lr, seed, out, log_every, device, init, c_res=0.3, rank=0,
+               modulation=False):
+    """Supervised training on exact local solutions (block elimination over
+    the window rows, several right-hand sides per window) plus the residual
     loss; second step trained on the residual of the first (Algorithm 2)."""
     import torch as t
     from paper_2509_03622_gb300 import workloads as wl
     dev = t.device(device)
     t.manual_seed(seed)
     t.backends.cuda.matmul.allow_tf32 = True
-    w0 = wl.unpack_weights(np.load(init)) if init else wl.nno_weights(seed)
+    w0 = initial_weights(init, seed, rank, modulation)
     model = build_model(t, w0).to(dev)
     opt = t.optim.Adam(model.parameters(), lr=lr)
     S = Sampler(t, dev, windows)
+    val = validation_set(t, dev)
+    print("validation before:", evaluate(t, model, val), flush=True)
     t0, it, hist = time.time(), 0, []
     R = rhs_per_win
     while time.time() - t0 < minutes * 60:
@@ -246,23 +394,23 @@ def train_data(minutes, windows, rhs_per_win, lr, seed, out, log_every, device, 
         for gp in opt.param_groups:
             gp["lr"] = lr * 0.5 * (1 + math.cos(math.pi * min(frac, 1.0)))
         P = S.batch()
-        with t.no_grad():
-            A = dense_operator(t, P)
-            LU, piv = t.linalg.lu_factor(A)
-            del A
         Pe = expand(P, R)
         Bt = windows * R
         sig = t.rand(Bt, device=dev) * 6.0
         r = S.smooth_noise((Bt, WIN, WIN), sig) if hasattr(S, "smooth_noise") else None
         g = t.randn(Bt, 4, WIN, dtype=t.complex64, device=dev)
+        g = t.where((t.rand(Bt, device=dev) < 0.5)[:, None, None], plane_wave_data(t, Pe), g)
         kindr = t.rand(Bt, device=dev)
         r = t.where((kindr < 0.25)[:, None, None], t.zeros_like(r), r)
         g = t.where((kindr > 0.5)[:, None, None], t.zeros_like(g), g)
         g = g * Pe["robin"][:, :, None]
         rhs = r + boundary_rhs(t, g, Pe)
         with t.no_grad():
-            b = rhs.reshape(windows, R, WIN * WIN).transpose(1, 2)
-            xs = t.linalg.lu_solve(LU, piv, b).transpose(1, 2).reshape(Bt, WIN, WIN)
+            xs = exact_local_solve(t, P, rhs.reshape(windows, R, WIN, WIN)).reshape(Bt, WIN, WIN)
+            # keep only samples the elimination solved accurately
+            rr = (rhs - local_apply(t, xs, Pe)).abs().pow(2).sum((1, 2)) / \
+                (rhs.abs() ** 2).sum((1, 2)).clamp(min=1e-30)
+            good = (rr < 1e-6).float()
         nx_ = (xs.abs() ** 2).sum((1, 2)).clamp(min=1e-30)
         nr_ = (rhs.abs() ** 2).sum((1, 2)).clamp(min=1e-30)
         opt.zero_grad()
@@ -274,18 +422,60 @@ def train_data(minutes, windows, rhs_per_win, lr, seed, out, log_every, device, 
         e2 = solve(t, model, res1d, t.zeros_like(g), Pe)
         tgt2 = (xs - e1.detach())
         l2 = ((e2 - tgt2).abs() ** 2).sum((1, 2)) / (tgt2.abs() ** 2).sum((1, 2)).clamp(min=1e-30)
-        loss = (l1.clamp(max=4.0).mean() + l2.clamp(max=4.0).mean() + c_res * p1.clamp(max=4.0).mean()) / (2 + c_res)
+        # relative L2 errors (not squared, not clamped): bounded gradients
+        # without switching off the samples a drifting network gets worst
+        ng = good.sum().clamp(min=1.0)
+        loss = ((good * l1.sqrt()).sum() + (good * l2.sqrt()).sum() + c_res * (good * p1.sqrt()).sum()) / ng / (2 + c_res)
         loss.backward()
         t.nn.utils.clip_grad_norm_(model.parameters(), 1.0)
         opt.step()
         it += 1
-        hist.append((float(l1.mean()), float(l2.mean()), float(p1.mean())))
+        hist.append((float(l1.detach().sqrt().mean()), float(l2.detach().sqrt().mean()),
+                     float(p1.detach().sqrt().mean()), float(good.mean())))
         if it % log_every == 0:
             h = np.mean(hist[-log_every:], axis=0)
             print(f"it {it} t {time.time() - t0:.0f}s field-err1 {h[0]:.4f} field-err2 {h[1]:.4f} "
-                  f"resid1 {h[2]:.4f}", flush=True)
+                  f"resid1 {h[2]:.4f} accepted {h[3]:.3f}", flush=True)
     np.save(out, wl.pack_weights(model.export()))
     print(f"saved {out} after {it} iterations")
+    print("validation after:", evaluate(t, model, val), flush=True)
+
+
+def validation_set(t, dev, windows=64, seed=12345):
+    """A fixed batch of windows, residual-only right-hand sides and their
+    exact solutions (same sampler as training, seeded)."""
+    g = t.Generator(device=dev)
+    state = t.random.get_rng_state() if dev.type == "cpu" else t.cuda.get_rng_state(dev)
+    t.manual_seed(seed)
+    S = Sampler(t, dev, windows)
+    P = S.batch()
+    sig = t.rand(windows, device=dev) * 6.0
+    r = S.smooth_noise((windows, WIN, WIN), sig)
+    with t.no_grad():
+        xs = exact_local_solve(t, P, r)
+    if dev.type == "cpu":
+        t.random.set_rng_state(state)
+    else:
+        t.cuda.set_rng_state(state, dev)
+    del g
+    return P, r, xs
+
+
+def evaluate(t, model, val):
+    """Mean relative field error and local residual of one network
+    application, and the residual after a second application to the first
+    one's residual (fixed-point recurrence of Algorithm 2)."""
+    P, r, xs = val
+    with t.no_grad():
+        zg = t.zeros(r.shape[0], 4, WIN, dtype=t.complex64, device=r.device)
+        e1 = solve(t, model, r, zg, P)
+        res1 = r - local_apply(t, e1, P)
+        e2 = e1 + solve(t, model, res1, zg, P)
+        res2 = r - local_apply(t, e2, P)
+        nr = (r.abs() ** 2).sum((1, 2)).sqrt()
+        ferr = ((e1 - xs).abs() ** 2).sum((1, 2)).sqrt() / (xs.abs() ** 2).sum((1, 2)).sqrt()
+        return {"field_err": float(ferr.mean()), "resid1": float(((res1.abs() ** 2).sum((1, 2)).sqrt() / nr).mean()),
+                "resid2": float(((res2.abs() ** 2).sum((1, 2)).sqrt() / nr).mean())}
 
 
 def pack(t, r, g, P):
@@ -387,9 +577,12 @@ if __name__ == "__main__":
     ap.add_argument("--mode", default="physics", choices=["physics", "data"])
     ap.add_argument("--windows", type=int, default=4, help="data mode: windows factored per step")
     ap.add_argument("--rhs", type=int, default=16, help="data mode: right-hand sides per window")
+    ap.add_argument("--rank", type=int, default=0, help="data mode: rank-r spectral weights (modified FNO)")
+    ap.add_argument("--modulation", action="store_true", help="data mode: the modulation path (modified FNO)")
     a = ap.parse_args()
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     if a.mode == "data":
-        train_data(a.minutes, a.windows, a.rhs, a.lr, a.seed, a.out, a.log_every, a.device, a.init)
+        train_data(a.minutes, a.windows, a.rhs, a.lr, a.seed, a.out, a.log_every, a.device, a.init,
+                   rank=a.rank, modulation=a.modulation)
     else:
         train(a.minutes, a.batch, a.recur, a.lr, a.seed, a.out, a.log_every, a.device, a.init)

@@ -85,3 +85,32 @@ def test_dense_operator_matches_stencil():
     y1 = (A @ e.reshape(2, -1, 1)).reshape(2, 80, 80)
     y2 = T.local_apply(torch, e, P)
     assert torch.allclose(y1, y2, rtol=1e-4, atol=1e-5 * y2.abs().max())
+
+
+def test_modified_fno_twin_matches_oracle():
+    """The training model of the modified FNO (modulation path, rank-8 R)
+    equals the oracle's forward, and its export round-trips through the
+    blob layout the library reads."""
+    w = wl.nno_weights(3, rank=8, modulation=True)
+    w["mod_fc_w"] *= 20.0
+    m = T.build_model(torch, w).double()
+    x = wl.rng(12).standard_normal((2, 15, 80, 80))
+    out = m(torch.from_numpy(x)).detach().numpy()
+    ref = np.stack([ON.forward(x[i], w) for i in range(2)])
+    assert np.max(np.abs(out - ref)) < 1e-12 * np.max(np.abs(ref))
+    back = wl.unpack_weights(wl.pack_weights(m.export()), rank=8, modulation=True)
+    assert all(np.array_equal(back[k], w[k]) for k in w)
+
+
+def test_exact_local_solve_by_row_elimination():
+    """The training targets: block elimination over the window rows solves
+    the local Robin problems of the sampler (residual at complex64 level)."""
+    torch.manual_seed(1)
+    S = T.Sampler(torch, torch.device("cpu"), 3)
+    P = S.batch()
+    rhs = torch.randn(3, 2, 80, 80, dtype=torch.complex64)
+    x = T.exact_local_solve(torch, P, rhs)
+    Pe = T.expand(P, 2)
+    r = rhs.reshape(6, 80, 80) - T.local_apply(torch, x.reshape(6, 80, 80), Pe)
+    rel = (r.abs() ** 2).sum((1, 2)).sqrt() / (rhs.reshape(6, 80, 80).abs() ** 2).sum((1, 2)).sqrt()
+    assert float(rel.max()) < 1e-5
