@@ -75,6 +75,9 @@ typedef struct {
   const float* eps;     /* device ptr [ny][nx] relative permittivity; the
                            library copies it                               */
   void*  stream;        /* cudaStream_t used for all work (NULL = legacy)  */
+  int    max_restart;   /* longest FGMRES restart the handle allocates its
+                           Krylov space for (V: max_restart + 1 vectors, Z:
+                           max_restart): 0 = 32, else 1..64              */
 } fdfd_desc;
 
 /* Two-level Schwarz set-up (Sec. 2.2, Methods, Algorithm 3 set-up). */
@@ -97,7 +100,8 @@ typedef struct {
                             p2_w[2][128], p2_b[2].  R is indexed
                             [out][in][ky][kx] with ky rows 0..15 = modes
                             0..15 and rows 16..31 = modes -16..-1.          */
-  size_t n_weights;      /* number of floats in the blob (4,199,442)       */
+  size_t n_weights;      /* number of floats in the blob (4,203,522 for the
+                            plain network; see r_rank and modulation)      */
   int inner_iters;       /* local solver of each window (Algorithm 3's
                             M.solve): 0 = one neural-operator application
                             with the residual and Robin data as inputs;
@@ -113,10 +117,26 @@ typedef struct {
                             Ritz vectors with |eta| >= ritz_tol kept; the
                             basis fields are combined, not solved again.
                             Needs k_coarse <= 64.                           */
+  int r_rank;            /* modified FNO (Sec. 2.1): 0 = each block's R is
+                            stored in full; r in 1..512 = the blob gives R
+                            as rank-r factors theta [32][32][r] and V
+                            [r][32][16] (re then im of each, in place of
+                            R_re, R_im), R = sum_r theta V, expanded at
+                            set-up                                          */
+  int modulation;        /* modified FNO (Sec. 2.1, Fig. 2): 1 = the blob
+                            ends with the modulation path, conv_w
+                            [16][5][3][3] (inputs (k0 dx)^2 eps, Re/Im 1/s_x,
+                            Re/Im 1/s_y), conv_b [16], fc_w [2048][144],
+                            fc_b [2048]; the real modulation m [4][32][16] of
+                            each window (3x3 stride-2 valid convolution,
+                            leaky-ReLU, 13x13 average pooling, fully
+                            connected) is computed at set-up and block b
+                            uses R (1 + m[b]).  Neither option combines
+                            with FDFD_PREC_FP8 (FDFD_EINVAL).               */
 } schwarz_desc;
 
 typedef struct {
-  int    restart;        /* FGMRES restart length, 1..32                  */
+  int    restart;        /* FGMRES restart length, 1..fdfd_desc.max_restart */
   int    max_iters;      /* total inner iterations                        */
   double tol;            /* true relative residual ||b~ - A~ E||/||b~||   */
   int    precond;        /* FDFD_PRECOND_*                                 */
@@ -157,7 +177,7 @@ typedef struct {
 
 /* Create a solver for the problem of Eq. 1 described by *desc: computes the
  * UPML stretching (Methods, Eq. 6) and the 5-point coefficients, copies eps,
- * allocates the Krylov workspace for restart <= 64.  FDFD_EINVAL for bad
+ * allocates the Krylov workspace for restarts up to desc.max_restart.  FDFD_EINVAL for bad
  * sizes (nx, ny not multiples of 64 or < 128, npml < 0 or >= n/2, dx or
  * wavelength <= 0).  *out is NULL on error. */
 int  fdfd_create(const fdfd_desc* desc, fdfd_handle* out);
@@ -211,10 +231,13 @@ int  fdfd_batch_create(fdfd_handle* hs, int n, int max_windows, fdfd_batch* out)
  * are device pointers of problem p (host arrays of n pointers); stats[p]
  * receives each problem's statistics (t_solve_ms is the batch's time).  With
  * FDFD_PRECOND_SCHWARZ every Arnoldi step applies the neural local solves of
- * all windows of all active problems as one batch (one launch per operator
- * stage per chunk), using hs[0]'s weights (every handle must have been set
- * up with the same blob and inner_iters = 0); coarse corrections are applied
- * per problem.  Returns the most severe status over the problems. */
+ * all windows of all active problems whose local solver is one network
+ * application (inner_iters = 0) as one batch (one launch per operator stage
+ * per chunk), using hs[0]'s weights (those handles must have been set up
+ * with the same blob); a problem set up with inner_iters > 0 applies its
+ * own preconditioner (its windows' NN-FGMRES) in the same lock-step
+ * iteration.  Coarse corrections are applied per problem.  Returns the most
+ * severe status over the problems. */
 int  fdfd_solve_batched(fdfd_batch b, const fdfd_c64* const* J_dev, fdfd_c64* const* E_dev,
                         const fdfd_solve_opts* opts, fdfd_solve_stats* stats);
 void fdfd_batch_destroy(fdfd_batch b);

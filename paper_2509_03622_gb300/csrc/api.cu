@@ -396,6 +396,7 @@ int fdfd_create(const fdfd_desc* d, fdfd_handle* out) {
     const int n = i < 2 ? d->nx : d->ny;
     if (d->npml[i] < 0 || 2 * d->npml[i] >= n) return FDFD_EINVAL;
   }
+  if (d->max_restart < 0 || d->max_restart > FDFD_MAXRESTART) return FDFD_EINVAL;
   fdfd_ctx* h = new fdfd_ctx();
   h->nx = d->nx; h->ny = d->ny; h->n = (size_t)d->nx * d->ny;
   h->dx = d->dx; h->wavelength = d->wavelength; h->pml_m = d->pml_m; h->pml_lnR = d->pml_lnR;
@@ -405,7 +406,7 @@ int fdfd_create(const fdfd_desc* d, fdfd_handle* out) {
   const double omega = 2.0 * M_PI * C0 / d->wavelength;
   h->sb = d->dx * d->dx * omega * MU0;
   h->stream = (cudaStream_t)d->stream;
-  h->rmax = RESTART_CAP;
+  h->rmax = d->max_restart ? d->max_restart : RESTART_CAP;
   int rc = FDFD_OK;
   const size_t n = h->n;
   if ((rc = dalloc(h, &h->eps, n)) || (rc = setup_coefs(h)) ||

@@ -99,7 +99,6 @@ extern "C" int fdfd_solve_batched(fdfd_batch bt, const fdfd_c64* const* Jp, fdfd
   for (int p = 0; p < n; ++p) {
     if (!Jp[p] || !Ep[p]) return FDFD_EINVAL;
     if (schwarz && !schwarz_weights(bt->hs[p])) return FDFD_ENOSETUP;
-    if (schwarz && schwarz_inner_iters(bt->hs[p]) != 0) return FDFD_EINVAL;  // one neural application per solve
   }
   if (schwarz && !bt->work.X) return FDFD_ENOSETUP;
   cudaStream_t s = h0->stream;
@@ -190,22 +189,32 @@ extern "C" int fdfd_solve_batched(fdfd_batch bt, const fdfd_c64* const* Jp, fdfd
     std::vector<int> act;
     for (int p = 0; p < n; ++p) if (ps[p].active) act.push_back(p);
     if (act.empty()) break;
-    // ---- preconditioner: one neural pass over all windows of all active problems ----
+    // ---- preconditioner: one neural pass over all windows of all active problems whose
+    // local solve is one network application; a problem whose local solver runs
+    // NN-FGMRES steps applies its own preconditioner (local FGMRES and coarse correction) ----
     if (schwarz) {
-      int nent = 0;
+      std::vector<int> one;
       for (int p : act) {
+        fdfd_ctx* h = bt->hs[p];
+        if (schwarz_inner_iters(h) == 0) { one.push_back(p); continue; }
+        const size_t off = (size_t)ps[p].j * h->n;
+        if ((rc = schwarz_apply(h, h->V + off, &h->st->vscale[ps[p].j], h->Z + off, 0))) return rc;
+      }
+      int nent = 0;
+      for (int p : one) {
         fdfd_ctx* h = bt->hs[p];
         const size_t off = (size_t)ps[p].j * h->n;
         bt->ptab_h[p] = ProbGeom{h->nx, h->ny, h->nx / FDFD_CORE, (float)h->k2, h->eps, h->isx, h->isy,
-                                 h->V + off, h->Z + off, &h->st->vscale[ps[p].j]};
+                                 h->V + off, h->Z + off, &h->st->vscale[ps[p].j], schwarz_modulation(h)};
         for (int w = 0; w < n_windows(h); ++w) bt->wtab_h[nent++] = make_int2(p, w);
       }
       CK(cudaMemcpyAsync(bt->ptab_d, bt->ptab_h, (size_t)n * sizeof(ProbGeom), cudaMemcpyHostToDevice, s));
-      if (last_set != (int)act.size()) {
+      if (last_set != (int)one.size()) {
         CK(cudaMemcpyAsync(bt->wtab_d, bt->wtab_h, (size_t)nent * sizeof(int2), cudaMemcpyHostToDevice, s));
-        last_set = (int)act.size();
+        last_set = (int)one.size();
       }
-      GridGeom g{h0->nx, h0->ny, h0->nx / FDFD_CORE, (float)h0->k2, h0->eps, h0->isx, h0->isy};
+      GridGeom g{h0->nx, h0->ny, h0->nx / FDFD_CORE, (float)h0->k2, h0->eps, h0->isx, h0->isy,
+                 nullptr};  // entries take their problem's modulation from the table
       for (int st0 = 0; st0 < nent; st0 += bt->cap) {
         const int cnt = nent - st0 < bt->cap ? nent - st0 : bt->cap;
         NnoInput in;
@@ -215,7 +224,7 @@ extern "C" int fdfd_solve_batched(fdfd_batch bt, const fdfd_c64* const* Jp, fdfd
         if ((rc = nno_forward(schwarz_weights(h0), &bt->work, g, in, out, cnt, s, h0))) return rc;
       }
       // (the pinned tables are rewritten only after the flag read below has synchronised the stream)
-      for (int p : act)
+      for (int p : one)
         if ((rc = schwarz_coarse(bt->hs[p], bt->hs[p]->Z + (size_t)ps[p].j * bt->hs[p]->n))) return rc;
     }
     // ---- per-problem Arnoldi step ----

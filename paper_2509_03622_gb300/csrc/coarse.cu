@@ -32,6 +32,7 @@
 #include <math.h>
 #include <vector>
 #include <cusolverDn.h>
+#include <cuda_fp16.h>
 #include "ctx.cuh"
 #include "nno.cuh"
 #include "local.cuh"
@@ -46,7 +47,7 @@ struct CoarseData {
   double2* C = nullptr;      // [n_win][9][320][k]   (set-up only)
   double2* G = nullptr;      // [n_win][9][k][k]     Galerkin blocks, FP64
   float2* Gf = nullptr;      // [n_win][9][k][k]     FP32 copy used by the sweeps
-  float2* Sinv = nullptr;    // [nwy][D][D]          row-major S_b^-1
+  __half2* Sinv = nullptr;   // [nwy][D][D]          row-major S_b^-1, complex half (re, im)
   float2* rcf = nullptr;     // [nc] right-hand side -Q^H e_bc
   float2* ycf = nullptr;     // [nc] forward sweep
   float2* zcf = nullptr;     // [nc] coarse solution
@@ -321,6 +322,11 @@ __global__ void __launch_bounds__(256) schur_update_kernel(float2* __restrict__ 
   }
 }
 
+__global__ void nonfinite_kernel(const float2* __restrict__ a, size_t n, int* flag) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(a[e].x) || !isfinite(a[e].y)) { atomicExch(flag, 1); return; }
+}
+
 __global__ void identity_kernel(float2* X, int D) {
   const size_t n = (size_t)D * D;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
@@ -374,22 +380,36 @@ __global__ void __launch_bounds__(256) sweep_t_kernel(float2* __restrict__ t, co
   if (lane == 0) t[row] = r ? make_float2(r[row].x - sr, r[row].y - si) : make_float2(sr, si);
 }
 
-// out = base + sgn * A t for a row-major D x D complex matrix A (warp per
-// row, two complex numbers per 16-byte load); base may be NULL.
+// out = base + sgn * A t for a row-major D x D complex matrix A stored as
+// complex half (warp per row, four complex entries per 16-byte load, FP32
+// products and sums); base may be NULL.
 __global__ void __launch_bounds__(256) gemv_rows_kernel(float2* __restrict__ out, const float2* __restrict__ base,
-                                                        const float2* __restrict__ A, const float2* __restrict__ t,
+                                                        const __half2* __restrict__ A, const float2* __restrict__ t,
                                                         int D, float sgn) {
   const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= D) return;
-  const float4* a4 = reinterpret_cast<const float4*>(A + (size_t)row * D);
+  const __half2* a = A + (size_t)row * D;
+  const uint4* a4 = reinterpret_cast<const uint4*>(a);
   const float4* t4 = reinterpret_cast<const float4*>(t);
   float sr = 0.f, si = 0.f;
-  const int n4 = D / 2;
-#pragma unroll 8
+  // 16-byte loads need every row 16-byte aligned (D a multiple of 4);
+  // otherwise the scalar loop below takes the whole row
+  const int n4 = (D & 3) ? 0 : D / 4;
+#pragma unroll 4
   for (int j = lane; j < n4; j += 32) {
-    const float4 m = __ldcs(a4 + j), v = __ldg(t4 + j);
-    sr += m.x * v.x - m.y * v.y + m.z * v.z - m.w * v.w;
-    si += m.x * v.y + m.y * v.x + m.z * v.w + m.w * v.z;
+    const uint4 m = __ldcs(a4 + j);
+    const float4 v0 = __ldg(t4 + 2 * j), v1 = __ldg(t4 + 2 * j + 1);
+    const float2 m0 = __half22float2(*reinterpret_cast<const __half2*>(&m.x));
+    const float2 m1 = __half22float2(*reinterpret_cast<const __half2*>(&m.y));
+    const float2 m2 = __half22float2(*reinterpret_cast<const __half2*>(&m.z));
+    const float2 m3 = __half22float2(*reinterpret_cast<const __half2*>(&m.w));
+    sr += m0.x * v0.x - m0.y * v0.y + m1.x * v0.z - m1.y * v0.w + m2.x * v1.x - m2.y * v1.y + m3.x * v1.z - m3.y * v1.w;
+    si += m0.x * v0.y + m0.y * v0.x + m1.x * v0.w + m1.y * v0.z + m2.x * v1.y + m2.y * v1.x + m3.x * v1.w + m3.y * v1.z;
+  }
+  for (int j = 4 * n4 + lane; j < D; j += 32) {  // D not a multiple of 4
+    const float2 m = __half22float2(a[j]), v = t[j];
+    sr += m.x * v.x - m.y * v.y;
+    si += m.x * v.y + m.y * v.x;
   }
   for (int o = 16; o > 0; o >>= 1) {
     sr += __shfl_xor_sync(0xffffffffu, sr, o);
@@ -398,6 +418,18 @@ __global__ void __launch_bounds__(256) gemv_rows_kernel(float2* __restrict__ out
   if (lane == 0) {
     const float2 b0 = base ? base[row] : make_float2(0.f, 0.f);
     out[row] = make_float2(b0.x + sgn * sr, b0.y + sgn * si);
+  }
+}
+
+__global__ void to_half_kernel(__half2* dst, const float2* src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = __floats2half2_rn(src[i].x, src[i].y);
+}
+
+__global__ void nonfinite_half_kernel(const __half2* __restrict__ a, size_t n, int* flag) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = __half22float2(a[e]);
+    if (!isfinite(v.x) || !isfinite(v.y)) { atomicExch(flag, 1); return; }
   }
 }
 
@@ -581,17 +613,17 @@ done:
 static int factor_rows(fdfd_ctx* h, CoarseData* c) {
   const int k = c->k, nwx = c->nwx, nwy = c->nwy, D = c->D;
   cudaStream_t s = h->stream;
-  float2 *S = nullptr, *T = nullptr;
+  float2 *S = nullptr, *T = nullptr, *X = nullptr;  // X: this row's inverse in FP32 (the next update reads it)
   int *ipiv = nullptr, *info = nullptr;
   cuComplex* work = nullptr;
   cusolverDnHandle_t sh = nullptr;
   size_t tb = 0;
   int rc = FDFD_OK, lwork = 0;
-  std::vector<int> hinfo(2 * nwy, 0);
+  std::vector<int> hinfo(2 * nwy + 1, 0);  // getrf / getrs info per row, then the FP32 non-finite flag
   const size_t DD = (size_t)D * D;
   const dim3 tile((D + 255) / 256, (D + RT - 1) / RT);
-  if ((rc = ca(&S, DD, &tb)) || (rc = ca(&T, DD, &tb)) || (rc = ca(&ipiv, (size_t)D, &tb)) ||
-      (rc = ca(&info, (size_t)2 * nwy, &tb)))
+  if ((rc = ca(&S, DD, &tb)) || (rc = ca(&T, DD, &tb)) || (rc = ca(&X, DD, &tb)) || (rc = ca(&ipiv, (size_t)D, &tb)) ||
+      (rc = ca(&info, (size_t)2 * nwy + 1, &tb)))
     goto done;
   if (cusolverDnCreate(&sh) != CUSOLVER_STATUS_SUCCESS || cusolverDnSetStream(sh, s) != CUSOLVER_STATUS_SUCCESS ||
       cusolverDnCgetrf_bufferSize(sh, D, D, reinterpret_cast<cuComplex*>(S), D, &lwork) != CUSOLVER_STATUS_SUCCESS) {
@@ -599,23 +631,36 @@ static int factor_rows(fdfd_ctx* h, CoarseData* c) {
     goto done;
   }
   if ((rc = ca(&work, (size_t)(lwork > 0 ? lwork : 1), &tb))) goto done;
+  if (cudaMemsetAsync(info + 2 * nwy, 0, sizeof(int), s) != cudaSuccess) { rc = FDFD_ECUDA; goto done; }
   for (int b = 0; b < nwy; ++b) {
-    float2* Sinv_b = c->Sinv + (size_t)b * DD;
     build_S_kernel<<<2048, 256, 0, s>>>(S, c->Gf, k, nwx, b);
-    if (b > 0) {
-      schur_T_kernel<<<tile, 256, 0, s>>>(T, c->Sinv + (size_t)(b - 1) * DD, c->Gf, k, nwx, b);
+    if (b > 0) {  // X holds S_{b-1}^-1 in FP32
+      schur_T_kernel<<<tile, 256, 0, s>>>(T, X, c->Gf, k, nwx, b);
       schur_update_kernel<<<tile, 256, 0, s>>>(S, T, c->Gf, k, nwx, b);
     }
-    identity_kernel<<<2048, 256, 0, s>>>(Sinv_b, D);
+    identity_kernel<<<2048, 256, 0, s>>>(X, D);
     if (cudaGetLastError() != cudaSuccess ||
         cusolverDnCgetrf(sh, D, D, reinterpret_cast<cuComplex*>(S), D, work, ipiv, info + 2 * b) !=
             CUSOLVER_STATUS_SUCCESS ||
         cusolverDnCgetrs(sh, CUBLAS_OP_N, D, D, reinterpret_cast<const cuComplex*>(S), D, ipiv,
-                         reinterpret_cast<cuComplex*>(Sinv_b), D, info + 2 * b + 1) != CUSOLVER_STATUS_SUCCESS) {
+                         reinterpret_cast<cuComplex*>(X), D, info + 2 * b + 1) != CUSOLVER_STATUS_SUCCESS) {
       rc = FDFD_ECUDA;
       goto done;
     }
+    // a Schur complement that is numerically singular leaves non-finite or
+    // overflowing entries in its inverse; flag them instead of solving with them
+    nonfinite_kernel<<<1024, 256, 0, s>>>(X, DD, info + 2 * nwy);
+    to_half_kernel<<<2048, 256, 0, s>>>(c->Sinv + (size_t)b * DD, X, DD);  // the stored copy the sweeps read
   }
+  if (cudaMemsetAsync(ipiv, 0, sizeof(int), s) != cudaSuccess) { rc = FDFD_ECUDA; goto done; }
+  nonfinite_half_kernel<<<4096, 256, 0, s>>>(c->Sinv, (size_t)nwy * DD, ipiv);  // beyond the half range
+  nonfinite_kernel<<<1024, 256, 0, s>>>(c->Gf, (size_t)nwx * nwy * 9 * k * k, ipiv);
+  if (cudaMemcpyAsync(hinfo.data(), ipiv, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    rc = FDFD_ECUDA;
+    goto done;
+  }
+  if (hinfo[0]) { rc = FDFD_ENUMERIC; goto done; }
   if (cudaMemcpyAsync(hinfo.data(), info, hinfo.size() * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     rc = FDFD_ECUDA;
@@ -626,7 +671,7 @@ static int factor_rows(fdfd_ctx* h, CoarseData* c) {
 done:
   cudaStreamSynchronize(s);
   if (sh) cusolverDnDestroy(sh);
-  void* tmp[] = {S, T, ipiv, info, work};
+  void* tmp[] = {S, T, X, ipiv, info, work};
   for (void* p : tmp) if (p) cudaFree(p);
   return rc;
 }
@@ -655,7 +700,7 @@ int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, 
   cudaStream_t s = h->stream;
   trials_gs_kernel<<<n_win, 256, 0, s>>>(c->Q, c->Qf, k, h->eps, h->k0dx, h->nx, h->ny, nwx, n_win);
   CKL();
-  GridGeom g{h->nx, h->ny, nwx, (float)h->k2, h->eps, h->isx, h->isy};
+  GridGeom g{h->nx, h->ny, nwx, (float)h->k2, h->eps, h->isx, h->isy, schwarz_modulation(h)};
   float2* rhs = nullptr;
   if (L && (rc = ca(&rhs, (size_t)n_win * 6400, bytes))) { coarse_free(c); return rc; }
   for (int m = 0; m < k; ++m) {

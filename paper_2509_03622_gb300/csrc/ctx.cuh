@@ -96,3 +96,5 @@ struct NnoWeights;
 const NnoWeights* schwarz_weights(fdfd_ctx* h);  // nullptr before schwarz_setup
 int schwarz_info(fdfd_ctx* h, fdfd_info* info);
 int schwarz_dfty_variant(fdfd_ctx* h);  // the DFT-y GEMM variant autotuned at set-up
+// Per-window modulation of the modified FNO ([n_win][4][512]), nullptr if none.
+const float* schwarz_modulation(fdfd_ctx* h);

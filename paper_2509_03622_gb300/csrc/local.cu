@@ -18,6 +18,9 @@
 
 namespace {
 
+constexpr double kTiny = 1e-30;  // below this a window norm counts as zero
+
+
 constexpr int LT = 256;
 constexpr int NP = FDFD_WIN * FDFD_WIN;
 
@@ -106,7 +109,10 @@ __global__ void __launch_bounds__(LT) local_start_kernel(const float2* __restric
     const double beta = sqrt(t);
     s.beta = beta;
     s.g[0] = make_double2(beta, 0.0);
-    s.vscale[0] = beta > 0 ? 1.0 / beta : 0.0;
+    // the outer solve's vectors are O(1) overall; a window whose restriction is
+    // below kTiny carries nothing of weight and its 1/beta would leave the FP32
+    // range of the network's scaling, so it is treated as empty
+    s.vscale[0] = beta > kTiny ? 1.0 / beta : 0.0;
     s.k = 0;
   }
 }
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
     const double2 gj = s.g[j];
     s.g[j + 1] = zmul(make_double2(-sn.x, sn.y), gj);
     s.g[j] = make_double2(c * gj.x, c * gj.y);
-    s.vscale[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    s.vscale[j + 1] = hn > kTiny ? 1.0 / hn : 0.0;
     s.k = j + 1;
   }
 }
@@ -258,7 +264,7 @@ int local_fgmres(fdfd_ctx* h, LocalWork* L, const NnoWeights* W, NnoWork* work, 
   const AxisCoef* lcy = transpose ? h->cyT : h->cy;
   const size_t ld = (size_t)n * NP;
   cudaStream_t s = h->stream;
-  GridGeom g{h->nx, h->ny, nwx, (float)h->k2, h->eps, h->isx, h->isy};
+  GridGeom g{h->nx, h->ny, nwx, (float)h->k2, h->eps, h->isx, h->isy, schwarz_modulation(h)};
   int rc;
   {
     ProfScope ps(h, 4, 1);

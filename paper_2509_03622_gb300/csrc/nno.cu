@@ -1591,7 +1591,9 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(const __grid_consta
       tc::fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(acc_empty(a));  // columns read: the first MMA may reuse them
-      const float f = rho * (float)sc * (float)sw;
+      // product in FP64: a window scale beyond the FP32 range (a window whose
+      // data is minute) must not turn a zero rho into 0 x Inf
+      const float f = (float)((double)rho * sc * sw);
       const float2 val = make_float2((o2[0] + lin[0] + P.p2b0) * f, (o2[1] + lin[1] + P.p2b1) * f);
       const int m = (u % UPW) * 128 + px;
       if (P.e_win) {
@@ -1667,9 +1669,15 @@ int up(T** dst, const std::vector<T>& v, size_t* bytes) {
 
 }  // namespace
 
-int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t* bytes) {
-  const size_t expect = 32 * 15 + 32 + 4 * (2 * 32 * 32 * 512 + 32 * 32 + 32) + 128 * 32 + 128 + 2 * 128 + 2;
-  if (!blob || nfloats != expect) return FDFD_EINVAL;
+size_t nno_blob_floats(int rank, int modulation) {
+  const size_t rblk = rank ? (size_t)2 * 32 * 32 * rank + (size_t)2 * rank * 512 : (size_t)2 * 32 * 32 * 512;
+  return 32 * 15 + 32 + 4 * (rblk + 32 * 32 + 32) + 128 * 32 + 128 + 2 * 128 + 2 +
+         (modulation ? 16 * 5 * 9 + 16 + (size_t)2048 * 144 + 2048 : 0);
+}
+
+int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, int rank, int modulation, size_t* bytes) {
+  if (rank < 0 || rank > 512) return FDFD_EINVAL;
+  if (!blob || nfloats != nno_blob_floats(rank, modulation)) return FDFD_EINVAL;
   const float* p = blob;
   int rc;
   {  // lift [32][15] -> [32][16]
@@ -1713,10 +1721,35 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
         (rc = up(&W->Gy, to_bf16(gy), bytes)) || (rc = up(&W->Gx, to_bf16(gx), bytes)))
       return rc;
   }
+  const float *w0p = nullptr, *b0p = nullptr;
+  std::vector<float> Rx;  // a block's R expanded from its rank-r factors
   for (int bl = 0; bl < 4; ++bl) {
     const float* Rr = p;
     const float* Ri = p + 32 * 32 * 512;
-    p += 2 * 32 * 32 * 512;
+    if (rank) {  // R[o][c][md] = sum_r theta[o][c][r] V[r][md], complex, FP64 sums
+      const float* tr = p;
+      const float* ti = tr + 32 * 32 * rank;
+      const float* vr = ti + 32 * 32 * rank;
+      const float* vi = vr + rank * 512;
+      p = vi + rank * 512;
+      Rx.assign((size_t)2 * 32 * 32 * 512, 0.f);
+      for (int oc = 0; oc < 32 * 32; ++oc)
+        for (int md = 0; md < 512; ++md) {
+          double re = 0.0, im = 0.0;
+          for (int r = 0; r < rank; ++r) {
+            const double a = tr[oc * rank + r], b = ti[oc * rank + r];
+            const double c = vr[r * 512 + md], d = vi[r * 512 + md];
+            re += a * c - b * d;
+            im += a * d + b * c;
+          }
+          Rx[(size_t)oc * 512 + md] = (float)re;
+          Rx[(size_t)32 * 32 * 512 + oc * 512 + md] = (float)im;
+        }
+      Rr = Rx.data();
+      Ri = Rx.data() + 32 * 32 * 512;
+    } else {
+      p += 2 * 32 * 32 * 512;
+    }
     std::vector<float> R(512 * 64 * 64);  // tiled per mode (r_off)
     for (int q = 0; q < 32; ++q)
       for (int kx = 0; kx < 16; ++kx) {
@@ -1729,6 +1762,7 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
           }
       }
     if ((rc = up(&W->R[bl], to_bf16(R), bytes))) return rc;
+    if (bl == 0) { w0p = p; b0p = p + 1024; }
     if ((rc = up(&W->W[bl], to_bf16(std::vector<float>(p, p + 1024)), bytes))) return rc;
     p += 1024;
     if ((rc = up(&W->bias[bl], std::vector<float>(p, p + 32), bytes))) return rc;
@@ -1737,8 +1771,8 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
   {  // block 0's residual path from the inputs: W0 L [32][16] and W0 l_b + b_0
     const float* lw = blob;
     const float* lb = blob + 32 * 15;
-    const float* w0 = blob + 32 * 15 + 32 + 2 * 32 * 32 * 512;
-    const float* b0 = w0 + 32 * 32;
+    const float* w0 = w0p;
+    const float* b0 = b0p;
     std::vector<float> wl(32 * 16, 0.f), bl0(32);
     for (int o = 0; o < 32; ++o) {
       double accb = b0[o];
@@ -1774,12 +1808,25 @@ int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t*
     p += 128 * 32 + 128 + 256;
     W->p2b[0] = (float)(p[0] + cb[0]);
     W->p2b[1] = (float)(p[1] + cb[1]);
+    p += 2;
+  }
+  if (modulation) {  // the modulation path, FP32
+    const size_t nc = 16 * 5 * 9, nfc = (size_t)2048 * 144;
+    if ((rc = up(&W->mod_conv_w, std::vector<float>(p, p + nc), bytes))) return rc;
+    p += nc;
+    if ((rc = up(&W->mod_conv_b, std::vector<float>(p, p + 16), bytes))) return rc;
+    p += 16;
+    if ((rc = up(&W->mod_fc_w, std::vector<float>(p, p + nfc), bytes))) return rc;
+    p += nfc;
+    if ((rc = up(&W->mod_fc_b, std::vector<float>(p, p + 2048), bytes))) return rc;
+    W->mod = true;
   }
   return FDFD_OK;
 }
 
 void nno_free_weights(NnoWeights* W) {
-  void* ptrs[] = {W->lift_w, W->lift_b, W->Fx, W->Fy, W->Gy, W->Gx, W->P1, W->qinv, W->P18, W->W0L, W->bias0L};
+  void* ptrs[] = {W->lift_w, W->lift_b, W->Fx, W->Fy, W->Gy, W->Gx, W->P1, W->qinv, W->P18, W->W0L, W->bias0L,
+                  W->mod_conv_w, W->mod_conv_b, W->mod_fc_w, W->mod_fc_b};
   for (void* q : ptrs) if (q) cudaFree(q);
   for (int b = 0; b < 4; ++b) {
     if (W->R[b]) cudaFree(W->R[b]);
@@ -1827,6 +1874,87 @@ __global__ void absmax_kernel(const bf16* X, size_t n_elem, unsigned* out) {
   }
   __syncthreads();
   if (threadIdx.x < 32) atomicMax(&out[threadIdx.x], m[threadIdx.x]);
+}
+
+// Modulation path (modified FNO, Sec. 2.1, Fig. 2) of every window, once per
+// set-up: one CTA per window.  Each of the 144 pooled features (channel o,
+// 3 x 3 cell) averages leaky-ReLU of the 3x3 stride-2 valid convolution over
+// its 13 x 13 outputs; the fully connected layer then gives the 2048
+// modulation values (4 blocks x 512 retained modes).
+__global__ void __launch_bounds__(256) modulation_kernel(const float* __restrict__ cw, const float* __restrict__ cb,
+                                                         const float* __restrict__ fw, const float* __restrict__ fb,
+                                                         GridGeom g, float* __restrict__ out) {
+  __shared__ float feat[144];
+  const int w = blockIdx.x;
+  const int a = w % g.nwx, bb = w / g.nwx;
+  const int x0 = min(max(FDFD_CORE * a - FDFD_OVL, 0), g.nx - FDFD_WIN);
+  const int y0 = min(max(FDFD_CORE * bb - FDFD_OVL, 0), g.ny - FDFD_WIN);
+  for (int f = threadIdx.x; f < 144; f += blockDim.x) {
+    const int o = f / 9, py = (f % 9) / 3, px = f % 3;
+    float sum = 0.f;
+    for (int Y = py * 13; Y < py * 13 + 13; ++Y)
+      for (int X = px * 13; X < px * 13 + 13; ++X) {
+        float acc = cb[o];
+        for (int dy = 0; dy < 3; ++dy) {
+          const int gy = y0 + 2 * Y + dy;
+          const float2 sy = g.isy[gy];
+          for (int dx = 0; dx < 3; ++dx) {
+            const int gx = x0 + 2 * X + dx;
+            const float2 sx = g.isx[gx];
+            const float* k = cw + ((o * 5) * 3 + dy) * 3 + dx;  // [o][c][dy][dx], c stride 9
+            acc += k[0] * (g.k2 * g.eps[(size_t)gy * g.nx + gx]) + k[9] * sx.x + k[18] * sx.y + k[27] * sy.x +
+                   k[36] * sy.y;
+          }
+        }
+        sum += acc >= 0.f ? acc : 0.01f * acc;
+      }
+    feat[f] = sum * (1.f / 169.f);
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < 2048; m += blockDim.x) {
+    const float* row = fw + (size_t)m * 144;
+    float acc = fb[m];
+    for (int f = 0; f < 144; ++f) acc += row[f] * feat[f];
+    out[(size_t)w * 2048 + m] = acc;
+  }
+}
+
+// R*_b = R_b (1 + mod_b): the modulation is real and the same for every
+// channel pair, so it scales row (mode, entry) of the retained spectrum Xh
+// (64 BF16 values, one 16-byte chunk per thread) before the mixing.
+__global__ void mod_scale_kernel(bf16* __restrict__ Xh, int rows, int n, NnoInput in, GridGeom g, int bl) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)512 * n * 8) return;
+  const int chunk = (int)(t & 7);
+  const size_t r = t >> 3;
+  const int b = (int)(r % n), md = (int)(r / n);
+  const float* mod = g.mod;
+  int w = in.win_id ? in.win_id[b] : b;
+  if (in.ptab) {
+    const int2 e = in.wtab[b];
+    mod = in.ptab[e.x].mod;
+    w = e.y;
+  }
+  if (!mod) return;
+  const float f = 1.f + mod[((size_t)w * 4 + bl) * 512 + md];
+  uint4* q = reinterpret_cast<uint4*>(Xh + ((size_t)md * rows + b) * 64) + chunk;
+  uint4 v = *q;
+  uint32_t* u = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    __nv_bfloat162 h2 = *reinterpret_cast<__nv_bfloat162*>(&u[i]);
+    float2 x = __bfloat1622float2(h2);
+    h2 = __floats2bfloat162_rn(x.x * f, x.y * f);
+    u[i] = *reinterpret_cast<uint32_t*>(&h2);
+  }
+  *q = v;
+}
+
+int nno_modulation(const NnoWeights* W, const GridGeom& g, int n_win, float* out, cudaStream_t s) {
+  if (!W->mod) return FDFD_EINVAL;
+  modulation_kernel<<<n_win, 256, 0, s>>>(W->mod_conv_w, W->mod_conv_b, W->mod_fc_w, W->mod_fc_b, g, out);
+  CKL();
+  return FDFD_OK;
 }
 
 // Spectral mixing of all n windows into the window-major layout G4 reads.
@@ -1979,6 +2107,12 @@ int nno_forward(const NnoWeights* W, NnoWork* k, const GridGeom& g, const NnoInp
     {
       ProfScope ps(h, 10, 1);
       if ((rc = launch_g2(k, W, n, k->g2_split, s))) return rc;
+    }
+    if (W->mod) {  // modified FNO: per-window, per-mode modulation of R
+      ProfScope ps(h, 11, 1);
+      const size_t tot = (size_t)512 * n * 8;
+      mod_scale_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(k->Xh, xh_rows(k->cap), n, in, g, bl);
+      CKL();
     }
     {
       ProfScope ps(h, 11, 1);

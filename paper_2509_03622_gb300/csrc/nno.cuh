@@ -29,6 +29,14 @@ struct NnoWeights {
   float* qinv = nullptr;    // [5][32]  1 / s[b][c], used by the writers
   bf16* W8[4] = {};         // [32 o][32 c]  W[b] diag(s[b])
   bf16* P18 = nullptr;      // [144][32]     P1 (extended as above) diag(s[4])
+  // Modulation path of the modified FNO (Sec. 2.1, Fig. 2), FP32: 3x3
+  // stride-2 valid convolution of the five auxiliary channels to 16, leaky-
+  // ReLU, 13x13 average pooling (3 x 3 cells), fully connected 144 -> 2048.
+  bool mod = false;
+  float* mod_conv_w = nullptr;  // [16][5][3][3]
+  float* mod_conv_b = nullptr;  // [16]
+  float* mod_fc_w = nullptr;    // [2048][144]
+  float* mod_fc_b = nullptr;    // [2048]
 };
 
 // Rows of the spectrum per mode: the windows rounded up to a whole 8-row
@@ -79,6 +87,7 @@ struct ProbGeom {
   const float2* v;       // preconditioner input field of this problem
   float2* z;             // output field (restricted prolongation)
   const double* scale;   // output scale (device scalar)
+  const float* mod;      // this problem's per-window modulation [n_win][4][512] or nullptr
 };
 
 // Where the packed inputs come from.
@@ -107,9 +116,19 @@ struct GridGeom {
   const float* eps;
   const float2* isx;
   const float2* isy;
+  const float* mod;                  // per-window modulation [n_win][4][512] (modified FNO) or nullptr
 };
 
-int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, size_t* bytes);
+// Blob layout (include/fdfd.h): rank > 0 gives each block's R as rank-r
+// factors (expanded here, in FP64, into the tiled R); modulation appends the
+// modulation path's weights.
+int nno_upload_weights(NnoWeights* W, const float* blob, size_t nfloats, int rank, int modulation,
+                       size_t* bytes);
+// Floats in a weight blob of that layout.
+size_t nno_blob_floats(int rank, int modulation);
+// The modulation of every window of a grid, once per set-up (it depends on
+// the permittivity and PML maps only): out [n_win][4][512].
+int nno_modulation(const NnoWeights* W, const GridGeom& g, int n_win, float* out, cudaStream_t s);
 void nno_free_weights(NnoWeights* W);
 int nno_alloc_work(NnoWork* w, int cap, size_t* bytes);
 // Autotuner: time the variants of the shape-dependent stage (the DFT-y

@@ -118,7 +118,7 @@ extern "C" int fdfd_nno_solve_noalloc(fdfd_handle h, const fdfd_c64* r_win, cons
   in.win_id = win_id;
   NnoOutput out;
   out.e_win = reinterpret_cast<float2*>(e_win);
-  GridGeom g{h->nx, h->ny, h->nx / FDFD_CORE, (float)h->k2, h->eps, h->isx, h->isy};
+  GridGeom g{h->nx, h->ny, h->nx / FDFD_CORE, (float)h->k2, h->eps, h->isx, h->isy, schwarz_modulation(h)};
   if ((rc = nno_forward(W, &k, g, in, out, n, h->stream, nullptr))) return rc;
   int e = 0;
   CK(cudaMemcpyAsync(&e, k.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));

@@ -20,6 +20,7 @@ struct SchwarzData {
   NnoWork work;
   LocalWork local;
   CoarseData* coarse = nullptr;
+  float* mod = nullptr;  // per-window modulation [n_win][4][512] of the modified FNO, or nullptr
   size_t bytes = 0;
 };
 
@@ -82,8 +83,10 @@ int schwarz_traces(fdfd_ctx* h, const float2* u, float2* g) {
   return FDFD_OK;
 }
 
+const float* schwarz_modulation(fdfd_ctx* h) { return (h && h->sw) ? h->sw->mod : nullptr; }
+
 static GridGeom geom(fdfd_ctx* h) {
-  return GridGeom{h->nx, h->ny, h->nx / FDFD_CORE, (float)h->k2, h->eps, h->isx, h->isy};
+  return GridGeom{h->nx, h->ny, h->nx / FDFD_CORE, (float)h->k2, h->eps, h->isx, h->isy, schwarz_modulation(h)};
 }
 
 // Seeded uniform complex field in [-1, 1)^2 (counter-based splitmix64), the
@@ -120,12 +123,20 @@ int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd) {
   if (sd->k_coarse < 0 || sd->k_coarse > 256) return FDFD_EINVAL;
   if (sd->precision != FDFD_PREC_BF16 && sd->precision != FDFD_PREC_FP8) return FDFD_EINVAL;
   if (sd->inner_iters < 0 || sd->inner_iters > LOCAL_MAXM) return FDFD_EINVAL;
+  if (sd->r_rank < 0 || sd->r_rank > 512 || (sd->modulation != 0 && sd->modulation != 1)) return FDFD_EINVAL;
+  // the FP8 calibration folds scales into the plain network's weights only
+  if ((sd->r_rank || sd->modulation) && sd->precision == FDFD_PREC_FP8) return FDFD_EINVAL;
   SchwarzData* S = new SchwarzData();
   S->nwx = h->nx / FDFD_CORE;
   S->n_win = S->nwx * (h->ny / FDFD_CORE);
   S->precision = sd->precision;
   S->inner = sd->inner_iters;
-  int rc = nno_upload_weights(&S->W, sd->weights, sd->n_weights, &S->bytes);
+  int rc = nno_upload_weights(&S->W, sd->weights, sd->n_weights, sd->r_rank, sd->modulation, &S->bytes);
+  if (!rc && S->W.mod) {  // modulation of every window: it depends on eps and the PML maps only
+    if (cudaMalloc((void**)&S->mod, (size_t)S->n_win * 2048 * sizeof(float)) != cudaSuccess) rc = FDFD_ENOMEM;
+    else S->bytes += (size_t)S->n_win * 2048 * sizeof(float);
+    if (!rc) rc = nno_modulation(&S->W, geom(h), S->n_win, S->mod, h->stream);
+  }
   if (!rc) rc = nno_alloc_work(&S->work, S->n_win < 64 ? 64 : S->n_win, &S->bytes);
   if (!rc) rc = nno_autotune(&S->W, &S->work, S->n_win, h->stream);
   if (!rc && sd->precision == FDFD_PREC_FP8) {  // calibrate the activation scales on a random residual
@@ -152,6 +163,7 @@ void schwarz_destroy(fdfd_ctx* h) {
   SchwarzData* S = h->sw;
   cudaStreamSynchronize(h->stream);
   if (S->coarse) coarse_free(S->coarse);
+  if (S->mod) cudaFree(S->mod);
   nno_free_weights(&S->W);
   nno_free_work(&S->work);
   local_free(&S->local);

@@ -30,12 +30,13 @@ PREC_BF16, PREC_FP8 = 0, 1
 class Desc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("wavelength", C.c_double),
                 ("npml", C.c_int * 4), ("pml_m", C.c_double), ("pml_lnR", C.c_double),
-                ("eps", C.c_void_p), ("stream", C.c_void_p)]
+                ("eps", C.c_void_p), ("stream", C.c_void_p), ("max_restart", C.c_int)]
 
 
 class SchwarzDesc(C.Structure):
     _fields_ = [("k_coarse", C.c_int), ("precision", C.c_int), ("weights", C.c_void_p),
-                ("n_weights", C.c_size_t), ("inner_iters", C.c_int), ("ritz_tol", C.c_double)]
+                ("n_weights", C.c_size_t), ("inner_iters", C.c_int), ("ritz_tol", C.c_double),
+                ("r_rank", C.c_int), ("modulation", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -157,7 +158,7 @@ class Solver:
     """Owns one fdfd_handle (fdfd_create ... fdfd_destroy)."""
 
     def __init__(self, eps, dx: float, wavelength: float, npml=20, pml_m: float = 3.0,
-                 pml_lnR: float = -30.0, stream=None):
+                 pml_lnR: float = -30.0, stream=None, max_restart: int = 0):
         import torch
         if eps.dtype != torch.float32 or eps.dim() != 2:
             raise TypeError("eps must be a 2D float32 CUDA tensor")
@@ -167,6 +168,7 @@ class Solver:
         np_ = (npml,) * 4 if np.isscalar(npml) else tuple(npml)
         d.npml = (C.c_int * 4)(*np_)
         d.pml_m, d.pml_lnR = pml_m, pml_lnR
+        d.max_restart = int(max_restart)
         d.eps = _ptr(eps).value
         s = stream if stream is not None else torch.cuda.current_stream()
         d.stream = C.c_void_p(s.cuda_stream).value
@@ -197,10 +199,13 @@ class Solver:
         _check(lib.fdfd_set_eps(self.h, _ptr(eps)), "fdfd_set_eps")
 
     def schwarz_setup(self, weights_blob: np.ndarray, k_coarse: int = 0, precision: int = PREC_BF16,
-                      inner_iters: int = 0, ritz_tol: float = 0.0):
+                      inner_iters: int = 0, ritz_tol: float = 0.0, rank: int = 0, modulation: bool = False):
+        """rank, modulation: the layout of the blob (modified FNO; see
+        workloads.weight_order)."""
         blob = np.ascontiguousarray(weights_blob, dtype=np.float32)
         sd = SchwarzDesc()
         sd.k_coarse, sd.precision, sd.inner_iters, sd.ritz_tol = k_coarse, precision, inner_iters, float(ritz_tol)
+        sd.r_rank, sd.modulation = int(rank), int(bool(modulation))
         sd.weights = blob.ctypes.data
         sd.n_weights = blob.size
         _check(lib.schwarz_setup(self.h, C.byref(sd)), "schwarz_setup")
