@@ -234,3 +234,134 @@ def test_dfty_variants_agree(F, monkeypatch):
     for var in ("1", "2"):
         d = np.linalg.norm(outs[var] - outs["0"]) / np.linalg.norm(outs["0"])
         assert d < 5e-3, (var, d)
+
+
+def _bf16_forward(x, w, blocks=4):
+    """The FNO of oracle.nno.forward with BF16 rounding where the GPU path
+    stores BF16: weights, the input channels, every block's input activation,
+    the retained half-spectrum and the mixed spectrum (FP64 arithmetic
+    otherwise).  Isolates the rounding the tensor-core path adds."""
+    rb = _bf16_round
+    rc = lambda z: rb(z.real) + 1j * rb(z.imag)
+    W = {k: rb(v) for k, v in w.items()}
+    h = ON.pointwise(W["lift_w"], W["lift_b"], rb(x))
+    rows = ON.retained_rows(80)
+    for b in range(blocks):
+        h = rb(h)
+        R = W[f"R{b}_re"] + 1j * W[f"R{b}_im"]
+        H = np.fft.rfft2(h, axes=(-2, -1))
+        Hk = rc(H[:, rows, :ON.MX])
+        Y = rc(np.einsum("oiyx,iyx->oyx", R, Hk))
+        Yf = np.zeros((32, 80, 41), dtype=np.complex128)
+        Yf[:, rows, :ON.MX] = Y
+        h = np.fft.irfft2(Yf, s=(80, 80), axes=(-2, -1)) + ON.pointwise(W[f"W{b}"], W[f"b{b}"], h)
+        if b < blocks - 1:
+            h = ON.leaky(h)
+    q = ON.leaky(ON.pointwise(W["p1_w"], W["p1_b"], rb(h)))
+    return ON.pointwise(W["p2_w"], W["p2_b"], rb(q))
+
+
+@pytest.mark.parametrize("seed_w", [0, 1])
+def test_nno_rounding_model(F, seed_w):
+    """The GPU neural solve against the BF16-rounding model of the same
+    network: a tighter bound (1.2e-2) than against the FP64 network, which
+    stays the outer bound (BF16_TOL)."""
+    import torch
+    S, eps, dx, w = _setup(F, seed_w=seed_w)
+    n = 256
+    win = OP.Windows(n, n)
+    sxn, _, syn, _ = OF.pml_factors(n, n, dx, LAM, 20)
+    k2 = OF.k0dx_of(dx, LAM) ** 2
+    ids = np.array([0, 5, 6, 15], dtype=np.int32)
+    g = wl.rng(70 + seed_w)
+    r = (g.standard_normal((len(ids), 80, 80)) + 1j * g.standard_normal((len(ids), 80, 80))).astype(np.complex64)
+    gb = np.zeros((len(ids), 4, 80), np.complex64)
+    e = torch.empty((len(ids), 80, 80), dtype=torch.complex64, device="cuda")
+    S.nno_solve(_t(r), _t(gb), _t(ids), e)
+    got = e.cpu().numpy()
+    e_model, e_fp64 = [], []
+    for i, wi in enumerate(ids):
+        x0, y0 = win.x0[wi], win.y0[wi]
+        args = (k2 * eps[y0:y0 + 80, x0:x0 + 80].astype(float), 1 / sxn[x0:x0 + 80], 1 / syn[y0:y0 + 80])
+        x, rho = ON.pack_inputs(r[i], gb[i], *args)
+        out = _bf16_forward(x, w)
+        ref_model = rho * (out[0] + 1j * out[1])
+        ref = ON.solve(r[i], gb[i], *args, w)
+        e_model.append(np.linalg.norm(got[i] - ref_model) / np.linalg.norm(ref_model))
+        e_fp64.append(np.linalg.norm(got[i] - ref) / np.linalg.norm(ref))
+    print(f"seed {seed_w}: vs BF16 model {max(e_model):.2e}, vs FP64 {max(e_fp64):.2e}")
+    assert max(e_fp64) < BF16_TOL
+    assert max(e_model) < 1.2e-2, e_model
+
+
+def _modified(seed=5, rank=16):
+    w = wl.nno_weights(seed, rank=rank, modulation=True)
+    w["mod_fc_w"] *= 20.0  # a modulation of order 0.1-1, well away from the plain network
+    return w
+
+
+def test_modified_fno_nno_solve_matches_oracle(F):
+    """Modified FNO (Sec. 2.1): rank-16 R expanded at set-up and the
+    per-window modulation computed on the GPU, against the oracle on windows
+    of every kind (corners in the PML, edge, interior)."""
+    import torch
+    n, dx = 256, LAM / 25
+    eps = wl.rectangles_eps(n, n, seed=1000)
+    w = _modified()
+    S = F.Solver(_t(eps), dx, LAM, npml=20)
+    S.schwarz_setup(wl.pack_weights(w), rank=16, modulation=True)
+    win = OP.Windows(n, n)
+    sxn, _, syn, _ = OF.pml_factors(n, n, dx, LAM, 20)
+    k2 = OF.k0dx_of(dx, LAM) ** 2
+    ids = np.array([0, 3, 5, 10, 15], dtype=np.int32)
+    g = wl.rng(17)
+    r = (g.standard_normal((len(ids), 80, 80)) + 1j * g.standard_normal((len(ids), 80, 80))).astype(np.complex64)
+    gb = (g.standard_normal((len(ids), 4, 80)) + 1j * g.standard_normal((len(ids), 4, 80))).astype(np.complex64)
+    e = torch.empty((len(ids), 80, 80), dtype=torch.complex64, device="cuda")
+    S.nno_solve(_t(r), _t(gb), _t(ids), e)
+    got = e.cpu().numpy()
+    mods = []
+    for i, wi in enumerate(ids):
+        x0, y0 = win.x0[wi], win.y0[wi]
+        args = (k2 * eps[y0:y0 + 80, x0:x0 + 80].astype(float), 1 / sxn[x0:x0 + 80], 1 / syn[y0:y0 + 80])
+        ref = ON.solve(r[i], gb[i], *args, w)
+        x, _ = ON.pack_inputs(r[i], gb[i], *args)
+        mods.append(np.abs(ON.modulation(x, w)).max())
+        err = np.linalg.norm(got[i] - ref) / np.linalg.norm(ref)
+        assert err < BF16_TOL, (wi, err)
+    assert max(mods) > 0.05  # the modulation is really exercised
+    S.close()
+
+
+def test_modified_fno_precond_matches_oracle(F):
+    """The two-level sweep (k = 4) with the modified FNO as local solver:
+    the coarse set-up's homogeneous solves use the same modulation."""
+    import torch
+    n, dx = 256, LAM / 25
+    eps = wl.rectangles_eps(n, n, seed=1000)
+    w = _modified(6)
+    S = F.Solver(_t(eps), dx, LAM, npml=20)
+    S.schwarz_setup(wl.pack_weights(w), k_coarse=4, rank=16, modulation=True)
+    O = OS.Schwarz(eps, dx, LAM, 20, weights=w, k_coarse=4)
+    v = wl.random_field(n, n, 19)
+    z = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    S.precond_apply(_t(v), z)
+    ref = O.apply(v.astype(np.complex128))
+    err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < BF16_TOL, err
+    S.close()
+
+
+def test_modified_fno_rejects_fp8_and_bad_layouts(F):
+    n, dx = 256, LAM / 25
+    eps = wl.rectangles_eps(n, n, seed=1000)
+    w = _modified()
+    S = F.Solver(_t(eps), dx, LAM, npml=20)
+    blob = wl.pack_weights(w)
+    for kw in (dict(rank=16, modulation=True, precision=F.PREC_FP8),  # FP8 folds plain weights only
+               dict(rank=8, modulation=True),                          # blob size does not match rank 8
+               dict(rank=16, modulation=False)):                       # nor a blob without the path
+        with pytest.raises(F.FDFDError) as ex:
+            S.schwarz_setup(blob, **kw)
+        assert ex.value.code == F.EINVAL
+    S.close()
