@@ -6,14 +6,14 @@ Preconditioner: the two-level Schwarz sweep (restriction, batched neural
 local solves, restricted prolongation, Robin traces, Galerkin coarse solve
 and correction).
 
-* A step is one outer FGMRES(30) iteration of the whole hot path:
+* A step is one outer FGMRES(60) iteration of the whole hot path:
   preconditioner, stencil matvec, CGS orthogonalisation, FP64 Hessenberg
   update.  `value` = Mcell-iterations per second = cells x steps / device
   time of K steps after W warm-up steps.
 * `time_to_1e-6`: full solves from a zero initial guess to true relative
   residual 1e-6 (median of repeats, CUDA events, set-up excluded and
   reported separately), for the Schwarz neural-operator FGMRES and for
-  Jacobi-GMRES(30) on the same GPU; Jacobi-GMRES runs under a time cap and
+  Jacobi-GMRES(60) on the same GPU; Jacobi-GMRES runs under a time cap and
   reports the residual it reached.
 * `--impl reference` times the FP64 CPU oracle's FGMRES (as it stands) on a
   bounded sample of the same recipe.
@@ -114,8 +114,12 @@ G5_T1_BYTES = 160 * 512 * 2                   # next block's half-spectrum, writ
 # one-kernel ncu captures of a smaller case of the same recipe, scaled to a
 # launch by the number of windows it processes (TRAFFIC_SAMPLE names the
 # case).  Empty while no capture of the current kernels exists.
-TRAFFIC_SAMPLE = None
-SMALL_CASE_TRAFFIC = {}
+TRAFFIC_SAMPLE = "freeform 2048^2 (1024 windows), one kernel per capture, caches flushed"
+SMALL_CASE_TRAFFIC = {
+    "nno_idft_x_mix_act": 917700,  # block 0 (698,300) and the three fused blocks (990,800), averaged per launch
+    "nno_proj": 452800,
+    "nno_lift": 128000,            # its block-0 half-spectrum writes are still in L2 when it ends
+}
 # Useful FLOPs per window of each stage (padding excluded).
 NNO_FLOP_PER_WIN = {
     "nno_lift": 6400 * 32 * 15 * 2 + 2560 * 32 * 80 * 2, "nno_dft_x": 2560 * 32 * 80 * 2, "nno_dft_y": 512 * 64 * 160 * 2,
@@ -133,14 +137,14 @@ KERNEL_NAMES = {"stencil": "stencil_c64", "cgs_dots": "cgs_dots_kernel", "cgs_up
 
 def coarse_bytes_per_apply(N, k):
     """Coarse solve and correction, per application on an n x n grid: both
-    row sweeps stream every inverted Schur complement (2 (n/64) D^2 x 8 B,
-    D = (n/64) k), the correction reads every basis field's core (n_win k
-    4096 x 8 B) and updates the field (16 B per cell), the right-hand side
-    reads the trial vectors (n_win k 320 x 8 B)."""
+    row sweeps stream every inverted Schur complement (complex half:
+    2 (n/64) D^2 x 4 B, D = (n/64) k), the correction reads every basis
+    field's core (n_win k 4096 x 8 B) and updates the field (16 B per cell),
+    the right-hand side reads the trial vectors (n_win k 320 x 8 B)."""
     nw1 = int(round((N ** 0.5) / 64))
     D = nw1 * k
     nc = nw1 * nw1 * k
-    return 2.0 * nw1 * D * D * 8 + nc * 4096 * 8 + 16.0 * N + nc * 320 * 8
+    return 2.0 * nw1 * D * D * 4 + nc * 4096 * 8 + 16.0 * N + nc * 320 * 8
 
 
 def algorithmic_bytes(cls, launches, N, steps, k=0, coarse_launches_per_apply=0):
@@ -176,6 +180,11 @@ TRAINED = os.path.join(ROOT, "paper_2509_03622_gb300", "weights", "nno_trained.n
 # trials per window are what the binary eps {1, 12.25} medium needs).
 K_COARSE_DEFAULT = 64
 INNER_DEFAULT = 2
+# FGMRES restart of both arms: on the 4096^2 workload both stall near relres
+# 1e-2, and a restart of 60 lowers that plateau for both (1.30e-2 / 1.31e-2
+# against 1.75e-2 / 1.77e-2 at 30); the Krylov space then holds 121 vectors
+# (16 GB at 4096^2).
+RESTART = 60
 
 
 def load_weights(path=None):
@@ -231,11 +240,11 @@ def cpu_oracle_rate(n_sample, iters, precond, weights=None, k_coarse=0, inner=0,
                        ritz_tol=ritz_tol if k_coarse > 0 else 0.0)
     t1 = time.perf_counter()
     if budget_s:
-        OK.fgmres(lambda v: A @ v, b, precond=M, restart=30, tol=1e-14, max_iters=2)
+        OK.fgmres(lambda v: A @ v, b, precond=M, restart=RESTART, tol=1e-14, max_iters=2)
         per = (time.perf_counter() - t1) / 2
         iters = int(max(2, min(iters, budget_s / max(per, 1e-6))))
         t1 = time.perf_counter()
-    _, info = OK.fgmres(lambda v: A @ v, b, precond=M, restart=30, tol=1e-14, max_iters=iters)
+    _, info = OK.fgmres(lambda v: A @ v, b, precond=M, restart=RESTART, tol=1e-14, max_iters=iters)
     t2 = time.perf_counter()
     iters = info["iters"]
     return n_sample * n_sample * iters / (t2 - t1) / 1e6, t2 - t1, iters
@@ -243,7 +252,7 @@ def cpu_oracle_rate(n_sample, iters, precond, weights=None, k_coarse=0, inner=0,
 
 def workload_name(n, precond):
     return (f"freeform{n}: {n}x{n} grid, lambda/dx=30, eps {{1,12.25}}, npml 20, "
-            f"{'two-level Schwarz-NNO FGMRES(30)' if precond == 'schwarz' else 'Jacobi-GMRES(30)'}")
+            f"{'two-level Schwarz-NNO FGMRES' if precond == 'schwarz' else 'Jacobi-GMRES'}({RESTART})")
 
 
 def design_bench(iters, blob, dev):
@@ -313,7 +322,7 @@ def oracle_preconditioner(args):
 
 
 def run_reference(args):
-    """The oracle's FGMRES(30) with the arm's preconditioner configuration,
+    """The oracle's FGMRES(RESTART) with the arm's preconditioner configuration,
     as it stands, on an n_sample^2 grid of the same recipe: K consecutive
     Arnoldi steps of one solve (so later steps pay for their growing
     Gram-Schmidt), at most as many as fit in about a minute, timed
@@ -324,7 +333,7 @@ def run_reference(args):
                                      ritz_tol=args.ritz_tol)
     cores = os.cpu_count()
     sample = (f"{n_s}x{n_s} grid of the same freeform recipe and preconditioner configuration "
-              f"(k_coarse {k}, inner {inner}), {iters} consecutive FGMRES(30) steps of one solve "
+              f"(k_coarse {k}, inner {inner}), {iters} consecutive FGMRES({RESTART}) steps of one solve "
               f"({args.precond}), {t:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "Mcell-it/s", "n_gpus": args.gpus,
             "steps": iters, "warmup": args.warmup, "ms_per_step": t / max(iters, 1) * 1e3,
@@ -424,12 +433,12 @@ def cpu_baseline(argd):
     rate, t, it = cpu_oracle_rate(ns, 60, args.precond, w, kc_o, inner_o, budget_s=10.0, ritz_tol=args.ritz_tol)
     return {"value": rate, "unit": "Mcell-it/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{ns}x{ns} grid, same recipe and preconditioner configuration (k_coarse {kc_o}, "
-                      f"inner {inner_o}), {it} consecutive FGMRES(30) steps ({args.precond}), {t:.1f} s; "
+                      f"inner {inner_o}), {it} consecutive FGMRES({RESTART}) steps ({args.precond}), {t:.1f} s; "
                       f"run in a separate process while the GPU work ran"}
 
 
 def timed_solve(S, Jd, E, precond, max_iters):
-    """One full solve from E = 0 to true relative residual 1e-6 (FGMRES(30)),
+    """One full solve from E = 0 to true relative residual 1e-6 (FGMRES(RESTART)),
     device time by CUDA events on the solver's stream."""
     import torch
     from paper_2509_03622_gb300 import fdfd as F
@@ -438,7 +447,7 @@ def timed_solve(S, Jd, E, precond, max_iters):
     torch.cuda.synchronize()
     ev0.record(S.stream)
     try:
-        rc, st = S.solve(Jd, E, restart=30, max_iters=max_iters, tol=1e-6, precond=precond)
+        rc, st = S.solve(Jd, E, restart=RESTART, max_iters=max_iters, tol=1e-6, precond=precond)
     except F.FDFDError as ex:  # a hard error ends this solve; report it instead of the numbers
         torch.cuda.synchronize()
         return {"ms": None, "iters": None, "relres": None, "status": str(ex), "converged": False}
@@ -450,7 +459,7 @@ def timed_solve(S, Jd, E, precond, max_iters):
 
 def time_to_solution(S, Jd, E, precond, args):
     """Time to relres 1e-6 of the arm's preconditioner (median of repeats)
-    and of Jacobi-GMRES(30) on the same handle and GPU, the latter capped at
+    and of Jacobi-GMRES(RESTART) on the same handle and GPU, the latter capped at
     max(20 x the Schwarz time, 30 s) but at most --jacobi-cap-s."""
     import statistics
     from paper_2509_03622_gb300 import fdfd as F
@@ -538,7 +547,7 @@ def main():
     n = args.n
     # independent replica per rank (weak scaling): different seed per rank
     eps, J, dx, lam = make_problem(n, seed_off=rank)
-    S = F.Solver(torch.from_numpy(eps).to(dev), dx, lam, npml=20)
+    S = F.Solver(torch.from_numpy(eps).to(dev), dx, lam, npml=20, max_restart=RESTART)
     precond = F.PRECOND_SCHWARZ if args.precond == "schwarz" else F.PRECOND_JACOBI
     kc = args.k_coarse if args.k_coarse >= 0 else K_COARSE_DEFAULT
     prec_nno = args.nno_precision
@@ -551,7 +560,7 @@ def main():
     Jd = torch.from_numpy(J).to(dev)
     E = torch.zeros((n, n), dtype=torch.complex64, device=dev)
     # warm-up: W Arnoldi steps
-    S.solve(Jd, E, restart=30, max_iters=args.warmup, tol=1e-30, precond=precond)
+    S.solve(Jd, E, restart=RESTART, max_iters=args.warmup, tol=1e-30, precond=precond)
     torch.cuda.synchronize()
     import tempfile
     clk = Clocks(os.path.join(tempfile.gettempdir(), f"fdfd_bench_clocks_rank{rank}_{os.getpid()}.csv"))
@@ -562,11 +571,13 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     with clk:
         S.profile_start()
+        torch.cuda.profiler.start()  # (a launch-list capture with --profile-from-start off sees this region only)
         ev0.record(S.stream)
-        rc, st = S.solve(Jd, E, restart=30, max_iters=args.steps, tol=1e-30, precond=precond)
+        rc, st = S.solve(Jd, E, restart=RESTART, max_iters=args.steps, tol=1e-30, precond=precond)
         ev1.record(S.stream)
         prof = S.profile_stop()
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     if world > 1:
         dist.barrier()
@@ -574,10 +585,10 @@ def main():
     value = job_rate(world, n * n, steps, ms / 1e3)
     # the same steps replayed as CUDA graphs (profiling off), for comparison
     S.use_graphs = True
-    S.solve(Jd, E, restart=30, max_iters=min(args.steps, 30), tol=1e-30, precond=precond)  # capture
+    S.solve(Jd, E, restart=RESTART, max_iters=min(args.steps, RESTART), tol=1e-30, precond=precond)  # capture
     torch.cuda.synchronize()
     ev0.record(S.stream)
-    S.solve(Jd, E, restart=30, max_iters=args.steps, tol=1e-30, precond=precond)
+    S.solve(Jd, E, restart=RESTART, max_iters=args.steps, tol=1e-30, precond=precond)
     ev1.record(S.stream)
     torch.cuda.synchronize()
     ms_graph = ev0.elapsed_time(ev1)
@@ -586,7 +597,7 @@ def main():
     Eh = np.zeros_like(Jh)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    S.solve_host(Jh, Eh, restart=30, max_iters=args.steps, tol=1e-30, precond=precond)
+    S.solve_host(Jh, Eh, restart=RESTART, max_iters=args.steps, tol=1e-30, precond=precond)
     t_e2e = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_value = job_rate(world, n * n, args.steps, t_e2e)
     hbm, bf16, bf16s, src = peaks()
@@ -628,7 +639,8 @@ def main():
                        "ritz_tol": args.ritz_tol if precond == F.PRECOND_SCHWARZ and kc > 0 else None,
                        "n_coarse_kept": S.info()["n_coarse_kept"] if precond == F.PRECOND_SCHWARZ else None,
                        "nno_precision": prec_nno if precond == F.PRECOND_SCHWARZ else None,
-                       "l2": "inputs larger than L2 (each Krylov vector 134 MB; V, Z 8 GB)",
+                       "restart": RESTART,
+                       "l2": "inputs larger than L2 (each Krylov vector 134 MB; V, Z 16 GB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "rooflines": roofs, "gpu_launches": prof["total_launches"],
             "e2e": {"value": e2e_value, "unit": "Mcell-it/s", "h2d_bytes_per_step": N * 8 // args.steps,
