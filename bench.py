@@ -139,12 +139,13 @@ def coarse_bytes_per_apply(N, k):
     """Coarse solve and correction, per application on an n x n grid: both
     row sweeps stream every inverted Schur complement (complex half:
     2 (n/64) D^2 x 4 B, D = (n/64) k), the correction reads every basis
-    field's core (n_win k 4096 x 8 B) and updates the field (16 B per cell),
-    the right-hand side reads the trial vectors (n_win k 320 x 8 B)."""
+    field's core (complex half, n_win k 4096 x 4 B) and updates the field
+    (16 B per cell), the right-hand side reads the trial vectors
+    (n_win k 320 x 8 B)."""
     nw1 = int(round((N ** 0.5) / 64))
     D = nw1 * k
     nc = nw1 * nw1 * k
-    return 2.0 * nw1 * D * D * 4 + nc * 4096 * 8 + 16.0 * N + nc * 320 * 8
+    return 2.0 * nw1 * D * D * 4 + nc * 4096 * 4 + 16.0 * N + nc * 320 * 8
 
 
 def algorithmic_bytes(cls, launches, N, steps, k=0, coarse_launches_per_apply=0):
@@ -157,7 +158,7 @@ def algorithmic_bytes(cls, launches, N, steps, k=0, coarse_launches_per_apply=0)
     if cls == "stencil":
         return 20.0 * N * launches
     if cls in ("cgs_dots", "cgs_update"):
-        js = [s % 30 for s in range(steps)]
+        js = [s % RESTART for s in range(steps)]
         extra = 8 if cls == "cgs_dots" else 16
         return float(sum((8 * (j + 1) + extra) * N for j in js))
     if cls == "residual64":

@@ -43,7 +43,8 @@ struct CoarseData {
   int k = 0, nc = 0, nwx = 0, nwy = 0, D = 0;
   double2* Q = nullptr;      // [n_win][k][320]
   float2* Qf = nullptr;      // [k][n_win][320]
-  float2* Phi = nullptr;     // [n_win][k][64*64] core of each basis field
+  float2* Phi = nullptr;     // [n_win][k][64*64] core of each basis field (set-up only)
+  __half2* Phih = nullptr;   // the same, complex half: what the correction reads
   double2* C = nullptr;      // [n_win][9][320][k]   (set-up only)
   double2* G = nullptr;      // [n_win][9][k][k]     Galerkin blocks, FP64
   float2* Gf = nullptr;      // [n_win][9][k][k]     FP32 copy used by the sweeps
@@ -381,43 +382,52 @@ __global__ void __launch_bounds__(256) sweep_t_kernel(float2* __restrict__ t, co
 }
 
 // out = base + sgn * A t for a row-major D x D complex matrix A stored as
-// complex half (warp per row, four complex entries per 16-byte load, FP32
-// products and sums); base may be NULL.
+// complex half: each row is split over GW warps (GEMV_ROWS rows per CTA, so
+// enough loads are in flight to stream A at HBM rate), four complex entries
+// per 16-byte load, FP32 products and sums; base may be NULL.
+constexpr int GW = 4, GEMV_ROWS = 8 / GW;
 __global__ void __launch_bounds__(256) gemv_rows_kernel(float2* __restrict__ out, const float2* __restrict__ base,
                                                         const __half2* __restrict__ A, const float2* __restrict__ t,
                                                         int D, float sgn) {
-  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (row >= D) return;
-  const __half2* a = A + (size_t)row * D;
-  const uint4* a4 = reinterpret_cast<const uint4*>(a);
-  const float4* t4 = reinterpret_cast<const float4*>(t);
+  __shared__ float2 red[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * GEMV_ROWS + warp / GW, part = warp % GW;
   float sr = 0.f, si = 0.f;
-  // 16-byte loads need every row 16-byte aligned (D a multiple of 4);
-  // otherwise the scalar loop below takes the whole row
-  const int n4 = (D & 3) ? 0 : D / 4;
+  if (row < D) {
+    const __half2* a = A + (size_t)row * D;
+    const uint4* a4 = reinterpret_cast<const uint4*>(a);
+    const float4* t4 = reinterpret_cast<const float4*>(t);
+    // 16-byte loads need every row 16-byte aligned (D a multiple of 4);
+    // otherwise the scalar loop below takes the whole row
+    const int n4 = (D & 3) ? 0 : D / 4;
 #pragma unroll 4
-  for (int j = lane; j < n4; j += 32) {
-    const uint4 m = __ldcs(a4 + j);
-    const float4 v0 = __ldg(t4 + 2 * j), v1 = __ldg(t4 + 2 * j + 1);
-    const float2 m0 = __half22float2(*reinterpret_cast<const __half2*>(&m.x));
-    const float2 m1 = __half22float2(*reinterpret_cast<const __half2*>(&m.y));
-    const float2 m2 = __half22float2(*reinterpret_cast<const __half2*>(&m.z));
-    const float2 m3 = __half22float2(*reinterpret_cast<const __half2*>(&m.w));
-    sr += m0.x * v0.x - m0.y * v0.y + m1.x * v0.z - m1.y * v0.w + m2.x * v1.x - m2.y * v1.y + m3.x * v1.z - m3.y * v1.w;
-    si += m0.x * v0.y + m0.y * v0.x + m1.x * v0.w + m1.y * v0.z + m2.x * v1.y + m2.y * v1.x + m3.x * v1.w + m3.y * v1.z;
-  }
-  for (int j = 4 * n4 + lane; j < D; j += 32) {  // D not a multiple of 4
-    const float2 m = __half22float2(a[j]), v = t[j];
-    sr += m.x * v.x - m.y * v.y;
-    si += m.x * v.y + m.y * v.x;
+    for (int j = part * 32 + lane; j < n4; j += 32 * GW) {
+      const uint4 m = __ldcs(a4 + j);
+      const float4 v0 = __ldg(t4 + 2 * j), v1 = __ldg(t4 + 2 * j + 1);
+      const float2 m0 = __half22float2(*reinterpret_cast<const __half2*>(&m.x));
+      const float2 m1 = __half22float2(*reinterpret_cast<const __half2*>(&m.y));
+      const float2 m2 = __half22float2(*reinterpret_cast<const __half2*>(&m.z));
+      const float2 m3 = __half22float2(*reinterpret_cast<const __half2*>(&m.w));
+      sr += m0.x * v0.x - m0.y * v0.y + m1.x * v0.z - m1.y * v0.w + m2.x * v1.x - m2.y * v1.y + m3.x * v1.z - m3.y * v1.w;
+      si += m0.x * v0.y + m0.y * v0.x + m1.x * v0.w + m1.y * v0.z + m2.x * v1.y + m2.y * v1.x + m3.x * v1.w + m3.y * v1.z;
+    }
+    for (int j = 4 * n4 + part * 32 + lane; j < D; j += 32 * GW) {  // D not a multiple of 4
+      const float2 m = __half22float2(a[j]), v = t[j];
+      sr += m.x * v.x - m.y * v.y;
+      si += m.x * v.y + m.y * v.x;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     sr += __shfl_xor_sync(0xffffffffu, sr, o);
     si += __shfl_xor_sync(0xffffffffu, si, o);
   }
-  if (lane == 0) {
+  if (lane == 0) red[warp] = make_float2(sr, si);
+  __syncthreads();
+  if (part == 0 && lane == 0 && row < D) {
+    float2 acc = red[warp];
+    for (int q = 1; q < GW; ++q) acc = make_float2(acc.x + red[warp + q].x, acc.y + red[warp + q].y);
     const float2 b0 = base ? base[row] : make_float2(0.f, 0.f);
-    out[row] = make_float2(b0.x + sgn * sr, b0.y + sgn * si);
+    out[row] = make_float2(b0.x + sgn * acc.x, b0.y + sgn * acc.y);
   }
 }
 
@@ -531,7 +541,7 @@ __global__ void to_f32_kernel(float2* dst, const double2* src, size_t n) {
 }
 
 // u[core(w)] += sum_m z[w,m] Phi[w][m]
-__global__ void correction_kernel(float2* u, const float2* Phi, const float2* z, int k, int nx, int nwx) {
+__global__ void correction_kernel(float2* u, const __half2* Phi, const float2* z, int k, int nx, int nwx) {
   const int w = blockIdx.y;
   const int a = w % nwx, b = w / nwx;
   __shared__ float2 zw[256];
@@ -539,9 +549,9 @@ __global__ void correction_kernel(float2* u, const float2* Phi, const float2* z,
   __syncthreads();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= 4096) return;
-  const float2* ph = Phi + (size_t)w * k * 4096 + p;
+  const __half2* ph = Phi + (size_t)w * k * 4096 + p;
   float2 acc = make_float2(0.f, 0.f);
-  for (int m = 0; m < k; ++m) acc = cadd(acc, cmul(zw[m], __ldg(ph + (size_t)m * 4096)));
+  for (int m = 0; m < k; ++m) acc = cadd(acc, cmul(zw[m], __half22float2(__ldcs(ph + (size_t)m * 4096))));
   const size_t g = (size_t)(FDFD_CORE * b + p / 64) * nx + FDFD_CORE * a + p % 64;
   u[g] = cadd(u[g], acc);
 }
@@ -557,7 +567,7 @@ int ca(T** p, size_t n, size_t* bytes) {
 
 void coarse_free(CoarseData* c) {
   if (!c) return;
-  void* ptrs[] = {c->Q, c->Qf, c->Phi, c->C, c->G, c->Gf, c->Sinv, c->rcf, c->ycf, c->zcf, c->tcf, c->ebc,
+  void* ptrs[] = {c->Q, c->Qf, c->Phi, c->Phih, c->C, c->G, c->Gf, c->Sinv, c->rcf, c->ycf, c->zcf, c->tcf, c->ebc,
                   c->tmp, c->dropped, c->eta, c->H};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete c;
@@ -732,11 +742,17 @@ int coarse_setup(fdfd_ctx* h, const NnoWeights* W, NnoWork* work, LocalWork* L, 
   to_f32_kernel<<<1024, 256, 0, s>>>(c->Gf, c->G, (size_t)n_win * 9 * k * k);
   dropped_kernel<<<(nc + 255) / 256, 256, 0, s>>>(c->dropped, c->Q, nc);
   CKL();
-  // C is a set-up temporary: the Galerkin blocks replace it
+  // C and the FP32 basis fields are set-up temporaries: the Galerkin blocks
+  // and a complex-half copy of the fields replace them
+  if ((rc = ca(&c->Phih, (size_t)nc * 4096, bytes))) { coarse_free(c); return rc; }
+  to_half_kernel<<<2048, 256, 0, s>>>(c->Phih, c->Phi, (size_t)nc * 4096);
+  CKL();
   cudaStreamSynchronize(s);
   cudaFree(c->C);
   c->C = nullptr;
-  *bytes -= c_bytes;
+  cudaFree(c->Phi);
+  c->Phi = nullptr;
+  *bytes -= c_bytes + (size_t)nc * 4096 * sizeof(float2);
   if ((rc = factor_rows(h, c))) { coarse_free(c); return rc; }
   {
     std::vector<int> dr(nc);
@@ -769,7 +785,7 @@ static int solve_launches(const CoarseData* c) { return 1 + (2 * c->nwy - 1) + 2
 static int solve_rows(fdfd_ctx* h, CoarseData* c) {
   const int D = c->D, k = c->k, nwx = c->nwx, nwy = c->nwy;
   const size_t DD = (size_t)D * D;
-  const int grid = (D + 7) / 8;
+  const int grid = (D + 7) / 8, ggrid = (D + GEMV_ROWS - 1) / GEMV_ROWS;
   cudaStream_t s = h->stream;
   for (int b = 0; b < nwy; ++b) {
     const float2* t = c->rcf + (size_t)b * D;
@@ -778,13 +794,13 @@ static int solve_rows(fdfd_ctx* h, CoarseData* c) {
                                           nwx, b, 0);
       t = c->tcf;
     }
-    gemv_rows_kernel<<<grid, 256, 0, s>>>(c->ycf + (size_t)b * D, nullptr, c->Sinv + (size_t)b * DD, t, D, 1.f);
+    gemv_rows_kernel<<<ggrid, 256, 0, s>>>(c->ycf + (size_t)b * D, nullptr, c->Sinv + (size_t)b * DD, t, D, 1.f);
   }
   CK(cudaMemcpyAsync(c->zcf + (size_t)(nwy - 1) * D, c->ycf + (size_t)(nwy - 1) * D, (size_t)D * sizeof(float2),
                      cudaMemcpyDeviceToDevice, s));
   for (int b = nwy - 2; b >= 0; --b) {
     sweep_t_kernel<<<grid, 256, 0, s>>>(c->tcf, nullptr, c->zcf + (size_t)(b + 1) * D, c->Gf, k, nwx, b, 6);
-    gemv_rows_kernel<<<grid, 256, 0, s>>>(c->zcf + (size_t)b * D, c->ycf + (size_t)b * D, c->Sinv + (size_t)b * DD,
+    gemv_rows_kernel<<<ggrid, 256, 0, s>>>(c->zcf + (size_t)b * D, c->ycf + (size_t)b * D, c->Sinv + (size_t)b * DD,
                                           c->tcf, D, -1.f);
   }
   CKL();
@@ -808,7 +824,7 @@ int coarse_apply(fdfd_ctx* h, CoarseData* c, float2* u, const float2* g_ref) {
   galerkin_rhs_kernel<<<n_win, 256, 0, s>>>(c->rcf, c->Qf, c->ebc, c->k, n_win);
   CKL();
   if ((rc = solve_rows(h, c))) return rc;
-  correction_kernel<<<dim3(4096 / 256, n_win), 256, 0, s>>>(u, c->Phi, c->zcf, c->k, h->nx, nwx);
+  correction_kernel<<<dim3(4096 / 256, n_win), 256, 0, s>>>(u, c->Phih, c->zcf, c->k, h->nx, nwx);
   CKL();
   return FDFD_OK;
 }

@@ -122,20 +122,43 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
                                                        float2* __restrict__ vnext, LocalState* st, int j, size_t ldv) {
   __shared__ double sh[LT / 32];
   __shared__ double2 hs[LOCAL_MAXM + 1];
-  const int b = blockIdx.x;
+  __shared__ double part[LT / 32][2 * (LOCAL_MAXM + 1)];
+  __shared__ float2 hf[LOCAL_MAXM + 1];
+  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   LocalState& s = st[b];
   const float2* w = w_io + (size_t)b * NP;
-  for (int i = 0; i <= j; ++i) {
-    const float2* vi = Vw + (size_t)i * ldv + (size_t)b * NP;
-    double dr = 0.0, di = 0.0;
-    for (int p = threadIdx.x; p < NP; p += LT) {
-      const float2 a = vi[p], q = w[p];
-      dr += (double)(a.x * q.x + a.y * q.y);
-      di += (double)(a.x * q.y - a.y * q.x);
+  // all dots (w, v_i), i <= j, in one pass: FP32 sums over each thread's 25
+  // pixels, FP64 across the block
+  float dr[LOCAL_MAXM + 1], di[LOCAL_MAXM + 1];
+#pragma unroll
+  for (int i = 0; i <= LOCAL_MAXM; ++i) { dr[i] = 0.f; di[i] = 0.f; }
+  for (int p = threadIdx.x; p < NP; p += LT) {
+    const float2 q = w[p];
+#pragma unroll
+    for (int i = 0; i <= LOCAL_MAXM; ++i)
+      if (i <= j) {
+        const float2 a = Vw[(size_t)i * ldv + (size_t)b * NP + p];
+        dr[i] += a.x * q.x + a.y * q.y;
+        di[i] += a.x * q.y - a.y * q.x;
+      }
+  }
+#pragma unroll
+  for (int i = 0; i <= LOCAL_MAXM; ++i)
+    if (i <= j) {
+      double r = dr[i], m = di[i];
+      for (int o = 16; o > 0; o >>= 1) {
+        r += __shfl_xor_sync(0xffffffffu, r, o);
+        m += __shfl_xor_sync(0xffffffffu, m, o);
+      }
+      if (lane == 0) { part[warp][2 * i] = r; part[warp][2 * i + 1] = m; }
     }
-    dr = block_sum<LT>(dr, sh);
-    di = block_sum<LT>(di, sh);
-    if (threadIdx.x == 0) hs[i] = make_double2(dr * s.vscale[i], di * s.vscale[i]);
+  __syncthreads();
+  if (threadIdx.x <= j) {
+    const int i = threadIdx.x;
+    double r = 0.0, m = 0.0;
+    for (int q = 0; q < LT / 32; ++q) { r += part[q][2 * i]; m += part[q][2 * i + 1]; }
+    hs[i] = make_double2(r * s.vscale[i], m * s.vscale[i]);
+    hf[i] = make_float2((float)(hs[i].x * s.vscale[i]), (float)(hs[i].y * s.vscale[i]));
   }
   __syncthreads();
   double acc = 0.0;
@@ -143,7 +166,7 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
     float2 q = w[p];
     for (int i = 0; i <= j; ++i) {
       const float2 a = Vw[(size_t)i * ldv + (size_t)b * NP + p];
-      const float hr = (float)(hs[i].x * s.vscale[i]), hi = (float)(hs[i].y * s.vscale[i]);
+      const float hr = hf[i].x, hi = hf[i].y;
       q.x -= hr * a.x - hi * a.y;
       q.y -= hr * a.y + hi * a.x;
     }
