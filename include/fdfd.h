@@ -417,6 +417,36 @@ int  fdfd_design_grad(fdfd_handle h, const fdfd_design* d, const float* rho_f, c
 int  fdfd_adam_step(fdfd_handle h, const fdfd_adam* a, int t, float g_scale, float* theta, const float* g,
                     float* m, float* v, int n);
 
+/* ---- figure of merit: port mode overlaps (Sec. 2.2, the inverse design's
+ * objective and the source of its adjoint solve) ---------------------------
+ * The overlap of a field with a port profile m on the vertical line
+ * x = port_x is c = dx sum_{i < nm} conj(m_i) E[y0 + i][port_x]; it is linear
+ * in E with dc/dE = conj(m_i) dx on the line.  Gradients of a real loss L
+ * follow the conjugate-Wirtinger convention G_z = 2 dL/d conj(z) (what
+ * PyTorch's autograd passes; for L = |c|^2, G_c = 2 c). */
+
+/* c_dev [2] (device doubles, re / im, overwritten) = the overlap, summed in
+ * FP64.  E [ny][nx] and mode [nm] device complex64.  Asynchronous on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream).  FDFD_EINVAL
+ * unless nx, ny, nm >= 1, 0 <= port_x < nx, y0 >= 0, y0 + nm <= ny and
+ * dx > 0. */
+int  fdfd_mode_overlap(const fdfd_c64* E, int nx, int ny, const fdfd_c64* mode, int nm, int port_x, int y0,
+                       double dx, double* c_dev, void* stream);
+
+/* The overlap's chain rule: with G_c = gc_re + j gc_im (host values),
+ * G_E = G_c conj(dc/dE) = G_c m_i dx on the port line.  grad_E [ny][nx]
+ * (device complex64) is overwritten with it, zero elsewhere (accumulate = 0),
+ * or has it added (accumulate = 1).  Asynchronous on `stream`; arguments as
+ * fdfd_mode_overlap. */
+int  fdfd_mode_overlap_grad(int nx, int ny, const fdfd_c64* mode, int nm, int port_x, int y0, double dx,
+                            double gc_re, double gc_im, fdfd_c64* grad_E, int accumulate, void* stream);
+
+/* Right-hand side of the adjoint system A~^T lam = dL/dE (Sec. 2.2, adjoint
+ * variable method) from a field gradient G_E = 2 dL/d conj(E) of a real
+ * loss: g = dL/dE = conj(G_E) / 2, over the handle's grid ([ny][nx] device
+ * complex64; g may alias grad_E).  On the handle's stream. */
+int  fdfd_adjoint_rhs(fdfd_handle h, const fdfd_c64* grad_E, fdfd_c64* g);
+
 /* Diagnostic: one tile GEMM on the tcgen05 path used by the neural operator
  * (no counterpart in the paper; validates the tensor-core operand encoding).
  * C[M][N] (float32, device) = A . B^T with A bf16 [M][K] (a_mn_major = 0)

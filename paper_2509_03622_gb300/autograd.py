@@ -60,7 +60,8 @@ class _FieldSolve(torch.autograd.Function):
         # set up again since (another fdfd_field call on it), restore it.
         if getattr(S, "_setup_version", None) != ctx.version:
             ctx.version = _setup(S, eps_saved, ctx.weights, ctx.opts)
-        g = (grad_E.conj() * 0.5).to(torch.complex64).contiguous()
+        g = torch.empty_like(E)
+        S.adjoint_rhs(grad_E.to(torch.complex64).contiguous(), g)  # g = dL/dE = conj(grad_E) / 2
         lam = torch.zeros_like(E)
         rc, st = S.solve_adjoint(g, lam, **ctx.kw)
         last_stats["adjoint"] = st
@@ -78,9 +79,29 @@ def fdfd_field(solver: "F.Solver", eps: torch.Tensor, J: torch.Tensor, weights=N
     return _FieldSolve.apply(eps, J, solver, weights, opts)
 
 
+class _Overlap(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, E, mode, port_x, y0, dx):
+        c = torch.empty(2, dtype=torch.float64, device=E.device)
+        F.mode_overlap(E.contiguous(), mode.contiguous(), port_x, y0, dx, c)
+        ctx.shape, ctx.args = E.shape, (port_x, y0, dx)
+        ctx.save_for_backward(mode)
+        return torch.view_as_complex(c)
+
+    @staticmethod
+    def backward(ctx, grad_c):
+        (mode,) = ctx.saved_tensors
+        port_x, y0, dx = ctx.args
+        grad_E = torch.empty(ctx.shape, dtype=torch.complex64, device=mode.device)
+        F.mode_overlap_grad(ctx.shape, mode.contiguous(), port_x, y0, dx, complex(grad_c.item()), grad_E)
+        return grad_E, None, None, None, None
+
+
 def mode_overlap(E: torch.Tensor, port_x: int, mode: torch.Tensor, y0: int, dx: float) -> torch.Tensor:
-    """c = sum_port conj(m) E dx along the vertical line x = port_x."""
-    return torch.sum(torch.conj(mode) * E[y0:y0 + mode.numel(), port_x]) * dx
+    """c = dx sum_port conj(m) E along the vertical line x = port_x, from the
+    library's overlap kernel (complex128 scalar tensor, differentiable in E:
+    its backward is the library's chain-rule kernel)."""
+    return _Overlap.apply(E, mode.to(torch.complex64), int(port_x), int(y0), float(dx))
 
 
 class FDFDSolve:

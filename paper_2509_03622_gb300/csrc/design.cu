@@ -157,3 +157,103 @@ int fdfd_adam_step(fdfd_handle h, const fdfd_adam* a, int t, float g_scale, floa
   CK(cudaStreamSynchronize(h->stream));
   return FDFD_OK;
 }
+
+// ---- figure of merit: port mode overlaps (Sec. 2.2, inverse design) ----
+// c = dx sum_i conj(m_i) E[y0 + i][port_x] is linear (holomorphic) in E with
+// dc/dE = conj(m_i) dx on the port line.  PyTorch passes gradients of a real
+// loss L as G_z = 2 dL/d conj(z); the chain rule through c is then
+// G_E = G_c conj(dc/dE) = G_c m_i dx, and the adjoint right-hand side of the
+// adjoint variable method is dL/dE = conj(G_E) / 2.
+namespace {
+constexpr int OT = 256;
+
+__global__ void __launch_bounds__(OT) overlap_kernel(const float2* __restrict__ E, const float2* __restrict__ m,
+                                                     int nm, int nx, int port_x, int y0, double dx,
+                                                     double* __restrict__ c) {
+  __shared__ double sr[OT / 32], si[OT / 32];
+  double ar = 0.0, ai = 0.0;
+  for (int i = threadIdx.x; i < nm; i += OT) {
+    const float2 e = E[(size_t)(y0 + i) * nx + port_x], w = m[i];
+    // conj(w) e = (w.x e.x + w.y e.y) + j (w.x e.y - w.y e.x)
+    ar += (double)w.x * e.x + (double)w.y * e.y;
+    ai += (double)w.x * e.y - (double)w.y * e.x;
+  }
+  for (int o = 16; o; o >>= 1) {
+    ar += __shfl_xor_sync(0xffffffffu, ar, o);
+    ai += __shfl_xor_sync(0xffffffffu, ai, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sr[warp] = ar; si[warp] = ai; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, ti = 0.0;
+    for (int w = 0; w < OT / 32; ++w) { tr += sr[w]; ti += si[w]; }
+    c[0] = tr * dx;
+    c[1] = ti * dx;
+  }
+}
+
+__global__ void __launch_bounds__(OT) overlap_grad_kernel(const float2* __restrict__ m, int nm, int nx, int port_x,
+                                                          int y0, double gr, double gi, float2* __restrict__ G,
+                                                          int accumulate) {
+  const int i = blockIdx.x * OT + threadIdx.x;
+  if (i >= nm) return;
+  const float2 w = m[i];
+  float2* p = G + (size_t)(y0 + i) * nx + port_x;
+  // (gr + j gi) dx (w.x + j w.y); gr, gi already carry dx
+  float2 v = make_float2((float)(gr * w.x - gi * w.y), (float)(gr * w.y + gi * w.x));
+  if (accumulate) {
+    const float2 o = *p;
+    v.x += o.x;
+    v.y += o.y;
+  }
+  *p = v;
+}
+
+// g = conj(G) / 2 (8-byte loads: any complex64 field is 8-byte aligned)
+__global__ void __launch_bounds__(OT) adjoint_rhs_kernel(const float2* __restrict__ G, float2* __restrict__ g,
+                                                         size_t n) {
+  const size_t stride = (size_t)gridDim.x * OT;
+  for (size_t i = (size_t)blockIdx.x * OT + threadIdx.x; i < n; i += stride) {
+    const float2 v = G[i];
+    g[i] = make_float2(0.5f * v.x, -0.5f * v.y);
+  }
+}
+
+bool port_ok(int nx, int ny, int nm, int port_x, int y0) {
+  return nx >= 1 && ny >= 1 && nm >= 1 && port_x >= 0 && port_x < nx && y0 >= 0 && (long long)y0 + nm <= ny;
+}
+}  // namespace
+
+int fdfd_mode_overlap(const fdfd_c64* E, int nx, int ny, const fdfd_c64* mode, int nm, int port_x, int y0,
+                      double dx, double* c_dev, void* stream) {
+  if (!E || !mode || !c_dev || !port_ok(nx, ny, nm, port_x, y0) || !(dx > 0.0)) return FDFD_EINVAL;
+  overlap_kernel<<<1, OT, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float2*>(E),
+                                                     reinterpret_cast<const float2*>(mode), nm, nx, port_x, y0, dx,
+                                                     c_dev);
+  CKL();
+  return FDFD_OK;
+}
+
+int fdfd_mode_overlap_grad(int nx, int ny, const fdfd_c64* mode, int nm, int port_x, int y0, double dx,
+                           double gc_re, double gc_im, fdfd_c64* grad_E, int accumulate, void* stream) {
+  if (!mode || !grad_E || !port_ok(nx, ny, nm, port_x, y0) || !(dx > 0.0)) return FDFD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!accumulate) CK(cudaMemsetAsync(grad_E, 0, (size_t)nx * ny * sizeof(fdfd_c64), s));
+  overlap_grad_kernel<<<(nm + OT - 1) / OT, OT, 0, s>>>(reinterpret_cast<const float2*>(mode), nm, nx, port_x, y0,
+                                                        gc_re * dx, gc_im * dx, reinterpret_cast<float2*>(grad_E),
+                                                        accumulate);
+  CKL();
+  return FDFD_OK;
+}
+
+int fdfd_adjoint_rhs(fdfd_handle h, const fdfd_c64* grad_E, fdfd_c64* g) {
+  if (!h || !grad_E || !g) return FDFD_EINVAL;
+  const size_t n = (size_t)h->nx * h->ny;
+  size_t blocks = (n + OT - 1) / OT;
+  if (blocks > 8192) blocks = 8192;
+  adjoint_rhs_kernel<<<(unsigned)blocks, OT, 0, h->stream>>>(reinterpret_cast<const float2*>(grad_E),
+                                                             reinterpret_cast<float2*>(g), n);
+  CKL();
+  return FDFD_OK;
+}

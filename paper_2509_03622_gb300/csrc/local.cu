@@ -117,9 +117,17 @@ __global__ void __launch_bounds__(LT) local_start_kernel(const float2* __restric
   }
 }
 
-// One CGS step of window b's Arnoldi process plus its Givens update.
+// One CGS step of window b's Arnoldi process plus its Givens update.  JT >= 0
+// fixes j = JT at compile time (accumulators for the j + 1 dots only, more
+// windows resident per SM); JT = -1 takes j at run time.  Both forms add in
+// the same order, so they give the same bits.
+static_assert(NP % LT == 0, "whole pixel rounds per thread");
+template <int JT>
 __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict__ Vw, float2* __restrict__ w_io,
-                                                       float2* __restrict__ vnext, LocalState* st, int j, size_t ldv) {
+                                                       float2* __restrict__ vnext, LocalState* st, int j_rt,
+                                                       size_t ldv) {
+  constexpr int NA = JT >= 0 ? JT + 1 : LOCAL_MAXM + 1;  // accumulator pairs
+  const int j = JT >= 0 ? JT : j_rt;
   __shared__ double sh[LT / 32];
   __shared__ double2 hs[LOCAL_MAXM + 1];
   __shared__ double part[LT / 32][2 * (LOCAL_MAXM + 1)];
@@ -129,13 +137,15 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
   const float2* w = w_io + (size_t)b * NP;
   // all dots (w, v_i), i <= j, in one pass: FP32 sums over each thread's 25
   // pixels, FP64 across the block
-  float dr[LOCAL_MAXM + 1], di[LOCAL_MAXM + 1];
+  float dr[NA], di[NA];
 #pragma unroll
-  for (int i = 0; i <= LOCAL_MAXM; ++i) { dr[i] = 0.f; di[i] = 0.f; }
-  for (int p = threadIdx.x; p < NP; p += LT) {
+  for (int i = 0; i < NA; ++i) { dr[i] = 0.f; di[i] = 0.f; }
+#pragma unroll(JT >= 0 ? 5 : 1)
+  for (int t = 0; t < NP / LT; ++t) {
+    const int p = threadIdx.x + t * LT;
     const float2 q = w[p];
 #pragma unroll
-    for (int i = 0; i <= LOCAL_MAXM; ++i)
+    for (int i = 0; i < NA; ++i)
       if (i <= j) {
         const float2 a = Vw[(size_t)i * ldv + (size_t)b * NP + p];
         dr[i] += a.x * q.x + a.y * q.y;
@@ -143,7 +153,7 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
       }
   }
 #pragma unroll
-  for (int i = 0; i <= LOCAL_MAXM; ++i)
+  for (int i = 0; i < NA; ++i)
     if (i <= j) {
       double r = dr[i], m = di[i];
       for (int o = 16; o > 0; o >>= 1) {
@@ -162,9 +172,13 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
   }
   __syncthreads();
   double acc = 0.0;
-  for (int p = threadIdx.x; p < NP; p += LT) {
+#pragma unroll(JT >= 0 ? 5 : 1)
+  for (int t = 0; t < NP / LT; ++t) {
+    const int p = threadIdx.x + t * LT;
     float2 q = w[p];
-    for (int i = 0; i <= j; ++i) {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      if (i > j) break;
       const float2 a = Vw[(size_t)i * ldv + (size_t)b * NP + p];
       const float hr = hf[i].x, hi = hf[i].y;
       q.x -= hr * a.x - hi * a.y;
@@ -310,7 +324,14 @@ int local_fgmres(fdfd_ctx* h, LocalWork* L, const NnoWeights* W, NnoWork* work, 
       ProfScope ps(h, 15, 2);
       local_apply_kernel<<<dim3(NP / LT / 5, n), LT, 0, s>>>(L->Z + (size_t)j * ld, L->w, nullptr, h->eps, lcx,
                                                               lcy, (float)h->k2, (float)h->k0dx, h->nx, h->ny, nwx);
-      local_cgs_kernel<<<n, LT, 0, s>>>(L->V, L->w, L->V + (size_t)(j + 1) * ld, L->st, j, ld);
+      float2* vn = L->V + (size_t)(j + 1) * ld;
+      switch (j) {  // the first steps (the usual inner counts) with j fixed at compile time
+        case 0: local_cgs_kernel<0><<<n, LT, 0, s>>>(L->V, L->w, vn, L->st, j, ld); break;
+        case 1: local_cgs_kernel<1><<<n, LT, 0, s>>>(L->V, L->w, vn, L->st, j, ld); break;
+        case 2: local_cgs_kernel<2><<<n, LT, 0, s>>>(L->V, L->w, vn, L->st, j, ld); break;
+        case 3: local_cgs_kernel<3><<<n, LT, 0, s>>>(L->V, L->w, vn, L->st, j, ld); break;
+        default: local_cgs_kernel<-1><<<n, LT, 0, s>>>(L->V, L->w, vn, L->st, j, ld); break;
+      }
       CKL();
     }
   }

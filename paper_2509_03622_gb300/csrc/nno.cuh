@@ -72,6 +72,8 @@ struct NnoWork {
   bf16* Yh = nullptr;       // [cap][512 (o,kx)][64 (q,ri)], chunks swizzled: yh_off
   bf16* T3 = nullptr;       // [cap][80 y][o/8][k/8][o%8][k%8]  k = (kx,ri), tiled
   float* rho = nullptr;     // [cap]
+  uint8_t* packed = nullptr;  // [cap][20 units][4 rows][x/8][k/8][x%8][k%8] BF16 input channels (16 per
+                              // pixel, the lift's A tiles); nullptr: the G5 kernels build them in place
   int* err = nullptr;       // bounded-wait failure flag
   int g2_split = 0;         // DFT-y GEMM variant, set by nno_autotune: 0 = A tiles by TMA,
                             // 1 or 2 = cp.async gather with that K split
@@ -142,11 +144,12 @@ struct fdfd_ctx;
 int nno_forward(const NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInput& in,
                 const NnoOutput& out, int n, cudaStream_t s, fdfd_ctx* h = nullptr,
                 unsigned* calib = nullptr);
-// Switch W to FP8 activations: calibrate the per-channel scales on a BF16
-// forward of `n` windows of `in` (max |x| per channel at the five activation
-// points, with 4x headroom, rounded up to a power of two) and upload the
-// scale-folded weights.  `blob` is the weight blob W was made from.
-int nno_enable_fp8(NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInput& in, int n,
+// Switch W to FP8 activations: calibrate the per-channel scales on BF16
+// forwards of `n` windows of each of the n_in inputs in[] (max |x| per
+// channel at the five activation points over all of them, with 4x headroom,
+// rounded up to a power of two) and upload the scale-folded weights.  `blob`
+// is the weight blob W was made from.
+int nno_enable_fp8(NnoWeights* W, NnoWork* work, const GridGeom& g, const NnoInput* in, int n_in, int n,
                    const float* blob, size_t nfloats, size_t* bytes, cudaStream_t s);
 // Direct access to the tcgen05 GEMM for self-tests: C[M][N] (fp32) =
 // A[M][K] . B[N][K]^T with A K-major (a_mn = 0, row stride K) or MN-major

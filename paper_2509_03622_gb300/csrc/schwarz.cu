@@ -139,11 +139,17 @@ int schwarz_create(fdfd_ctx* h, const schwarz_desc* sd) {
   }
   if (!rc) rc = nno_alloc_work(&S->work, S->n_win < 64 ? 64 : S->n_win, &S->bytes);
   if (!rc) rc = nno_autotune(&S->W, &S->work, S->n_win, h->stream);
-  if (!rc && sd->precision == FDFD_PREC_FP8) {  // calibrate the activation scales on a random residual
+  if (!rc && sd->precision == FDFD_PREC_FP8) {  // calibrate the activation scales on random inputs
     fill_uniform_kernel<<<1024, 256, 0, h->stream>>>(h->w, h->n, 0x5EEDull);
-    NnoInput in;
-    in.v_global = h->w;
-    rc = nno_enable_fp8(&S->W, &S->work, geom(h), in, S->n_win, sd->weights, sd->n_weights, &S->bytes, h->stream);
+    // calibrate on both kinds of input the network meets: residual windows
+    // (the sweeps and local solves) and Robin data with no source (the
+    // coarse set-up's trials); the random field doubles as that Robin data
+    // (n_win x 320 values, fewer than the grid's cells)
+    NnoInput in[2];
+    in[0].v_global = h->w;
+    in[1].g_win = h->w;
+    rc = nno_enable_fp8(&S->W, &S->work, geom(h), in, 2, S->n_win, sd->weights, sd->n_weights, &S->bytes,
+                        h->stream);
   }
   if (!rc && S->inner > 0) rc = local_alloc(&S->local, S->n_win, S->inner, &S->bytes);
   h->sw = S;

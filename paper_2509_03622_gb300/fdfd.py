@@ -104,6 +104,10 @@ _SIGS = {
     "fdfd_design_eps": ([_P, C.POINTER(DesignDesc), _P, _P, _P], C.c_int),
     "fdfd_design_grad": ([_P, C.POINTER(DesignDesc), _P, _P, _P, _P], C.c_int),
     "fdfd_adam_step": ([_P, C.POINTER(AdamDesc), C.c_int, C.c_float, _P, _P, _P, _P, C.c_int], C.c_int),
+    "fdfd_mode_overlap": ([_P, C.c_int, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P], C.c_int),
+    "fdfd_mode_overlap_grad": ([C.c_int, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                _P, C.c_int, _P], C.c_int),
+    "fdfd_adjoint_rhs": ([_P, _P, _P], C.c_int),
     "fdfd_profile_start": ([_P], C.c_int),
     "fdfd_selftest_gemm": ([_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     "fdfd_selftest_wait": ([], C.c_int),
@@ -139,6 +143,30 @@ def _ptr(t):
 
 def status_string(code: int) -> str:
     return lib.fdfd_status_string(code).decode()
+
+
+def mode_overlap(E, mode, port_x: int, y0: int, dx: float, c, stream=None):
+    """c (float64 CUDA tensor [2], re / im) = dx sum conj(mode) E along the
+    vertical line x = port_x from row y0 (fdfd_mode_overlap), on `stream`
+    (default: PyTorch's current stream)."""
+    import torch
+    if c.dtype != torch.float64 or c.numel() < 2:
+        raise TypeError("c must be a float64 tensor of 2 elements")
+    st = stream if stream is not None else torch.cuda.current_stream(E.device).cuda_stream
+    ny, nx = E.shape
+    _check(lib.fdfd_mode_overlap(_ptr(E), nx, ny, _ptr(mode), mode.numel(), int(port_x), int(y0), float(dx),
+                                 _ptr(c), C.c_void_p(st)), "fdfd_mode_overlap")
+
+
+def mode_overlap_grad(shape, mode, port_x: int, y0: int, dx: float, gc: complex, grad_E, accumulate=False,
+                      stream=None):
+    """grad_E (=|+=) gc * mode * dx on the port line (fdfd_mode_overlap_grad)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream(grad_E.device).cuda_stream
+    ny, nx = shape
+    _check(lib.fdfd_mode_overlap_grad(nx, ny, _ptr(mode), mode.numel(), int(port_x), int(y0), float(dx),
+                                      float(gc.real), float(gc.imag), _ptr(grad_E), int(accumulate),
+                                      C.c_void_p(st)), "fdfd_mode_overlap_grad")
 
 
 def selftest_wait() -> int:
@@ -241,6 +269,11 @@ class Solver:
         rc = _check(lib.fdfd_solve_adjoint(self.h, _ptr(g), _ptr(lam), C.byref(o), C.byref(st)),
                     "fdfd_solve_adjoint")
         return rc, st.as_dict()
+
+    def adjoint_rhs(self, grad_E, g):
+        """g = conj(grad_E) / 2: the adjoint right-hand side dL/dE from
+        autograd's field gradient (fdfd_adjoint_rhs)."""
+        _check(lib.fdfd_adjoint_rhs(self.h, _ptr(grad_E), _ptr(g)), "fdfd_adjoint_rhs")
 
     def grad_eps(self, E, lam, grad, accumulate=False):
         _check(lib.fdfd_grad_eps(self.h, _ptr(E), _ptr(lam), _ptr(grad), int(accumulate)), "fdfd_grad_eps")

@@ -58,6 +58,17 @@ def test_host_side_validation(lib):
     assert not h.value
     assert lib.status_string(lib.ENUMERIC).startswith("NaN")
     assert lib.lib.fdfd_solve(None, None, None, None, None) == lib.EINVAL
+    # figure-of-merit entry points: arguments are checked before any launch
+    # (the fake pointers below are never dereferenced)
+    fake, c = C.c_void_p(16), C.c_void_p(32)
+    assert lib.lib.fdfd_mode_overlap(None, 128, 128, fake, 8, 5, 0, 1e-8, c, None) == lib.EINVAL
+    assert lib.lib.fdfd_mode_overlap(fake, 128, 128, fake, 8, 128, 0, 1e-8, c, None) == lib.EINVAL  # port_x = nx
+    assert lib.lib.fdfd_mode_overlap(fake, 128, 128, fake, 8, 5, 121, 1e-8, c, None) == lib.EINVAL  # y0 + nm > ny
+    assert lib.lib.fdfd_mode_overlap(fake, 128, 128, fake, 0, 5, 0, 1e-8, c, None) == lib.EINVAL   # nm = 0
+    assert lib.lib.fdfd_mode_overlap(fake, 128, 128, fake, 8, 5, 0, 0.0, c, None) == lib.EINVAL    # dx = 0
+    assert lib.lib.fdfd_mode_overlap_grad(128, 128, fake, 8, -1, 0, 1e-8, 1.0, 0.0, c, 0, None) == lib.EINVAL
+    assert lib.lib.fdfd_mode_overlap_grad(128, 128, None, 8, 5, 0, 1e-8, 1.0, 0.0, c, 0, None) == lib.EINVAL
+    assert lib.lib.fdfd_adjoint_rhs(None, fake, c) == lib.EINVAL
 
 
 def test_no_oracle_in_product_path():

@@ -141,3 +141,45 @@ def test_multi_wavelength_fdfdsolve_gradient():
     assert len(solve.solvers) == 3
     solve.close()
     assert solve.solvers is None
+
+
+@pytest.mark.parametrize("port_x,y0,nm", [(77, 11, 37), (127, 28, 100), (0, 0, 128)])
+def test_overlap_kernels_match_oracle(port_x, y0, nm):
+    """The figure of merit's kernels against the oracle's definitions on the
+    same complex64 field: the overlap c (FP64 sums of exact products, so to
+    1e-12), the chain rule for F = |c|^2 (G_c = 2c) followed by the adjoint
+    right-hand side conj(G_E)/2, which must equal the oracle's adjoint source
+    conj(c) conj(m) dx (complex64 output: 1e-6), zero off the port line; and
+    accumulation adds.  Ports on the first and last column and a profile
+    spanning every row cover the edges."""
+    import torch
+    from paper_2509_03622_gb300 import fdfd as F
+    n, dx = 128, LAM / 30
+    g = wl.rng(77)
+    E = (g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))).astype(np.complex64)
+    m = (g.standard_normal(nm) + 1j * g.standard_normal(nm)).astype(np.complex64)
+    Et, mt = torch.from_numpy(E).cuda(), torch.from_numpy(m).cuda()
+    c = torch.empty(2, dtype=torch.float64, device="cuda")
+    F.mode_overlap(Et, mt, port_x, y0, dx, c)
+    torch.cuda.synchronize()
+    cg = complex(c[0].item(), c[1].item())
+    Fo, go = OF.fom_and_adjoint_source(E.astype(complex), port_x, m.astype(complex), y0, dx)
+    c_ref = OF.mode_overlap(E.astype(complex), port_x, m.astype(complex), y0, dx)
+    assert abs(cg - c_ref) <= 1e-12 * abs(c_ref)
+    assert abs(abs(cg) ** 2 - Fo) <= 1e-12 * Fo
+    S = F.Solver(torch.ones((n, n), device="cuda"), dx, LAM, npml=20)
+    GE = torch.full((n, n), 7.0 + 3.0j, dtype=torch.complex64, device="cuda")  # overwritten
+    F.mode_overlap_grad((n, n), mt, port_x, y0, dx, 2 * cg, GE)
+    gt = torch.empty_like(GE)
+    S.adjoint_rhs(GE, gt)
+    torch.cuda.synchronize()
+    gg = gt.cpu().numpy()
+    assert np.linalg.norm(gg - go) <= 1e-6 * np.linalg.norm(go)
+    off = np.ones((n, n), bool)
+    off[y0:y0 + nm, port_x] = False
+    assert not np.any(gg[off])
+    F.mode_overlap_grad((n, n), mt, port_x, y0, dx, 2 * cg, GE, accumulate=True)
+    S.adjoint_rhs(GE, GE)  # in place
+    torch.cuda.synchronize()
+    assert np.linalg.norm(GE.cpu().numpy() - 2 * go) <= 1e-6 * np.linalg.norm(2 * go)
+    S.close()
