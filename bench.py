@@ -112,16 +112,24 @@ WIN_BYTES = {
 G5_T1_BYTES = 160 * 512 * 2                   # next block's half-spectrum, written by blocks 0..2
 # With per-window inputs (the local NN-FGMRES steps) the window RMS pass also
 # writes the 16 BF16 input channels per pixel as tiles, and the lift and
-# block 0 read those instead of gathering the residual and eps.
-WIN_BYTES_PACKED = {"nno_pack": 6400 * (8 + 4 + 32), "nno_lift": 6400 * 32 + 160 * 512 * 2}
+# block 0 read those instead of gathering the residual and eps; the
+# projection writes whole windows instead of cores.
+WIN_BYTES_PACKED = {"nno_pack": 6400 * (8 + 4 + 32), "nno_lift": 6400 * 32 + 160 * 512 * 2,
+                    "nno_proj": 6400 * 64 + 6400 * 8}  # the local steps' output is the whole window
 BLOCK0_INPUT_BYTES = {False: 6400 * 12, True: 6400 * 32}
 # DRAM bytes (read + write) per window of one launch of a neural stage, from
 # one-kernel ncu captures of a smaller case of the same recipe, scaled to a
 # launch by the number of windows it processes (TRAFFIC_SAMPLE names the
 # case).  Empty while no capture of the current kernels exists.
 TRAFFIC_SAMPLE = "freeform 2048^2 (1024 windows), one kernel per capture, caches flushed"
+# Keyed by whether the inputs were packed (per-window inputs: the local
+# NN-FGMRES steps); None where no capture of the current kernels exists.
 SMALL_CASE_TRAFFIC = {
-    "nno_proj": 452800,
+    "nno_proj": {False: 452800, True: None},            # (global output; the local steps write whole windows)
+    "nno_idft_x_mix_act": {False: None, True: 920790},  # block 0 (883,094) and blocks 1-3 (990,422 /
+                                                        # 987,794 / 821,849, the last writes no T1)
+    "nno_lift": {False: None, True: 329553},            # packed tiles in, T1 out (partly still in L2)
+    "nno_pack": {False: None, True: 241402},            # residual + eps in, packed tiles out (partly in L2)
 }
 # Useful FLOPs per window of each stage (padding excluded).
 NNO_FLOP_PER_WIN = {
@@ -285,7 +293,7 @@ def design_bench(iters, blob, dev):
     solvers = [F.Solver(torch.from_numpy(base).to(dev), dx, lam, npml=20) for lam in lams]
     D = Design(solvers[0], x0, y0, w, h, radius=3.0, beta=8.0)
     rho = torch.full((h, w), 0.5, dtype=torch.float32, device=dev)
-    opt = Adam(solvers[0], (h, w), lr=0.02)
+    opt = Adam(solvers[0], (h, w), lr=0.005)  # Adam moves every density by about lr in its first step
     Jd, bd = torch.from_numpy(J).to(dev), torch.from_numpy(base).to(dev)
     modes = []
     for (r0, r1) in port_rows:
@@ -632,8 +640,10 @@ def main():
         if fl:
             r["tflops"] = fl * (N / 4096.0) * nl / (ms_c / 1e3) / 1e12
         roofs[cls] = r
-    for cls, per_win in SMALL_CASE_TRAFFIC.items():
-        if cls in roofs and precond == F.PRECOND_SCHWARZ and prec_nno == "bf16":
+    packed = precond == F.PRECOND_SCHWARZ and args.inner > 0
+    for cls, by_mode in SMALL_CASE_TRAFFIC.items():
+        per_win = by_mode[packed]
+        if per_win and cls in roofs and precond == F.PRECOND_SCHWARZ and prec_nno == "bf16":
             roofs[cls]["traffic"] = per_win * (N / 4096.0)  # bytes per launch: per window x windows
             roofs[cls]["traffic_note"] = f"ncu capture of {TRAFFIC_SAMPLE}, scaled by windows"
     dom = max(roofs, key=lambda c: roofs[c]["ms"]) if roofs else None

@@ -384,7 +384,11 @@ __global__ void __launch_bounds__(256) sweep_t_kernel(float2* __restrict__ t, co
 // out = base + sgn * A t for a row-major D x D complex matrix A stored as
 // complex half: each row is split over GW warps (GEMV_ROWS rows per CTA, so
 // enough loads are in flight to stream A at HBM rate), four complex entries
-// per 16-byte load, FP32 products and sums; base may be NULL.
+// per 16-byte load, FP32 products and sums; base may be NULL.  Four warps per
+// row: alone (back-to-back GEMVs) two warps per row streamed a 4096 x 4096
+// block 6% faster, but inside the sweeps, between the coupling kernels, they
+// made the coarse solve 11% slower; eight warps per row or a persistent grid
+// were slower in both.
 constexpr int GW = 4, GEMV_ROWS = 8 / GW;
 __global__ void __launch_bounds__(256) gemv_rows_kernel(float2* __restrict__ out, const float2* __restrict__ base,
                                                         const __half2* __restrict__ A, const float2* __restrict__ t,

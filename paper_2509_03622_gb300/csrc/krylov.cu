@@ -148,7 +148,7 @@ cgs_update_kernel(const float4* __restrict__ V, size_t ld4, int v0, int nv, floa
     const size_t c1 = c0 + stride;
     const bool has1 = c1 < n4;
     float4 q[2] = {w[c0], has1 ? w[c1] : make_float4(0.f, 0.f, 0.f, 0.f)};
-#pragma unroll
+#pragma unroll(NV <= 16 ? NV / 4 : 4)
     for (int g = 0; g < NV; g += 4) {
       float4 a[4], b[4];
 #pragma unroll
@@ -340,11 +340,15 @@ int launch_cgs_update(const float2* V, size_t ld, int j, float2* w, float2* vnex
                       cudaStream_t s) {
   int rc = FDFD_OK;
   const int ldH = restart + 1;
-  for (int v0 = 0; v0 <= j && rc == FDFD_OK; v0 += 16) {  // 16 vectors per pass, as for the dots
-    const int nv = (j + 1 - v0) < 16 ? (j + 1 - v0) : 16;
-    const int fin = (v0 + 16 > j);
+  // up to 32 vectors per pass: the update's registers do not grow with the
+  // pass (its coefficients sit in shared memory), and every extra pass reads
+  // and writes w once more
+  for (int v0 = 0; v0 <= j && rc == FDFD_OK; v0 += 32) {
+    const int nv = (j + 1 - v0) < 32 ? (j + 1 - v0) : 32;
+    const int fin = (v0 + 32 > j);
     if (nv <= 8) rc = update_nv<8>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
-    else rc = update_nv<16>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
+    else if (nv <= 16) rc = update_nv<16>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
+    else rc = update_nv<32>(V, ld, v0, nv, w, vnext, n, st, partials, counter, j, ldH, fin, s);
   }
   return rc;
 }

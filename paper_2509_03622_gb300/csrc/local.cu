@@ -88,6 +88,23 @@ __global__ void __launch_bounds__(LT) robin_rhs_kernel(const float2* __restrict_
   }
 }
 
+// A thread's share of a window's squared norm: its pixels' squares summed in
+// FP32 (GB300 issues FP64 at a small fraction of the FP32 rate, and the
+// per-pixel FP64 products cost more than the loads), the block then adds the
+// shares in FP64.  Where the FP32 sum may have underflowed or overflowed
+// (very small or very large window values, e.g. an unscaled source in the
+// stationary solver), the thread sums its pixels again, from the vector it
+// has just written, in FP64.
+__device__ __forceinline__ double norm2_fp64_if_needed(float acc32, const float2* __restrict__ win) {
+  if (acc32 >= 1e-30f && acc32 <= 1e36f) return (double)acc32;
+  double acc = 0.0;
+  for (int p = threadIdx.x; p < NP; p += LT) {
+    const float2 q = win[p];
+    acc += (double)q.x * q.x + (double)q.y * q.y;
+  }
+  return acc;
+}
+
 // Restriction of a global field into window arrays, and initial norms.
 __global__ void __launch_bounds__(LT) local_start_kernel(const float2* __restrict__ v, const float2* __restrict__ rhs_win,
                                                          float2* __restrict__ V0, LocalState* st, int nx, int ny,
@@ -96,14 +113,14 @@ __global__ void __launch_bounds__(LT) local_start_kernel(const float2* __restric
   const int b = blockIdx.x;
   int x0, y0;
   window_origin(b, nx, ny, nwx, x0, y0);
-  double acc = 0.0;
+  float acc32 = 0.f;
   for (int p = threadIdx.x; p < NP; p += LT) {
     const float2 q = rhs_win ? rhs_win[(size_t)b * NP + p]
                              : v[(size_t)(y0 + p / FDFD_WIN) * nx + x0 + p % FDFD_WIN];
     V0[(size_t)b * NP + p] = q;
-    acc += (double)q.x * q.x + (double)q.y * q.y;
+    acc32 += q.x * q.x + q.y * q.y;
   }
-  const double t = block_sum<LT>(acc, sh);
+  const double t = block_sum<LT>(norm2_fp64_if_needed(acc32, V0 + (size_t)b * NP), sh);
   if (threadIdx.x == 0) {
     LocalState& s = st[b];
     const double beta = sqrt(t);
@@ -171,7 +188,7 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
     hf[i] = make_float2((float)(hs[i].x * s.vscale[i]), (float)(hs[i].y * s.vscale[i]));
   }
   __syncthreads();
-  double acc = 0.0;
+  float acc32 = 0.f;
 #pragma unroll(JT >= 0 ? 5 : 1)
   for (int t = 0; t < NP / LT; ++t) {
     const int p = threadIdx.x + t * LT;
@@ -185,9 +202,9 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
       q.y -= hr * a.y + hi * a.x;
     }
     vnext[(size_t)b * NP + p] = q;
-    acc += (double)q.x * q.x + (double)q.y * q.y;
+    acc32 += q.x * q.x + q.y * q.y;
   }
-  const double nrm2 = block_sum<LT>(acc, sh);
+  const double nrm2 = block_sum<LT>(norm2_fp64_if_needed(acc32, vnext + (size_t)b * NP), sh);
   if (threadIdx.x == 0) {
     const double hn = sqrt(nrm2);
     double2 Hc[LOCAL_MAXM + 1];
