@@ -88,21 +88,51 @@ __global__ void __launch_bounds__(LT) robin_rhs_kernel(const float2* __restrict_
   }
 }
 
-// A thread's share of a window's squared norm: its pixels' squares summed in
-// FP32 (GB300 issues FP64 at a small fraction of the FP32 rate, and the
-// per-pixel FP64 products cost more than the loads), the block then adds the
-// shares in FP64.  Where the FP32 sum may have underflowed or overflowed
-// (very small or very large window values, e.g. an unscaled source in the
-// stationary solver), the thread sums its pixels again, from the vector it
-// has just written, in FP64.
-__device__ __forceinline__ double norm2_fp64_if_needed(float acc32, const float2* __restrict__ win) {
-  if (acc32 >= 1e-30f && acc32 <= 1e36f) return (double)acc32;
+// Window reductions.  GB300 issues FP64 at a small fraction of the FP32 rate
+// (tens of cycles per warp instruction), so per-pixel FP64 products and
+// FP64 warp shuffles cost more than a window's loads: each thread sums its
+// 25 pixels in FP32, each warp its 32 threads in FP32, and only the block's
+// eight warp partials are added in FP64.
+__device__ __forceinline__ float warp_sum_f32(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// FP64 sum of the block's per-thread values v (valid in thread 0).
+__device__ __forceinline__ double block_sum_warps(float v, double* sh) {
+  v = warp_sum_f32(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < LT / 32; ++w) t += sh[w];
+  return t;
+}
+// A thread's share of a window's squared norm, acc32 being its FP32 sum of
+// squares.  Where that sum may have underflowed or overflowed although the
+// thread's values are not all zero (very small or very large window values,
+// e.g. an unscaled source in the stationary solver), the thread sums its
+// pixels again, from the vector it has just written, in FP64 into acc64 and
+// sets exact64; all-zero windows (frequent while the Krylov vectors are
+// still local) take the FP32 path.
+__device__ __forceinline__ float norm2_share(float acc32, bool nonzero, const float2* __restrict__ win, bool& exact64,
+                                             double& acc64) {
+  exact64 = nonzero && !(acc32 >= 1e-30f && acc32 <= 1e36f);
+  if (!exact64) return acc32;
   double acc = 0.0;
   for (int p = threadIdx.x; p < NP; p += LT) {
     const float2 q = win[p];
     acc += (double)q.x * q.x + (double)q.y * q.y;
   }
-  return acc;
+  acc64 = acc;
+  return 0.f;
+}
+// Block sum of the norm shares: FP32 warp sums where every thread took the
+// FP32 path, else (rare) an FP64 sum of all threads' shares.
+__device__ __forceinline__ double block_norm2(float share, bool exact64, double acc64, double* sh) {
+  if (!__syncthreads_or(exact64)) return block_sum_warps(share, sh);
+  const double v = exact64 ? acc64 : (double)share;
+  return block_sum<LT>(v, sh);
 }
 
 // Restriction of a global field into window arrays, and initial norms.
@@ -114,13 +144,19 @@ __global__ void __launch_bounds__(LT) local_start_kernel(const float2* __restric
   int x0, y0;
   window_origin(b, nx, ny, nwx, x0, y0);
   float acc32 = 0.f;
-  for (int p = threadIdx.x; p < NP; p += LT) {
+  bool nz = false;
+#pragma unroll 5
+  for (int t = 0; t < NP / LT; ++t) {  // five pixels' loads in flight per thread
+    const int p = threadIdx.x + t * LT;
     const float2 q = rhs_win ? rhs_win[(size_t)b * NP + p]
                              : v[(size_t)(y0 + p / FDFD_WIN) * nx + x0 + p % FDFD_WIN];
     V0[(size_t)b * NP + p] = q;
     acc32 += q.x * q.x + q.y * q.y;
+    nz |= (q.x != 0.f) | (q.y != 0.f);
   }
-  const double t = block_sum<LT>(norm2_fp64_if_needed(acc32, V0 + (size_t)b * NP), sh);
+  bool ex; double a64 = 0.0;
+  const float share = norm2_share(acc32, nz, V0 + (size_t)b * NP, ex, a64);
+  const double t = block_norm2(share, ex, a64, sh);
   if (threadIdx.x == 0) {
     LocalState& s = st[b];
     const double beta = sqrt(t);
@@ -172,12 +208,8 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
 #pragma unroll
   for (int i = 0; i < NA; ++i)
     if (i <= j) {
-      double r = dr[i], m = di[i];
-      for (int o = 16; o > 0; o >>= 1) {
-        r += __shfl_xor_sync(0xffffffffu, r, o);
-        m += __shfl_xor_sync(0xffffffffu, m, o);
-      }
-      if (lane == 0) { part[warp][2 * i] = r; part[warp][2 * i + 1] = m; }
+      const float r = warp_sum_f32(dr[i]), m = warp_sum_f32(di[i]);
+      if (lane == 0) { part[warp][2 * i] = (double)r; part[warp][2 * i + 1] = (double)m; }
     }
   __syncthreads();
   if (threadIdx.x <= j) {
@@ -189,6 +221,7 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
   }
   __syncthreads();
   float acc32 = 0.f;
+  bool nz = false;
 #pragma unroll(JT >= 0 ? 5 : 1)
   for (int t = 0; t < NP / LT; ++t) {
     const int p = threadIdx.x + t * LT;
@@ -203,8 +236,11 @@ __global__ void __launch_bounds__(LT) local_cgs_kernel(const float2* __restrict_
     }
     vnext[(size_t)b * NP + p] = q;
     acc32 += q.x * q.x + q.y * q.y;
+    nz |= (q.x != 0.f) | (q.y != 0.f);
   }
-  const double nrm2 = block_sum<LT>(norm2_fp64_if_needed(acc32, vnext + (size_t)b * NP), sh);
+  bool ex; double a64 = 0.0;
+  const float share = norm2_share(acc32, nz, vnext + (size_t)b * NP, ex, a64);
+  const double nrm2 = block_norm2(share, ex, a64, sh);
   if (threadIdx.x == 0) {
     const double hn = sqrt(nrm2);
     double2 Hc[LOCAL_MAXM + 1];

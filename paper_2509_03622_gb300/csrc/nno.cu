@@ -1629,6 +1629,22 @@ __global__ void __launch_bounds__(PJ_THREADS, 1) proj_kernel(const __grid_consta
   }
 }
 
+// Sum over a 256-thread block of per-thread FP32 partials (valid in thread
+// 0): FP32 within each warp, FP64 across the eight warps.  GB300 issues FP64
+// at a small fraction of the FP32 rate, and per-window reductions are not
+// amortised over many elements per thread, so FP64 warp shuffles would cost
+// more than the window's loads.
+__device__ __forceinline__ double win_sum(float v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < 8; ++w) t += sh[w];
+  return t;
+}
+
 // Window RMS rho (residual and Robin data together, over the 6400 pixels):
 // the inputs are divided by it and the network's output multiplied by it.
 __global__ void __launch_bounds__(256) rho_kernel(NnoInput in, GridGeom g, float* rho_out) {
@@ -1642,7 +1658,7 @@ __global__ void __launch_bounds__(256) rho_kernel(NnoInput in, GridGeom g, float
   }
   if (ws.g)
     for (int t = threadIdx.x; t < 320; t += 256) { const float2 q = ws.g[t]; acc += q.x * q.x + q.y * q.y; }
-  const double tot = block_sum<256>((double)acc, sh);
+  const double tot = win_sum(acc, sh);
   if (threadIdx.x == 0) rho_out[b] = (float)sqrt(tot / NPIX);
 }
 
@@ -1665,7 +1681,7 @@ __global__ void __launch_bounds__(256) rho_pack_kernel(NnoInput in, GridGeom g, 
   }
   if (ws.g)
     for (int t = threadIdx.x; t < 320; t += 256) { const float2 q = ws.g[t]; acc += q.x * q.x + q.y * q.y; }
-  const double tot = block_sum<256>((double)acc, sh);
+  const double tot = win_sum(acc, sh);
   if (threadIdx.x == 0) {
     const float rho = (float)sqrt(tot / NPIX);
     rho_out[b] = rho;
