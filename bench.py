@@ -445,6 +445,8 @@ def batch_bench(args):
 def cpu_baseline(argd):
     """The oracle's FGMRES with the arm's preconditioner configuration on a
     bounded sample (about 10 s of steps after its set-up)."""
+    global RESTART
+    RESTART = argd.get("restart", RESTART)  # a spawned worker starts from the module default
     args = argparse.Namespace(**argd)
     w, kc_o, inner_o = oracle_preconditioner(args)
     ns = args.cpu_sample if args.precond == "schwarz" else 1024
@@ -506,6 +508,7 @@ def time_to_solution(S, Jd, E, precond, args):
 
 
 def main():
+    global RESTART
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
@@ -514,6 +517,8 @@ def main():
     ap.add_argument("--precond", default="schwarz", choices=["schwarz", "jacobi"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--k-coarse", type=int, default=-1)
+    ap.add_argument("--restart", type=int, default=RESTART,
+                    help="FGMRES restart length of every solve the bench runs (1..60)")
     ap.add_argument("--inner", type=int, default=INNER_DEFAULT,
                     help="NN-FGMRES steps per local solve (0 = one network application)")
     ap.add_argument("--design", type=int, default=0,
@@ -536,6 +541,9 @@ def main():
     ap.add_argument("--nno-precision", default="bf16", choices=["bf16", "fp8"],
                     help="neural-operator activations: BF16, or E4M3 with per-channel scales")
     args = ap.parse_args()
+    if not 1 <= args.restart <= 60:
+        ap.error("--restart must be in 1..60")
+    RESTART = args.restart
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
