@@ -126,10 +126,10 @@ TRAFFIC_SAMPLE = "freeform 2048^2 (1024 windows), one kernel per capture, caches
 # NN-FGMRES steps); None where no capture of the current kernels exists.
 SMALL_CASE_TRAFFIC = {
     "nno_proj": {False: 452800, True: None},            # (global output; the local steps write whole windows)
-    "nno_idft_x_mix_act": {False: None, True: 920790},  # block 0 (883,094) and blocks 1-3 (990,422 /
-                                                        # 987,794 / 821,849, the last writes no T1)
-    "nno_lift": {False: None, True: 329553},            # packed tiles in, T1 out (partly still in L2)
-    "nno_pack": {False: None, True: 241402},            # residual + eps in, packed tiles out (partly in L2)
+    "nno_idft_x_mix_act": {False: None, True: 919329},  # block 0 (881,333) and blocks 1-3 (988,546 /
+                                                        # 985,683 / 821,754, the last writes no T1)
+    "nno_lift": {False: None, True: 327850},            # packed tiles in, T1 out (partly still in L2)
+    "nno_pack": {False: None, True: 258716},            # residual + eps in, packed tiles out (partly in L2)
 }
 # Useful FLOPs per window of each stage (padding excluded).
 NNO_FLOP_PER_WIN = {

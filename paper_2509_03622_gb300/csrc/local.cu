@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(LT) local_apply_kernel(const float2* __restric
   window_origin(w, nx, ny, nwx, x0, y0);
   const bool il = x0 > 0, ir = x0 + FDFD_WIN < nx, ib = y0 > 0, it = y0 + FDFD_WIN < ny;
   const float2* xb = x + (size_t)b * NP;
+#pragma unroll 5
   for (int p = blockIdx.x * LT + threadIdx.x; p < NP; p += gridDim.x * LT) {
     const int ly = p / FDFD_WIN, lx = p % FDFD_WIN, gx = x0 + lx, gy = y0 + ly;
     const AxisCoef a = cx[gx], c = cy[gy];
@@ -302,6 +303,7 @@ __global__ void __launch_bounds__(LT) local_sum_kernel(const float2* __restrict_
   for (int i = 0; i < s.k; ++i) y[i] = make_float2((float)s.y[i].x * f, (float)s.y[i].y * f);
   const int a = b % nwx, bb = b / nwx;
   const int cx0 = FDFD_CORE * a - x0, cy0 = FDFD_CORE * bb - y0;
+#pragma unroll 5
   for (int p = blockIdx.x * LT + threadIdx.x; p < NP; p += gridDim.x * LT) {
     const int ly = p / FDFD_WIN, lx = p % FDFD_WIN;
     float2 acc = make_float2(0.f, 0.f);

@@ -960,10 +960,18 @@ g5_kernel(bf16* X, const bf16* T3, const bf16* Gx, const bf16* Wb, const float* 
       tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + G5_G1 + g * 32 + hf * 16, v);
       const int y = (int)(wy0 % 80) + q;
       bf16* base = T1 + (wy0 / 80) * (size_t)(160 * 512);
+      // channel pairs as BF16x2: columns i (ri = 0) and i + 1 (ri = 1) share kx; even
+      // lanes store channels (lane, lane + 1) of column i, odd lanes channels
+      // (lane - 1, lane) of column i + 1, each taking the other value from its
+      // neighbour lane (half the store instructions of one BF16 per lane)
+      const bool ev = (lane & 1) == 0;
+      const int c0 = lane & ~1;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int col = hf * 16 + i, kx = col >> 1, ri = col & 1;
-        base[(ri * 80 + y) * 512 + kx * 32 + lane] = __float2bfloat16_rn(v[i]);
+      for (int i = 0; i < 16; i += 2) {
+        const float nb = __shfl_xor_sync(0xffffffffu, ev ? v[i + 1] : v[i], 1);
+        const __nv_bfloat162 pr = ev ? __floats2bfloat162_rn(v[i], nb) : __floats2bfloat162_rn(nb, v[i + 1]);
+        const int col = hf * 16 + i + (ev ? 0 : 1), kx = col >> 1, ri = col & 1;
+        *reinterpret_cast<__nv_bfloat162*>(base + (ri * 80 + y) * 512 + kx * 32 + c0) = pr;
       }
       tc::fence_before();
       __syncwarp();
@@ -1311,10 +1319,18 @@ g5f_kernel(bf16* X, const bf16* Yh, const bf16* Gy, const bf16* Gx, const bf16* 
       tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + G5F_G1 + g * 32 + hf * 16, v);
       const int y = (int)(wy0 % 80) + q;
       bf16* base = T1 + (wy0 / 80) * (size_t)(160 * 512);
+      // channel pairs as BF16x2: columns i (ri = 0) and i + 1 (ri = 1) share kx; even
+      // lanes store channels (lane, lane + 1) of column i, odd lanes channels
+      // (lane - 1, lane) of column i + 1, each taking the other value from its
+      // neighbour lane (half the store instructions of one BF16 per lane)
+      const bool ev = (lane & 1) == 0;
+      const int c0 = lane & ~1;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int col = hf * 16 + i, kx = col >> 1, ri = col & 1;
-        base[(ri * 80 + y) * 512 + kx * 32 + lane] = __float2bfloat16_rn(v[i]);
+      for (int i = 0; i < 16; i += 2) {
+        const float nb = __shfl_xor_sync(0xffffffffu, ev ? v[i + 1] : v[i], 1);
+        const __nv_bfloat162 pr = ev ? __floats2bfloat162_rn(v[i], nb) : __floats2bfloat162_rn(nb, v[i + 1]);
+        const int col = hf * 16 + i + (ev ? 0 : 1), kx = col >> 1, ri = col & 1;
+        *reinterpret_cast<__nv_bfloat162*>(base + (ri * 80 + y) * 512 + kx * 32 + c0) = pr;
       }
       tc::fence_before();
       __syncwarp();
@@ -1645,6 +1661,7 @@ __device__ __forceinline__ double win_sum(float v, double* sh) {
   return t;
 }
 
+static_assert(NPIX % 256 == 0, "whole pixel rounds per thread in the per-window passes");
 // Window RMS rho (residual and Robin data together, over the 6400 pixels):
 // the inputs are divided by it and the network's output multiplied by it.
 __global__ void __launch_bounds__(256) rho_kernel(NnoInput in, GridGeom g, float* rho_out) {
@@ -1652,7 +1669,9 @@ __global__ void __launch_bounds__(256) rho_kernel(NnoInput in, GridGeom g, float
   const int b = blockIdx.x;
   const WinSrc ws = win_src(in, g, b);
   float acc = 0.f;
-  for (int p = threadIdx.x; p < NPIX; p += 256) {
+#pragma unroll 5
+  for (int t = 0; t < NPIX / 256; ++t) {  // 25 pixels per thread, five loads in flight
+    const int p = threadIdx.x + 256 * t;
     const float2 r = win_residual(ws, p / 80, p % 80);
     acc += r.x * r.x + r.y * r.y;
   }
@@ -1675,7 +1694,9 @@ __global__ void __launch_bounds__(256) rho_pack_kernel(NnoInput in, GridGeom g, 
   const int b = blockIdx.x;
   const WinSrc ws = win_src(in, g, b);
   float acc = 0.f;
-  for (int p = threadIdx.x; p < NPIX; p += 256) {
+#pragma unroll 5
+  for (int t = 0; t < NPIX / 256; ++t) {  // 25 pixels per thread, five loads in flight
+    const int p = threadIdx.x + 256 * t;
     const float2 r = win_residual(ws, p / 80, p % 80);
     acc += r.x * r.x + r.y * r.y;
   }
@@ -1690,7 +1711,9 @@ __global__ void __launch_bounds__(256) rho_pack_kernel(NnoInput in, GridGeom g, 
   __syncthreads();
   const float inv = s_inv;
   uint8_t* base = packed + (size_t)b * (NPIX * 32);
-  for (int p = threadIdx.x; p < NPIX; p += 256) {
+#pragma unroll 5
+  for (int t = 0; t < NPIX / 256; ++t) {
+    const int p = threadIdx.x + 256 * t;
     const int y = p / 80, x = p % 80;
     uint4 lo, hi;
     win_channels(ws, y, x, inv, lo, hi);
