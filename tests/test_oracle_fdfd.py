@@ -163,3 +163,28 @@ def test_adjoint_gradient_matches_central_differences():
         em = eps0.copy(); em[py, px] -= h
         fd = (F_of(ep) - F_of(em)) / (2 * h)
         assert abs(fd - grad[py, px]) <= 1e-5 * abs(fd) + 1e-12 * abs(F)
+
+
+def test_mode_overlap_definition():
+    """c = dx sum conj(m) E on the port line: a field equal to a complex
+    (phase-ramped) profile on that line and anything elsewhere overlaps it by
+    dx sum |m|^2, real and positive (a missing conjugate would give
+    dx sum m^2, complex here); a field orthogonal to it on the line gives 0;
+    the adjoint source is conj(c) conj(m) dx on the line and zero elsewhere."""
+    n, dx, x, y0 = 48, 2e-8, 31, 7
+    m = np.exp(-((np.arange(20) - 9.5) / 4.0) ** 2) * np.exp(0.7j * np.arange(20))
+    g = wl.rng(5)
+    E = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    E[y0:y0 + m.size, x] = m
+    c = fdfd.mode_overlap(E, x, m, y0, dx)
+    assert abs(c - dx * np.sum(np.abs(m) ** 2)) <= 1e-14 * abs(c)
+    r = g.standard_normal(m.size) + 1j * g.standard_normal(m.size)
+    v = r - (np.sum(np.conj(m) * r) / np.sum(np.abs(m) ** 2)) * m  # orthogonal to m
+    E2 = E.copy()
+    E2[y0:y0 + m.size, x] = v
+    assert abs(fdfd.mode_overlap(E2, x, m, y0, dx)) <= 1e-14 * dx * np.linalg.norm(m) * np.linalg.norm(v)
+    F, src = fdfd.fom_and_adjoint_source(E, x, m, y0, dx)
+    assert abs(F - abs(c) ** 2) <= 1e-14 * F
+    ref = np.zeros_like(E)
+    ref[y0:y0 + m.size, x] = np.conj(c) * np.conj(m) * dx
+    assert np.array_equal(src, ref)
