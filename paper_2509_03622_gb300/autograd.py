@@ -83,7 +83,7 @@ class _Overlap(torch.autograd.Function):
     @staticmethod
     def forward(ctx, E, mode, port_x, y0, dx):
         c = torch.empty(2, dtype=torch.float64, device=E.device)
-        F.mode_overlap(E.contiguous(), mode.contiguous(), port_x, y0, dx, c)
+        F.mode_overlap(E.to(torch.complex64).contiguous(), mode.contiguous(), port_x, y0, dx, c)
         ctx.shape, ctx.args = E.shape, (port_x, y0, dx)
         ctx.save_for_backward(mode)
         return torch.view_as_complex(c)

@@ -152,6 +152,8 @@ def mode_overlap(E, mode, port_x: int, y0: int, dx: float, c, stream=None):
     import torch
     if c.dtype != torch.float64 or c.numel() < 2:
         raise TypeError("c must be a float64 tensor of 2 elements")
+    if E.dtype != torch.complex64 or mode.dtype != torch.complex64 or E.dim() != 2:
+        raise TypeError("E must be a 2-D complex64 field and mode a complex64 profile")
     st = stream if stream is not None else torch.cuda.current_stream(E.device).cuda_stream
     ny, nx = E.shape
     _check(lib.fdfd_mode_overlap(_ptr(E), nx, ny, _ptr(mode), mode.numel(), int(port_x), int(y0), float(dx),
@@ -162,6 +164,8 @@ def mode_overlap_grad(shape, mode, port_x: int, y0: int, dx: float, gc: complex,
                       stream=None):
     """grad_E (=|+=) gc * mode * dx on the port line (fdfd_mode_overlap_grad)."""
     import torch
+    if grad_E.dtype != torch.complex64 or mode.dtype != torch.complex64 or tuple(grad_E.shape) != tuple(shape):
+        raise TypeError("grad_E must be a complex64 field of the given shape and mode a complex64 profile")
     st = stream if stream is not None else torch.cuda.current_stream(grad_E.device).cuda_stream
     ny, nx = shape
     _check(lib.fdfd_mode_overlap_grad(nx, ny, _ptr(mode), mode.numel(), int(port_x), int(y0), float(dx),
@@ -273,6 +277,11 @@ class Solver:
     def adjoint_rhs(self, grad_E, g):
         """g = conj(grad_E) / 2: the adjoint right-hand side dL/dE from
         autograd's field gradient (fdfd_adjoint_rhs)."""
+        import torch
+        if grad_E.dtype != torch.complex64 or g.dtype != torch.complex64:
+            raise TypeError("grad_E and g must be complex64")
+        if grad_E.numel() != self.nx * self.ny or g.numel() != self.nx * self.ny:
+            raise ValueError("grad_E and g must cover the handle's grid")
         _check(lib.fdfd_adjoint_rhs(self.h, _ptr(grad_E), _ptr(g)), "fdfd_adjoint_rhs")
 
     def grad_eps(self, E, lam, grad, accumulate=False):

@@ -93,3 +93,19 @@ def test_host_side_validation_of_the_extensions(lib):
     assert L.fdfd_design_grad(None, C.byref(d), None, None, None, None) == lib.EINVAL
     a = lib.AdamDesc(0.01, 0.9, 0.999, 1e-8)
     assert L.fdfd_adam_step(None, C.byref(a), 1, 1.0, None, None, None, None, 4) == lib.EINVAL
+
+
+def test_overlap_binding_rejects_wrong_dtypes(lib):
+    """The figure-of-merit bindings check dtypes before passing pointers (the
+    library reads complex64 fields and a two-double result)."""
+    import torch
+    c = torch.zeros(2, dtype=torch.float64)
+    with pytest.raises(TypeError):
+        lib.mode_overlap(torch.zeros((64, 64), dtype=torch.complex128), torch.zeros(4, dtype=torch.complex64),
+                         1, 0, 1e-8, c)
+    with pytest.raises(TypeError):
+        lib.mode_overlap(torch.zeros((64, 64), dtype=torch.complex64), torch.zeros(4, dtype=torch.complex64),
+                         1, 0, 1e-8, torch.zeros(2, dtype=torch.float32))
+    with pytest.raises(TypeError):
+        lib.mode_overlap_grad((64, 64), torch.zeros(4, dtype=torch.complex64), 1, 0, 1e-8, 1.0,
+                              torch.zeros((32, 64), dtype=torch.complex64))
