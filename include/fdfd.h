@@ -88,8 +88,9 @@ typedef struct {
                             activation entering each Fourier block and the
                             projection is stored as E4M3 with power-of-two
                             per-channel scales (calibrated at set-up on a
-                            seeded random residual, 4x headroom below the
-                            E4M3 maximum, saturating), converted to BF16 in
+                            seeded random residual and seeded random Robin
+                            data, 4x headroom below the E4M3 maximum,
+                            saturating), converted to BF16 in
                             shared memory for the tensor cores, the scales
                             folded into the weights that read it; halves
                             the activation traffic (precision pattern).    */
