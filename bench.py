@@ -518,7 +518,7 @@ def main():
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--k-coarse", type=int, default=-1)
     ap.add_argument("--restart", type=int, default=RESTART,
-                    help="FGMRES restart length of every solve the bench runs (1..60)")
+                    help="FGMRES restart length of every solve the bench runs (1..64)")
     ap.add_argument("--inner", type=int, default=INNER_DEFAULT,
                     help="NN-FGMRES steps per local solve (0 = one network application)")
     ap.add_argument("--design", type=int, default=0,
@@ -541,8 +541,8 @@ def main():
     ap.add_argument("--nno-precision", default="bf16", choices=["bf16", "fp8"],
                     help="neural-operator activations: BF16, or E4M3 with per-channel scales")
     args = ap.parse_args()
-    if not 1 <= args.restart <= 60:
-        ap.error("--restart must be in 1..60")
+    if not 1 <= args.restart <= 64:
+        ap.error("--restart must be in 1..64")
     RESTART = args.restart
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
