@@ -154,7 +154,10 @@ class Sampler:
         mode 0: interior (both sides Robin), 1: grid edge at the low side
         (PML cells 0..npml-1, low side Dirichlet), 2: edge at the high side."""
         t, B, npml = self.t, self.B, self.npml
-        mode = t.randint(0, 5, (B,), device=self.dev).clamp(max=2)  # 60% interior
+        # 60% interior (draws 0-2), 20% each grid edge (3 -> low side, 4 -> high
+        # side): most windows of a large grid have no PML at all
+        u = t.randint(0, 5, (B,), device=self.dev)
+        mode = t.where(u < 3, t.zeros_like(u), u - 2)
         pn = t.arange(WIN, device=self.dev, dtype=t.float32) + 0.5
         ph = t.arange(WIN + 1, device=self.dev, dtype=t.float32)
         A = (4.0 * 30.0 / (2.0 * npml * k0dx))[:, None]  # -(m+1) lnR / (2 npml k0dx)

@@ -114,3 +114,22 @@ def test_exact_local_solve_by_row_elimination():
     r = rhs.reshape(6, 80, 80) - T.local_apply(torch, x.reshape(6, 80, 80), Pe)
     rel = (r.abs() ** 2).sum((1, 2)).sqrt() / (rhs.reshape(6, 80, 80).abs() ** 2).sum((1, 2)).sqrt()
     assert float(rel.max()) < 1e-5
+
+
+def test_sampler_window_kinds_match_large_grids():
+    """Most windows of a large grid have no PML side: the sampler draws an
+    interior axis (Robin data on both sides) 60% of the time and each grid
+    edge 20%, so about 36% of its windows are fully interior, 64% have no PML
+    on a given axis, and none has PML on both sides of one axis."""
+    S = T.Sampler(torch, torch.device("cpu"), 4000)
+    torch.manual_seed(1)
+    k0dx = torch.full((4000,), 2 * np.pi / 25)
+    _, _, _, rl, rh = S.axis(k0dx)
+    interior = (rl & rh).float().mean().item()
+    low, high = (~rl).float().mean().item(), (~rh).float().mean().item()
+    assert abs(interior - 0.6) < 0.03, interior
+    assert abs(low - 0.2) < 0.03 and abs(high - 0.2) < 0.03, (low, high)
+    assert not bool(((~rl) & (~rh)).any())
+    P = S.batch()
+    full = P["robin"].all(1).float().mean().item()
+    assert abs(full - 0.36) < 0.04, full
